@@ -1,0 +1,344 @@
+"""Pins of the CPU oracle to facts outside itself (CPU only).
+
+Each test ties one oracle function to something the paper or mathematics
+fixes: hand-derived trajectories and objective values (tests/golden), the
+parameter counts the paper prints, closed forms, an independent Philox
+implementation, exhaustive search, and invariants.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2506_19866_gb300 import synth
+from tests.helpers import case_network, load_golden, oracle_problem
+
+
+# ------------------------------------------------------------ Sections 2.1-2.2
+@pytest.mark.parametrize("case", load_golden("trajectories.json")["cases"], ids=lambda c: c["name"])
+def test_hand_trajectories(case):
+    net, x = case_network(case)
+    T = case["T"]
+    tc = O.Timecourse([case["init"]], np.zeros((1, T, case["n_nodes"])),
+                      np.zeros((1, T, case["n_nodes"])), knockout=[case["knockout"]])
+    S = O.simulate(net, tc, x, 0)
+    np.testing.assert_array_equal(S, np.array(case["S"], dtype=np.uint8), err_msg=case["why"])
+
+
+# ---------------------------------------------------------------- Section 2.3
+@pytest.mark.parametrize("case", load_golden("objective.json")["cases"], ids=lambda c: c["name"])
+def test_hand_objective(case):
+    N, T = case["n_nodes"], case["T"]
+    ref = np.array(case["ref"], np.uint8)
+    obs = np.array(case["observed"], np.uint8)
+    C = ref.shape[0]
+    net = O.Network([0, 1], [1, 0], np.zeros(N, np.uint8))
+    tc = O.Timecourse(np.zeros((C, N)), ref, obs)
+    np.testing.assert_array_equal(O.weights(net, tc), np.array(case["W"], np.uint8))
+    assert O.score_trajectory(net, tc, np.array(case["S"], np.uint8)) == case["y"]
+    # with every weight forced to 1 the objective is the unweighted Manhattan distance
+    flat_obs = obs.copy()
+    flat_obs[:, 1:, :] = 0
+    S = np.array(case["S"], np.uint8)
+    unweighted = 0
+    for t in range(T):
+        tc_t = O.Timecourse(np.zeros((C, N)), ref[:, t:t + 1], obs[:, t:t + 1])
+        unweighted += O.score_trajectory(net, tc_t, S[:, t:t + 1])
+    assert unweighted == case["unweighted"]
+
+
+def test_objective_zero_iff_match():
+    w = synth.tiny(5, n_nodes=4)
+    net, tc, xs, _ = oracle_problem(w)
+    y, traj = O.objective(net, tc, xs, return_traj=True)
+    assert y == 0
+    # any single observed mismatch costs exactly its weight times the distance
+    W = O.weights(net, tc)
+    k = np.flatnonzero(tc.observed.reshape(-1))[0]
+    bad = traj.reshape(-1).copy()
+    bad[k] = (bad[k] + 1) % 3
+    dist = abs(int(bad[k]) - int(tc.ref.reshape(-1)[k]))
+    assert O.score_trajectory(net, tc, bad.reshape(traj.shape)) == W.reshape(-1)[k] * dist
+
+
+# --------------------------------------------- parameter counts (Sections 1, 2.5)
+def test_paper_parameter_counts():
+    # the paper's two systems: 9 nodes / 25 edges -> 102 parameters and
+    # 63 nodes / 178 edges -> 723 parameters, with x = [w, p, t, u, m, d]
+    for name, N, E, P in (("hpg_9n_25e", 9, 25, 102), ("mtb_63n_178e", 63, 178, 723)):
+        w = synth.make(name)
+        assert (w.N, w.E) == (N, E)
+        assert O.n_params(O.Network(w.src, w.dst, w.fast)) == P
+        assert int(w.observed[0].any(axis=0).sum()) == {102: 5, 723: 35}[P]
+        assert w.T == 20
+
+
+def test_domains():
+    net = O.Network([0, 1], [1, 0], np.array([0, 1], np.uint8))
+    E, N = 2, 2
+    assert list(O.domain(net, 0)) == [0, 1, 2]                  # w
+    assert list(O.domain(net, E)) == [-1, 0, 1]                 # p
+    assert list(O.domain(net, 2 * E)) == [1, 2]                 # t
+    assert list(O.domain(net, 3 * E)) == [1, 2, 3, 4, 5, 6]     # u, slow node
+    assert list(O.domain(net, 3 * E + 1)) == [10, 11, 12]       # u, fast node
+    assert list(O.domain(net, 3 * E + N)) == [0, 1, 2]          # m
+    assert list(O.domain(net, 3 * E + 2 * N)) == [1, 2]         # d
+
+
+# ------------------------------------------------------ Section 2.4.1 schedule
+def test_paper_schedule_levels():
+    # T = 1000 down to T_min = 0.001 with rho = 0.99: the number of levels is the
+    # smallest n with 1000 * 0.99^n <= 0.001, i.e. ceil(ln(1e-6) / ln(0.99)).
+    assert O.count_levels(1000.0, 0.001, 0.99) == math.ceil(math.log(1e-6) / math.log(0.99)) == 1375
+    assert O.level_temperature(10.0, 0.995, 0) == 10.0
+    assert abs(O.level_temperature(10.0, 0.995, 2000) - 10.0 * 0.995 ** 2000) < 1e-12
+
+
+# ------------------------------------------------------------------ Philox
+def _triton_philox(key, ctrs):
+    import os
+    os.environ["TRITON_INTERPRET"] = "1"
+    triton = pytest.importorskip("triton")
+    import torch
+    import triton.language as tl
+
+    @triton.jit
+    def _k(out_ptr, seed, c0p, c1p, c2p, c3p, n, BLOCK: tl.constexpr):
+        offs = tl.arange(0, BLOCK)
+        m = offs < n
+        a, b, c, d = tl.philox(seed, tl.load(c0p + offs, mask=m), tl.load(c1p + offs, mask=m),
+                               tl.load(c2p + offs, mask=m), tl.load(c3p + offs, mask=m))
+        tl.store(out_ptr + offs * 4 + 0, a, mask=m)
+        tl.store(out_ptr + offs * 4 + 1, b, mask=m)
+        tl.store(out_ptr + offs * 4 + 2, c, mask=m)
+        tl.store(out_ptr + offs * 4 + 3, d, mask=m)
+
+    n = ctrs.shape[0]
+    cols = [torch.from_numpy(np.ascontiguousarray(ctrs[:, k]).view(np.int32)).view(torch.uint32)
+            for k in range(4)]
+    out = torch.zeros(4 * n, dtype=torch.uint32)
+    _k[(1,)](out, key, *cols, n, BLOCK=triton.next_power_of_2(n))
+    return out.view(torch.int32).numpy().view(np.uint32).reshape(n, 4)
+
+
+def test_philox_matches_independent_implementation():
+    # Triton's interpreter carries its own Philox4x32-10 (same published round
+    # function and constants, written independently); key = (seed_lo, seed_hi).
+    rng = np.random.default_rng(7)
+    ctrs = rng.integers(0, 2 ** 32, size=(32, 4), dtype=np.uint64).astype(np.uint32)
+    ctrs[0] = 0
+    ctrs[1] = 0xFFFFFFFF
+    for key in (0, 1, 0x123456789ABCDEF, 2 ** 64 - 1):
+        ref = _triton_philox(key, ctrs)
+        mine = np.stack([O.philox(key, c) for c in ctrs])
+        np.testing.assert_array_equal(mine, ref)
+
+
+def test_philox_uniform_chi2():
+    words = np.concatenate([O.philox(0, [g, 0, c, 0]) for g in range(64) for c in range(64)])
+    counts = np.bincount((words >> 28).astype(np.int64), minlength=16)
+    expected = words.size / 16
+    chi2 = float(((counts - expected) ** 2 / expected).sum())
+    assert chi2 < 37.7  # 15 d.o.f., p = 0.001
+
+
+# ----------------------------------------------------------- Table 1 acceptance
+def test_threshold_closed_form_and_bounds():
+    for T in (0.01, 0.5, 1.0, 10.0, 1000.0):
+        prev = 2 ** 32
+        for dE in (1, 2, 3, 5, 10, 50, 200, 1000):
+            thr = O.threshold(T, dE)
+            assert thr <= prev
+            prev = thr
+            a = math.exp(-dE / T)
+            assert abs(thr / 2 ** 32 - a) <= 2 ** -32 + 1e-15 * a
+        # beyond 32 ln 2 * T the acceptance probability is below 2^-32
+        assert O.threshold(T, int(32 * math.log(2) * T) + 2) == 0
+
+
+def test_metropolis_acceptance_rate():
+    # accept iff r < thr with r the third Philox word: for fixed (T, dE) the
+    # empirical rate matches exp(-dE / T) within 4 sigma
+    n = 20000
+    r2 = np.array([O.philox(3, [g, 0, 5, 0])[2] for g in range(n)], dtype=np.uint64)
+    for T, dE in ((1.0, 1), (2.0, 3), (10.0, 5), (0.5, 1)):
+        p = math.exp(-dE / T)
+        rate = float((r2 < O.threshold(T, dE)).mean())
+        assert abs(rate - p) < 4 * math.sqrt(p * (1 - p) / n)
+
+
+# -------------------------------------------------- GetCandidate (Table 1, 2.5.3)
+def _constraints_by_definition(src, dst, N, x):
+    E = len(src)
+    w, p = x[:E], x[E:2 * E]
+    out_ok = np.bincount(src[w != 0], minlength=N) >= 1
+    in_ok = np.bincount(dst[(w != 0) & (p == 1)], minlength=N) >= 1
+    return bool(out_ok.all() and in_ok.all())
+
+
+def test_propose_is_exactly_the_valid_single_changes():
+    w = synth.tiny(3, n_nodes=4, indeg=2)
+    net = O.Network(w.src, w.dst, w.fast)
+    x = O.init_chain(net, 1, 0)
+    n_null = 0
+    for k in range(2000):
+        r = O.philox(9, [k, 0, 0, 0])
+        moved, j, v = O.propose(net, x, r[0], r[1])
+        # the alternatives by definition: domain values != x_j whose single
+        # change keeps both constraints (Section 2.5.3), ascending
+        alts = []
+        for val in O.domain(net, j):
+            if val == x[j]:
+                continue
+            y = x.copy()
+            y[j] = val
+            if _constraints_by_definition(w.src, w.dst, w.N, y):
+                alts.append(int(val))
+        if moved:
+            assert v == alts[(int(r[1]) * len(alts)) >> 32]
+            x[j] = v
+        else:
+            assert alts == []
+            n_null += 1
+        assert _constraints_by_definition(w.src, w.dst, w.N, x)
+    assert n_null > 0  # the walk reaches vectors where some change is blocked
+    # index choice: r0 in [k * 2^32 / n, (k+1) * 2^32 / n) picks the k-th free index
+    P = net.P
+    for k in (0, 1, P // 2, P - 1):
+        lo = -(-k * 2 ** 32 // P)
+        assert O.propose(net, x, lo, 0)[1] == k
+        if k > 0:
+            assert O.propose(net, x, lo - 1, 0)[1] == k - 1
+
+
+def test_propose_respects_frozen():
+    w = synth.tiny(4, n_nodes=4, indeg=2)
+    net0 = O.Network(w.src, w.dst, w.fast)
+    x = O.init_chain(net0, 2, 0)
+    frozen = np.ones(net0.P, np.uint8)
+    frozen[[1, net0.P - 1]] = 0
+    net = O.Network(w.src, w.dst, w.fast, frozen, x)
+    seen = set()
+    for k in range(200):
+        r = O.philox(1, [k, 0, 0, 0])
+        moved, j, v = O.propose(net, x, r[0], r[1])
+        seen.add(j)
+    assert seen == {1, net0.P - 1}
+
+
+# --------------------------------------------------------- initialisation
+def test_init_valid_and_uniform():
+    w = synth.make("n120_c8_t21")
+    net = O.Network(w.src, w.dst, w.fast)
+    X = O.init_chains(net, 0, 200)
+    E, N = w.E, w.N
+    for x in X:
+        assert O.check_params(net, x) == 0
+        assert _constraints_by_definition(w.src, w.dst, N, x)
+    # t, m, d are never touched by the repair: uniform over their domains
+    for lo, hi, k in ((2 * E, 3 * E, 2), (3 * E + N, 3 * E + 2 * N, 3), (3 * E + 2 * N, 3 * E + 3 * N, 2)):
+        vals = X[:, lo:hi].reshape(-1)
+        counts = np.unique(vals, return_counts=True)[1]
+        expected = vals.size / k
+        chi2 = float(((counts - expected) ** 2 / expected).sum())
+        assert len(counts) == k and chi2 < 16.3  # p = 0.001 at <= 2 d.o.f.
+    # distinct chains start from distinct vectors
+    assert len({x.tobytes() for x in X}) == len(X)
+
+
+def test_init_reports_unsatisfiable():
+    # node 0's only in-edge has p frozen at -1: no activating input is possible
+    net = O.Network([1, 0], [0, 1], np.zeros(2, np.uint8),
+                    frozen=np.array([0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0], np.uint8),
+                    frozen_val=np.array([0, 0, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0], np.int8))
+    with pytest.raises(ValueError):
+        O.init_chain(net, 0, 0)
+
+
+# --------------------------------------------------------- simulation invariants
+@pytest.mark.parametrize("name", synth.WORKLOADS)
+def test_planted_parameters_score_zero(name):
+    w = synth.make(name)
+    net, tc, xs, flipped = oracle_problem(w)
+    y, traj = O.objective(net, tc, xs, return_traj=True)
+    if w.noise_frac == 0:
+        assert y == 0
+    else:
+        # every flipped entry costs at most weight 3 times distance 2
+        assert 0 < y <= 6 * int(flipped.sum())
+    assert traj.max() <= 2
+    assert (traj[tc.knockout.astype(bool)[:, None, :].repeat(w.T, axis=1)] == 0).all()
+    # deterministic
+    assert O.objective(net, tc, xs) == y
+
+
+# --------------------------------------------------------------- annealing
+def _planted_tiny(seed, n_nodes=3, free_frac=0.35):
+    w = synth.tiny(seed, n_nodes=n_nodes, indeg=2, n_cond=2, n_times=6, obs_frac=0.7)
+    net0, tc, xs, _ = oracle_problem(w, noise=False)
+    rng = np.random.default_rng(seed)
+    frozen = (rng.random(net0.P) > free_frac).astype(np.uint8)
+    net = O.Network(w.src, w.dst, w.fast, frozen, xs)
+    return w, net, tc, xs
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_bruteforce_optimum_reached_by_anneal(seed):
+    w, net, tc, xs = _planted_tiny(seed)
+    n_valid, best, bx = O.bruteforce(net, tc)
+    assert n_valid >= 1
+    assert best == 0  # the planted vector is in the space and scores 0
+    # a perturbed target: flip observed entries so the optimum is not 0
+    R2, _ = synth.flip_noise(tc.ref, tc.observed, 0.2, seed)
+    tc2 = O.Timecourse(tc.init, R2, tc.observed, tc.knockout)
+    n2, best2, bx2 = O.bruteforce(net, tc2)
+    assert O.objective(net, tc2, bx2) == best2
+    sched = O.Schedule(T0=5.0, alpha=0.99)
+    ch = O.start_chains(net, tc2, 11, 8)
+    O.anneal(net, tc2, sched, 11, ch, 0, 600)
+    assert int(ch.d_best.min()) == best2
+    for x in ch.x_best:
+        assert O.check_params(net, x) == 0
+
+
+def test_anneal_invariants_and_resume():
+    w = synth.tiny(8, n_nodes=5, indeg=2)
+    net, tc, xs, _ = oracle_problem(w)
+    sched = O.Schedule(T0=3.0, alpha=0.99)
+    a = O.start_chains(net, tc, 5, 6)
+    O.anneal(net, tc, sched, 5, a, 0, 120)
+    for k in range(6):
+        assert a.d_cur[k] == O.objective(net, tc, a.x_cur[k])
+        assert a.d_best[k] == O.objective(net, tc, a.x_best[k])
+        assert a.d_best[k] <= a.d_cur[k]
+        assert O.check_params(net, a.x_cur[k]) == 0
+        assert a.n_uphill[k] <= a.n_accept[k] and a.n_accept[k] + a.n_null[k] <= 120
+    # two calls of 60 steps equal one call of 120 (counter-based generator)
+    b = O.start_chains(net, tc, 5, 6)
+    O.anneal(net, tc, sched, 5, b, 0, 60)
+    O.anneal(net, tc, sched, 5, b, 60, 60)
+    np.testing.assert_array_equal(a.x_cur, b.x_cur)
+    np.testing.assert_array_equal(a.x_best, b.x_best)
+    np.testing.assert_array_equal(a.n_accept, b.n_accept)
+    # a subset of chains run alone follows the same trajectories
+    ids = [1, 4]
+    c = O.start_chains(net, tc, 5, 2, chain_ids=ids)
+    O.anneal(net, tc, sched, 5, c, 0, 120, chain_ids=ids)
+    np.testing.assert_array_equal(c.x_cur, a.x_cur[ids])
+    np.testing.assert_array_equal(c.d_best, a.d_best[ids])
+
+
+def test_paper_mode_levels():
+    w = synth.tiny(9, n_nodes=5, indeg=2)
+    net, tc, xs, _ = oracle_problem(w)
+    sched = O.Schedule(T0=5.0, alpha=0.9, iters_per_level=10, reset_to_best=True, global_sync=True)
+    ch = O.start_chains(net, tc, 2, 5)
+    O.anneal(net, tc, sched, 2, ch, 0, 30)
+    # after each level every chain holds the global best
+    assert len(set(ch.d_best.tolist())) == 1
+    assert len({x.tobytes() for x in ch.x_best}) == 1
+    assert ch.d_best[0] == O.objective(net, tc, ch.x_best[0])
+    # sync requires every chain
+    with pytest.raises(RuntimeError):
+        O.anneal(net, tc, sched, 2, ch, 30, 10, chain_ids=[0, 1, 2, 3, 4])
