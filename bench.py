@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Throughput of the GPU annealing path: candidate evaluations per second.
+
+One step = one rn_anneal call that advances every chain of the workload by
+--sweeps-per-step proposals (each proposal: Philox draw, GetCandidate with the
+Section 2.5.3 constraints, simulation of every condition and time step,
+scoring, Metropolis acceptance).  The default workload is the 120-node,
+8-condition, 21-time-point network with 4096 chains, on one GPU.
+
+Prints one JSON line (rank 0).  With --impl reference the CPU oracle is timed
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2506_19866_gb300 import synth  # noqa: E402
+
+METRIC = "candidate evals/sec"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="n120_c8_t21")
+    ap.add_argument("--sweeps-per-step", type=int, default=500)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def algorithmic_ops_per_eval(w):
+    """Integer operations of one evaluation: C (T-1) (2E + 12N) + 3 n_obs
+    (image: 2 per edge, priority update: 12 per node, score: 3 per observed
+    entry)."""
+    return w.C * (w.T - 1) * (2 * w.E + 12 * w.N) + 3 * int(w.observed.sum())
+
+
+def workload_config(w, sweeps_per_step):
+    return {"workload": w.name, "nodes": w.N, "edges": w.E, "params": w.P, "conditions": w.C,
+            "time_points": w.T, "chains": w.n_chains, "sweeps_per_step": sweeps_per_step,
+            "full_run_sweeps": w.sweeps, "schedule": f"geometric T0={w.T0} alpha={w.alpha:.10f}",
+            "noise_frac": w.noise_frac,
+            "l2": "working set (network tables + chain state, ~20 MB) is L2-resident by design; "
+                  "L2 flushed with a 512 MiB write between timed steps, outside the step events"}
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "power_w_max": float(max(pw)), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- CPU oracle --
+def _oracle_worker(args):
+    name, seed, chain_ids, sweeps, g0 = args
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    from paper_2506_19866_gb300 import synth as S
+    w = S.make(name)
+    net, tc = _oracle_problem(O, S, w)
+    ch = O.start_chains(net, tc, seed, len(chain_ids), chain_ids=chain_ids)
+    t0 = time.perf_counter()
+    O.anneal(net, tc, O.Schedule(w.T0, w.alpha), seed, ch, g0, sweeps, chain_ids=chain_ids)
+    dt = time.perf_counter() - t0
+    evals = len(chain_ids) * sweeps - int(ch.n_null.sum())
+    return evals, dt
+
+
+def _oracle_problem(O, S, w):
+    net = O.Network(w.src, w.dst, w.fast)
+    xs = O.init_chain(net, w.planted_seed, 0)
+    blank = O.Timecourse(w.init, np.zeros((w.C, w.T, w.N), np.uint8), w.observed, w.knockout)
+    _, traj = O.objective(net, blank, xs, return_traj=True)
+    R, _ = S.flip_noise(traj, w.observed, w.noise_frac, w.noise_seed)
+    return net, O.Timecourse(w.init, R, w.observed, w.knockout)
+
+
+def oracle_rate(name, seconds, cores=None):
+    """The oracle as it stands, one process per host core (spawned), each
+    annealing its own chains of the workload; sweeps sized to about `seconds`."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    w = synth.make(name)
+    # calibrate on one chain
+    ev, dt = _oracle_worker((name, w.chain_seed, [0], 3, 0))
+    per_eval = dt / max(ev, 1)
+    chains_per_proc = 2
+    sweeps = max(1, int(seconds / (per_eval * chains_per_proc)))
+    jobs = [(name, w.chain_seed, [2 * k, 2 * k + 1], sweeps, 0) for k in range(cores)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t0
+    evals = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return {"value": evals / busy, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes x {chains_per_proc} chains x {sweeps} sweeps of "
+                      f"{name} from step 0 ({evals} evaluations, {busy:.1f} s per process, "
+                      f"{wall:.1f} s wall incl. process start)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    w = synth.make(args.workload)
+    per_step = min(20.0, max(1.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_rate(args.workload, min(per_step, 5.0))
+    vals, samples, cores = [], [], None
+    t_all = 0.0
+    for _ in range(args.steps):
+        r = oracle_rate(args.workload, per_step)
+        vals.append(r["value"])
+        samples.append(r["sample"])
+        cores = r["cores"]
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": workload_config(w, args.sweeps_per_step),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": samples[0] + f"; {args.steps} such steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm --
+def setup_problem(R, ctx, w):
+    """Network, planted vector (the library's sampler, seed planted_seed, chain
+    0), reference data = the planted trajectories (library evaluate) with the
+    noise flips, loaded into the context."""
+    nid = R.rn_load_network(ctx, w.src, w.dst, w.fast)
+    zero = np.zeros((w.C, w.T, w.N), np.uint8)
+    R.rn_load_timecourse(ctx, nid, w.init, zero, w.observed, w.knockout)
+    R.rn_init_chains(ctx, nid, 1, w.planted_seed)
+    xs = R.rn_get_chain_state(ctx, nid, 1)["x_cur"][0]
+    _, traj = R.rn_evaluate(ctx, nid, xs, traj_shape=(w.C, w.T, w.N))
+    ref, _ = synth.flip_noise(traj[0], w.observed, w.noise_frac, w.noise_seed)
+    R.rn_load_timecourse(ctx, nid, w.init, ref, w.observed, w.knockout)
+    return nid, ref
+
+
+def peak_int32(device_index):
+    """Measured ALU issue rate (ops per SM per clock) from the peaks library."""
+    import ctypes
+    from paper_2506_19866_gb300 import build as B
+    lib = ctypes.CDLL(B.PEAKS_LIB)
+    lib.rnpk_ops_per_sm_clock.restype = ctypes.c_double
+    lib.rnpk_ops_per_sm_clock.argtypes = [ctypes.c_int, ctypes.c_int]
+    return {"alu": lib.rnpk_ops_per_sm_clock(0, 8), "imad": lib.rnpk_ops_per_sm_clock(1, 8),
+            "lds": lib.rnpk_ops_per_sm_clock(2, 8)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2506_19866_gb300 import build as B
+    from paper_2506_19866_gb300 import rnanneal as R
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    B.build()
+    torch.cuda.set_device(local_rank)
+    # a dedicated stream: the legacy default stream has handle 0, which the
+    # library would read as "create your own"
+    stream = torch.cuda.Stream(device=local_rank)
+    torch.cuda.set_stream(stream)
+    w = synth.make(args.workload)
+    S = args.sweeps_per_step
+    ctx = R.rn_create(local_rank, stream.cuda_stream)
+    nid, ref = setup_problem(R, ctx, w)
+    seed = w.chain_seed + rank
+    R.rn_init_chains(ctx, nid, w.n_chains, seed)
+    sched = R.schedule(w.T0, w.alpha)
+    R.rn_prepare_schedule(ctx, sched, (args.warmup + args.steps) * S)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        R.rn_anneal(ctx, sched, S)
+    R.rn_synchronize(ctx)
+    before = R.rn_get_chain_state(ctx, nid, w.n_chains)["counters"]
+    l0 = R.rn_launch_count(ctx)
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    times = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R.rn_anneal(ctx, sched, S)
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    launches = R.rn_launch_count(ctx) - l0
+    step_ms = [a.elapsed_time(b) for a, b in times]
+    after = R.rn_get_chain_state(ctx, nid, w.n_chains)["counters"]
+    nulls = int((after[:, 2] - before[:, 2]).sum())
+    evals = w.n_chains * S * args.steps - nulls
+    total_s = sum(step_ms) / 1000.0
+
+    t_max, evals_all = total_s, evals
+    if dist is not None:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e = torch.tensor([evals], dtype=torch.float64, device="cuda")
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        t_max, evals_all = float(t.item()), int(e.item())
+    value = evals_all / t_max
+
+    # roofline of the anneal kernel (the only kernel of a step)
+    ops_eval = algorithmic_ops_per_eval(w)
+    per_launch_ops = ops_eval * evals / max(1, launches)
+    mean_launch_s = total_s / max(1, launches)
+    achieved = per_launch_ops / mean_launch_s
+    peaks = peak_int32(local_rank) if rank == 0 else {}
+    sm_count = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    f_hz = (clk.get("sm_mhz") or 0.0) * 1e6
+    alu_per_clk = peaks.get("alu", 0.0)
+    peak = sm_count * alu_per_clk * f_hz if f_hz and alu_per_clk > 0 else None
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": None if peak is None else peak / 1e12,
+                "unit": "Tops/s", "frac": None if peak is None else achieved / peak,
+                "traffic": None,
+                "kernel": "anneal_kernel", "ops_per_eval": ops_eval,
+                "peak_basis": (f"{sm_count} SMs x {alu_per_clk:.1f} int32 ALU ops/clk/SM "
+                               f"(measured, peaks.cu) x median SM clock {clk.get('sm_mhz')} MHz "
+                               "sampled during the timed steps"),
+                "measured_issue_rates_per_sm_clk": peaks}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": workload_config(w, S),
+            "node_updates_per_s": value * w.C * (w.T - 1) * w.N,
+            "null_moves_frac": nulls / (w.n_chains * S * args.steps),
+            "wall_s_timed_loop": t_wall,
+            "roofline": roofline, "clocks": clk, "gpu_launches": launches}
+
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e(args, R, w, local_rank, stream)
+    R.rn_destroy(ctx)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = oracle_rate(args.workload, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def e2e(args, R, w, device, stream):
+    """Whole user path per step through the C ABI with host buffers: create a
+    context, load the network and the time courses, draw the chains, anneal
+    one step, read the best vector back."""
+    import torch
+    nid_ref = None
+    ctx0 = R.rn_create(device, stream.cuda_stream)
+    _, ref = setup_problem(R, ctx0, w)
+    R.rn_destroy(ctx0)
+    S = args.sweeps_per_step
+    h2d = (w.src.nbytes + w.dst.nbytes + w.fast.nbytes + w.init.nbytes + w.knockout.nbytes
+           + ref.nbytes + w.observed.nbytes)
+    d2h = w.P + 4 * w.n_chains + 8
+    rates = []
+    for _ in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = R.rn_create(device, stream.cuda_stream)
+        nid = R.rn_load_network(ctx, w.src, w.dst, w.fast)
+        R.rn_load_timecourse(ctx, nid, w.init, ref, w.observed, w.knockout)
+        R.rn_init_chains(ctx, nid, w.n_chains, w.chain_seed)
+        R.rn_anneal(ctx, R.schedule(w.T0, w.alpha), S)
+        x, score, chain = R.rn_get_best(ctx, nid)
+        dt = time.perf_counter() - t0
+        nulls = int(R.rn_get_chain_state(ctx, nid, w.n_chains)["counters"][:, 2].sum())
+        R.rn_destroy(ctx)
+        rates.append((w.n_chains * S - nulls) / dt)
+    return {"value": float(np.median(rates)), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h),
+            "path": "rn_create + rn_load_network + rn_load_timecourse + rn_init_chains + "
+                    "rn_anneal(one step) + rn_get_best, host buffers, wall clock"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * rnanneal.h -- C ABI of the GB300 (sm_103a) library for parallel simulated
+ * annealing over the integer parameters of ternary discrete-logic models of
+ * regulatory networks (arXiv 2506.19866).
+ *
+ * The problem (Sections 2.1-2.3): a directed network of N nodes with states
+ * s_i in {0,1,2}; each edge j -> i carries weight w in {0,1,2}, polarity
+ * p in {-1,0,1} and threshold t in {1,2} (Section 2.1); each node carries
+ * speed u ({1..6} slow, {10,11,12} fast), memory m in {0,1,2} and step size
+ * d in {1,2} (Section 2.2).  Given initial states, sparse time courses R and
+ * the observation mask, find the parameter vector
+ *     x = [w(E), p(E), t(E), u(N), m(N), d(N)],  P = 3E + 3N  (Section 2.3)
+ * minimising the gradient-weighted Manhattan distance y between the simulated
+ * trajectories S(x) and R, subject to the structural constraints of
+ * Section 2.5.3, with the parallel annealing loop of Table 1.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns RN_OK (0) or a negative RN_E* code; the message
+ *     of the last failure on a context is rn_last_error(ctx).  A failing call
+ *     leaves the context's previous state usable unless the code is
+ *     RN_ECUDA, after which the context should be destroyed.
+ *   - Host arrays are read during the call and copied; the library keeps no
+ *     pointer to them.  Output host arrays are written before the call returns.
+ *   - Arrays are dense, row-major, in the shapes given ([C][T][N] means
+ *     index (c * T + t) * N + i).  Edge order is the caller's order and defines
+ *     the layout of x.
+ *   - The context owns all device memory it allocates.  Work runs on the
+ *     stream given to rn_create (NULL: the library creates its own), so a
+ *     caller may pass the CUDA stream its framework is using.
+ *   - Contexts are not thread-safe; one context per host thread.
+ *   - The step generator is Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ *     64-bit seed; step g of chain k uses counter (g_lo, g_hi, k, 0): word 0
+ *     picks the parameter, word 1 its new value, word 2 decides acceptance.
+ *     Results are bit-identical across runs, devices and call splittings.
+ */
+#ifndef RNANNEAL_H
+#define RNANNEAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RN_OK 0
+#define RN_EINVAL (-1)        /* bad argument, shape or value */
+#define RN_ECONSTRAINT (-2)   /* Section 2.5.3 constraints cannot hold / do not hold */
+#define RN_ENOMEM (-3)        /* device or host allocation failed */
+#define RN_ECUDA (-4)         /* a CUDA call failed */
+#define RN_ETIMEOUT (-5)      /* a device-side wait gave up (error flag set by a kernel) */
+#define RN_ESTATE (-6)        /* call made in the wrong order (e.g. anneal before init) */
+#define RN_EUNSUPPORTED (-7)  /* shape outside what the compiled kernels cover */
+
+typedef struct rn_ctx rn_ctx;
+
+/* Annealing schedule (Table 1 and Section 2.4.1).  Level l runs at
+ * T_l = T0 * alpha^l (repeated multiplication in double precision) for
+ * iters_per_level proposals per chain.  reset_to_best: each level starts from
+ * the chain's x_best (Table 1, first lines of the while loop).  global_sync:
+ * each level ends with the serial argmin of Table 1 -- the lowest delta_best
+ * over all chains of a network (lowest chain index on ties) is copied into
+ * every chain's x_best.  The paper's runs use T0 = 1000, alpha = 0.99,
+ * iters_per_level = 5000, reset_to_best = global_sync = 1; one proposal per
+ * level with both flags 0 is a plain geometric anneal.  Acceptance of a
+ * candidate with dE = delta_cand - delta_cur > 0 is r < thr(T_l, dE) with
+ * thr = min(floor(exp(-dE / T_l) * 2^32), 2^32 - 1) computed on the host. */
+typedef struct {
+    double T0;
+    double alpha;
+    int64_t iters_per_level;
+    int32_t reset_to_best;
+    int32_t global_sync;
+} rn_schedule;
+
+/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t the
+ * library should use (NULL: create one).  Fails with RN_ECUDA if the device
+ * cannot be used or is not an sm_103 part. */
+int rn_create(rn_ctx **out, int device, void *stream);
+
+/* Free every device buffer and the context itself.  NULL is accepted. */
+int rn_destroy(rn_ctx *ctx);
+
+/* Message of the last failure on ctx ("" if none).  Valid until the next call
+ * on ctx.  NULL ctx gives the message of the last rn_create failure. */
+const char *rn_last_error(const rn_ctx *ctx);
+
+/* Register a network (Section 2.1 topology, Section 2.2 speed classes).
+ *   src, dst   [E] node indices of each edge (0 <= index < N).
+ *   fast       [N] 1 = fast node (u in {10,11,12}), 0 = slow (u in {1..6}).
+ *   frozen     [P] 1 = parameter j is fixed at frozen_val[j] and never
+ *              proposed, or NULL (everything free).
+ *   frozen_val [P] values of the fixed parameters (ignored where frozen = 0),
+ *              or NULL iff frozen is NULL.
+ * Rejected with RN_EINVAL: N < 1, E < 1, N > 65535, an index out of range,
+ * a self-loop, a duplicate edge, a node without an in-edge or an out-edge
+ * (the constraints of Section 2.5.3 could never hold), a fixed value outside
+ * its domain.  On success *net_id receives the network's handle. */
+int rn_load_network(rn_ctx *ctx, int32_t n_nodes, int32_t n_edges, const int32_t *src,
+                    const int32_t *dst, const uint8_t *fast, const uint8_t *frozen,
+                    const int8_t *frozen_val, int32_t *net_id);
+
+/* Attach experimental data to a network (Section 2.3).
+ *   n_cond     C >= 1 conditions; a condition is an initial state plus an
+ *              optional set of knocked-out nodes (held at 0, never updated).
+ *   n_times    T >= 1 time points including t0 (T - 1 update steps).
+ *   init       [C][N] initial states, 0..2.
+ *   knockout   [C][N] 1 = knocked out in that condition, or NULL.
+ *   ref        [C][T][N] reference data R, 0..2 (ignored where unobserved).
+ *   observed   [C][T][N] 1 = entry observed.
+ * The weight of an entry is observed * (|G| + 1), with G the difference of R
+ * to the previous time point of the same condition where both are observed
+ * and 0 otherwise (0 in row t0).  Replaces earlier data and invalidates the
+ * chains' objective values (call rn_init_chains again). */
+int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times,
+                       const uint8_t *init, const uint8_t *knockout, const uint8_t *ref,
+                       const uint8_t *observed);
+
+/* Create n_chains >= 1 annealing chains for a network and evaluate them.
+ *   seed   Philox key of every draw of these chains.
+ *   x0     [n_chains][P] starting vectors (checked: domains, fixed values,
+ *          constraints -> RN_EINVAL / RN_ECONSTRAINT), or NULL to draw them on
+ *          the device: each free x_j is dom_j[floor(r * |dom_j| / 2^32)] with r
+ *          word (j & 3) of Philox(seed; j >> 2, 0, chain, 1); then every node
+ *          without an activating in-edge gets one (p = +1, w = 1 + (r1 & 1) on
+ *          the floor(r0 * n / 2^32)-th eligible in-edge, r = Philox(seed; i, 0,
+ *          chain, 3)), then every node without a nonzero out-edge gets one
+ *          (w = 1 + (r1 & 1), r = Philox(seed; i, 1, chain, 3)).  A network
+ *          whose fixed parameters make this impossible gives RN_ECONSTRAINT.
+ * Sets x_best = x_cur = x0, delta_best = delta_cur = y(x0), global step 0. */
+int rn_init_chains(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed, const int8_t *x0);
+
+/* Precompute the acceptance-threshold tables of a schedule for global steps
+ * 0 .. total_steps - 1 and keep them on the device, so that later rn_anneal
+ * calls with an identical schedule inside that range do no host work and
+ * return without waiting for the device.  Optional: rn_anneal computes the
+ * tables it needs when they are not cached.  The cache covers every network
+ * loaded so far (their largest possible dE). */
+int rn_prepare_schedule(rn_ctx *ctx, const rn_schedule *sched, int64_t total_steps);
+
+/* Advance every chain of every initialised network by `sweeps` proposal
+ * steps (global steps g .. g + sweeps - 1, continuing from earlier calls).
+ * Per step and chain (Table 1): draw r; GetCandidate picks the
+ * floor(r0 * n_free / 2^32)-th free parameter and the floor(r1 * n_alt / 2^32)-th
+ * of its alternative values (ascending, != current, keeping both constraints
+ * of Section 2.5.3); with no alternative the step is a null move and nothing
+ * is simulated; otherwise the candidate is simulated over every condition and
+ * scored, and accepted iff dE <= 0 or r2 < thr(T_l, dE).  x_best follows
+ * strict improvements.  Asynchronous on the context stream except for the
+ * small threshold-table upload; RN_ESTATE if a network has no chains. */
+int rn_anneal(rn_ctx *ctx, const rn_schedule *sched, int64_t sweeps);
+
+/* Best vector over a network's chains: lowest delta_best, lowest chain index
+ * on ties.  x [P] (may be NULL), *score, *chain (may be NULL).  Synchronises
+ * the context stream. */
+int rn_get_best(rn_ctx *ctx, int32_t net, int8_t *x, int32_t *score, int32_t *chain);
+
+/* Objective y of n parameter vectors (Simulate() of Table 1), host buffers.
+ *   x      [n][P] vectors (domains are checked; constraints are not required).
+ *   score  [n] out.
+ *   traj   [n][C][T][N] out: simulated trajectories S, or NULL. */
+int rn_evaluate(rn_ctx *ctx, int32_t net, int32_t n, const int8_t *x, int32_t *score,
+                uint8_t *traj);
+
+/* As rn_evaluate with device pointers (x_dev [n][P], score_dev [n],
+ * traj_dev [n][C][T][N] or NULL) and no host synchronisation: the work is
+ * queued on the context stream.  Values outside a domain give undefined
+ * scores (not checked). */
+int rn_evaluate_device(rn_ctx *ctx, int32_t net, int32_t n, const int8_t *x_dev,
+                       int32_t *score_dev, uint8_t *traj_dev);
+
+/* Number of parameters P = 3E + 3N of a network. */
+int rn_n_params(rn_ctx *ctx, int32_t net, int32_t *n_params);
+
+/* Checkpoint / parity access to the chain state of a network (host buffers,
+ * each may be NULL): x_cur, x_best [n][P]; d_cur, d_best [n];
+ * counters [n][3] = accepted moves, accepted uphill moves (dE > 0), null
+ * moves; *step = next global step.  rn_set_chain_state restores all of them
+ * (every pointer required, vectors checked as in rn_init_chains), so that a
+ * resumed run continues bit-identically. */
+int rn_get_chain_state(rn_ctx *ctx, int32_t net, int8_t *x_cur, int32_t *d_cur, int8_t *x_best,
+                       int32_t *d_best, int64_t *counters, int64_t *step);
+int rn_set_chain_state(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed,
+                       const int8_t *x_cur, const int32_t *d_cur, const int8_t *x_best,
+                       const int32_t *d_best, const int64_t *counters, int64_t step);
+
+/* Number of kernels this context has launched since rn_create. */
+int rn_launch_count(rn_ctx *ctx, int64_t *count);
+
+/* Wait for all queued work on the context stream; reports device-side errors. */
+int rn_synchronize(rn_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,963 @@
+// rn_api.cu -- host side of the C ABI declared in include/rnanneal.h.
+//
+// Builds the device layout of each network (lane/slot placement of nodes,
+// padded per-slot in-edge tables, error tables of the time courses), owns the
+// chain state, computes the Metropolis threshold tables in double precision on
+// the host (Table 1: A = exp(-dE / T)), and launches the kernels of
+// rn_kernels.cu on the context stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/rnanneal.h"
+#include "rn_launch.h"
+
+namespace {
+
+using namespace rn;
+
+// Device buffer owned by the context.
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t alloc(size_t count)
+    {
+        release();
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        n = count;
+        return cudaSuccess;
+    }
+    cudaError_t reserve(size_t count)
+    {
+        return count <= n ? cudaSuccess : alloc(count);
+    }
+    cudaError_t upload(const std::vector<T> &v)
+    {
+        cudaError_t e = alloc(v.size());
+        if (e != cudaSuccess) return e;
+        if (v.empty()) return cudaSuccess;
+        return cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    }
+};
+
+struct Network {
+    int32_t N = 0, E = 0, P = 0;
+    std::vector<int32_t> src, dst;
+    std::vector<uint8_t> fast, frozen;
+    std::vector<int8_t> frozen_val;
+    bool has_frozen = false;
+    // lane / slot layout
+    int npl = 0, dtab = 0;
+    int D[kMaxSlots] = {0, 0, 0, 0};
+    std::vector<int32_t> node_q, edge_id, edge_pos, free_list, in_ptr, in_edges, out_ptr,
+        out_edges;
+    std::vector<int16_t> q_node;
+    std::vector<uint8_t> edge_q2;
+    bool supported = false;
+    // device copies
+    DevBuf<int32_t> d_edge_id, d_edge_pos, d_node_q, d_src, d_dst, d_free, d_in_ptr, d_in_edges,
+        d_out_ptr, d_out_edges;
+    DevBuf<int16_t> d_q_node;
+    DevBuf<uint8_t> d_edge_q2, d_fast, d_frozen;
+    DevBuf<int8_t> d_frozen_val;
+    // time course: conditions are simulated cg at a time, G groups
+    bool has_tc = false;
+    int32_t C = 0, T = 0, cg = 1, G = 0;
+    int d0 = -1, d1 = -1;               // register capacities of the anneal kernel
+    int64_t max_score = 0;
+    DevBuf<uint16_t> d_init_code, d_out_bits;
+    DevBuf<uint32_t> d_obs;
+    // chains
+    int32_t n_chains = 0;
+    int32_t pstride = 0;
+    uint64_t seed = 0;
+    int64_t step = 0;
+    bool chains_valid = false;
+    DevBuf<int8_t> d_x_cur, d_x_best;
+    DevBuf<int32_t> d_d_cur, d_d_best;
+    DevBuf<int64_t> d_cnt;
+
+    DevNet dev() const
+    {
+        DevNet n{};
+        n.N = N; n.E = E; n.P = P; n.n_free = (int32_t)free_list.size();
+        n.C = C; n.T = T; n.G = G;
+        n.npl = npl; n.cg = cg; n.dtab = dtab;
+        for (int k = 0; k < kMaxSlots; ++k) n.D[k] = D[k];
+        n.edge_id = d_edge_id.p; n.edge_q2 = d_edge_q2.p; n.edge_pos = d_edge_pos.p;
+        n.node_q = d_node_q.p; n.q_node = d_q_node.p; n.src = d_src.p; n.dst = d_dst.p;
+        n.fast = d_fast.p; n.free_list = d_free.p;
+        n.in_ptr = d_in_ptr.p; n.in_edges = d_in_edges.p;
+        n.out_ptr = d_out_ptr.p; n.out_edges = d_out_edges.p;
+        n.frozen = has_frozen ? d_frozen.p : nullptr;
+        n.frozen_val = has_frozen ? d_frozen_val.p : nullptr;
+        n.init_code = d_init_code.p; n.out_bits = d_out_bits.p; n.obs = d_obs.p;
+        return n;
+    }
+    DevChains chains() const
+    {
+        DevChains c{};
+        c.n = n_chains; c.pstride = pstride; c.seed = seed;
+        c.x_cur = d_x_cur.p; c.x_best = d_x_best.p;
+        c.d_cur = d_d_cur.p; c.d_best = d_d_best.p; c.cnt = d_cnt.p;
+        return c;
+    }
+};
+
+}  // namespace
+
+struct SchedCache {
+    bool valid = false;
+    double T0 = 0, alpha = 0;
+    int64_t iters = 0, l0 = 0, l1 = -1, cap = 0;
+    DevBuf<uint32_t> thr;
+    DevBuf<int32_t> off, len;
+};
+
+struct rn_ctx {
+    int device = 0;
+    int64_t launches = 0;
+    SchedCache cache;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<std::unique_ptr<Network>> nets;
+    DevBuf<uint32_t> thr;
+    DevBuf<int32_t> thr_off, thr_len;
+    DevBuf<int32_t> status;
+    DevBuf<int32_t> winner;
+    DevBuf<int8_t> xbuf;
+    DevBuf<int32_t> sbuf;
+    DevBuf<uint8_t> tbuf;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(rn_ctx *ctx, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+int cuda_fail(rn_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, e == cudaErrorMemoryAllocation ? RN_ENOMEM : RN_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define RN_CUDA(ctx, call)                                         \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+Network *get_net(rn_ctx *ctx, int32_t id)
+{
+    if (!ctx || id < 0 || id >= (int32_t)ctx->nets.size()) return nullptr;
+    return ctx->nets[(size_t)id].get();
+}
+
+// Domain of parameter j (Sections 2.1 and 2.2).
+int domain_of(const Network &n, int32_t j, int8_t vals[6])
+{
+    const int32_t E = n.E, N = n.N;
+    if (j < E || (j >= 3 * E + N && j < 3 * E + 2 * N)) {   // w, m
+        vals[0] = 0; vals[1] = 1; vals[2] = 2;
+        return 3;
+    }
+    if (j < 2 * E) { vals[0] = -1; vals[1] = 0; vals[2] = 1; return 3; }   // p
+    if (j < 3 * E || j >= 3 * E + 2 * N) { vals[0] = 1; vals[1] = 2; return 2; }   // t, d
+    if (n.fast[(size_t)(j - 3 * E)]) { vals[0] = 10; vals[1] = 11; vals[2] = 12; return 3; }
+    for (int k = 0; k < 6; ++k) vals[k] = (int8_t)(k + 1);
+    return 6;
+}
+
+bool in_domain(const Network &n, int32_t j, int8_t v)
+{
+    int8_t vals[6];
+    const int k = domain_of(n, j, vals);
+    for (int a = 0; a < k; ++a)
+        if (vals[a] == v) return true;
+    return false;
+}
+
+// Domains, fixed values, and the two constraints of Section 2.5.3.
+int check_vector(rn_ctx *ctx, const Network &n, const int8_t *x, int64_t which)
+{
+    for (int32_t j = 0; j < n.P; ++j) {
+        if (!in_domain(n, j, x[j]))
+            return fail(ctx, RN_EINVAL, "vector %lld: parameter %d = %d is outside its domain",
+                        (long long)which, j, (int)x[j]);
+        if (n.has_frozen && n.frozen[(size_t)j] && x[j] != n.frozen_val[(size_t)j])
+            return fail(ctx, RN_EINVAL, "vector %lld: fixed parameter %d changed",
+                        (long long)which, j);
+    }
+    std::vector<int> out_nz((size_t)n.N, 0), pos_in((size_t)n.N, 0);
+    for (int32_t e = 0; e < n.E; ++e) {
+        if (x[e] != 0) out_nz[(size_t)n.src[(size_t)e]]++;
+        if (x[e] != 0 && x[n.E + e] == 1) pos_in[(size_t)n.dst[(size_t)e]]++;
+    }
+    for (int32_t i = 0; i < n.N; ++i)
+        if (out_nz[(size_t)i] == 0 || pos_in[(size_t)i] == 0)
+            return fail(ctx, RN_ECONSTRAINT,
+                        "vector %lld: node %d lacks a nonzero out-edge or an activating in-edge",
+                        (long long)which, i);
+    return RN_OK;
+}
+
+// Acceptance threshold of Table 1 as a 32-bit word: floor(exp(-dE / T) * 2^32),
+// capped at 2^32 - 1.
+uint32_t threshold(double T, int64_t dE)
+{
+    const double a = std::exp(-(double)dE / T) * 4294967296.0;
+    const double f = std::floor(a);
+    return f >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)f;
+}
+
+// Node placement: nodes ranked by in-degree (descending, then index); rank r
+// goes to slot r / 32, lane r % 32, internal index q = lane * npl + slot.
+void build_layout(Network &n)
+{
+    const int32_t N = n.N, E = n.E;
+    n.npl = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : 0;
+    n.in_ptr.assign((size_t)N + 1, 0);
+    n.out_ptr.assign((size_t)N + 1, 0);
+    for (int32_t e = 0; e < E; ++e) {
+        n.in_ptr[(size_t)n.dst[(size_t)e] + 1]++;
+        n.out_ptr[(size_t)n.src[(size_t)e] + 1]++;
+    }
+    for (int32_t i = 0; i < N; ++i) {
+        n.in_ptr[(size_t)i + 1] += n.in_ptr[(size_t)i];
+        n.out_ptr[(size_t)i + 1] += n.out_ptr[(size_t)i];
+    }
+    n.in_edges.assign((size_t)E, 0);
+    n.out_edges.assign((size_t)E, 0);
+    {
+        std::vector<int32_t> fi(n.in_ptr.begin(), n.in_ptr.end() - 1);
+        std::vector<int32_t> fo(n.out_ptr.begin(), n.out_ptr.end() - 1);
+        for (int32_t e = 0; e < E; ++e) {
+            n.in_edges[(size_t)fi[(size_t)n.dst[(size_t)e]]++] = e;
+            n.out_edges[(size_t)fo[(size_t)n.src[(size_t)e]]++] = e;
+        }
+    }
+    n.free_list.clear();
+    for (int32_t j = 0; j < n.P; ++j)
+        if (!(n.has_frozen && n.frozen[(size_t)j])) n.free_list.push_back(j);
+
+    n.supported = false;
+    if (n.npl == 0) return;
+    const int npl = n.npl;
+    std::vector<int32_t> order((size_t)N);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return n.in_ptr[(size_t)a + 1] - n.in_ptr[(size_t)a] >
+               n.in_ptr[(size_t)b + 1] - n.in_ptr[(size_t)b];
+    });
+    n.node_q.assign((size_t)N, 0);
+    n.q_node.assign((size_t)32 * npl, (int16_t)-1);
+    for (int k = 0; k < kMaxSlots; ++k) n.D[k] = 0;
+    for (int32_t r = 0; r < N; ++r) {
+        const int32_t i = order[(size_t)r];
+        const int slot = r / 32, lane = r % 32;
+        const int q = lane * npl + slot;
+        n.node_q[(size_t)i] = q;
+        n.q_node[(size_t)q] = (int16_t)i;
+        n.D[slot] = std::max(n.D[slot], n.in_ptr[(size_t)i + 1] - n.in_ptr[(size_t)i]);
+    }
+    n.dtab = 1;
+    for (int k = 0; k < npl; ++k) n.dtab = std::max(n.dtab, n.D[k]);
+    if (n.dtab > 16) return;
+    n.edge_id.assign((size_t)npl * n.dtab * 32, -1);
+    n.edge_q2.assign((size_t)E, 0);
+    n.edge_pos.assign((size_t)E, 0);
+    for (int32_t e = 0; e < E; ++e)
+        n.edge_q2[(size_t)e] = (uint8_t)(2 * n.node_q[(size_t)n.src[(size_t)e]]);
+    for (int q = 0; q < 32 * npl; ++q) {
+        const int i = n.q_node[(size_t)q];
+        const int lane = q / npl, slot = q % npl;
+        if (i < 0) continue;
+        int d = 0;
+        for (int32_t k = n.in_ptr[(size_t)i]; k < n.in_ptr[(size_t)i + 1]; ++k, ++d) {
+            const int32_t e = n.in_edges[(size_t)k];
+            const size_t idx = ((size_t)slot * n.dtab + d) * 32 + lane;
+            n.edge_id[idx] = e;
+            n.edge_pos[(size_t)e] = (lane << 16) | (slot << 8) | d;
+        }
+    }
+    n.supported = true;
+}
+
+int require_supported(rn_ctx *ctx, const Network &n)
+{
+    if (!n.supported)
+        return fail(ctx, RN_EUNSUPPORTED,
+                    "network with %d nodes and maximum in-degree %d is outside the compiled "
+                    "kernels (N <= 128, in-degree <= 16)",
+                    n.N, n.dtab);
+    return RN_OK;
+}
+
+int evaluate_device_impl(rn_ctx *ctx, Network &n, int32_t count, const int8_t *x, int64_t xstride,
+                         int32_t *score, int32_t *score2, uint8_t *traj)
+{
+    if (count <= 0) return RN_OK;
+    const cudaError_t e = launch_evaluate(n.dev(), x, xstride, count, score, score2, traj,
+                                          ctx->sm_count, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "evaluate kernel");
+    ctx->launches += 1;
+    return RN_OK;
+}
+
+int alloc_chains(rn_ctx *ctx, Network &n, int32_t count)
+{
+    n.pstride = (n.P + 15) & ~15;
+    const size_t rows = (size_t)count * (size_t)n.pstride;
+    RN_CUDA(ctx, n.d_x_cur.reserve(rows));
+    RN_CUDA(ctx, n.d_x_best.reserve(rows));
+    RN_CUDA(ctx, n.d_d_cur.reserve((size_t)count));
+    RN_CUDA(ctx, n.d_d_best.reserve((size_t)count));
+    RN_CUDA(ctx, n.d_cnt.reserve((size_t)count * 3));
+    n.n_chains = count;
+    return RN_OK;
+}
+
+int upload_rows(rn_ctx *ctx, Network &n, int8_t *dst, const int8_t *src, int32_t count)
+{
+    std::vector<int8_t> rows((size_t)count * n.pstride, 0);
+    for (int32_t c = 0; c < count; ++c)
+        std::memcpy(&rows[(size_t)c * n.pstride], src + (size_t)c * n.P, (size_t)n.P);
+    RN_CUDA(ctx, cudaMemcpyAsync(dst, rows.data(), rows.size(), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RN_OK;
+}
+
+int download_rows(rn_ctx *ctx, const Network &n, int8_t *dst, const int8_t *src)
+{
+    std::vector<int8_t> rows((size_t)n.n_chains * n.pstride);
+    RN_CUDA(ctx, cudaMemcpyAsync(rows.data(), src, rows.size(), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int32_t c = 0; c < n.n_chains; ++c)
+        std::memcpy(dst + (size_t)c * n.P, &rows[(size_t)c * n.pstride], (size_t)n.P);
+    return RN_OK;
+}
+
+// Threshold tables of levels [l0, l1]: T_l by repeated multiplication from T0,
+// D_l = the largest dE <= cap with a nonzero threshold (cap = the largest dE
+// any candidate can reach, and beyond 32 ln 2 T the threshold is 0).
+int build_thresholds(rn_ctx *ctx, const rn_schedule &s, int64_t l0, int64_t l1, int64_t max_dE,
+                     std::vector<uint32_t> &thr, std::vector<int32_t> &off,
+                     std::vector<int32_t> &len)
+{
+    double T = s.T0;
+    for (int64_t l = 0; l < l0; ++l) T *= s.alpha;
+    thr.clear();
+    off.clear();
+    len.clear();
+    for (int64_t l = l0; l <= l1; ++l) {
+        if (l > l0) T *= s.alpha;
+        if (!(T > 0.0) || !std::isfinite(T))
+            return fail(ctx, RN_EINVAL, "temperature of level %lld is not a positive number",
+                        (long long)l);
+        const double lim = std::floor(22.2 * T) + 2.0;
+        const int64_t cap = std::min<int64_t>(max_dE, lim > 1e9 ? (int64_t)1e9 : (int64_t)lim);
+        off.push_back((int32_t)thr.size());
+        int64_t D = 0;
+        const size_t start = thr.size();
+        for (int64_t dE = 1; dE <= cap; ++dE) {
+            const uint32_t t = threshold(T, dE);
+            thr.push_back(t);
+            if (t != 0) D = dE;
+        }
+        thr.resize(start + (size_t)D);
+        len.push_back((int32_t)D);
+        if (thr.size() > (size_t)1 << 30)
+            return fail(ctx, RN_ENOMEM, "threshold tables exceed 2^30 entries");
+    }
+    return RN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rn_create(rn_ctx **out, int device, void *stream)
+{
+    if (!out) return fail(nullptr, RN_EINVAL, "out is NULL");
+    *out = nullptr;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess)
+        return fail(nullptr, RN_ECUDA, "cudaSetDevice(%d): %s", device, cudaGetErrorString(e));
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess)
+        return fail(nullptr, RN_ECUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(nullptr, RN_ECUDA, "device %d is sm_%d%d; this library is built for sm_103a",
+                    device, prop.major, prop.minor);
+    auto ctx = std::make_unique<rn_ctx>();
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess)
+            return fail(nullptr, RN_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        ctx->own_stream = true;
+    }
+    if (ctx->status.alloc(1) != cudaSuccess || ctx->winner.alloc(1) != cudaSuccess)
+        return fail(nullptr, RN_ENOMEM, "cannot allocate context buffers");
+    *out = ctx.release();
+    return RN_OK;
+}
+
+int rn_destroy(rn_ctx *ctx)
+{
+    if (!ctx) return RN_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return RN_OK;
+}
+
+const char *rn_last_error(const rn_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int rn_load_network(rn_ctx *ctx, int32_t n_nodes, int32_t n_edges, const int32_t *src,
+                    const int32_t *dst, const uint8_t *fast, const uint8_t *frozen,
+                    const int8_t *frozen_val, int32_t *net_id)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    if (!src || !dst || !fast || !net_id) return fail(ctx, RN_EINVAL, "NULL array");
+    if (n_nodes < 1 || n_nodes > 65535) return fail(ctx, RN_EINVAL, "n_nodes %d out of range", n_nodes);
+    if (n_edges < 1) return fail(ctx, RN_EINVAL, "n_edges %d out of range", n_edges);
+    if ((frozen == nullptr) != (frozen_val == nullptr))
+        return fail(ctx, RN_EINVAL, "frozen and frozen_val must both be given or both be NULL");
+    auto n = std::make_unique<Network>();
+    n->N = n_nodes;
+    n->E = n_edges;
+    n->P = 3 * n_edges + 3 * n_nodes;
+    n->src.assign(src, src + n_edges);
+    n->dst.assign(dst, dst + n_edges);
+    n->fast.assign(fast, fast + n_nodes);
+    std::set<std::pair<int32_t, int32_t>> seen;
+    std::vector<int> indeg((size_t)n_nodes, 0), outdeg((size_t)n_nodes, 0);
+    for (int32_t e = 0; e < n_edges; ++e) {
+        const int32_t a = src[e], b = dst[e];
+        if (a < 0 || a >= n_nodes || b < 0 || b >= n_nodes)
+            return fail(ctx, RN_EINVAL, "edge %d: node index out of range", e);
+        if (a == b) return fail(ctx, RN_EINVAL, "edge %d is a self-loop", e);
+        if (!seen.insert({a, b}).second) return fail(ctx, RN_EINVAL, "edge %d is a duplicate", e);
+        outdeg[(size_t)a]++;
+        indeg[(size_t)b]++;
+    }
+    for (int32_t i = 0; i < n_nodes; ++i) {
+        if (fast[i] > 1) return fail(ctx, RN_EINVAL, "fast[%d] must be 0 or 1", i);
+        if (indeg[(size_t)i] == 0 || outdeg[(size_t)i] == 0)
+            return fail(ctx, RN_EINVAL, "node %d has no in-edge or no out-edge", i);
+    }
+    if (frozen) {
+        n->has_frozen = true;
+        n->frozen.assign(frozen, frozen + n->P);
+        n->frozen_val.assign(frozen_val, frozen_val + n->P);
+        for (int32_t j = 0; j < n->P; ++j) {
+            if (n->frozen[(size_t)j] > 1) return fail(ctx, RN_EINVAL, "frozen[%d] must be 0 or 1", j);
+            if (n->frozen[(size_t)j] && !in_domain(*n, j, n->frozen_val[(size_t)j]))
+                return fail(ctx, RN_EINVAL, "fixed parameter %d is outside its domain", j);
+            if (!n->frozen[(size_t)j]) n->frozen_val[(size_t)j] = 0;
+        }
+    } else {
+        n->frozen.assign((size_t)n->P, 0);
+        n->frozen_val.assign((size_t)n->P, 0);
+    }
+    build_layout(*n);
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    RN_CUDA(ctx, n->d_src.upload(n->src));
+    RN_CUDA(ctx, n->d_dst.upload(n->dst));
+    RN_CUDA(ctx, n->d_fast.upload(n->fast));
+    RN_CUDA(ctx, n->d_frozen.upload(n->frozen));
+    RN_CUDA(ctx, n->d_frozen_val.upload(n->frozen_val));
+    RN_CUDA(ctx, n->d_free.upload(n->free_list));
+    RN_CUDA(ctx, n->d_in_ptr.upload(n->in_ptr));
+    RN_CUDA(ctx, n->d_in_edges.upload(n->in_edges));
+    RN_CUDA(ctx, n->d_out_ptr.upload(n->out_ptr));
+    RN_CUDA(ctx, n->d_out_edges.upload(n->out_edges));
+    if (n->supported) {
+        RN_CUDA(ctx, n->d_edge_id.upload(n->edge_id));
+        RN_CUDA(ctx, n->d_edge_q2.upload(n->edge_q2));
+        RN_CUDA(ctx, n->d_edge_pos.upload(n->edge_pos));
+        RN_CUDA(ctx, n->d_node_q.upload(n->node_q));
+        RN_CUDA(ctx, n->d_q_node.upload(n->q_node));
+    }
+    *net_id = (int32_t)ctx->nets.size();
+    ctx->nets.push_back(std::move(n));
+    return RN_OK;
+}
+
+int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times,
+                       const uint8_t *init, const uint8_t *knockout, const uint8_t *ref,
+                       const uint8_t *observed)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Network *n = get_net(ctx, net);
+    if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
+    if (!init || !ref || !observed) return fail(ctx, RN_EINVAL, "NULL array");
+    if (n_cond < 1 || n_times < 1) return fail(ctx, RN_EINVAL, "n_cond and n_times must be >= 1");
+    if ((int64_t)n_times > 256)
+        return fail(ctx, RN_EINVAL, "n_times %d exceeds 256", n_times);
+    const int32_t N = n->N, C = n_cond, T = n_times;
+    const size_t ctn = (size_t)C * T * N;
+    for (size_t k = 0; k < (size_t)C * N; ++k) {
+        if (init[k] > 2) return fail(ctx, RN_EINVAL, "init value %d outside 0..2", init[k]);
+        if (knockout && knockout[k] > 1) return fail(ctx, RN_EINVAL, "knockout must be 0 or 1");
+    }
+    for (size_t k = 0; k < ctn; ++k) {
+        if (observed[k] > 1) return fail(ctx, RN_EINVAL, "observed must be 0 or 1");
+        if (observed[k] && ref[k] > 2) return fail(ctx, RN_EINVAL, "reference value outside 0..2");
+    }
+    // weight = observed * (|G| + 1), G from consecutive observed points (Section 2.3)
+    std::vector<uint8_t> W(ctn, 0);
+    int64_t max_score = 0;
+    for (int32_t c = 0; c < C; ++c)
+        for (int32_t t = 0; t < T; ++t)
+            for (int32_t i = 0; i < N; ++i) {
+                const size_t k = ((size_t)c * T + t) * N + i;
+                if (!observed[k]) continue;
+                int g = 0;
+                if (t > 0 && observed[k - N]) g = std::abs((int)ref[k] - (int)ref[k - N]);
+                W[k] = (uint8_t)(g + 1);
+                max_score += 2 * W[k];
+            }
+    n->C = C;
+    n->T = T;
+    n->max_score = max_score;
+    n->has_tc = true;
+    n->chains_valid = false;
+    if (!n->supported) return RN_OK;
+    const int npl = n->npl;
+    const int cg = C >= 2 ? 4 : 1;
+    const int G = (C + cg - 1) / cg;
+    int drest = 0;
+    for (int k = 1; k < npl; ++k) drest = std::max(drest, n->D[k]);
+    anneal_capacity(npl, n->D[0], drest, &n->d0, &n->d1);
+    // error table of an entry: byte b = W |b - R| for b = 0, 1, 2
+    std::vector<uint32_t> obs((size_t)C * T * 32 * npl, 0u);
+    // state codes: nibble c = initial state of condition g * cg + c; a node that
+    // never moves in a condition (padding, knocked out, condition beyond C)
+    // starts at 0 and has its bit k * cg + c set in out_bits
+    std::vector<uint16_t> init_code((size_t)G * 32 * npl, 0), out_bits((size_t)G * 32, 0);
+    for (int g = 0; g < G; ++g)
+        for (int q = 0; q < 32 * npl; ++q) {
+            const int i = n->q_node[(size_t)q];
+            const int lane = q / npl, slot = q % npl;
+            for (int c = 0; c < cg; ++c) {
+                const int cc = g * cg + c;
+                const bool out =
+                    i < 0 || cc >= C || (knockout && knockout[(size_t)cc * N + i]);
+                if (out) {
+                    out_bits[(size_t)g * 32 + lane] |= (uint16_t)(1u << (slot * cg + c));
+                    continue;
+                }
+                init_code[(size_t)g * 32 * npl + q] |=
+                    (uint16_t)(init[(size_t)cc * N + i] << (4 * c));
+            }
+        }
+    for (int32_t c = 0; c < C; ++c) {
+        for (int q = 0; q < 32 * npl; ++q) {
+            const int i = n->q_node[(size_t)q];
+            const int lane = q / npl, slot = q % npl;
+            if (i < 0) continue;
+            for (int32_t t = 0; t < T; ++t) {
+                const size_t k = ((size_t)c * T + t) * N + i;
+                const int w = W[k], r = ref[k];
+                uint32_t word = 0;
+                if (w)
+                    for (int b = 0; b < 3; ++b) word |= (uint32_t)(w * std::abs(b - r)) << (8 * b);
+                obs[(((size_t)c * T + t) * 32 + lane) * npl + slot] = word;
+            }
+        }
+    }
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    RN_CUDA(ctx, n->d_obs.upload(obs));
+    RN_CUDA(ctx, n->d_init_code.upload(init_code));
+    RN_CUDA(ctx, n->d_out_bits.upload(out_bits));
+    n->cg = cg;
+    n->G = G;
+    return RN_OK;
+}
+
+int rn_n_params(rn_ctx *ctx, int32_t net, int32_t *n_params)
+{
+    if (!ctx) return RN_EINVAL;
+    Network *n = get_net(ctx, net);
+    if (!n || !n_params) return fail(ctx, RN_EINVAL, "unknown network %d", net);
+    *n_params = n->P;
+    return RN_OK;
+}
+
+int rn_init_chains(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed, const int8_t *x0)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Network *n = get_net(ctx, net);
+    if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
+    if (!n->has_tc) return fail(ctx, RN_ESTATE, "network %d has no time course", net);
+    if (n_chains < 1) return fail(ctx, RN_EINVAL, "n_chains must be >= 1");
+    int rc = require_supported(ctx, *n);
+    if (rc) return rc;
+    if (x0)
+        for (int32_t c = 0; c < n_chains; ++c)
+            if ((rc = check_vector(ctx, *n, x0 + (size_t)c * n->P, c))) return rc;
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    n->chains_valid = false;
+    if ((rc = alloc_chains(ctx, *n, n_chains))) return rc;
+    n->seed = seed;
+    n->step = 0;
+    const DevChains ch = n->chains();
+    if (x0) {
+        if ((rc = upload_rows(ctx, *n, ch.x_cur, x0, n_chains))) return rc;
+        RN_CUDA(ctx, cudaMemcpyAsync(ch.x_best, ch.x_cur, (size_t)n_chains * n->pstride,
+                                     cudaMemcpyDeviceToDevice, ctx->stream));
+        RN_CUDA(ctx, cudaMemsetAsync(ch.cnt, 0, sizeof(int64_t) * 3 * (size_t)n_chains,
+                                     ctx->stream));
+    } else {
+        RN_CUDA(ctx, ctx->status.reserve((size_t)n_chains));
+        RN_CUDA(ctx, launch_init(n->dev(), ch, ctx->status.p, ctx->stream));
+        ctx->launches += 1;
+        std::vector<int32_t> st((size_t)n_chains);
+        RN_CUDA(ctx, cudaMemcpyAsync(st.data(), ctx->status.p, sizeof(int32_t) * st.size(),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+        RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int32_t c = 0; c < n_chains; ++c)
+            if (st[(size_t)c] != 0)
+                return fail(ctx, RN_ECONSTRAINT,
+                            "chain %d: the fixed parameters leave a node without a possible "
+                            "activating in-edge or nonzero out-edge", c);
+    }
+    if ((rc = evaluate_device_impl(ctx, *n, n_chains, ch.x_cur, n->pstride, ch.d_cur, ch.d_best,
+                                   nullptr)))
+        return rc;
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    n->chains_valid = true;
+    return RN_OK;
+}
+
+int rn_anneal(rn_ctx *ctx, const rn_schedule *s, int64_t sweeps)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    if (!s) return fail(ctx, RN_EINVAL, "schedule is NULL");
+    if (sweeps < 0) return fail(ctx, RN_EINVAL, "sweeps must be >= 0");
+    if (s->iters_per_level < 1) return fail(ctx, RN_EINVAL, "iters_per_level must be >= 1");
+    if (!(s->T0 > 0.0) || !(s->alpha > 0.0) || !std::isfinite(s->T0) || !std::isfinite(s->alpha))
+        return fail(ctx, RN_EINVAL, "T0 and alpha must be positive");
+    bool any = false;
+    for (auto &np : ctx->nets) any |= np->chains_valid;
+    if (!any) return fail(ctx, RN_ESTATE, "no network has chains (call rn_init_chains)");
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t iters = s->iters_per_level;
+    // at most this many threshold entries per launch segment
+    const size_t budget = (size_t)1 << 24;
+    for (auto &np : ctx->nets) {
+        Network &n = *np;
+        if (!n.chains_valid) continue;
+        const DevNet dn = n.dev();
+        const DevChains ch = n.chains();
+        int64_t g = n.step;
+        const int64_t g_end = n.step + sweeps;
+        while (g < g_end) {
+            // one segment: stop at the end of a level when levels end with a sync,
+            // and when the threshold tables would exceed the budget
+            int64_t seg_end = g_end;
+            if (s->global_sync) seg_end = std::min(seg_end, (g / iters + 1) * iters);
+            int64_t l0 = g / iters, l1 = (seg_end - 1) / iters;
+            DevSched sc{};
+            const SchedCache &cc = ctx->cache;
+            const bool cached = cc.valid && cc.T0 == s->T0 && cc.alpha == s->alpha &&
+                                cc.iters == iters && l0 >= cc.l0 && l1 <= cc.l1 &&
+                                cc.cap >= n.max_score;
+            if (cached) {
+                sc.level0 = cc.l0;
+                sc.thr_off = cc.off.p;
+                sc.thr_len = cc.len.p;
+                sc.thr = cc.thr.p;
+            } else {
+                std::vector<uint32_t> thr;
+                std::vector<int32_t> off, len;
+                int rc = build_thresholds(ctx, *s, l0, l1, n.max_score, thr, off, len);
+                if (rc) return rc;
+                while (thr.size() > budget && l1 > l0) {
+                    l1 = l0 + (l1 - l0) / 2;
+                    seg_end = std::min(seg_end, (l1 + 1) * iters);
+                    if ((rc = build_thresholds(ctx, *s, l0, l1, n.max_score, thr, off, len)))
+                        return rc;
+                }
+                if (thr.empty()) thr.push_back(0);
+                // the device tables may still be read by an earlier launch
+                RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+                RN_CUDA(ctx, ctx->thr.reserve(thr.size()));
+                RN_CUDA(ctx, ctx->thr_off.reserve(off.size()));
+                RN_CUDA(ctx, ctx->thr_len.reserve(len.size()));
+                RN_CUDA(ctx, cudaMemcpy(ctx->thr.p, thr.data(), thr.size() * sizeof(uint32_t),
+                                        cudaMemcpyHostToDevice));
+                RN_CUDA(ctx, cudaMemcpy(ctx->thr_off.p, off.data(), off.size() * sizeof(int32_t),
+                                        cudaMemcpyHostToDevice));
+                RN_CUDA(ctx, cudaMemcpy(ctx->thr_len.p, len.data(), len.size() * sizeof(int32_t),
+                                        cudaMemcpyHostToDevice));
+                sc.level0 = l0;
+                sc.thr_off = ctx->thr_off.p;
+                sc.thr_len = ctx->thr_len.p;
+                sc.thr = ctx->thr.p;
+            }
+            sc.g0 = g;
+            sc.g1 = seg_end;
+            sc.iters = iters;
+            sc.reset_to_best = s->reset_to_best;
+            cudaError_t e = launch_anneal(dn, n.d0, n.d1, ch, sc, ctx->sm_count, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "anneal kernel");
+            ctx->launches += 1;
+            if (s->global_sync && seg_end % iters == 0) {
+                e = launch_level_sync(ch, ctx->winner.p, ctx->stream);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "level sync kernels");
+                ctx->launches += 2;
+            }
+            g = seg_end;
+        }
+        n.step = g_end;
+    }
+    return RN_OK;
+}
+
+int rn_prepare_schedule(rn_ctx *ctx, const rn_schedule *s, int64_t total_steps)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    if (!s || total_steps < 1 || s->iters_per_level < 1)
+        return fail(ctx, RN_EINVAL, "bad schedule or step count");
+    if (!(s->T0 > 0.0) || !(s->alpha > 0.0) || !std::isfinite(s->T0) || !std::isfinite(s->alpha))
+        return fail(ctx, RN_EINVAL, "T0 and alpha must be positive");
+    int64_t cap = 1;
+    for (auto &np : ctx->nets) cap = std::max(cap, np->max_score);
+    const int64_t l1 = (total_steps - 1) / s->iters_per_level;
+    std::vector<uint32_t> thr;
+    std::vector<int32_t> off, len;
+    int rc = build_thresholds(ctx, *s, 0, l1, cap, thr, off, len);
+    if (rc) return rc;
+    if (thr.empty()) thr.push_back(0);
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    SchedCache &cc = ctx->cache;
+    cc.valid = false;
+    RN_CUDA(ctx, cc.thr.alloc(thr.size()));
+    RN_CUDA(ctx, cc.off.alloc(off.size()));
+    RN_CUDA(ctx, cc.len.alloc(len.size()));
+    RN_CUDA(ctx, cudaMemcpy(cc.thr.p, thr.data(), thr.size() * sizeof(uint32_t),
+                            cudaMemcpyHostToDevice));
+    RN_CUDA(ctx, cudaMemcpy(cc.off.p, off.data(), off.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice));
+    RN_CUDA(ctx, cudaMemcpy(cc.len.p, len.data(), len.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice));
+    cc.T0 = s->T0;
+    cc.alpha = s->alpha;
+    cc.iters = s->iters_per_level;
+    cc.l0 = 0;
+    cc.l1 = l1;
+    cc.cap = cap;
+    cc.valid = true;
+    return RN_OK;
+}
+
+int rn_launch_count(rn_ctx *ctx, int64_t *count)
+{
+    if (!ctx || !count) return RN_EINVAL;
+    *count = ctx->launches;
+    return RN_OK;
+}
+
+int rn_get_best(rn_ctx *ctx, int32_t net, int8_t *x, int32_t *score, int32_t *chain)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Network *n = get_net(ctx, net);
+    if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
+    if (!n->chains_valid) return fail(ctx, RN_ESTATE, "network %d has no chains", net);
+    if (!score) return fail(ctx, RN_EINVAL, "score is NULL");
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const DevChains ch = n->chains();
+    std::vector<int32_t> d((size_t)ch.n);
+    RN_CUDA(ctx, cudaMemcpyAsync(d.data(), ch.d_best, sizeof(int32_t) * d.size(),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int32_t b = 0;
+    for (int32_t c = 1; c < ch.n; ++c)
+        if (d[(size_t)c] < d[(size_t)b]) b = c;
+    *score = d[(size_t)b];
+    if (chain) *chain = b;
+    if (x) {
+        RN_CUDA(ctx, cudaMemcpyAsync(x, ch.x_best + (size_t)b * ch.pstride, (size_t)n->P,
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+        RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return RN_OK;
+}
+
+int rn_evaluate(rn_ctx *ctx, int32_t net, int32_t count, const int8_t *x, int32_t *score,
+                uint8_t *traj)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Network *n = get_net(ctx, net);
+    if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
+    if (!n->has_tc) return fail(ctx, RN_ESTATE, "network %d has no time course", net);
+    if (count < 0 || (count > 0 && (!x || !score))) return fail(ctx, RN_EINVAL, "bad arguments");
+    int rc = require_supported(ctx, *n);
+    if (rc) return rc;
+    if (count == 0) return RN_OK;
+    for (int32_t v = 0; v < count; ++v)
+        for (int32_t j = 0; j < n->P; ++j)
+            if (!in_domain(*n, j, x[(size_t)v * n->P + j]))
+                return fail(ctx, RN_EINVAL, "vector %d: parameter %d is outside its domain", v, j);
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const size_t xs = (size_t)count * n->P;
+    const size_t ts = (size_t)count * n->C * n->T * n->N;
+    RN_CUDA(ctx, ctx->xbuf.reserve(xs));
+    RN_CUDA(ctx, ctx->sbuf.reserve((size_t)count));
+    if (traj) RN_CUDA(ctx, ctx->tbuf.reserve(ts));
+    RN_CUDA(ctx, cudaMemcpyAsync(ctx->xbuf.p, x, xs, cudaMemcpyHostToDevice, ctx->stream));
+    if ((rc = evaluate_device_impl(ctx, *n, count, ctx->xbuf.p, n->P, ctx->sbuf.p, nullptr,
+                                   traj ? ctx->tbuf.p : nullptr)))
+        return rc;
+    RN_CUDA(ctx, cudaMemcpyAsync(score, ctx->sbuf.p, sizeof(int32_t) * (size_t)count,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    if (traj)
+        RN_CUDA(ctx, cudaMemcpyAsync(traj, ctx->tbuf.p, ts, cudaMemcpyDeviceToHost, ctx->stream));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RN_OK;
+}
+
+int rn_evaluate_device(rn_ctx *ctx, int32_t net, int32_t count, const int8_t *x_dev,
+                       int32_t *score_dev, uint8_t *traj_dev)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Network *n = get_net(ctx, net);
+    if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
+    if (!n->has_tc) return fail(ctx, RN_ESTATE, "network %d has no time course", net);
+    if (count < 0 || (count > 0 && (!x_dev || !score_dev)))
+        return fail(ctx, RN_EINVAL, "bad arguments");
+    int rc = require_supported(ctx, *n);
+    if (rc) return rc;
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    return evaluate_device_impl(ctx, *n, count, x_dev, n->P, score_dev, nullptr, traj_dev);
+}
+
+int rn_get_chain_state(rn_ctx *ctx, int32_t net, int8_t *x_cur, int32_t *d_cur, int8_t *x_best,
+                       int32_t *d_best, int64_t *counters, int64_t *step)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Network *n = get_net(ctx, net);
+    if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
+    if (!n->chains_valid) return fail(ctx, RN_ESTATE, "network %d has no chains", net);
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const DevChains ch = n->chains();
+    int rc;
+    if (x_cur && (rc = download_rows(ctx, *n, x_cur, ch.x_cur))) return rc;
+    if (x_best && (rc = download_rows(ctx, *n, x_best, ch.x_best))) return rc;
+    if (d_cur)
+        RN_CUDA(ctx, cudaMemcpyAsync(d_cur, ch.d_cur, sizeof(int32_t) * (size_t)ch.n,
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+    if (d_best)
+        RN_CUDA(ctx, cudaMemcpyAsync(d_best, ch.d_best, sizeof(int32_t) * (size_t)ch.n,
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+    if (counters)
+        RN_CUDA(ctx, cudaMemcpyAsync(counters, ch.cnt, sizeof(int64_t) * 3 * (size_t)ch.n,
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (step) *step = n->step;
+    return RN_OK;
+}
+
+int rn_set_chain_state(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed,
+                       const int8_t *x_cur, const int32_t *d_cur, const int8_t *x_best,
+                       const int32_t *d_best, const int64_t *counters, int64_t step)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Network *n = get_net(ctx, net);
+    if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
+    if (!n->has_tc) return fail(ctx, RN_ESTATE, "network %d has no time course", net);
+    if (n_chains < 1 || !x_cur || !d_cur || !x_best || !d_best || !counters || step < 0)
+        return fail(ctx, RN_EINVAL, "bad arguments");
+    int rc = require_supported(ctx, *n);
+    if (rc) return rc;
+    for (int32_t c = 0; c < n_chains; ++c) {
+        if ((rc = check_vector(ctx, *n, x_cur + (size_t)c * n->P, c))) return rc;
+        if ((rc = check_vector(ctx, *n, x_best + (size_t)c * n->P, c))) return rc;
+    }
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    n->chains_valid = false;
+    if ((rc = alloc_chains(ctx, *n, n_chains))) return rc;
+    const DevChains ch = n->chains();
+    if ((rc = upload_rows(ctx, *n, ch.x_cur, x_cur, n_chains))) return rc;
+    if ((rc = upload_rows(ctx, *n, ch.x_best, x_best, n_chains))) return rc;
+    RN_CUDA(ctx, cudaMemcpyAsync(ch.d_cur, d_cur, sizeof(int32_t) * (size_t)n_chains,
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    RN_CUDA(ctx, cudaMemcpyAsync(ch.d_best, d_best, sizeof(int32_t) * (size_t)n_chains,
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    RN_CUDA(ctx, cudaMemcpyAsync(ch.cnt, counters, sizeof(int64_t) * 3 * (size_t)n_chains,
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    n->seed = seed;
+    n->step = step;
+    n->chains_valid = true;
+    return RN_OK;
+}
+
+int rn_synchronize(rn_ctx *ctx)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RN_OK;
+}
+
+}  // extern "C"

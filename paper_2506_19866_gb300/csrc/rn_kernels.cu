@@ -1,0 +1,203 @@
+// rn_kernels.cu -- initialisation, level-sync and evaluate kernels, and the
+// dispatch of every launch to its compiled layout.
+//
+//   init_kernel      the seeded sample-and-repair x0 of each chain
+//   argmin_kernel / broadcast_kernel
+//                    the serial argmin + broadcast that ends a level of Table 1
+//   evaluate_kernel  (rn_kernels.cuh) instantiated with register capacity 16
+#include "rn_kernels.cuh"
+
+namespace rn {
+
+// Seeded sample-and-repair x0 (the paper draws x0 with a constraint solver),
+// one thread per chain: uniform draws, then an activating in-edge for every
+// node without one, then a nonzero out-edge for every node without one.
+__global__ void init_kernel(DevNet net, DevChains ch, int32_t *status)
+{
+    const int chain = blockIdx.x * blockDim.x + threadIdx.x;
+    if (chain >= ch.n) return;
+    int8_t *x = ch.x_cur + (size_t)chain * ch.pstride;
+    const int E = net.E, N = net.N, P = net.P;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    for (int j = 0; j < P; ++j) {
+        if ((j & 3) == 0) r = philox(ch.seed, (uint32_t)(j >> 2), 0u, (uint32_t)chain, 1u);
+        if (net.frozen && net.frozen[j]) {
+            x[j] = net.frozen_val[j];
+            continue;
+        }
+        int kind, idx;
+        if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
+        else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
+        int8_t vals[6];
+        const int nd = domain(kind, kind == 3 && net.fast[idx], vals);
+        const uint32_t word = (j & 3) == 0 ? r.x : (j & 3) == 1 ? r.y : (j & 3) == 2 ? r.z : r.w;
+        x[j] = vals[pick(word, (uint32_t)nd)];
+    }
+    for (int j = P; j < ch.pstride; ++j) x[j] = 0;
+    int ok = 1;
+    for (int i = 0; i < N && ok; ++i) {
+        int has = 0, n_cand = 0;
+        for (int k = net.in_ptr[i]; k < net.in_ptr[i + 1]; ++k) {
+            const int e = net.in_edges[k];
+            has |= (x[e] != 0) && (x[E + e] == 1);
+            const bool p_ok = !(net.frozen && net.frozen[E + e]) || net.frozen_val[E + e] == 1;
+            const bool w_ok = !(net.frozen && net.frozen[e]) || net.frozen_val[e] != 0;
+            n_cand += p_ok && w_ok;
+        }
+        if (has) continue;
+        if (n_cand == 0) { ok = 0; break; }
+        const uint4 q = philox(ch.seed, (uint32_t)i, 0u, (uint32_t)chain, 3u);
+        int want = (int)pick(q.x, (uint32_t)n_cand);
+        for (int k = net.in_ptr[i]; k < net.in_ptr[i + 1]; ++k) {
+            const int e = net.in_edges[k];
+            const bool p_ok = !(net.frozen && net.frozen[E + e]) || net.frozen_val[E + e] == 1;
+            const bool w_ok = !(net.frozen && net.frozen[e]) || net.frozen_val[e] != 0;
+            if (!(p_ok && w_ok)) continue;
+            if (want-- != 0) continue;
+            if (!(net.frozen && net.frozen[E + e])) x[E + e] = 1;
+            if (!(net.frozen && net.frozen[e])) x[e] = (int8_t)(1 + (q.y & 1u));
+            break;
+        }
+    }
+    for (int i = 0; i < N && ok; ++i) {
+        int has = 0, n_cand = 0;
+        for (int k = net.out_ptr[i]; k < net.out_ptr[i + 1]; ++k) {
+            const int e = net.out_edges[k];
+            has |= x[e] != 0;
+            n_cand += !(net.frozen && net.frozen[e]);
+        }
+        if (has) continue;
+        if (n_cand == 0) { ok = 0; break; }
+        const uint4 q = philox(ch.seed, (uint32_t)i, 1u, (uint32_t)chain, 3u);
+        int want = (int)pick(q.x, (uint32_t)n_cand);
+        for (int k = net.out_ptr[i]; k < net.out_ptr[i + 1]; ++k) {
+            const int e = net.out_edges[k];
+            if (net.frozen && net.frozen[e]) continue;
+            if (want-- != 0) continue;
+            x[e] = (int8_t)(1 + (q.y & 1u));
+            break;
+        }
+    }
+    int8_t *xb = ch.x_best + (size_t)chain * ch.pstride;
+    for (int j = 0; j < ch.pstride; ++j) xb[j] = x[j];
+    ch.cnt[3 * (size_t)chain + 0] = 0;
+    ch.cnt[3 * (size_t)chain + 1] = 0;
+    ch.cnt[3 * (size_t)chain + 2] = 0;
+    status[chain] = ok ? 0 : -2;
+}
+
+// Table 1, end of a level: the lowest delta_best over the chains (lowest chain
+// index on ties).  One block.
+__global__ void argmin_kernel(const int32_t *__restrict__ d_best, int32_t n, int32_t *out)
+{
+    __shared__ unsigned long long best[32];
+    unsigned long long b = ~0ull;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const unsigned long long key =
+            ((unsigned long long)(uint32_t)d_best[k] << 32) | (uint32_t)k;
+        b = min(b, key);
+    }
+    for (int o = 16; o > 0; o >>= 1) b = min(b, __shfl_xor_sync(kFull, b, o));
+    if ((threadIdx.x & 31) == 0) best[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        b = threadIdx.x < (blockDim.x >> 5) ? best[threadIdx.x] : ~0ull;
+        for (int o = 16; o > 0; o >>= 1) b = min(b, __shfl_xor_sync(kFull, b, o));
+        if (threadIdx.x == 0) *out = (int32_t)(uint32_t)b;
+    }
+}
+
+// ... and its broadcast into every chain's x_best.
+__global__ void broadcast_kernel(DevChains ch, const int32_t *win)
+{
+    const int w = *win;
+    const int rows_per_block = blockDim.x / 32;
+    const int lane = threadIdx.x & 31;
+    const int chain = blockIdx.x * rows_per_block + (threadIdx.x >> 5);
+    if (chain >= ch.n || chain == w) return;
+    warp_copy16(ch.x_best + (size_t)chain * ch.pstride, ch.x_best + (size_t)w * ch.pstride,
+                ch.pstride, lane);
+    if (lane == 0) ch.d_best[chain] = ch.d_best[w];
+}
+
+template <int NPL, int CG>
+static cudaError_t launch_eval_t(const DevNet &net, const int8_t *X, int64_t xstride, int32_t n,
+                                 int32_t *score, int32_t *score2, uint8_t *traj, int grid,
+                                 cudaStream_t st)
+{
+    evaluate_kernel<NPL, CG, 16, 16><<<grid, 128, 4 * 256, st>>>(net, X, xstride, n, score,
+                                                                   score2, traj);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_evaluate(const DevNet &net, const int8_t *X, int64_t xstride, int32_t n,
+                            int32_t *score, int32_t *score2, uint8_t *traj, int sm_count,
+                            cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    int grid = (n + 3) / 4;
+    if (grid > sm_count * 16) grid = sm_count * 16;
+#define RN_EV(NPL_, CG_)                                                                  \
+    if (net.npl == NPL_ && net.cg == CG_)                                                 \
+        return launch_eval_t<NPL_, CG_>(net, X, xstride, n, score, score2, traj, grid, st);
+    RN_EV(1, 1) RN_EV(1, 4) RN_EV(2, 1) RN_EV(2, 4) RN_EV(4, 1) RN_EV(4, 4)
+#undef RN_EV
+    return cudaErrorNotSupported;
+}
+
+bool anneal_layout_supported(int npl, int cg, int d0, int d1)
+{
+    if (cg != 1 && cg != 4) return false;
+    if (npl == 1) return d0 == 4 || d0 == 8 || d0 == 12 || d0 == 16;
+    if (npl != 2 && npl != 4) return false;
+    static const int pairs[][2] = {{4, 4}, {8, 4}, {8, 8}, {12, 8}, {16, 8}, {16, 16}};
+    for (auto &p : pairs)
+        if (p[0] == d0 && p[1] == d1) return true;
+    return false;
+}
+
+void anneal_capacity(int npl, int D0, int Drest, int *d0, int *d1)
+{
+    auto up = [](int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 12 ? 12 : d <= 16 ? 16 : -1; };
+    *d0 = up(D0);
+    if (npl == 1) {
+        *d1 = 1;
+        return;
+    }
+    static const int pairs[][2] = {{4, 4}, {8, 4}, {8, 8}, {12, 8}, {16, 8}, {16, 16}};
+    *d1 = -1;
+    for (auto &p : pairs)   // smallest compiled pair covering (D0, Drest)
+        if (p[0] >= D0 && p[1] >= Drest) {
+            *d0 = p[0];
+            *d1 = p[1];
+            return;
+        }
+    *d0 = -1;
+}
+
+cudaError_t launch_anneal(const DevNet &net, int d0, int d1, const DevChains &ch,
+                          const DevSched &sc, int sm_count, cudaStream_t st)
+{
+    if (ch.n <= 0 || sc.g1 <= sc.g0) return cudaSuccess;
+    switch (net.npl) {
+    case 1: return launch_anneal_npl1(net, d0, d1, ch, sc, sm_count, st);
+    case 2: return launch_anneal_npl2(net, d0, d1, ch, sc, sm_count, st);
+    case 4: return launch_anneal_npl4(net, d0, d1, ch, sc, sm_count, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t launch_init(const DevNet &net, const DevChains &ch, int32_t *status, cudaStream_t st)
+{
+    init_kernel<<<(ch.n + 127) / 128, 128, 0, st>>>(net, ch, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_sync(const DevChains &ch, int32_t *winner, cudaStream_t st)
+{
+    argmin_kernel<<<1, 1024, 0, st>>>(ch.d_best, ch.n, winner);
+    broadcast_kernel<<<(ch.n + 7) / 8, 256, 0, st>>>(ch, winner);
+    return cudaGetLastError();
+}
+
+}  // namespace rn

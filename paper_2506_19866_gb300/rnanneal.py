@@ -1,0 +1,212 @@
+"""Python binding of librnanneal.so (include/rnanneal.h), argument marshalling only.
+
+Every function has the name of the C entry point it calls and raises
+RNError on a negative return code.  Host arrays are numpy arrays; device
+arrays (rn_evaluate_device) are torch CUDA tensors or raw device addresses.
+There is no fallback: if the library is missing, loading fails with an
+ImportError naming the build step.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librnanneal.so")
+
+RN_OK, RN_EINVAL, RN_ECONSTRAINT, RN_ENOMEM, RN_ECUDA, RN_ETIMEOUT, RN_ESTATE, \
+    RN_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+_NAMES = {-1: "RN_EINVAL", -2: "RN_ECONSTRAINT", -3: "RN_ENOMEM", -4: "RN_ECUDA",
+          -5: "RN_ETIMEOUT", -6: "RN_ESTATE", -7: "RN_EUNSUPPORTED"}
+
+# every entry point the header declares, with its ctypes signature
+_c_int, _c_i32, _c_i64, _c_u64, _vp = (ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
+                                       ctypes.c_uint64, ctypes.c_void_p)
+
+
+class rn_schedule(ctypes.Structure):
+    _fields_ = [("T0", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("iters_per_level", ctypes.c_int64), ("reset_to_best", ctypes.c_int32),
+                ("global_sync", ctypes.c_int32)]
+
+
+SIGNATURES = {
+    "rn_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _vp]),
+    "rn_destroy": (_c_int, [_vp]),
+    "rn_last_error": (ctypes.c_char_p, [_vp]),
+    "rn_load_network": (_c_int, [_vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "rn_load_timecourse": (_c_int, [_vp, _c_i32, _c_i32, _c_i32, _vp, _vp, _vp, _vp]),
+    "rn_init_chains": (_c_int, [_vp, _c_i32, _c_i32, _c_u64, _vp]),
+    "rn_anneal": (_c_int, [_vp, ctypes.POINTER(rn_schedule), _c_i64]),
+    "rn_get_best": (_c_int, [_vp, _c_i32, _vp, _vp, _vp]),
+    "rn_evaluate": (_c_int, [_vp, _c_i32, _c_i32, _vp, _vp, _vp]),
+    "rn_evaluate_device": (_c_int, [_vp, _c_i32, _c_i32, _vp, _vp, _vp]),
+    "rn_n_params": (_c_int, [_vp, _c_i32, _vp]),
+    "rn_get_chain_state": (_c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "rn_set_chain_state": (_c_int, [_vp, _c_i32, _c_i32, _c_u64, _vp, _vp, _vp, _vp, _vp,
+                                    _c_i64]),
+    "rn_prepare_schedule": (_c_int, [_vp, ctypes.POINTER(rn_schedule), _c_i64]),
+    "rn_launch_count": (_c_int, [_vp, _vp]),
+    "rn_synchronize": (_c_int, [_vp]),
+}
+
+
+class RNError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load librnanneal.so and declare its signatures."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: run __graft_entry__.build() (or "
+                              f"python -m paper_2506_19866_gb300.build) first")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(ctx, rc):
+    if rc != RN_OK:
+        msg = load_library().rn_last_error(ctx)
+        raise RNError(rc, msg.decode() if msg else "")
+
+
+def _arr(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _dev(t):
+    if t is None:
+        return None
+    return int(t) if isinstance(t, int) else int(t.data_ptr())
+
+
+def rn_create(device: int = 0, stream=None):
+    h = _vp()
+    s = None if stream is None else int(stream)
+    _check(None, load_library().rn_create(ctypes.byref(h), int(device), s))
+    return h.value
+
+
+def rn_destroy(ctx):
+    load_library().rn_destroy(ctx)
+
+
+def rn_last_error(ctx):
+    return load_library().rn_last_error(ctx).decode()
+
+
+def rn_load_network(ctx, src, dst, fast, frozen=None, frozen_val=None):
+    src, dst = _arr(src, np.int32), _arr(dst, np.int32)
+    fast = _arr(fast, np.uint8)
+    frozen, frozen_val = _arr(frozen, np.uint8), _arr(frozen_val, np.int8)
+    out = ctypes.c_int32(-1)
+    _check(ctx, load_library().rn_load_network(ctx, fast.size, src.size, _p(src), _p(dst),
+                                               _p(fast), _p(frozen), _p(frozen_val),
+                                               ctypes.byref(out)))
+    return out.value
+
+
+def rn_load_timecourse(ctx, net, init, ref, observed, knockout=None):
+    init, ref, observed = _arr(init, np.uint8), _arr(ref, np.uint8), _arr(observed, np.uint8)
+    knockout = _arr(knockout, np.uint8)
+    C, T = ref.shape[0], ref.shape[1]
+    _check(ctx, load_library().rn_load_timecourse(ctx, int(net), C, T, _p(init), _p(knockout),
+                                                  _p(ref), _p(observed)))
+
+
+def rn_init_chains(ctx, net, n_chains, seed, x0=None):
+    x0 = _arr(x0, np.int8)
+    _check(ctx, load_library().rn_init_chains(ctx, int(net), int(n_chains), int(seed), _p(x0)))
+
+
+def schedule(T0, alpha, iters_per_level=1, reset_to_best=False, global_sync=False):
+    return rn_schedule(float(T0), float(alpha), int(iters_per_level), int(bool(reset_to_best)),
+                       int(bool(global_sync)))
+
+
+def rn_anneal(ctx, sched: rn_schedule, sweeps):
+    _check(ctx, load_library().rn_anneal(ctx, ctypes.byref(sched), int(sweeps)))
+
+
+def rn_n_params(ctx, net):
+    out = ctypes.c_int32(0)
+    _check(ctx, load_library().rn_n_params(ctx, int(net), ctypes.byref(out)))
+    return out.value
+
+
+def rn_get_best(ctx, net):
+    P = rn_n_params(ctx, net)
+    x = np.zeros(P, dtype=np.int8)
+    score, chain = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(ctx, load_library().rn_get_best(ctx, int(net), _p(x), ctypes.byref(score),
+                                           ctypes.byref(chain)))
+    return x, score.value, chain.value
+
+
+def rn_evaluate(ctx, net, x, traj_shape=None):
+    """x: [n][P] int8.  traj_shape (C, T, N) requests trajectories."""
+    x = _arr(np.atleast_2d(x), np.int8)
+    n = x.shape[0]
+    score = np.zeros(n, dtype=np.int32)
+    traj = None if traj_shape is None else np.zeros((n, *traj_shape), dtype=np.uint8)
+    _check(ctx, load_library().rn_evaluate(ctx, int(net), n, _p(x), _p(score), _p(traj)))
+    return score if traj is None else (score, traj)
+
+
+def rn_evaluate_device(ctx, net, n, x_dev, score_dev, traj_dev=None):
+    _check(ctx, load_library().rn_evaluate_device(ctx, int(net), int(n), _dev(x_dev),
+                                                  _dev(score_dev), _dev(traj_dev)))
+
+
+def rn_get_chain_state(ctx, net, n_chains):
+    P = rn_n_params(ctx, net)
+    st = dict(x_cur=np.zeros((n_chains, P), np.int8), d_cur=np.zeros(n_chains, np.int32),
+              x_best=np.zeros((n_chains, P), np.int8), d_best=np.zeros(n_chains, np.int32),
+              counters=np.zeros((n_chains, 3), np.int64))
+    step = ctypes.c_int64(0)
+    _check(ctx, load_library().rn_get_chain_state(ctx, int(net), _p(st["x_cur"]), _p(st["d_cur"]),
+                                                  _p(st["x_best"]), _p(st["d_best"]),
+                                                  _p(st["counters"]), ctypes.byref(step)))
+    st["step"] = step.value
+    return st
+
+
+def rn_set_chain_state(ctx, net, seed, st):
+    xc, xb = _arr(st["x_cur"], np.int8), _arr(st["x_best"], np.int8)
+    dc, db = _arr(st["d_cur"], np.int32), _arr(st["d_best"], np.int32)
+    cnt = _arr(st["counters"], np.int64)
+    _check(ctx, load_library().rn_set_chain_state(ctx, int(net), xc.shape[0], int(seed), _p(xc),
+                                                  _p(dc), _p(xb), _p(db), _p(cnt),
+                                                  int(st["step"])))
+
+
+def rn_synchronize(ctx):
+    _check(ctx, load_library().rn_synchronize(ctx))
+
+
+def rn_prepare_schedule(ctx, sched: rn_schedule, total_steps):
+    _check(ctx, load_library().rn_prepare_schedule(ctx, ctypes.byref(sched), int(total_steps)))
+
+
+def rn_launch_count(ctx):
+    out = ctypes.c_int64(0)
+    _check(ctx, load_library().rn_launch_count(ctx, ctypes.byref(out)))
+    return out.value

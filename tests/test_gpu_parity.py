@@ -1,0 +1,240 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Scores, trajectories, initial vectors and whole annealing trajectories
+(x_cur, x_best, objective values and counters of every compared chain) must be
+identical: the method is integer, and both sides draw the same Philox words.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2506_19866_gb300 import rnanneal as R
+from paper_2506_19866_gb300 import synth
+from tests.gpu_util import Problem, random_vectors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2506_19866_gb300 import build
+    build.build()
+
+
+@pytest.fixture
+def ctx(built):
+    # one context per test: rn_anneal advances every network of a context
+    h = R.rn_create(0)
+    yield h
+    R.rn_destroy(h)
+
+
+def _eval_parity(p, X):
+    score, traj = R.rn_evaluate(p.ctx, p.id, X, traj_shape=p.shape)
+    for k in range(X.shape[0]):
+        y, t = O.objective(p.net, p.tc, X[k], return_traj=True)
+        np.testing.assert_array_equal(traj[k], t, err_msg=f"vector {k}")
+        assert score[k] == y, f"vector {k}"
+
+
+@pytest.mark.parametrize("name", synth.WORKLOADS)
+def test_evaluate_workloads(ctx, name):
+    p = Problem(synth.make(name), ctx)
+    X = np.concatenate([p.xs[None], O.init_chains(p.net, 5, 8), random_vectors(p.net, 8, 1)])
+    _eval_parity(p, X)
+    if p.w.noise_frac == 0:
+        assert R.rn_evaluate(ctx, p.id, p.xs)[0] == 0
+
+
+@pytest.mark.parametrize("n_nodes", [2, 3, 5, 31, 32, 33, 63, 64, 65, 97, 127, 128])
+def test_evaluate_sizes(ctx, n_nodes):
+    # word and slot boundaries of the lane layout, 1-4 nodes per lane
+    w = synth.random_network(100 + n_nodes, n_nodes, lam=3.0, cap=min(9, n_nodes - 1),
+                             n_cond=3, n_times=9, obs_frac=0.4)
+    p = Problem(w, ctx)
+    _eval_parity(p, random_vectors(p.net, 12, n_nodes))
+
+
+@pytest.mark.parametrize("T", [1, 2, 33])
+def test_evaluate_time_lengths(ctx, T):
+    w = synth.random_network(7, 40, lam=4.0, cap=12, n_cond=2, n_times=T, obs_frac=0.6)
+    p = Problem(w, ctx)
+    _eval_parity(p, random_vectors(p.net, 6, T))
+
+
+def test_evaluate_high_degree(ctx):
+    # in-degree up to 16 (the largest compiled slot capacity)
+    w = synth.random_network(9, 60, lam=10.0, cap=16, n_cond=2, n_times=12, obs_frac=0.5)
+    p = Problem(w, ctx)
+    assert np.bincount(w.dst).max() > 12
+    _eval_parity(p, random_vectors(p.net, 8, 2))
+
+
+def test_evaluate_device_entry(ctx):
+    import torch
+    p = Problem(synth.make("n120_c8_t21"), ctx)
+    X = O.init_chains(p.net, 3, 33)
+    xd = torch.from_numpy(X).cuda()
+    sd = torch.zeros(33, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    R.rn_evaluate_device(ctx, p.id, 33, xd, sd)
+    R.rn_synchronize(ctx)
+    expect = [O.objective(p.net, p.tc, x) for x in X]
+    np.testing.assert_array_equal(sd.cpu().numpy(), expect)
+
+
+@pytest.mark.parametrize("name", ["n15_c3_t11", "n120_c8_t21", "mtb_63n_178e"])
+def test_init_chains(ctx, name):
+    p = Problem(synth.make(name), ctx)
+    n = 64
+    R.rn_init_chains(ctx, p.id, n, 12345)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    X = O.init_chains(p.net, 12345, n)
+    np.testing.assert_array_equal(st["x_cur"], X)
+    np.testing.assert_array_equal(st["x_best"], X)
+    d = np.array([O.objective(p.net, p.tc, x) for x in X])
+    np.testing.assert_array_equal(st["d_cur"], d)
+    np.testing.assert_array_equal(st["d_best"], d)
+    assert st["step"] == 0 and not st["counters"].any()
+
+
+def _oracle_run(p, seed, n_chains, sched, g0, sweeps, ids=None):
+    ids = list(range(n_chains)) if ids is None else list(ids)
+    ch = O.start_chains(p.net, p.tc, seed, len(ids), chain_ids=ids)
+    O.anneal(p.net, p.tc, sched, seed, ch, g0, sweeps, chain_ids=None if sched.global_sync else ids)
+    return ch
+
+
+def _compare(st, ch, ids):
+    np.testing.assert_array_equal(st["x_cur"][ids], ch.x_cur)
+    np.testing.assert_array_equal(st["x_best"][ids], ch.x_best)
+    np.testing.assert_array_equal(st["d_cur"][ids], ch.d_cur)
+    np.testing.assert_array_equal(st["d_best"][ids], ch.d_best)
+    np.testing.assert_array_equal(st["counters"][ids, 0], ch.n_accept)
+    np.testing.assert_array_equal(st["counters"][ids, 1], ch.n_uphill)
+    np.testing.assert_array_equal(st["counters"][ids, 2], ch.n_null)
+
+
+def test_anneal_small_all_chains(ctx):
+    # the 15-node configuration: 64 chains, T0 = 10, alpha = 0.995, every chain compared
+    w = synth.make("n15_c3_t11")
+    p = Problem(w, ctx)
+    R.rn_init_chains(ctx, p.id, w.n_chains, w.chain_seed)
+    sched = R.schedule(w.T0, w.alpha)
+    R.rn_anneal(ctx, sched, 300)
+    R.rn_anneal(ctx, sched, 200)
+    st = R.rn_get_chain_state(ctx, p.id, w.n_chains)
+    assert st["step"] == 500
+    ch = _oracle_run(p, w.chain_seed, w.n_chains, O.Schedule(w.T0, w.alpha), 0, 500)
+    _compare(st, ch, list(range(w.n_chains)))
+    x, score, chain = R.rn_get_best(ctx, p.id)
+    assert score == int(ch.d_best.min()) and chain == int(np.argmin(ch.d_best))
+    np.testing.assert_array_equal(x, ch.x_best[chain])
+
+
+def test_anneal_large_subset(ctx):
+    # the 120-node configuration at its full chain count (4096), 16 chains compared
+    w = synth.make("n120_c8_t21")
+    p = Problem(w, ctx)
+    R.rn_init_chains(ctx, p.id, w.n_chains, w.chain_seed)
+    sched = R.schedule(w.T0, w.alpha)
+    R.rn_anneal(ctx, sched, 60)
+    st = R.rn_get_chain_state(ctx, p.id, w.n_chains)
+    ids = [0, 1, 2, 3, 151, 152, 600, 1023, 1024, 2047, 2048, 3000, 4000, 4093, 4094, 4095]
+    ch = _oracle_run(p, w.chain_seed, w.n_chains, O.Schedule(w.T0, w.alpha), 0, 60, ids)
+    _compare(st, ch, ids)
+    # every chain: the stored objective is the objective of the stored vector
+    sample = np.arange(0, w.n_chains, 97)
+    y = R.rn_evaluate(ctx, p.id, st["x_cur"][sample])
+    np.testing.assert_array_equal(y, st["d_cur"][sample])
+    assert (st["d_best"] <= st["d_cur"]).all()
+
+
+def test_anneal_paper_mode(ctx):
+    # Table 1 with levels: reset to x_best and a global argmin at each level end
+    w = synth.make("hpg_9n_25e")
+    p = Problem(w, ctx)
+    n = 40
+    R.rn_init_chains(ctx, p.id, n, 77)
+    sched = R.schedule(50.0, 0.9, iters_per_level=7, reset_to_best=True, global_sync=True)
+    R.rn_anneal(ctx, sched, 25)
+    R.rn_anneal(ctx, sched, 24)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    ch = _oracle_run(p, 77, n, O.Schedule(50.0, 0.9, 7, True, True), 0, 49)
+    _compare(st, ch, list(range(n)))
+
+
+def test_checkpoint_resume(ctx):
+    w = synth.make("mtb_63n_178e")
+    p = Problem(w, ctx)
+    n = 96
+    sched = R.schedule(5.0, 0.99)
+    R.rn_init_chains(ctx, p.id, n, 9)
+    R.rn_anneal(ctx, sched, 40)
+    saved = R.rn_get_chain_state(ctx, p.id, n)
+    R.rn_anneal(ctx, sched, 40)
+    straight = R.rn_get_chain_state(ctx, p.id, n)
+    ctx2 = R.rn_create(0)
+    try:
+        q = Problem(w, ctx2)
+        R.rn_set_chain_state(ctx2, q.id, 9, saved)
+        R.rn_anneal(ctx2, sched, 40)
+        resumed = R.rn_get_chain_state(ctx2, q.id, n)
+    finally:
+        R.rn_destroy(ctx2)
+    for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"):
+        np.testing.assert_array_equal(resumed[k], straight[k])
+    assert resumed["step"] == straight["step"] == 80
+
+
+def test_frozen_parameters(ctx):
+    w = synth.tiny(21, n_nodes=4, indeg=2)
+    base = Problem(w, ctx)
+    frozen = np.ones(base.net.P, np.uint8)
+    frozen[[0, 3, base.net.P - 2]] = 0
+    p = Problem(w, ctx, frozen=frozen, frozen_val=base.xs)
+    R.rn_init_chains(ctx, p.id, 16, 4)
+    R.rn_anneal(ctx, R.schedule(2.0, 0.99), 50)
+    st = R.rn_get_chain_state(ctx, p.id, 16)
+    ch = _oracle_run(p, 4, 16, O.Schedule(2.0, 0.99), 0, 50)
+    _compare(st, ch, list(range(16)))
+    # everything fixed: every step is a null move
+    q = Problem(w, ctx, frozen=np.ones(base.net.P, np.uint8), frozen_val=base.xs)
+    R.rn_init_chains(ctx, q.id, 4, 4)
+    R.rn_anneal(ctx, R.schedule(2.0, 0.99), 10)
+    st = R.rn_get_chain_state(ctx, q.id, 4)
+    assert (st["counters"][:, 2] == 10).all() and not st["counters"][:, :2].any()
+
+
+def test_rejects_bad_input(ctx):
+    w = synth.make("n15_c3_t11")
+    with pytest.raises(R.RNError) as e:
+        R.rn_load_network(ctx, [0, 1, 1], [1, 0, 1], [0, 0])      # self-loop
+    assert e.value.code == R.RN_EINVAL
+    with pytest.raises(R.RNError) as e:
+        R.rn_load_network(ctx, [0, 0], [1, 1], [0, 0])            # duplicate, node 0 no in-edge
+    assert e.value.code == R.RN_EINVAL
+    with pytest.raises(R.RNError) as e:
+        R.rn_load_network(ctx, [0, 1], [1, 2], [0, 0, 0])         # node 2 has no out-edge
+    assert e.value.code == R.RN_EINVAL
+    net = R.rn_load_network(ctx, w.src, w.dst, w.fast)
+    with pytest.raises(R.RNError) as e:
+        R.rn_init_chains(ctx, net, 4, 0)                         # no time course yet
+    assert e.value.code == R.RN_ESTATE
+    bad_init = w.init.copy()
+    bad_init[0, 0] = 3
+    with pytest.raises(R.RNError) as e:
+        R.rn_load_timecourse(ctx, net, bad_init, np.zeros((w.C, w.T, w.N)), w.observed)
+    assert e.value.code == R.RN_EINVAL
+    R.rn_load_timecourse(ctx, net, w.init, np.zeros((w.C, w.T, w.N)), w.observed, w.knockout)
+    x0 = O.init_chains(O.Network(w.src, w.dst, w.fast), 1, 2)
+    x0[1, :w.E] = 0                                             # every weight 0
+    with pytest.raises(R.RNError) as e:
+        R.rn_init_chains(ctx, net, 2, 0, x0)
+    assert e.value.code == R.RN_ECONSTRAINT
+    big = synth.random_network(3, 200, lam=3.0, cap=8, n_cond=1, n_times=4, obs_frac=0.5)
+    bn = R.rn_load_network(ctx, big.src, big.dst, big.fast)
+    R.rn_load_timecourse(ctx, bn, big.init, np.zeros((1, 4, 200)), big.observed)
+    with pytest.raises(R.RNError) as e:
+        R.rn_init_chains(ctx, bn, 2, 0)
+    assert e.value.code == R.RN_EUNSUPPORTED
