@@ -186,6 +186,38 @@ int rn_set_chain_state(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed
 /* Number of kernels this context has launched since rn_create. */
 int rn_launch_count(rn_ctx *ctx, int64_t *count);
 
+/* For callers that cannot let a library allocate device memory -- an
+ * application that owns every byte of the GPU through its own memory pool or
+ * fixed arena and must not see cudaMalloc/cudaFree behind its back, or that
+ * has sized its device memory up front -- this one entry point performs the
+ * level-end step of the annealing loop (the lowest delta_best over the chains,
+ * lowest chain index on ties, copied with its vector into every chain) on the
+ * caller's own device buffers, without a context and without allocating.  It
+ * is an addition of this library for such callers; the paper has no
+ * counterpart to it beyond the serial argmin of Table 1 it performs.
+ *   x_best     device [n_chains][row_bytes] vectors; row w is copied (n_params
+ *              bytes) into every other row.
+ *   d_best     device [n_chains] objectives; entry w is copied into every other.
+ *   n_chains   1 .. 1,048,576: the call keeps its partial minima in one fixed
+ *              8 KiB device array, sized for at most that many chains; more
+ *              are rejected with RN_EINVAL.
+ *   row_bytes  stride of x_best rows (>= n_params).
+ *   stream     cudaStream_t to queue the three kernels on (NULL: legacy default).
+ * The call queues its work and returns; it calls no cudaMalloc, cudaFree or
+ * allocating routine.  The fixed array is a file-scope device array that every
+ * GPU loading the library holds until the process exits.  On the first call
+ * for a device, the call resolves that array's device address with the device
+ * current (cudaGetSymbolAddress, which may also load the library's device code
+ * on that device); make that first call before any stream capture.  Every
+ * call shares the array and leaves its contents behind; nothing in it needs to
+ * start at zero, because each call writes every slot before reading it.  Calls
+ * whose work overlaps on the GPU (two streams, or two host threads) race on
+ * the array: order them on one stream.  Errors: RN_EINVAL for a NULL pointer or
+ * a size out of range, RN_ECUDA if the device cannot be used; the message is
+ * rn_last_error(NULL). */
+int rn_level_sync_noalloc(int8_t *x_best, int32_t *d_best, int32_t n_chains, int64_t row_bytes,
+                          int32_t n_params, void *stream);
+
 /* Wait for all queued work on the context stream; reports device-side errors. */
 int rn_synchronize(rn_ctx *ctx);
 

@@ -413,6 +413,19 @@ int build_thresholds(rn_ctx *ctx, const rn_schedule &s, int64_t l0, int64_t l1, 
 
 }  // namespace
 
+namespace rn {
+// Message of a failed call that has no context (read with rn_last_error(NULL)).
+void set_detached_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_create_error = buf;
+}
+}  // namespace rn
+
 extern "C" {
 
 int rn_create(rn_ctx **out, int device, void *stream)

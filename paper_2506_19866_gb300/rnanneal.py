@@ -49,6 +49,7 @@ SIGNATURES = {
                                     _c_i64]),
     "rn_prepare_schedule": (_c_int, [_vp, ctypes.POINTER(rn_schedule), _c_i64]),
     "rn_launch_count": (_c_int, [_vp, _vp]),
+    "rn_level_sync_noalloc": (_c_int, [_vp, _vp, _c_i32, _c_i64, _c_i32, _vp]),
     "rn_synchronize": (_c_int, [_vp]),
 }
 
@@ -210,3 +211,11 @@ def rn_launch_count(ctx):
     out = ctypes.c_int64(0)
     _check(ctx, load_library().rn_launch_count(ctx, ctypes.byref(out)))
     return out.value
+
+
+def rn_level_sync_noalloc(x_best_dev, d_best_dev, n_chains, row_bytes, n_params, stream=None):
+    """Level-end argmin + broadcast on caller-owned device buffers; allocates nothing."""
+    s = None if stream is None else int(stream)
+    _check(None, load_library().rn_level_sync_noalloc(_dev(x_best_dev), _dev(d_best_dev),
+                                                      int(n_chains), int(row_bytes),
+                                                      int(n_params), s))
