@@ -102,7 +102,7 @@ int rn_load_network(rn_ctx *ctx, int32_t n_nodes, int32_t n_edges, const int32_t
 /* Attach experimental data to a network (Section 2.3).
  *   n_cond     C >= 1 conditions; a condition is an initial state plus an
  *              optional set of knocked-out nodes (held at 0, never updated).
- *   n_times    T >= 1 time points including t0 (T - 1 update steps).
+ *   n_times    1 <= T <= 128 time points including t0 (T - 1 update steps).
  *   init       [C][N] initial states, 0..2.
  *   knockout   [C][N] 1 = knocked out in that condition, or NULL.
  *   ref        [C][T][N] reference data R, 0..2 (ignored where unobserved).

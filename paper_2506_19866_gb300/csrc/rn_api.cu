@@ -90,7 +90,7 @@ struct Network {
     int d0 = -1, d1 = -1;               // register capacities of the anneal kernel
     int64_t max_score = 0;
     DevBuf<uint16_t> d_init_code, d_out_bits;
-    DevBuf<uint32_t> d_obs;
+    DevBuf<uint32_t> d_obs, d_init_s4, d_movable;
     // chains
     int32_t n_chains = 0;
     int32_t pstride = 0;
@@ -116,6 +116,7 @@ struct Network {
         n.frozen = has_frozen ? d_frozen.p : nullptr;
         n.frozen_val = has_frozen ? d_frozen_val.p : nullptr;
         n.init_code = d_init_code.p; n.out_bits = d_out_bits.p; n.obs = d_obs.p;
+        n.init_s4 = d_init_s4.p; n.movable = d_movable.p;
         return n;
     }
     DevChains chains() const
@@ -553,8 +554,8 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
     if (!init || !ref || !observed) return fail(ctx, RN_EINVAL, "NULL array");
     if (n_cond < 1 || n_times < 1) return fail(ctx, RN_EINVAL, "n_cond and n_times must be >= 1");
-    if ((int64_t)n_times > 256)
-        return fail(ctx, RN_EINVAL, "n_times %d exceeds 256", n_times);
+    if ((int64_t)n_times > 128)
+        return fail(ctx, RN_EINVAL, "n_times %d exceeds 128", n_times);
     const int32_t N = n->N, C = n_cond, T = n_times;
     const size_t ctn = (size_t)C * T * N;
     for (size_t k = 0; k < (size_t)C * N; ++k) {
@@ -596,6 +597,8 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     // never moves in a condition (padding, knocked out, condition beyond C)
     // starts at 0 and has its bit k * cg + c set in out_bits
     std::vector<uint16_t> init_code((size_t)G * 32 * npl, 0), out_bits((size_t)G * 32, 0);
+    // the same per byte for the byte-SIMD path: initial states and "may move" bits
+    std::vector<uint32_t> init_s4((size_t)G * 32 * npl, 0), movable((size_t)G * 32 * npl, 0);
     for (int g = 0; g < G; ++g)
         for (int q = 0; q < 32 * npl; ++q) {
             const int i = n->q_node[(size_t)q];
@@ -608,8 +611,10 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
                     out_bits[(size_t)g * 32 + lane] |= (uint16_t)(1u << (slot * cg + c));
                     continue;
                 }
-                init_code[(size_t)g * 32 * npl + q] |=
-                    (uint16_t)(init[(size_t)cc * N + i] << (4 * c));
+                const uint32_t s0 = init[(size_t)cc * N + i];
+                init_code[(size_t)g * 32 * npl + q] |= (uint16_t)(s0 << (4 * c));
+                init_s4[(size_t)g * 32 * npl + q] |= s0 << (8 * c);
+                movable[(size_t)g * 32 * npl + q] |= 0x80u << (8 * c);
             }
         }
     for (int32_t c = 0; c < C; ++c) {
@@ -631,6 +636,8 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     RN_CUDA(ctx, n->d_obs.upload(obs));
     RN_CUDA(ctx, n->d_init_code.upload(init_code));
     RN_CUDA(ctx, n->d_out_bits.upload(out_bits));
+    RN_CUDA(ctx, n->d_init_s4.upload(init_s4));
+    RN_CUDA(ctx, n->d_movable.upload(movable));
     n->cg = cg;
     n->G = G;
     return RN_OK;

@@ -51,6 +51,8 @@ struct DevNet {
     const int8_t *frozen_val;           // [P] or null
     const uint16_t *init_code;          // [G][32 * npl] initial state codes of a group
     const uint16_t *out_bits;           // [G][32] bit (k * cg + c): never moves
+    const uint32_t *init_s4;            // [G][32 * npl] byte c: initial state, condition c
+    const uint32_t *movable;            // [G][32 * npl] bit 7 of byte c: may move in c
     const uint32_t *obs;                // [C][T][32][npl] error table of each entry
 };
 
@@ -162,13 +164,12 @@ __device__ __forceinline__ void load_regs(Regs<NPL, D0, D1> &R, const DevNet &ne
 }
 
 // Biased image terms of the slot's node for the CG conditions, one byte each:
-// sum over its D in-edges.  D is warp uniform: the jump into the unrolled
-// sequence does not diverge.
+// `acc` plus the sum over its D in-edges.  D is warp uniform: the jump into
+// the unrolled sequence does not diverge.
 template <int DC>
 __device__ __forceinline__ uint32_t image(const uint32_t (&lut)[DC], int D, uint32_t base,
-                                          const uint8_t *sm)
+                                          const uint8_t *sm, uint32_t acc = 0)
 {
-    uint32_t acc = 0;
 #define RN_EDGE(dd)                                                                    \
     case (dd) + 1:                                                                     \
         if constexpr (DC > (dd)) {                                                     \
@@ -195,6 +196,26 @@ __device__ __forceinline__ void images(uint32_t (&acc)[NPL], const Regs<NPL, D0,
 #pragma unroll
     for (int k = 1; k < NPL; ++k) acc[k] = image<D1>(R.lutr[k - 1], net.D[k], base, sm);
 }
+
+// Byte-SIMD helpers: prmt with sign replication (selector nibble bit 3 set
+// copies the top bit of the selected byte into all 8 bits of the result byte),
+// and the 16-bit-lane maximum.
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+constexpr uint32_t kB1 = 0x01010101u;   // 1 in every byte
+constexpr uint32_t kH = 0x80808080u;    // top bit of every byte
 
 template <int NPL>
 __device__ __forceinline__ void store_codes(uint8_t *p, const uint32_t (&code)[NPL])
@@ -238,6 +259,137 @@ __device__ __forceinline__ void load_obs(uint32_t (&w)[NPL], const uint32_t *ob)
     }
 }
 
+// Simulate(x) for groups of 4 conditions, with the priority update of
+// Section 2.2 done byte-SIMD within registers: byte c of every per-node word
+// belongs to condition c of the group.
+//
+//   a    = image byte 128 + K_i (the accumulator starts at (128 - 4 D) per byte)
+//   tgt  = [K >= 1] + [K >= 2] = clamp(K, 0, 2)      (bit 7 of a - 1 and a - 2)
+//   dp   = tgt - s + 2 in [0, 4]; UP = dp >= 3, DN = dp <= 1 (told to move up/down)
+//   cu   = consecutive up drives, cd = consecutive down drives (reset by a move)
+//   EL   = cu >= m + 1 or cd >= m + 1, only where the node may move
+//   ua   = u * (steps since the last update), 16-bit lanes (two words)
+//   the nodes whose eligible priority equals the warp maximum of their
+//   condition move to tgt (d = 2) or one level toward it (d = 1).
+// Byte values stay within their byte: a in [64, 192] for D <= 16, counters
+// below 128 for T <= 128, priorities below 2^15.
+template <int NPL, int D0, int D1>
+__device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, const DevNet &net,
+                                                  uint8_t *sm, uint32_t base, int lane,
+                                                  uint8_t *traj)
+{
+    const int T = net.T;
+    uint8_t *my_codes = sm + base + 2 * lane * NPL;
+    uint32_t U2[NPL], CM[NPL];
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+        U2[k] = (uint32_t)R.u[k] * 0x00010001u;
+        CM[k] = (uint32_t)(128 - R.m1[k]) * kB1;
+    }
+    uint32_t score = 0;
+    for (int g = 0; g < net.G; ++g) {
+        uint32_t code[NPL], s4[NPL], cu[NPL], cd[NPL], ua01[NPL], ua23[NPL], mov[NPL];
+        load_codes<NPL>(code, net.init_code + (size_t)g * 32 * NPL + lane * NPL);
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            const size_t q = (size_t)g * 32 * NPL + lane * NPL + k;
+            s4[k] = __ldg(net.init_s4 + q);
+            mov[k] = __ldg(net.movable + q);
+            cu[k] = 0;
+            cd[k] = 0;
+            ua01[k] = U2[k];
+            ua23[k] = U2[k];
+        }
+        store_codes<NPL>(my_codes, code);
+        const int ncg = min(net.C - 4 * g, 4);
+        for (int tau = 0; tau < T; ++tau) {
+            if (tau > 0) {
+                uint32_t acc[NPL];
+                acc[0] = image<D0>(R.lut0, net.D[0], base, sm, kH - 0x04040404u * net.D[0]);
+#pragma unroll
+                for (int k = 1; k < NPL; ++k)
+                    acc[k] = image<D1>(R.lutr[k - 1], net.D[k], base, sm,
+                                       kH - 0x04040404u * net.D[k]);
+                uint32_t sn[NPL], pr01[NPL], pr23[NPL], elm[NPL];
+                uint32_t m01 = 0, m23 = 0;
+#pragma unroll
+                for (int k = 0; k < NPL; ++k) {
+                    const uint32_t a = acc[k];
+                    const uint32_t tgt = (((a - kB1) >> 7) & kB1) + (((a - 2 * kB1) >> 7) & kB1);
+                    const uint32_t dp = tgt + 2 * kB1 - s4[k];
+                    const uint32_t up = (dp + 0x7D7D7D7Du) & kH;
+                    const uint32_t dn = ~(dp + 0x7E7E7E7Eu) & kH;
+                    cu[k] = (cu[k] + kB1) & prmt(up, 0u, 0xBA98u);
+                    cd[k] = (cd[k] + kB1) & prmt(dn, 0u, 0xBA98u);
+                    const uint32_t el = ((cu[k] + CM[k]) | (cd[k] + CM[k])) & mov[k];
+                    elm[k] = prmt(el, 0u, 0xBA98u);
+                    sn[k] = R.d2[k] ? tgt : s4[k] + (up >> 7) - (dn >> 7);
+                    pr01[k] = ua01[k] & prmt(el, 0u, 0x9988u);
+                    pr23[k] = ua23[k] & prmt(el, 0u, 0xBBAAu);
+                    m01 = max_u16x2(m01, pr01[k]);
+                    m23 = max_u16x2(m23, pr23[k]);
+                }
+                const uint32_t p0 = __reduce_max_sync(kFull, m01 & 0xffffu);
+                const uint32_t p1 = __reduce_max_sync(kFull, m01 >> 16);
+                const uint32_t p2 = __reduce_max_sync(kFull, m23 & 0xffffu);
+                const uint32_t p3 = __reduce_max_sync(kFull, m23 >> 16);
+                const uint32_t P01 = prmt(p0, p1, 0x5410u), P23 = prmt(p2, p3, 0x5410u);
+#pragma unroll
+                for (int k = 0; k < NPL; ++k) {
+                    const uint32_t nz01 = ((pr01[k] ^ P01) + 0x7FFF7FFFu) & 0x80008000u;
+                    const uint32_t nz23 = ((pr23[k] ^ P23) + 0x7FFF7FFFu) & 0x80008000u;
+                    const uint32_t upd = elm[k] & ~prmt(nz01, nz23, 0xFDB9u);
+                    s4[k] = (s4[k] & ~upd) | (sn[k] & upd);
+                    cu[k] &= ~upd;
+                    cd[k] &= ~upd;
+                    const uint32_t u01 = prmt(upd, 0u, 0x9988u), u23 = prmt(upd, 0u, 0xBBAAu);
+                    ua01[k] = ((ua01[k] + U2[k]) & ~u01) | (U2[k] & u01);
+                    ua23[k] = ((ua23[k] + U2[k]) & ~u23) | (U2[k] & u23);
+                    const uint32_t x = s4[k] | (s4[k] >> 4);
+                    code[k] = prmt(x, 0u, 0x4420u);
+                }
+                store_codes<NPL>(my_codes, code);
+            }
+            __syncwarp();
+            // error at this time point: PRMT of two conditions' entry tables
+            // (byte b = W |b - R|) with a selector built from the state codes
+            const size_t row = (size_t)T * 32 * NPL;
+            const uint32_t *ob = net.obs + ((size_t)4 * g * T + tau) * 32 * NPL + lane * NPL;
+            uint32_t w0[NPL], w1[NPL], w2[NPL], w3[NPL];
+            load_obs<NPL>(w0, ob);
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) w1[k] = w2[k] = w3[k] = 0u;
+            if (ncg > 1) load_obs<NPL>(w1, ob + row);
+            if (ncg > 2) load_obs<NPL>(w2, ob + 2 * row);
+            if (ncg > 3) load_obs<NPL>(w3, ob + 3 * row);
+            uint32_t t = 0;
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+                const uint32_t sel01 = (code[k] & 0xffu) + 0x3340u;
+                const uint32_t sel23 = (code[k] >> 8) + 0x3340u;
+                t += __byte_perm(w0[k], w1[k], sel01) + __byte_perm(w2[k], w3[k], sel23);
+            }
+            score += (t & 0xffu) + (t >> 8);
+            if (traj) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (c >= ncg) break;
+                    const int cc = 4 * g + c;
+#pragma unroll
+                    for (int k = 0; k < NPL; ++k) {
+                        const int i = net.q_node[lane * NPL + k];
+                        if (i >= 0)
+                            traj[((size_t)cc * T + tau) * net.N + i] =
+                                (uint8_t)((s4[k] >> (8 * c)) & 0xffu);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    return (int32_t)__reduce_add_sync(kFull, score);
+}
+
 // Simulate(x) of Table 1 for the warp's vector: every condition, every time
 // step (Sections 2.1-2.2), scored against the entry tables (Section 2.3).
 // Returns y in every lane.  With traj != null, writes S to traj[C][T][N].
@@ -246,6 +398,7 @@ template <int NPL, int CG, int D0, int D1>
 __device__ __forceinline__ int32_t simulate(const Regs<NPL, D0, D1> &R, const DevNet &net,
                                             uint8_t *sm, uint32_t base, int lane, uint8_t *traj)
 {
+    if constexpr (CG == 4) return simulate_swar4<NPL, D0, D1>(R, net, sm, base, lane, traj);
     const int T = net.T;
     uint8_t *my_codes = sm + base + 2 * lane * NPL;
     uint32_t score = 0;

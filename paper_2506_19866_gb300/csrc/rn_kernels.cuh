@@ -118,8 +118,17 @@ __device__ __forceinline__ void set_node(Regs<NPL, D0, D1> &R, int kind, int slo
     }
 }
 
+// Three 4-warp blocks per SM (at most 168 registers a thread) unless the
+// register tables alone need more room.
+template <int NPL, int D0, int D1>
+constexpr int anneal_min_blocks()
+{
+    return D0 + (NPL - 1) * D1 <= 40 ? 3 : 2;
+}
+
 template <int NPL, int CG, int D0, int D1>
-__global__ void __launch_bounds__(128) anneal_kernel(DevNet net, DevChains ch, DevSched sc)
+__global__ void __launch_bounds__(128, (anneal_min_blocks<NPL, D0, D1>()))
+    anneal_kernel(DevNet net, DevChains ch, DevSched sc)
 {
     extern __shared__ __align__(256) uint8_t sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
