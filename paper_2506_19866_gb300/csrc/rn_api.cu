@@ -306,16 +306,60 @@ void build_layout(Network &n)
     n.edge_pos.assign((size_t)E, 0);
     for (int32_t e = 0; e < E; ++e)
         n.edge_q2[(size_t)e] = (uint8_t)(2 * n.node_q[(size_t)n.src[(size_t)e]]);
-    for (int q = 0; q < 32 * npl; ++q) {
-        const int i = n.q_node[(size_t)q];
-        const int lane = q / npl, slot = q % npl;
-        if (i < 0) continue;
-        int d = 0;
-        for (int32_t k = n.in_ptr[(size_t)i]; k < n.in_ptr[(size_t)i + 1]; ++k, ++d) {
-            const int32_t e = n.in_edges[(size_t)k];
-            const size_t idx = ((size_t)slot * n.dtab + d) * 32 + lane;
-            n.edge_id[idx] = e;
-            n.edge_pos[(size_t)e] = (lane << 16) | (slot << 8) | d;
+    // Column d of slot k is read by the 32 lanes at once: each lane gathers the
+    // 2-byte state code of one source.  A shared-memory bank serves one 4-byte
+    // word per wavefront, so the in-edges of each lane are spread over the
+    // columns greedily such that no two lanes of a column read different words
+    // of one bank; a padding entry reads a word already read in its column.
+    for (int slot = 0; slot < npl; ++slot) {
+        std::vector<std::vector<std::pair<int, int32_t>>> rem(32);   // (word, edge)
+        for (int lane = 0; lane < 32; ++lane) {
+            const int i = n.q_node[(size_t)(lane * npl + slot)];
+            if (i < 0) continue;
+            for (int32_t k = n.in_ptr[(size_t)i]; k < n.in_ptr[(size_t)i + 1]; ++k) {
+                const int32_t e = n.in_edges[(size_t)k];
+                rem[(size_t)lane].push_back({n.node_q[(size_t)n.src[(size_t)e]] >> 1, e});
+            }
+        }
+        for (int d = 0; d < n.D[slot]; ++d) {
+            int used[32];
+            for (int b = 0; b < 32; ++b) used[b] = -1;
+            std::vector<int> lanes(32);
+            std::iota(lanes.begin(), lanes.end(), 0);
+            std::stable_sort(lanes.begin(), lanes.end(), [&](int a, int b) {
+                return rem[(size_t)a].size() > rem[(size_t)b].size();
+            });
+            std::vector<int> padded;
+            for (int lane : lanes) {
+                auto &r = rem[(size_t)lane];
+                int pick = -1;
+                for (size_t t = 0; t < r.size(); ++t) {
+                    const int b = r[t].first & 31;
+                    if (used[b] < 0 || used[b] == r[t].first) {
+                        pick = (int)t;
+                        break;
+                    }
+                }
+                if (pick < 0 && !r.empty() && (int)r.size() >= n.D[slot] - d) pick = 0;
+                if (pick < 0) {
+                    padded.push_back(lane);
+                    continue;
+                }
+                const int word = r[(size_t)pick].first;
+                const int32_t e = r[(size_t)pick].second;
+                r.erase(r.begin() + pick);
+                if (used[word & 31] < 0) used[word & 31] = word;
+                n.edge_id[((size_t)slot * n.dtab + d) * 32 + lane] = e;
+                n.edge_pos[(size_t)e] = (lane << 16) | (slot << 8) | d;
+            }
+            int pad_word = 0;
+            for (int b = 0; b < 32; ++b)
+                if (used[b] >= 0) {
+                    pad_word = used[b];
+                    break;
+                }
+            for (int lane : padded)   // padding: -1 - (byte offset of a read code)
+                n.edge_id[((size_t)slot * n.dtab + d) * 32 + lane] = -1 - 4 * pad_word;
         }
     }
     n.supported = true;

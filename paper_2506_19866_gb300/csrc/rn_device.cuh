@@ -37,7 +37,7 @@ struct DevNet {
     int32_t C, T, G;                    // conditions, time points, condition groups
     int32_t npl, cg, dtab;              // nodes per lane, conditions per group, table stride
     int32_t D[kMaxSlots];               // padded in-degree of each slot
-    const int32_t *edge_id;             // [npl][dtab][32] edge index or -1 (padding)
+    const int32_t *edge_id;             // [npl][dtab][32] edge index, or -1 - (code offset) for padding
     const uint8_t *edge_q2;             // [E] 2 * internal index of the edge's source
     const int32_t *edge_pos;            // [E] (lane << 16) | (slot << 8) | d
     const int32_t *node_q;              // [N] internal index of node i
@@ -145,6 +145,7 @@ __device__ __forceinline__ void load_regs(Regs<NPL, D0, D1> &R, const DevNet &ne
         if (d < net.D[k]) {
             const int e = net.edge_id[(k * net.dtab + d) * 32 + lane];
             if (e >= 0) w = edge_word(x[e], x[E + e], x[2 * E + e], net.edge_q2[e]);
+            else w = 0x00040404u | ((uint32_t)(-1 - e) << 24);   // padding reading a shared word
         }
         word = w;
     });
