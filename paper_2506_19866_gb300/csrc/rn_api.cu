@@ -152,6 +152,9 @@ struct rn_ctx {
     DevBuf<int32_t> thr_off, thr_len;
     DevBuf<int32_t> status;
     DevBuf<int32_t> winner;
+    DevBuf<unsigned int> queue;   // work-item counter of the anneal kernel
+    DevBuf<int32_t> done;         // chunks finished per chain in the current launch
+    DevBuf<int32_t> dev_err;      // set by a kernel whose wait gave up
     DevBuf<int8_t> xbuf;
     DevBuf<int32_t> sbuf;
     DevBuf<uint8_t> tbuf;
@@ -365,6 +368,19 @@ void build_layout(Network &n)
     n.supported = true;
 }
 
+// After a synchronisation: a kernel whose bounded wait gave up has set the
+// device flag; report it (and clear it) as RN_ETIMEOUT.
+int check_device_flag(rn_ctx *ctx)
+{
+    int32_t flag = 0;
+    RN_CUDA(ctx, cudaMemcpy(&flag, ctx->dev_err.p, sizeof flag, cudaMemcpyDeviceToHost));
+    if (!flag) return RN_OK;
+    RN_CUDA(ctx, cudaMemset(ctx->dev_err.p, 0, sizeof flag));
+    return fail(ctx, RN_ETIMEOUT,
+                "a device-side wait for another work item gave up; the chain state of the "
+                "last rn_anneal call is incomplete");
+}
+
 int require_supported(rn_ctx *ctx, const Network &n)
 {
     if (!n.supported)
@@ -498,8 +514,12 @@ int rn_create(rn_ctx **out, int device, void *stream)
             return fail(nullptr, RN_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
         ctx->own_stream = true;
     }
-    if (ctx->status.alloc(1) != cudaSuccess || ctx->winner.alloc(1) != cudaSuccess)
+    if (ctx->status.alloc(1) != cudaSuccess || ctx->winner.alloc(1) != cudaSuccess ||
+        ctx->queue.alloc(1) != cudaSuccess || ctx->done.alloc(1) != cudaSuccess ||
+        ctx->dev_err.alloc(1) != cudaSuccess)
         return fail(nullptr, RN_ENOMEM, "cannot allocate context buffers");
+    if (cudaMemset(ctx->dev_err.p, 0, sizeof(int32_t)) != cudaSuccess)
+        return fail(nullptr, RN_ECUDA, "cannot clear the device error flag");
     *out = ctx.release();
     return RN_OK;
 }
@@ -814,6 +834,10 @@ int rn_anneal(rn_ctx *ctx, const rn_schedule *s, int64_t sweeps)
             sc.g1 = seg_end;
             sc.iters = iters;
             sc.reset_to_best = s->reset_to_best;
+            RN_CUDA(ctx, ctx->done.reserve((size_t)ch.n));
+            sc.queue = ctx->queue.p;
+            sc.done = ctx->done.p;
+            sc.err = ctx->dev_err.p;
             cudaError_t e = launch_anneal(dn, n.d0, n.d1, ch, sc, ctx->sm_count, ctx->stream);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "anneal kernel");
             ctx->launches += 1;
@@ -889,6 +913,7 @@ int rn_get_best(rn_ctx *ctx, int32_t net, int8_t *x, int32_t *score, int32_t *ch
     RN_CUDA(ctx, cudaMemcpyAsync(d.data(), ch.d_best, sizeof(int32_t) * d.size(),
                                  cudaMemcpyDeviceToHost, ctx->stream));
     RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (int rc = check_device_flag(ctx)) return rc;
     int32_t b = 0;
     for (int32_t c = 1; c < ch.n; ++c)
         if (d[(size_t)c] < d[(size_t)b]) b = c;
@@ -962,7 +987,9 @@ int rn_get_chain_state(rn_ctx *ctx, int32_t net, int8_t *x_cur, int32_t *d_cur, 
     if (!n->chains_valid) return fail(ctx, RN_ESTATE, "network %d has no chains", net);
     RN_CUDA(ctx, cudaSetDevice(ctx->device));
     const DevChains ch = n->chains();
-    int rc;
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int rc = check_device_flag(ctx);
+    if (rc) return rc;
     if (x_cur && (rc = download_rows(ctx, *n, x_cur, ch.x_cur))) return rc;
     if (x_best && (rc = download_rows(ctx, *n, x_best, ch.x_best))) return rc;
     if (d_cur)
@@ -1021,7 +1048,7 @@ int rn_synchronize(rn_ctx *ctx)
     ctx->err.clear();
     RN_CUDA(ctx, cudaSetDevice(ctx->device));
     RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return RN_OK;
+    return check_device_flag(ctx);
 }
 
 }  // extern "C"

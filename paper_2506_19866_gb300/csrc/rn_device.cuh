@@ -67,15 +67,25 @@ struct DevChains {
 };
 
 // Steps [g0, g1) of one launch and the acceptance tables of their levels.
+// The steps of every chain are cut into chunks of `chunk` steps; the work
+// items (chunk j, chain c) are handed out in order j * n + c from a queue, and
+// item (j, c) starts once chunk j - 1 of chain c is done.
 struct DevSched {
     int64_t g0, g1;
     int64_t iters;                      // proposals per level
     int64_t level0;                     // level of thr_off[0]
     int32_t reset_to_best;
+    int64_t chunk;                      // steps per work item
+    int32_t n_chunks;
     const int32_t *thr_off;             // [levels] start of the level's table
     const int32_t *thr_len;             // [levels] D_l: largest dE with a nonzero threshold
     const uint32_t *thr;                // entries for dE = 1 .. D_l
+    unsigned int *queue;                // next work item (zeroed before the launch)
+    int32_t *done;                      // [n] chunks finished per chain (zeroed before the launch)
+    int32_t *err;                       // set to 1 when a wait gives up
 };
+
+constexpr int kWaitLimit = 1 << 22;     // polls of a predecessor flag before giving up
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round
 // multiplies counter words 0 and 2 by 0xD2511F53 / 0xCD9E8D57 and crosses the

@@ -97,6 +97,23 @@ __device__ __forceinline__ void warp_copy16(void *dst, const void *src, int byte
     for (int k = lane; k < (bytes >> 4); k += 32) d[k] = s[k];
 }
 
+// Chain state moves between warps of different SMs from one work item to the
+// next: read it from L2 (never from a possibly stale L1 line) ...
+__device__ __forceinline__ void warp_load_cg(void *dst, const void *src, int bytes, int lane)
+{
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    for (int k = lane; k < (bytes >> 4); k += 32) d[k] = __ldcg(s + k);
+}
+
+// ... and write it to L2.
+__device__ __forceinline__ void warp_store_cg(void *dst, const void *src, int bytes, int lane)
+{
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    for (int k = lane; k < (bytes >> 4); k += 32) __stcg(d + k, s[k]);
+}
+
 // Replace the table word of (slot, d) == kd (encoded slot * 32 + d).
 template <int NPL, int D0, int D1>
 __device__ __forceinline__ void set_word(Regs<NPL, D0, D1> &R, int kd, uint32_t w)
@@ -140,30 +157,63 @@ __global__ void __launch_bounds__(128, (anneal_min_blocks<NPL, D0, D1>()))
     uint8_t *pos_in = sm + base + L.pos_off;
     const int E = net.E, N = net.N;
 
-    // chain c is processed by block c % gridDim.x, so every block gets the same
-    // number of chains within one
-    for (int chain = blockIdx.x + gridDim.x * warp; chain < ch.n; chain += gridDim.x * wpb) {
+    (void)wpb;
+    const int64_t n_items = (int64_t)sc.n_chunks * ch.n;
+    for (;;) {
+        // next work item: chunk j of chain c, in the order j * n + c
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(sc.queue, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if ((int64_t)item >= n_items) break;
+        const int chunk_j = (int)(item / (unsigned)ch.n);
+        const int chain = (int)(item - (unsigned)chunk_j * (unsigned)ch.n);
+        if (chunk_j > 0) {
+            // chunk j - 1 of this chain was handed out n items earlier, to a warp
+            // that is running; wait (bounded) until it is finished
+            int ok = 1;
+            if (lane == 0) {
+                const volatile int32_t *flag = sc.done + chain;
+                const volatile int32_t *failed = sc.err;
+                int polls = 0;
+                while (*flag < chunk_j) {
+                    if (*failed) {   // another warp gave up: stop as well
+                        ok = 0;
+                        break;
+                    }
+                    if (++polls > kWaitLimit) {
+                        ok = 0;
+                        atomicExch(sc.err, 1);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                __threadfence();
+            }
+            if (!__shfl_sync(kFull, ok, 0)) return;
+        }
+        const int64_t g_lo = sc.g0 + (int64_t)chunk_j * sc.chunk;
+        const int64_t g_hi = min(sc.g1, g_lo + sc.chunk);
         int8_t *xg = ch.x_cur + (size_t)chain * ch.pstride;
         int8_t *xb = ch.x_best + (size_t)chain * ch.pstride;
-        warp_copy16(xs, xg, ch.pstride, lane);
+        warp_load_cg(xs, xg, ch.pstride, lane);
         __syncwarp();
         Regs<NPL, D0, D1> R;
         load_regs<NPL, D0, D1>(R, net, xs, lane);
         count_constraints(net, xs, out_nz, pos_in, lane);
         __syncwarp();
-        int32_t d_cur = ch.d_cur[chain], d_best = ch.d_best[chain];
+        int32_t d_cur = __ldcg(ch.d_cur + chain), d_best = __ldcg(ch.d_best + chain);
         int32_t n_acc = 0, n_up = 0, n_null = 0;
 
-        int64_t level = sc.g0 / sc.iters;
-        int64_t in_level = sc.g0 - level * sc.iters;
-        for (int64_t g = sc.g0; g < sc.g1; ++g) {
+        int64_t level = g_lo / sc.iters;
+        int64_t in_level = g_lo - level * sc.iters;
+        for (int64_t g = g_lo; g < g_hi; ++g) {
             if (in_level == sc.iters) {
                 in_level = 0;
                 ++level;
             }
             if (sc.reset_to_best && in_level == 0) {
                 // Table 1: every level starts from the chain's x_best
-                warp_copy16(xs, xb, ch.pstride, lane);
+                warp_load_cg(xs, xb, ch.pstride, lane);
                 __syncwarp();
                 load_regs<NPL, D0, D1>(R, net, xs, lane);
                 count_constraints(net, xs, out_nz, pos_in, lane);
@@ -256,7 +306,7 @@ __global__ void __launch_bounds__(128, (anneal_min_blocks<NPL, D0, D1>()))
                 n_up += dE > 0;
                 if (d_cand < d_best) {
                     d_best = d_cand;
-                    warp_copy16(xb, xs, ch.pstride, lane);
+                    warp_store_cg(xb, xs, ch.pstride, lane);
                 }
             } else if (lane == owner) {
                 if (kind < 3) set_word<NPL, D0, D1>(R, slot_or_kd, w_old);
@@ -264,14 +314,19 @@ __global__ void __launch_bounds__(128, (anneal_min_blocks<NPL, D0, D1>()))
             }
             __syncwarp();
         }
-        warp_copy16(xg, xs, ch.pstride, lane);
+        warp_store_cg(xg, xs, ch.pstride, lane);
         if (lane == 0) {
-            ch.d_cur[chain] = d_cur;
-            ch.d_best[chain] = d_best;
-            ch.cnt[3 * (size_t)chain + 0] += n_acc;
-            ch.cnt[3 * (size_t)chain + 1] += n_up;
-            ch.cnt[3 * (size_t)chain + 2] += n_null;
+            __stcg(ch.d_cur + chain, d_cur);
+            __stcg(ch.d_best + chain, d_best);
+            int64_t *cnt = ch.cnt + 3 * (size_t)chain;
+            __stcg(cnt + 0, __ldcg(cnt + 0) + n_acc);
+            __stcg(cnt + 1, __ldcg(cnt + 1) + n_up);
+            __stcg(cnt + 2, __ldcg(cnt + 2) + n_null);
         }
+        // publish: every lane's stores, then the chunk counter of the chain
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicExch(sc.done + chain, chunk_j + 1);
         __syncwarp();
     }
 }
@@ -291,10 +346,18 @@ cudaError_t launch_anneal_t(const DevNet &net, const DevChains &ch, const DevSch
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int grid = sm_count * per_sm;
-    const int need = (ch.n + wpb - 1) / wpb;
-    if (grid > need) grid = need;
-    kern<<<grid, wpb * 32, smem, st>>>(net, ch, sc);
+    // one resident grid; with more chains than resident warps, the steps of
+    // every chain are cut into chunks of 16 so that all warps stay busy to the
+    // end (the last round costs at most one chunk)
+    const int grid = sm_count * per_sm;
+    const int64_t warps = (int64_t)grid * wpb, steps = sc.g1 - sc.g0;
+    DevSched s = sc;
+    s.chunk = ch.n > warps ? (steps < 16 ? steps : 16) : steps;
+    s.n_chunks = (int32_t)((steps + s.chunk - 1) / s.chunk);
+    err = cudaMemsetAsync(s.queue, 0, sizeof(unsigned int), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(s.done, 0, sizeof(int32_t) * (size_t)ch.n, st);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, wpb * 32, smem, st>>>(net, ch, s);
     return cudaGetLastError();
 }
 
