@@ -72,7 +72,7 @@ struct Network {
     bool has_frozen = false;
     // lane / slot layout
     int npl = 0, dtab = 0;
-    int D[kMaxSlots] = {0, 0, 0, 0};
+    int D[kMaxSlots] = {};
     std::vector<int32_t> node_q, edge_id, edge_pos, free_list, in_ptr, in_edges, out_ptr,
         out_edges;
     std::vector<int16_t> q_node;
@@ -256,7 +256,9 @@ uint32_t threshold(double T, int64_t dE)
 void build_layout(Network &n)
 {
     const int32_t N = n.N, E = n.E;
-    n.npl = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : 0;
+    // 1, 2 or 4 nodes per lane for the register-table kernels; above 128
+    // nodes, ceil(N / 32) for the shared-memory path (up to 512 nodes)
+    n.npl = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : N <= 32 * kMaxSlots ? (N + 31) / 32 : 0;
     n.in_ptr.assign((size_t)N + 1, 0);
     n.out_ptr.assign((size_t)N + 1, 0);
     for (int32_t e = 0; e < E; ++e) {
@@ -307,8 +309,9 @@ void build_layout(Network &n)
     n.edge_id.assign((size_t)npl * n.dtab * 32, -1);
     n.edge_q2.assign((size_t)E, 0);
     n.edge_pos.assign((size_t)E, 0);
-    for (int32_t e = 0; e < E; ++e)
-        n.edge_q2[(size_t)e] = (uint8_t)(2 * n.node_q[(size_t)n.src[(size_t)e]]);
+    if (npl <= kRegSlots)   // one-byte code offsets of the register-table words
+        for (int32_t e = 0; e < E; ++e)
+            n.edge_q2[(size_t)e] = (uint8_t)(2 * n.node_q[(size_t)n.src[(size_t)e]]);
     // Column d of slot k is read by the 32 lanes at once: each lane gathers the
     // 2-byte state code of one source.  A shared-memory bank serves one 4-byte
     // word per wavefront, so the in-edges of each lane are spread over the
@@ -386,7 +389,7 @@ int require_supported(rn_ctx *ctx, const Network &n)
     if (!n.supported)
         return fail(ctx, RN_EUNSUPPORTED,
                     "network with %d nodes and maximum in-degree %d is outside the compiled "
-                    "kernels (N <= 128, in-degree <= 16)",
+                    "kernels (N <= 512, in-degree <= 16)",
                     n.N, n.dtab);
     return RN_OK;
 }
@@ -650,7 +653,9 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     n->chains_valid = false;
     if (!n->supported) return RN_OK;
     const int npl = n->npl;
-    const int cg = C >= 2 ? 4 : 1;
+    // 4 conditions per group (byte-SIMD) unless there is a single condition;
+    // the shared-memory path always uses groups of 4
+    const int cg = (C >= 2 || npl > kRegSlots) ? 4 : 1;
     const int G = (C + cg - 1) / cg;
     int drest = 0;
     for (int k = 1; k < npl; ++k) drest = std::max(drest, n->D[k]);

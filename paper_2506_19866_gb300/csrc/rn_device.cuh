@@ -27,7 +27,8 @@
 
 namespace rn {
 
-constexpr int kMaxSlots = 4;          // nodes per lane in the register-table kernels
+constexpr int kMaxSlots = 16;         // nodes per lane (N <= 512)
+constexpr int kRegSlots = 4;          // nodes per lane of the register-table kernels (N <= 128)
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int32_t kOutUA = -(1 << 22);   // priority seed of a node that never moves
 

@@ -120,13 +120,52 @@ __global__ void broadcast_kernel(DevChains ch, const int32_t *win)
     if (lane == 0) ch.d_best[chain] = ch.d_best[w];
 }
 
+// Simulate(x) with the shared-memory tables (networks of more than 128 nodes).
+__global__ void __launch_bounds__(128) evaluate_smem_kernel(DevNet net, const int8_t *__restrict__ X,
+                                                            int64_t xstride, int32_t n,
+                                                            int32_t *__restrict__ score,
+                                                            int32_t *__restrict__ score2,
+                                                            uint8_t *__restrict__ traj,
+                                                            uint32_t region_bytes,
+                                                            uint32_t lut_words)
+{
+    extern __shared__ __align__(256) uint8_t sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    SmemPath P = make_smem_path(net, sm, warp, wpb, region_bytes, lut_words);
+    for (int v = blockIdx.x * wpb + warp; v < n; v += gridDim.x * wpb) {
+        P.load(net, X + (size_t)v * xstride, lane);
+        __syncwarp();
+        uint8_t *tv = traj ? traj + (size_t)v * net.C * net.T * net.N : nullptr;
+        const int32_t y = P.simulate(net, lane, tv);
+        if (lane == 0) {
+            score[v] = y;
+            if (score2) score2[v] = y;
+        }
+        __syncwarp();
+    }
+}
+
+// The annealing kernel with the shared-memory tables.
+__global__ void __launch_bounds__(128, 2)
+    anneal_smem_kernel(DevNet net, DevChains ch, DevSched sc, uint32_t region_bytes,
+                       uint32_t lut_words)
+{
+    extern __shared__ __align__(256) uint8_t sm[];
+    anneal_items(net, ch, sc, sm, region_bytes, [&](int warp, int wpb) {
+        SmemPathR P;
+        static_cast<SmemPath &>(P) = make_smem_path(net, sm, warp, wpb, region_bytes, lut_words);
+        return P;
+    });
+}
+
 template <int NPL, int CG>
 static cudaError_t launch_eval_t(const DevNet &net, const int8_t *X, int64_t xstride, int32_t n,
                                  int32_t *score, int32_t *score2, uint8_t *traj, int grid,
                                  cudaStream_t st)
 {
-    evaluate_kernel<NPL, CG, 16, 16><<<grid, 128, 4 * 256, st>>>(net, X, xstride, n, score,
-                                                                   score2, traj);
+    evaluate_kernel<NPL, CG, 16, 16><<<grid, 128, 4 * kCodeBytesPerWarp, st>>>(
+        net, X, xstride, n, score, score2, traj);
     return cudaGetLastError();
 }
 
@@ -137,6 +176,16 @@ cudaError_t launch_evaluate(const DevNet &net, const int8_t *X, int64_t xstride,
     if (n <= 0) return cudaSuccess;
     int grid = (n + 3) / 4;
     if (grid > sm_count * 16) grid = sm_count * 16;
+    if (net.npl > kRegSlots) {
+        const WarpRegion R = warp_region(true, net.D, net.npl, 0, 0);
+        const size_t smem = 4 * ((size_t)kCodeBytesPerWarp + R.bytes);
+        cudaError_t e = cudaFuncSetAttribute(evaluate_smem_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        evaluate_smem_kernel<<<grid, 128, smem, st>>>(net, X, xstride, n, score, score2, traj,
+                                                      R.bytes, R.lut_words);
+        return cudaGetLastError();
+    }
 #define RN_EV(NPL_, CG_)                                                                  \
     if (net.npl == NPL_ && net.cg == CG_)                                                 \
         return launch_eval_t<NPL_, CG_>(net, X, xstride, n, score, score2, traj, grid, st);
@@ -175,10 +224,35 @@ void anneal_capacity(int npl, int D0, int Drest, int *d0, int *d1)
     *d0 = -1;
 }
 
+static cudaError_t launch_anneal_smem(const DevNet &net, const DevChains &ch, const DevSched &sc,
+                                      int sm_count, cudaStream_t st)
+{
+    const int wpb = 4;
+    const WarpRegion R = warp_region(true, net.D, net.npl, ch.pstride, net.N);
+    const size_t smem = (size_t)wpb * (kCodeBytesPerWarp + R.bytes);
+    cudaError_t err = cudaFuncSetAttribute(anneal_smem_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, anneal_smem_kernel, wpb * 32,
+                                                        smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = sm_count * per_sm;
+    DevSched s = sc;
+    plan_chunks(s, ch.n, (int64_t)grid * wpb);
+    err = cudaMemsetAsync(s.queue, 0, sizeof(unsigned int), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(s.done, 0, sizeof(int32_t) * (size_t)ch.n, st);
+    if (err != cudaSuccess) return err;
+    anneal_smem_kernel<<<grid, wpb * 32, smem, st>>>(net, ch, s, R.bytes, R.lut_words);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_anneal(const DevNet &net, int d0, int d1, const DevChains &ch,
                           const DevSched &sc, int sm_count, cudaStream_t st)
 {
     if (ch.n <= 0 || sc.g1 <= sc.g0) return cudaSuccess;
+    if (net.npl > kRegSlots) return launch_anneal_smem(net, ch, sc, sm_count, st);
     switch (net.npl) {
     case 1: return launch_anneal_npl1(net, d0, d1, ch, sc, sm_count, st);
     case 2: return launch_anneal_npl2(net, d0, d1, ch, sc, sm_count, st);

@@ -1,34 +1,120 @@
 // rn_kernels.cuh -- kernel templates of the annealing path (instantiated in
-// rn_anneal{1,2,4}.cu and rn_kernels.cu).
+// rn_anneal{1,2,4}.cu, rn_batch.cu and rn_kernels.cu).
 //
-//   evaluate_kernel  Simulate(x) of Table 1 for a batch of vectors, warp each
-//   anneal_kernel    persistent annealing kernel, warp per chain (Table 1 inner
-//                    loop: GetCandidate, Simulate, Metropolis acceptance)
+//   evaluate_kernel        Simulate(x) of Table 1 for a batch of vectors, warp each
+//   evaluate_smem_kernel   the same with the shared-memory tables (N > 128)
+//   anneal_kernel          persistent annealing kernel, warp per chain (Table 1
+//                          inner loop: GetCandidate, Simulate, Metropolis
+//                          acceptance), register tables
+//   anneal_smem_kernel     the same with shared-memory tables
+//   anneal_batch_kernel    one persistent launch over every chain of many networks
+//
+// Shared memory of a block: a code region (1 KiB per warp: the 16-bit state
+// codes of the warp's nodes, so that every code offset fits the table words),
+// then one region per warp (x, constraint counters, and for the shared-memory
+// path the table words and per-node update state).
 #pragma once
 
 #include "rn_device.cuh"
 #include "rn_launch.h"
+#include "rn_smem.cuh"
 
 namespace rn {
 
-// Shared-memory layout of one warp in the annealing kernel; every warp's base
-// is 256-byte aligned (the state-code offsets in the table words are one byte).
-struct WarpSmem {
-    uint32_t per_warp;   // bytes per warp (multiple of 256)
-    uint32_t x_off;      // current vector x (pstride bytes)
-    uint32_t out_off;    // out_nz[N]: out-edges with w != 0
-    uint32_t pos_off;    // pos_in[N]: in-edges with w != 0 and p = +1
+__host__ __device__ inline uint32_t round16(uint32_t v) { return (v + 15u) & ~15u; }
+
+// Region of one warp after the code region.
+struct WarpRegion {
+    uint32_t lut_words;   // shared-memory path: table words (0 for the register path)
+    uint32_t bytes;       // total bytes (multiple of 16)
 };
 
-__host__ __device__ inline WarpSmem warp_smem(int pstride, int N)
+__host__ __device__ inline WarpRegion warp_region(bool smem_path, const int *D, int npl,
+                                                  int pstride, int N)
 {
-    WarpSmem s;
-    s.x_off = 256u;
-    s.out_off = s.x_off + (uint32_t)pstride;
-    s.pos_off = s.out_off + (((uint32_t)N + 15u) & ~15u);
-    s.per_warp = (s.pos_off + (((uint32_t)N + 15u) & ~15u) + 255u) & ~255u;
-    return s;
+    WarpRegion r;
+    if (smem_path) {
+        r.lut_words = smem_path_lut_words(D, npl);
+        r.bytes = round16(smem_path_warp_bytes(r.lut_words, npl, pstride, N));
+    } else {
+        r.lut_words = 0;
+        r.bytes = round16((uint32_t)pstride + 2u * round16((uint32_t)N));
+    }
+    return r;
 }
+
+// ------------------------------------------------------ register table path --
+template <int NPL, int CG, int D0, int D1>
+struct RegPath {
+    Regs<NPL, D0, D1> R;
+    uint8_t *sm;
+    uint32_t codes;       // offset of the warp's code array (256-byte aligned)
+    // undo record of the owner lane
+    int undo_kd, undo_kind, undo_slot;
+    uint32_t undo_val;
+
+    __device__ void load(const DevNet &net, const int8_t *x, int lane)
+    {
+        load_regs<NPL, D0, D1>(R, net, x, lane);
+    }
+
+    __device__ void change_edge(const DevNet &, int lane, int owner, int pos, int w, int p, int t,
+                                int)
+    {
+        if (lane != owner) return;
+        const int kd = ((pos >> 8) & 0xff) * 32 + (pos & 0xff);
+        uint32_t old = 0;
+        for_each_word<NPL, D0, D1>(R, [&](int k, int d, uint32_t &word) {
+            old = (k * 32 + d == kd) ? word : old;
+        });
+        undo_kd = kd;
+        undo_kind = 0;
+        undo_val = old;
+        const uint32_t nw = edge_word(w, p, t, old >> 24);
+        for_each_word<NPL, D0, D1>(R, [&](int k, int d, uint32_t &word) {
+            word = (k * 32 + d == kd) ? nw : word;
+        });
+    }
+
+    __device__ void change_node(int lane, int owner, int slot, int kind, int v)
+    {
+        if (lane != owner) return;
+        undo_kind = kind;
+        undo_slot = slot;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            if (k != slot) continue;
+            if (kind == 3) { undo_val = (uint32_t)R.u[k]; R.u[k] = v; }
+            else if (kind == 4) { undo_val = (uint32_t)R.m1[k]; R.m1[k] = v + 1; }
+            else { undo_val = (uint32_t)R.d2[k]; R.d2[k] = v == 2; }
+        }
+    }
+
+    __device__ void undo(int lane, int owner)
+    {
+        if (lane != owner) return;
+        if (undo_kind == 0) {
+            const int kd = undo_kd;
+            const uint32_t ov = undo_val;
+            for_each_word<NPL, D0, D1>(R, [&](int k, int d, uint32_t &word) {
+                word = (k * 32 + d == kd) ? ov : word;
+            });
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            if (k != undo_slot) continue;
+            if (undo_kind == 3) R.u[k] = (int32_t)undo_val;
+            else if (undo_kind == 4) R.m1[k] = (int32_t)undo_val;
+            else R.d2[k] = (int32_t)undo_val;
+        }
+    }
+
+    __device__ int32_t simulate(const DevNet &net, int lane, uint8_t *traj)
+    {
+        return rn::simulate<NPL, CG, D0, D1>(R, net, sm, codes, lane, traj);
+    }
+};
 
 // ---------------------------------------------------------------- evaluate --
 template <int NPL, int CG, int D0, int D1>
@@ -40,19 +126,34 @@ __global__ void __launch_bounds__(128) evaluate_kernel(DevNet net, const int8_t 
 {
     extern __shared__ __align__(256) uint8_t sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t base = (uint32_t)warp * 256u;
     const int wpb = blockDim.x >> 5;
+    RegPath<NPL, CG, D0, D1> P;
+    P.sm = sm;
+    P.codes = (uint32_t)warp * kCodeBytesPerWarp;
     for (int v = blockIdx.x * wpb + warp; v < n; v += gridDim.x * wpb) {
-        Regs<NPL, D0, D1> R;
-        load_regs<NPL, D0, D1>(R, net, X + (size_t)v * xstride, lane);
+        P.load(net, X + (size_t)v * xstride, lane);
         uint8_t *tv = traj ? traj + (size_t)v * net.C * net.T * net.N : nullptr;
-        const int32_t y = simulate<NPL, CG, D0, D1>(R, net, sm, base, lane, tv);
+        const int32_t y = P.simulate(net, lane, tv);
         if (lane == 0) {
             score[v] = y;
             if (score2) score2[v] = y;
         }
         __syncwarp();
     }
+}
+
+__device__ __forceinline__ SmemPath make_smem_path(const DevNet &net, uint8_t *sm, int warp,
+                                                   int wpb, uint32_t region_bytes,
+                                                   uint32_t lut_words)
+{
+    SmemPath P;
+    P.sm = sm;
+    P.codes = (uint32_t)warp * kCodeBytesPerWarp;
+    uint8_t *region = sm + (uint32_t)wpb * kCodeBytesPerWarp + (uint32_t)warp * region_bytes;
+    P.lut = reinterpret_cast<uint32_t *>(region);
+    P.node = P.lut + lut_words;
+    P.npl = net.npl;
+    return P;
 }
 
 // -------------------------------------------------------------- annealing --
@@ -114,25 +215,172 @@ __device__ __forceinline__ void warp_store_cg(void *dst, const void *src, int by
     for (int k = lane; k < (bytes >> 4); k += 32) __stcg(d + k, s[k]);
 }
 
-// Replace the table word of (slot, d) == kd (encoded slot * 32 + d).
-template <int NPL, int D0, int D1>
-__device__ __forceinline__ void set_word(Regs<NPL, D0, D1> &R, int kd, uint32_t w)
+// Wait (bounded) until `done` reaches `need`; false if the wait gave up or
+// another warp reported a failure.  One lane polls; the result is broadcast.
+__device__ __forceinline__ bool wait_for_chunk(const int32_t *done, int need, int32_t *err,
+                                               int lane)
 {
-    for_each_word<NPL, D0, D1>(R, [&](int k, int d, uint32_t &word) {
-        word = (k * 32 + d == kd) ? w : word;
-    });
+    int ok = 1;
+    if (lane == 0) {
+        const volatile int32_t *flag = done;
+        const volatile int32_t *failed = err;
+        int polls = 0;
+        while (*flag < need) {
+            if (*failed) {
+                ok = 0;
+                break;
+            }
+            if (++polls > kWaitLimit) {
+                ok = 0;
+                atomicExch(err, 1);
+                break;
+            }
+            __nanosleep(256);
+        }
+        __threadfence();
+    }
+    return __shfl_sync(kFull, ok, 0) != 0;
 }
 
-template <int NPL, int D0, int D1>
-__device__ __forceinline__ void set_node(Regs<NPL, D0, D1> &R, int kind, int slot, int v)
+// Steps [g_lo, g_hi) of one chain (Table 1 inner loop), its state in and out
+// of global memory through L2, then the chain's chunk counter is published.
+template <typename Path>
+__device__ __forceinline__ void run_chunk(Path &P, const DevNet &net, const DevChains &ch,
+                                          const DevSched &sc, int chain, int64_t g_lo,
+                                          int64_t g_hi, int8_t *xs, uint8_t *out_nz,
+                                          uint8_t *pos_in, int32_t *done_flag, int done_value,
+                                          int lane)
 {
+    const int E = net.E, N = net.N;
+    int8_t *xg = ch.x_cur + (size_t)chain * ch.pstride;
+    int8_t *xb = ch.x_best + (size_t)chain * ch.pstride;
+    warp_load_cg(xs, xg, ch.pstride, lane);
+    __syncwarp();
+    P.load(net, xs, lane);
+    count_constraints(net, xs, out_nz, pos_in, lane);
+    __syncwarp();
+    int32_t d_cur = __ldcg(ch.d_cur + chain), d_best = __ldcg(ch.d_best + chain);
+    int32_t n_acc = 0, n_up = 0, n_null = 0;
+
+    int64_t level = g_lo / sc.iters;
+    int64_t in_level = g_lo - level * sc.iters;
+    for (int64_t g = g_lo; g < g_hi; ++g) {
+        if (in_level == sc.iters) {
+            in_level = 0;
+            ++level;
+        }
+        if (sc.reset_to_best && in_level == 0) {
+            // Table 1: every level starts from the chain's x_best
+            warp_load_cg(xs, xb, ch.pstride, lane);
+            __syncwarp();
+            P.load(net, xs, lane);
+            count_constraints(net, xs, out_nz, pos_in, lane);
+            __syncwarp();
+            d_cur = d_best;
+        }
+        ++in_level;
+        const uint4 r = philox(ch.seed, (uint32_t)g, (uint32_t)((uint64_t)g >> 32),
+                               (uint32_t)chain, 0u);
+        if (net.n_free == 0) {
+            ++n_null;
+            continue;
+        }
+        // GetCandidate: the pick(r0)-th free parameter ...
+        const int j = net.free_list[pick(r.x, (uint32_t)net.n_free)];
+        int kind, idx;
+        if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
+        else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
+        const int cur = xs[j];
+        int8_t vals[6];
+        const int nd = domain(kind, kind == 3 && net.fast[idx], vals);
+        // ... and the pick(r1)-th of its values != current that keep the
+        // constraints of Section 2.5.3
+        bool blocked0 = false, blocked_all = false;
+        if (kind == 0 && cur != 0) {
+            const int a = net.src[idx], b = net.dst[idx];
+            blocked0 = out_nz[a] < 2 || (xs[E + idx] == 1 && pos_in[b] < 2);
+        } else if (kind == 1 && cur == 1 && xs[idx] != 0) {
+            blocked_all = pos_in[net.dst[idx]] < 2;
+        }
+        int8_t alts[6];
+        int n_alt = 0;
+        if (!blocked_all) {
 #pragma unroll
-    for (int k = 0; k < NPL; ++k) {
-        if (k != slot) continue;
-        if (kind == 3) R.u[k] = v;
-        else if (kind == 4) R.m1[k] = v + 1;
-        else R.d2[k] = v == 2;
+            for (int k = 0; k < 6; ++k) {
+                if (k >= nd) break;
+                const int v = vals[k];
+                if (v == cur || (blocked0 && v == 0)) continue;
+                alts[n_alt++] = (int8_t)v;
+            }
+        }
+        if (n_alt == 0) {
+            ++n_null;
+            continue;
+        }
+        const int v = alts[pick(r.y, (uint32_t)n_alt)];
+
+        // apply the candidate to the owner lane's table entry
+        int owner;
+        if (kind < 3) {
+            const int pos = net.edge_pos[idx];
+            owner = pos >> 16;
+            int w = xs[idx], p = xs[E + idx], t = xs[2 * E + idx];
+            if (kind == 0) w = v; else if (kind == 1) p = v; else t = v;
+            P.change_edge(net, lane, owner, pos, w, p, t, idx);
+        } else {
+            const int q = net.node_q[idx];
+            owner = q / net.npl;
+            P.change_node(lane, owner, q - owner * net.npl, kind, v);
+        }
+        __syncwarp();
+        const int32_t d_cand = P.simulate(net, lane, nullptr);
+
+        // Metropolis acceptance against the host-computed threshold table
+        const int32_t dE = d_cand - d_cur;
+        bool accept = dE <= 0;
+        if (!accept) {
+            const int64_t l = level - sc.level0;
+            if (dE <= sc.thr_len[l]) accept = r.z < __ldg(sc.thr + sc.thr_off[l] + dE - 1);
+        }
+        if (accept) {
+            if (lane == 0) {
+                if (kind == 0 && (cur == 0) != (v == 0)) {
+                    const int delta = v != 0 ? 1 : -1;
+                    out_nz[net.src[idx]] += delta;
+                    if (xs[E + idx] == 1) pos_in[net.dst[idx]] += delta;
+                } else if (kind == 1 && xs[idx] != 0) {
+                    if (cur == 1) pos_in[net.dst[idx]] -= 1;
+                    if (v == 1) pos_in[net.dst[idx]] += 1;
+                }
+                xs[j] = (int8_t)v;
+            }
+            __syncwarp();
+            d_cur = d_cand;
+            ++n_acc;
+            n_up += dE > 0;
+            if (d_cand < d_best) {
+                d_best = d_cand;
+                warp_store_cg(xb, xs, ch.pstride, lane);
+            }
+        } else {
+            P.undo(lane, owner);
+        }
+        __syncwarp();
     }
+    warp_store_cg(xg, xs, ch.pstride, lane);
+    if (lane == 0) {
+        __stcg(ch.d_cur + chain, d_cur);
+        __stcg(ch.d_best + chain, d_best);
+        int64_t *cnt = ch.cnt + 3 * (size_t)chain;
+        __stcg(cnt + 0, __ldcg(cnt + 0) + n_acc);
+        __stcg(cnt + 1, __ldcg(cnt + 1) + n_up);
+        __stcg(cnt + 2, __ldcg(cnt + 2) + n_null);
+    }
+    // publish: every lane's stores, then the chunk counter of the chain
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicExch(done_flag, done_value);
+    __syncwarp();
 }
 
 // Three 4-warp blocks per SM (at most 168 registers a thread) unless the
@@ -143,192 +391,74 @@ constexpr int anneal_min_blocks()
     return D0 + (NPL - 1) * D1 <= 40 ? 3 : 2;
 }
 
-template <int NPL, int CG, int D0, int D1>
-__global__ void __launch_bounds__(128, (anneal_min_blocks<NPL, D0, D1>()))
-    anneal_kernel(DevNet net, DevChains ch, DevSched sc)
+// Work item i of a single-network launch: chunk i / n of chain i % n.
+template <typename MakePath>
+__device__ __forceinline__ void anneal_items(const DevNet &net, const DevChains &ch,
+                                             const DevSched &sc, uint8_t *sm,
+                                             uint32_t region_bytes, MakePath make_path)
 {
-    extern __shared__ __align__(256) uint8_t sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const WarpSmem L = warp_smem(ch.pstride, net.N);
-    const uint32_t base = (uint32_t)warp * L.per_warp;
-    int8_t *xs = reinterpret_cast<int8_t *>(sm + base + L.x_off);
-    uint8_t *out_nz = sm + base + L.out_off;
-    uint8_t *pos_in = sm + base + L.pos_off;
-    const int E = net.E, N = net.N;
-
-    (void)wpb;
+    uint8_t *region = sm + (uint32_t)wpb * kCodeBytesPerWarp + (uint32_t)warp * region_bytes;
+    auto P = make_path(warp, wpb);
+    const uint32_t lut_bytes = (uint32_t)((uint8_t *)P.node_end() - region);
+    int8_t *xs = reinterpret_cast<int8_t *>(region + lut_bytes);
+    uint8_t *out_nz = region + lut_bytes + ch.pstride;
+    uint8_t *pos_in = out_nz + round16((uint32_t)net.N);
     const int64_t n_items = (int64_t)sc.n_chunks * ch.n;
     for (;;) {
-        // next work item: chunk j of chain c, in the order j * n + c
         unsigned int item = 0;
         if (lane == 0) item = atomicAdd(sc.queue, 1u);
         item = __shfl_sync(kFull, item, 0);
         if ((int64_t)item >= n_items) break;
-        const int chunk_j = (int)(item / (unsigned)ch.n);
-        const int chain = (int)(item - (unsigned)chunk_j * (unsigned)ch.n);
-        if (chunk_j > 0) {
-            // chunk j - 1 of this chain was handed out n items earlier, to a warp
-            // that is running; wait (bounded) until it is finished
-            int ok = 1;
-            if (lane == 0) {
-                const volatile int32_t *flag = sc.done + chain;
-                const volatile int32_t *failed = sc.err;
-                int polls = 0;
-                while (*flag < chunk_j) {
-                    if (*failed) {   // another warp gave up: stop as well
-                        ok = 0;
-                        break;
-                    }
-                    if (++polls > kWaitLimit) {
-                        ok = 0;
-                        atomicExch(sc.err, 1);
-                        break;
-                    }
-                    __nanosleep(256);
-                }
-                __threadfence();
-            }
-            if (!__shfl_sync(kFull, ok, 0)) return;
-        }
-        const int64_t g_lo = sc.g0 + (int64_t)chunk_j * sc.chunk;
+        const int cj = (int)(item / (unsigned)ch.n);
+        const int chain = (int)(item - (unsigned)cj * (unsigned)ch.n);
+        // chunk cj - 1 of this chain was handed out n items earlier, to a running warp
+        if (cj > 0 && !wait_for_chunk(sc.done + chain, cj, sc.err, lane)) return;
+        const int64_t g_lo = sc.g0 + (int64_t)cj * sc.chunk;
         const int64_t g_hi = min(sc.g1, g_lo + sc.chunk);
-        int8_t *xg = ch.x_cur + (size_t)chain * ch.pstride;
-        int8_t *xb = ch.x_best + (size_t)chain * ch.pstride;
-        warp_load_cg(xs, xg, ch.pstride, lane);
-        __syncwarp();
-        Regs<NPL, D0, D1> R;
-        load_regs<NPL, D0, D1>(R, net, xs, lane);
-        count_constraints(net, xs, out_nz, pos_in, lane);
-        __syncwarp();
-        int32_t d_cur = __ldcg(ch.d_cur + chain), d_best = __ldcg(ch.d_best + chain);
-        int32_t n_acc = 0, n_up = 0, n_null = 0;
-
-        int64_t level = g_lo / sc.iters;
-        int64_t in_level = g_lo - level * sc.iters;
-        for (int64_t g = g_lo; g < g_hi; ++g) {
-            if (in_level == sc.iters) {
-                in_level = 0;
-                ++level;
-            }
-            if (sc.reset_to_best && in_level == 0) {
-                // Table 1: every level starts from the chain's x_best
-                warp_load_cg(xs, xb, ch.pstride, lane);
-                __syncwarp();
-                load_regs<NPL, D0, D1>(R, net, xs, lane);
-                count_constraints(net, xs, out_nz, pos_in, lane);
-                __syncwarp();
-                d_cur = d_best;
-            }
-            ++in_level;
-            const uint4 r = philox(ch.seed, (uint32_t)g, (uint32_t)((uint64_t)g >> 32),
-                                   (uint32_t)chain, 0u);
-            if (net.n_free == 0) {
-                ++n_null;
-                continue;
-            }
-            // GetCandidate: the pick(r0)-th free parameter ...
-            const int j = net.free_list[pick(r.x, (uint32_t)net.n_free)];
-            int kind, idx;
-            if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
-            else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
-            const int cur = xs[j];
-            int8_t vals[6];
-            const int nd = domain(kind, kind == 3 && net.fast[idx], vals);
-            // ... and the pick(r1)-th of its values != current that keep the
-            // constraints of Section 2.5.3
-            bool blocked0 = false, blocked_all = false;
-            if (kind == 0 && cur != 0) {
-                const int a = net.src[idx], b = net.dst[idx];
-                blocked0 = out_nz[a] < 2 || (xs[E + idx] == 1 && pos_in[b] < 2);
-            } else if (kind == 1 && cur == 1 && xs[idx] != 0) {
-                blocked_all = pos_in[net.dst[idx]] < 2;
-            }
-            int8_t alts[6];
-            int n_alt = 0;
-            if (!blocked_all) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    if (k >= nd) break;
-                    const int v = vals[k];
-                    if (v == cur || (blocked0 && v == 0)) continue;
-                    alts[n_alt++] = (int8_t)v;
-                }
-            }
-            if (n_alt == 0) {
-                ++n_null;
-                continue;
-            }
-            const int v = alts[pick(r.y, (uint32_t)n_alt)];
-
-            // apply the candidate to the owner lane's registers
-            int owner, slot_or_kd;
-            uint32_t w_old = 0;
-            if (kind < 3) {
-                const int pos = net.edge_pos[idx];
-                owner = pos >> 16;
-                slot_or_kd = ((pos >> 8) & 0xff) * 32 + (pos & 0xff);
-                int w = xs[idx], p = xs[E + idx], t = xs[2 * E + idx];
-                const uint32_t q2 = net.edge_q2[idx];
-                w_old = edge_word(w, p, t, q2);
-                if (kind == 0) w = v; else if (kind == 1) p = v; else t = v;
-                if (lane == owner) set_word<NPL, D0, D1>(R, slot_or_kd, edge_word(w, p, t, q2));
-            } else {
-                const int q = net.node_q[idx];
-                owner = q / NPL;
-                slot_or_kd = q - owner * NPL;
-                if (lane == owner) set_node<NPL, D0, D1>(R, kind, slot_or_kd, v);
-            }
-            const int32_t d_cand = simulate<NPL, CG, D0, D1>(R, net, sm, base, lane, nullptr);
-
-            // Metropolis acceptance against the host-computed threshold table
-            const int32_t dE = d_cand - d_cur;
-            bool accept = dE <= 0;
-            if (!accept) {
-                const int64_t l = level - sc.level0;
-                if (dE <= sc.thr_len[l]) accept = r.z < __ldg(sc.thr + sc.thr_off[l] + dE - 1);
-            }
-            if (accept) {
-                if (lane == 0) {
-                    if (kind == 0 && (cur == 0) != (v == 0)) {
-                        const int delta = v != 0 ? 1 : -1;
-                        out_nz[net.src[idx]] += delta;
-                        if (xs[E + idx] == 1) pos_in[net.dst[idx]] += delta;
-                    } else if (kind == 1 && xs[idx] != 0) {
-                        if (cur == 1) pos_in[net.dst[idx]] -= 1;
-                        if (v == 1) pos_in[net.dst[idx]] += 1;
-                    }
-                    xs[j] = (int8_t)v;
-                }
-                __syncwarp();
-                d_cur = d_cand;
-                ++n_acc;
-                n_up += dE > 0;
-                if (d_cand < d_best) {
-                    d_best = d_cand;
-                    warp_store_cg(xb, xs, ch.pstride, lane);
-                }
-            } else if (lane == owner) {
-                if (kind < 3) set_word<NPL, D0, D1>(R, slot_or_kd, w_old);
-                else set_node<NPL, D0, D1>(R, kind, slot_or_kd, cur);
-            }
-            __syncwarp();
-        }
-        warp_store_cg(xg, xs, ch.pstride, lane);
-        if (lane == 0) {
-            __stcg(ch.d_cur + chain, d_cur);
-            __stcg(ch.d_best + chain, d_best);
-            int64_t *cnt = ch.cnt + 3 * (size_t)chain;
-            __stcg(cnt + 0, __ldcg(cnt + 0) + n_acc);
-            __stcg(cnt + 1, __ldcg(cnt + 1) + n_up);
-            __stcg(cnt + 2, __ldcg(cnt + 2) + n_null);
-        }
-        // publish: every lane's stores, then the chunk counter of the chain
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) atomicExch(sc.done + chain, chunk_j + 1);
-        __syncwarp();
+        run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, out_nz, pos_in, sc.done + chain, cj + 1,
+                  lane);
     }
+}
+
+// Register-path wrapper exposing where its (empty) table region ends.
+template <int NPL, int CG, int D0, int D1>
+struct RegPathR : RegPath<NPL, CG, D0, D1> {
+    uint8_t *region;
+    __device__ uint8_t *node_end() const { return region; }
+};
+
+struct SmemPathR : SmemPath {
+    __device__ uint8_t *node_end() const
+    {
+        return reinterpret_cast<uint8_t *>(node + npl * kF_N * 32);
+    }
+};
+
+template <int NPL, int CG, int D0, int D1>
+__global__ void __launch_bounds__(128, (anneal_min_blocks<NPL, D0, D1>()))
+    anneal_kernel(DevNet net, DevChains ch, DevSched sc, uint32_t region_bytes)
+{
+    extern __shared__ __align__(256) uint8_t sm[];
+    anneal_items(net, ch, sc, sm, region_bytes, [&](int warp, int wpb) {
+        RegPathR<NPL, CG, D0, D1> P;
+        P.sm = sm;
+        P.codes = (uint32_t)warp * kCodeBytesPerWarp;
+        P.region = sm + (uint32_t)wpb * kCodeBytesPerWarp + (uint32_t)warp * region_bytes;
+        return P;
+    });
+}
+
+// One resident grid; with more chains than resident warps, the steps of every
+// chain are cut into chunks of 16 so that all warps stay busy to the end (the
+// last round costs at most one chunk).
+inline void plan_chunks(DevSched &s, int64_t n_chains, int64_t warps)
+{
+    const int64_t steps = s.g1 - s.g0;
+    s.chunk = n_chains > warps ? (steps < 16 ? steps : 16) : steps;
+    if (s.chunk < 1) s.chunk = 1;
+    s.n_chunks = (int32_t)((steps + s.chunk - 1) / s.chunk);
 }
 
 template <int NPL, int CG, int D0, int D1>
@@ -336,8 +466,8 @@ cudaError_t launch_anneal_t(const DevNet &net, const DevChains &ch, const DevSch
                             int sm_count, cudaStream_t st)
 {
     const int wpb = 4;
-    const WarpSmem L = warp_smem(ch.pstride, net.N);
-    const size_t smem = (size_t)wpb * L.per_warp;
+    const WarpRegion R = warp_region(false, net.D, net.npl, ch.pstride, net.N);
+    const size_t smem = (size_t)wpb * (kCodeBytesPerWarp + R.bytes);
     auto kern = anneal_kernel<NPL, CG, D0, D1>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
@@ -346,18 +476,13 @@ cudaError_t launch_anneal_t(const DevNet &net, const DevChains &ch, const DevSch
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    // one resident grid; with more chains than resident warps, the steps of
-    // every chain are cut into chunks of 16 so that all warps stay busy to the
-    // end (the last round costs at most one chunk)
     const int grid = sm_count * per_sm;
-    const int64_t warps = (int64_t)grid * wpb, steps = sc.g1 - sc.g0;
     DevSched s = sc;
-    s.chunk = ch.n > warps ? (steps < 16 ? steps : 16) : steps;
-    s.n_chunks = (int32_t)((steps + s.chunk - 1) / s.chunk);
+    plan_chunks(s, ch.n, (int64_t)grid * wpb);
     err = cudaMemsetAsync(s.queue, 0, sizeof(unsigned int), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(s.done, 0, sizeof(int32_t) * (size_t)ch.n, st);
     if (err != cudaSuccess) return err;
-    kern<<<grid, wpb * 32, smem, st>>>(net, ch, s);
+    kern<<<grid, wpb * 32, smem, st>>>(net, ch, s, R.bytes);
     return cudaGetLastError();
 }
 

@@ -46,13 +46,32 @@ def test_evaluate_workloads(ctx, name):
         assert R.rn_evaluate(ctx, p.id, p.xs)[0] == 0
 
 
-@pytest.mark.parametrize("n_nodes", [2, 3, 5, 31, 32, 33, 63, 64, 65, 97, 127, 128])
+@pytest.mark.parametrize("n_nodes", [2, 3, 5, 31, 32, 33, 63, 64, 65, 97, 127, 128,
+                                     129, 160, 200, 300, 511])
 def test_evaluate_sizes(ctx, n_nodes):
-    # word and slot boundaries of the lane layout, 1-4 nodes per lane
+    # word and slot boundaries of the lane layout: 1-4 nodes per lane in
+    # registers, 5-16 nodes per lane with the shared-memory tables
     w = synth.random_network(100 + n_nodes, n_nodes, lam=3.0, cap=min(9, n_nodes - 1),
                              n_cond=3, n_times=9, obs_frac=0.4)
     p = Problem(w, ctx)
     _eval_parity(p, random_vectors(p.net, 12, n_nodes))
+
+
+@pytest.mark.parametrize("n_nodes,n_cond", [(150, 1), (300, 5)])
+def test_anneal_shared_memory_path(ctx, n_nodes, n_cond):
+    # networks above 128 nodes anneal with the shared-memory tables
+    w = synth.random_network(7 + n_nodes, n_nodes, lam=4.0, cap=12, n_cond=n_cond, n_times=9,
+                             obs_frac=0.3)
+    p = Problem(w, ctx)
+    n = 600
+    R.rn_init_chains(ctx, p.id, n, 5)
+    sched = R.schedule(4.0, 0.99)
+    R.rn_anneal(ctx, sched, 20)
+    R.rn_anneal(ctx, sched, 20)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    ids = [0, 1, 31, 32, 299, 598, 599]
+    ch = _oracle_run(p, 5, n, O.Schedule(4.0, 0.99), 0, 40, ids)
+    _compare(st, ch, ids)
 
 
 @pytest.mark.parametrize("T", [1, 2, 33])
@@ -232,9 +251,9 @@ def test_rejects_bad_input(ctx):
     with pytest.raises(R.RNError) as e:
         R.rn_init_chains(ctx, net, 2, 0, x0)
     assert e.value.code == R.RN_ECONSTRAINT
-    big = synth.random_network(3, 200, lam=3.0, cap=8, n_cond=1, n_times=4, obs_frac=0.5)
+    big = synth.random_network(3, 600, lam=3.0, cap=8, n_cond=1, n_times=4, obs_frac=0.5)
     bn = R.rn_load_network(ctx, big.src, big.dst, big.fast)
-    R.rn_load_timecourse(ctx, bn, big.init, np.zeros((1, 4, 200)), big.observed)
+    R.rn_load_timecourse(ctx, bn, big.init, np.zeros((1, 4, 600)), big.observed)
     with pytest.raises(R.RNError) as e:
         R.rn_init_chains(ctx, bn, 2, 0)
     assert e.value.code == R.RN_EUNSUPPORTED
