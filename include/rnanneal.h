@@ -186,6 +186,23 @@ int rn_set_chain_state(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed
 /* Number of kernels this context has launched since rn_create. */
 int rn_launch_count(rn_ctx *ctx, int64_t *count);
 
+/* Batched annealing.  When two or more networks of a context have chains (and
+ * the schedule has no global_sync), rn_anneal advances all of them in one
+ * persistent launch over every chain; results are bit-identical to annealing
+ * each network alone.  The first batched call tunes the launch on the real
+ * batch (table path per network -- register tables or shared-memory tables --
+ * and warps per block), timing each candidate for a few steps from the current
+ * state, which is restored afterwards.  With the threshold tables cached by
+ * rn_prepare_schedule, the launch is captured once in a CUDA graph and replayed.
+ * This reports the configuration in use:
+ *   info[0] networks in the batch (0: no batch yet)
+ *   info[1] warps per block
+ *   info[2] networks on the shared-memory table path
+ *   info[3] 1 if calls replay a CUDA graph
+ *   trial_ms[4] (may be NULL) milliseconds of the tuning candidates
+ *   (register tables where they fit / shared memory for all) x (4 / 2 warps). */
+int rn_batch_config(rn_ctx *ctx, int32_t info[4], double trial_ms[4]);
+
 /* For callers that cannot let a library allocate device memory -- an
  * application that owns every byte of the GPU through its own memory pool or
  * fixed arena and must not see cudaMalloc/cudaFree behind its back, or that

@@ -139,9 +139,43 @@ struct SchedCache {
     DevBuf<int32_t> off, len;
 };
 
+// Device descriptors of a batched launch over every network with chains, the
+// autotuned configuration, and the CUDA graph that replays the launch.
+struct BatchState {
+    bool valid = false;
+    uint64_t gen = 0;                 // context generation it was built for
+    std::vector<int> order;           // context network ids, most work per chain first
+    int32_t total = 0;
+    DevBuf<rn::DevNet> nets;
+    DevBuf<rn::DevChains> chains;
+    DevBuf<int64_t> g0;
+    DevBuf<int32_t> item_net, item_chain, path;
+    std::vector<int32_t> host_path;   // chosen table path per network (batch order)
+    uint32_t region_bytes = 0;
+    int wpb = 4, grid = 0;
+    bool tuned = false;
+    bool g0_synced = false;           // device g0 equals the host step counters
+    double tune_ms[4] = {0, 0, 0, 0}; // trial times of the candidate configurations
+    // graph of [queue reset, batched kernel, step advance]
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_sweeps = -1;
+    void drop_graph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        graph_sweeps = -1;
+    }
+    ~BatchState() { drop_graph(); }
+};
+
 struct rn_ctx {
     int device = 0;
     int64_t launches = 0;
+    uint64_t gen = 1;                 // bumped whenever networks or chains change
+    BatchState batch;
     SchedCache cache;
     int sm_count = 0;
     cudaStream_t stream = nullptr;
@@ -475,6 +509,281 @@ int build_thresholds(rn_ctx *ctx, const rn_schedule &s, int64_t l0, int64_t l1, 
     return RN_OK;
 }
 
+// Threshold tables of levels [l0, l1] into sc: the schedule cache when it
+// covers them (cached = true), else freshly built into the context buffers.
+int thresholds_for(rn_ctx *ctx, const rn_schedule &s, int64_t l0, int64_t l1, int64_t cap,
+                   DevSched &sc, bool &cached)
+{
+    const SchedCache &cc = ctx->cache;
+    cached = cc.valid && cc.T0 == s.T0 && cc.alpha == s.alpha && cc.iters == s.iters_per_level &&
+             l0 >= cc.l0 && l1 <= cc.l1 && cc.cap >= cap;
+    if (cached) {
+        sc.level0 = cc.l0;
+        sc.thr_off = cc.off.p;
+        sc.thr_len = cc.len.p;
+        sc.thr = cc.thr.p;
+        return RN_OK;
+    }
+    std::vector<uint32_t> thr;
+    std::vector<int32_t> off, len;
+    int rc = build_thresholds(ctx, s, l0, l1, cap, thr, off, len);
+    if (rc) return rc;
+    if (thr.empty()) thr.push_back(0);
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // earlier launches may read the tables
+    RN_CUDA(ctx, ctx->thr.reserve(thr.size()));
+    RN_CUDA(ctx, ctx->thr_off.reserve(off.size()));
+    RN_CUDA(ctx, ctx->thr_len.reserve(len.size()));
+    RN_CUDA(ctx, cudaMemcpy(ctx->thr.p, thr.data(), thr.size() * sizeof(uint32_t),
+                            cudaMemcpyHostToDevice));
+    RN_CUDA(ctx, cudaMemcpy(ctx->thr_off.p, off.data(), off.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice));
+    RN_CUDA(ctx, cudaMemcpy(ctx->thr_len.p, len.data(), len.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice));
+    sc.level0 = l0;
+    sc.thr_off = ctx->thr_off.p;
+    sc.thr_len = ctx->thr_len.p;
+    sc.thr = ctx->thr.p;
+    return RN_OK;
+}
+
+// Networks annealed together in one launch: every network with chains, when
+// all of them use groups of 4 conditions (the batched kernel's update).
+bool batchable(rn_ctx *ctx, const rn_schedule &s)
+{
+    int k = 0;
+    for (auto &np : ctx->nets) {
+        if (!np->chains_valid) continue;
+        if (np->cg != 4) return false;
+        ++k;
+    }
+    return k >= 2 && !s.global_sync;
+}
+
+int batch_region(rn_ctx *ctx, BatchState &B)
+{
+    B.region_bytes = 0;
+    for (size_t b = 0; b < B.order.size(); ++b) {
+        const Network &n = *ctx->nets[(size_t)B.order[b]];
+        B.region_bytes = std::max(B.region_bytes, batch_region_bytes(B.host_path[b] == 0, n.D,
+                                                                     n.npl, n.pstride, n.N));
+    }
+    RN_CUDA(ctx, B.path.upload(B.host_path));
+    const cudaError_t e = batch_resident_warps(B.wpb, B.region_bytes, ctx->sm_count, &B.grid);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batched kernel configuration");
+    return RN_OK;
+}
+
+int upload_batch_steps(rn_ctx *ctx, BatchState &B)
+{
+    std::vector<int64_t> g0;
+    for (int id : B.order) g0.push_back(ctx->nets[(size_t)id]->step);
+    RN_CUDA(ctx, cudaMemcpyAsync(B.g0.p, g0.data(), sizeof(int64_t) * g0.size(),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    B.g0_synced = true;
+    return RN_OK;
+}
+
+// Descriptors of every network with chains: work order (most work per chain
+// first), global chain lists, default table paths (register tables where the
+// batched kernel's capacities fit, shared memory otherwise).
+int build_batch(rn_ctx *ctx)
+{
+    BatchState &B = ctx->batch;
+    B.drop_graph();
+    B.valid = false;
+    B.order.clear();
+    for (size_t id = 0; id < ctx->nets.size(); ++id)
+        if (ctx->nets[id]->chains_valid) B.order.push_back((int)id);
+    auto work = [&](int id) {
+        const Network &n = *ctx->nets[(size_t)id];
+        return (int64_t)n.C * std::max(1, n.T - 1) * (n.N + n.E);
+    };
+    std::stable_sort(B.order.begin(), B.order.end(),
+                     [&](int a, int b) { return work(a) > work(b); });
+    std::vector<DevNet> nets;
+    std::vector<DevChains> chains;
+    std::vector<int32_t> item_net, item_chain;
+    B.host_path.clear();
+    for (size_t b = 0; b < B.order.size(); ++b) {
+        const Network &n = *ctx->nets[(size_t)B.order[b]];
+        nets.push_back(n.dev());
+        chains.push_back(n.chains());
+        int drest = 0;
+        for (int k = 1; k < n.npl; ++k) drest = std::max(drest, n.D[k]);
+        B.host_path.push_back(batch_path_fits(n.npl, n.D[0], drest) ? n.npl : 0);
+        for (int32_t c = 0; c < n.n_chains; ++c) {
+            item_net.push_back((int32_t)b);
+            item_chain.push_back(c);
+        }
+    }
+    B.total = (int32_t)item_net.size();
+    RN_CUDA(ctx, B.nets.upload(nets));
+    RN_CUDA(ctx, B.chains.upload(chains));
+    RN_CUDA(ctx, B.item_net.upload(item_net));
+    RN_CUDA(ctx, B.item_chain.upload(item_chain));
+    RN_CUDA(ctx, B.g0.alloc(B.order.size()));
+    RN_CUDA(ctx, ctx->done.reserve((size_t)B.total));
+    int rc = batch_region(ctx, B);
+    if (rc) return rc;
+    if ((rc = upload_batch_steps(ctx, B))) return rc;
+    B.tuned = false;
+    B.valid = true;
+    B.gen = ctx->gen;
+    return RN_OK;
+}
+
+DevBatch batch_desc(const BatchState &B, int64_t sweeps)
+{
+    DevBatch d{};
+    d.n_nets = (int32_t)B.order.size();
+    d.total = B.total;
+    d.sweeps = sweeps;
+    d.region_bytes = B.region_bytes;
+    d.nets = B.nets.p;
+    d.chains = B.chains.p;
+    d.g0 = B.g0.p;
+    d.item_net = B.item_net.p;
+    d.item_chain = B.item_chain.p;
+    d.path = B.path.p;
+    return d;
+}
+
+// Autotuner: the table path of the networks (register tables where they fit,
+// or shared-memory tables for all) and the warps per block (2 or 4), each
+// timed on the real batch for a few steps from the current state, which is
+// saved before and restored after the trials.  The fastest is kept.
+int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
+{
+    BatchState &B = ctx->batch;
+    size_t bytes = 0;
+    for (int id : B.order) {
+        const Network &n = *ctx->nets[(size_t)id];
+        bytes += (size_t)n.n_chains * (2 * (size_t)n.pstride + 8 + 24);
+    }
+    DevBuf<uint8_t> save;
+    RN_CUDA(ctx, save.alloc(bytes));
+    auto copy_state = [&](bool to_save) -> int {
+        size_t o = 0;
+        for (int id : B.order) {
+            const Network &n = *ctx->nets[(size_t)id];
+            const size_t rows = (size_t)n.n_chains * n.pstride;
+            void *bufs[5] = {n.d_x_cur.p, n.d_x_best.p, n.d_d_cur.p, n.d_d_best.p, n.d_cnt.p};
+            const size_t sz[5] = {rows, rows, 4 * (size_t)n.n_chains, 4 * (size_t)n.n_chains,
+                                  24 * (size_t)n.n_chains};
+            for (int k = 0; k < 5; ++k) {
+                void *dst = to_save ? (void *)(save.p + o) : bufs[k];
+                const void *src = to_save ? bufs[k] : (const void *)(save.p + o);
+                RN_CUDA(ctx, cudaMemcpyAsync(dst, src, sz[k], cudaMemcpyDeviceToDevice,
+                                             ctx->stream));
+                o += sz[k];
+            }
+        }
+        return RN_OK;
+    };
+    const std::vector<int32_t> best_fit = B.host_path;
+    std::vector<int32_t> all_smem(B.host_path.size(), 0);
+    const int64_t trial = std::min<int64_t>(sweeps, 16);
+    double best = 1e300;
+    int best_cfg = 0;
+    cudaEvent_t e0, e1;
+    RN_CUDA(ctx, cudaEventCreate(&e0));
+    RN_CUDA(ctx, cudaEventCreate(&e1));
+    int rc = copy_state(true);
+    for (int cfg = 0; cfg < 4 && !rc; ++cfg) {
+        B.host_path = (cfg & 1) ? all_smem : best_fit;
+        B.wpb = (cfg & 2) ? 2 : 4;
+        if ((rc = batch_region(ctx, B))) break;
+        DevSched sc = sc0;
+        sc.g0 = 0;
+        sc.g1 = trial;
+        plan_chunks(sc, B.total, (int64_t)B.grid * B.wpb);
+        const DevBatch d = batch_desc(B, trial);
+        cudaEventRecord(e0, ctx->stream);
+        const cudaError_t e = launch_batch(d, sc, B.wpb, B.grid, ctx->stream);
+        cudaEventRecord(e1, ctx->stream);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "batched kernel (autotune)"); break; }
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = RN_ECUDA; break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        B.tune_ms[cfg] = ms;
+        if (ms < best) { best = ms; best_cfg = cfg; }
+        if ((rc = copy_state(false))) break;
+        if ((rc = upload_batch_steps(ctx, B))) break;
+        ctx->launches += 2;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (int frc = check_device_flag(ctx)) return frc;
+    B.host_path = (best_cfg & 1) ? all_smem : best_fit;
+    B.wpb = (best_cfg & 2) ? 2 : 4;
+    if ((rc = batch_region(ctx, B))) return rc;
+    B.tuned = true;
+    return RN_OK;
+}
+
+// Every network with chains advances by `sweeps` steps in one persistent
+// launch; with cached threshold tables the launch is replayed from a CUDA graph.
+int anneal_batched(rn_ctx *ctx, const rn_schedule &s, int64_t sweeps)
+{
+    BatchState &B = ctx->batch;
+    int rc;
+    if (!B.valid || B.gen != ctx->gen)
+        if ((rc = build_batch(ctx))) return rc;
+    const int64_t iters = s.iters_per_level;
+    int64_t lmin = INT64_MAX, lmax = 0, cap = 1;
+    for (int id : B.order) {
+        const Network &n = *ctx->nets[(size_t)id];
+        lmin = std::min(lmin, n.step / iters);
+        lmax = std::max(lmax, (n.step + sweeps - 1) / iters);
+        cap = std::max(cap, n.max_score);
+    }
+    DevSched sc{};
+    bool cached = false;
+    if ((rc = thresholds_for(ctx, s, lmin, lmax, cap, sc, cached))) return rc;
+    sc.iters = iters;
+    sc.reset_to_best = s.reset_to_best;
+    sc.queue = ctx->queue.p;
+    sc.done = ctx->done.p;
+    sc.err = ctx->dev_err.p;
+    if (!B.tuned) {
+        B.drop_graph();
+        if ((rc = tune_batch(ctx, sc, sweeps))) return rc;
+    }
+    if (!B.g0_synced) {
+        B.drop_graph();
+        if ((rc = upload_batch_steps(ctx, B))) return rc;
+    }
+    sc.g0 = 0;
+    sc.g1 = sweeps;
+    plan_chunks(sc, B.total, (int64_t)B.grid * B.wpb);
+    const DevBatch d = batch_desc(B, sweeps);
+    if (cached) {
+        const bool same = B.exec && B.graph_sweeps == sweeps;
+        if (!same) {
+            B.drop_graph();
+            RN_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            const cudaError_t e = launch_batch(d, sc, B.wpb, B.grid, ctx->stream);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "batched kernel (capture)");
+            if (ec != cudaSuccess) return cuda_fail(ctx, ec, "cudaStreamEndCapture");
+            B.graph = g;
+            RN_CUDA(ctx, cudaGraphInstantiate(&B.exec, B.graph, 0));
+            B.graph_sweeps = sweeps;
+        }
+        RN_CUDA(ctx, cudaGraphLaunch(B.exec, ctx->stream));
+    } else {
+        const cudaError_t e = launch_batch(d, sc, B.wpb, B.grid, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batched kernel");
+    }
+    ctx->launches += 2;
+    for (int id : B.order) ctx->nets[(size_t)id]->step += sweeps;
+    return RN_OK;
+}
+
 }  // namespace
 
 namespace rn {
@@ -608,6 +917,7 @@ int rn_load_network(rn_ctx *ctx, int32_t n_nodes, int32_t n_edges, const int32_t
     }
     *net_id = (int32_t)ctx->nets.size();
     ctx->nets.push_back(std::move(n));
+    ctx->gen++;
     return RN_OK;
 }
 
@@ -708,6 +1018,7 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     RN_CUDA(ctx, n->d_init_s4.upload(init_s4));
     RN_CUDA(ctx, n->d_movable.upload(movable));
     n->cg = cg;
+    ctx->gen++;
     n->G = G;
     return RN_OK;
 }
@@ -765,6 +1076,7 @@ int rn_init_chains(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed, co
         return rc;
     RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     n->chains_valid = true;
+    ctx->gen++;
     return RN_OK;
 }
 
@@ -781,6 +1093,10 @@ int rn_anneal(rn_ctx *ctx, const rn_schedule *s, int64_t sweeps)
     for (auto &np : ctx->nets) any |= np->chains_valid;
     if (!any) return fail(ctx, RN_ESTATE, "no network has chains (call rn_init_chains)");
     RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (sweeps == 0) return RN_OK;
+    // several networks: one persistent launch over all of their chains
+    if (batchable(ctx, *s)) return anneal_batched(ctx, *s, sweeps);
+    ctx->batch.g0_synced = false;
     const int64_t iters = s->iters_per_level;
     // at most this many threshold entries per launch segment
     const size_t budget = (size_t)1 << 24;
@@ -876,6 +1192,7 @@ int rn_prepare_schedule(rn_ctx *ctx, const rn_schedule *s, int64_t total_steps)
     if (thr.empty()) thr.push_back(0);
     RN_CUDA(ctx, cudaSetDevice(ctx->device));
     RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->batch.drop_graph();   // a replayed graph reads the old tables
     SchedCache &cc = ctx->cache;
     cc.valid = false;
     RN_CUDA(ctx, cc.thr.alloc(thr.size()));
@@ -901,6 +1218,23 @@ int rn_launch_count(rn_ctx *ctx, int64_t *count)
 {
     if (!ctx || !count) return RN_EINVAL;
     *count = ctx->launches;
+    return RN_OK;
+}
+
+int rn_batch_config(rn_ctx *ctx, int32_t info[4], double trial_ms[4])
+{
+    if (!ctx || !info) return RN_EINVAL;
+    const BatchState &B = ctx->batch;
+    const bool on = B.valid && B.gen == ctx->gen;
+    info[0] = on ? (int32_t)B.order.size() : 0;
+    info[1] = on ? B.wpb : 0;
+    int32_t shared = 0;
+    if (on)
+        for (int32_t p : B.host_path) shared += p == 0;
+    info[2] = shared;
+    info[3] = on && B.exec ? 1 : 0;
+    if (trial_ms)
+        for (int k = 0; k < 4; ++k) trial_ms[k] = B.tune_ms[k];
     return RN_OK;
 }
 
@@ -1044,6 +1378,7 @@ int rn_set_chain_state(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed
     n->seed = seed;
     n->step = step;
     n->chains_valid = true;
+    ctx->gen++;
     return RN_OK;
 }
 

@@ -1,0 +1,154 @@
+// rn_batch.cu -- one persistent launch over the chains of many networks.
+//
+// Every chain of every network is one "global chain" r; global chains are
+// ordered by network, the network with the most work per chain first.  Work
+// item i is chunk i / total of global chain i % total, so that, as in the
+// single-network kernel, the predecessor of an item (the previous chunk of the
+// same chain) was handed out `total` items earlier.  Each warp copies the
+// descriptors of its item's network into its shared memory and runs the chunk
+// with that network's table path: register tables with 1, 2 or 4 nodes per
+// lane, or the shared-memory tables.  Results are those of separate
+// single-network runs, bit for bit (same per-chain code, same Philox counters).
+#include "rn_kernels.cuh"
+
+namespace rn {
+
+// Register-table capacities of the batched kernel: slot 0 up to 16 in-edges,
+// the other slots up to 8; a network that needs more uses the shared-memory path.
+constexpr int kBatchD0 = 16, kBatchD1 = 8;
+
+// Code region, then the per-warp copies of the item's DevNet and DevChains,
+// rounded up so that the warp regions stay 256-byte aligned.
+__host__ __device__ inline uint32_t batch_head_bytes(int wpb)
+{
+    const uint32_t b = (uint32_t)wpb * (kCodeBytesPerWarp + (uint32_t)sizeof(DevNet) +
+                                        (uint32_t)sizeof(DevChains));
+    return (b + 255u) & ~255u;
+}
+
+__device__ __forceinline__ void warp_copy_words(void *dst, const void *src, int bytes, int lane)
+{
+    uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    for (int k = lane; k < bytes / 4; k += 32) d[k] = __ldcg(s + k);
+}
+
+__global__ void __launch_bounds__(128, 2) anneal_batch_kernel(DevBatch b, DevSched sc)
+{
+    extern __shared__ __align__(256) uint8_t sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    uint8_t *desc = sm + (uint32_t)wpb * kCodeBytesPerWarp;
+    DevNet *net_s = reinterpret_cast<DevNet *>(desc) + warp;
+    DevChains *ch_s =
+        reinterpret_cast<DevChains *>(desc + (uint32_t)wpb * sizeof(DevNet)) + warp;
+    uint8_t *region = sm + batch_head_bytes(wpb) + (uint32_t)warp * b.region_bytes;
+    const uint32_t codes = (uint32_t)warp * kCodeBytesPerWarp;
+    const int64_t n_items = (int64_t)sc.n_chunks * b.total;
+    for (;;) {
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(sc.queue, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if ((int64_t)item >= n_items) break;
+        const int cj = (int)(item / (unsigned)b.total);
+        const int r = (int)(item - (unsigned)cj * (unsigned)b.total);
+        if (cj > 0 && !wait_for_chunk(sc.done + r, cj, sc.err, lane)) return;
+        const int nb = __ldg(b.item_net + r), chain = __ldg(b.item_chain + r);
+        warp_copy_words(net_s, b.nets + nb, (int)sizeof(DevNet), lane);
+        warp_copy_words(ch_s, b.chains + nb, (int)sizeof(DevChains), lane);
+        __syncwarp();
+        const DevNet &net = *net_s;
+        const DevChains &ch = *ch_s;
+        const int64_t g0 = __ldcg(b.g0 + nb);
+        const int64_t g_lo = g0 + (int64_t)cj * sc.chunk;
+        const int64_t g_hi = min(g0 + b.sweeps, g_lo + sc.chunk);
+        const int path = __ldg(b.path + nb);
+        int32_t *flag = sc.done + r;
+        if (path == 1) {
+            RegPath<1, 4, kBatchD0, 1> P;
+            P.sm = sm;
+            P.codes = codes;
+            int8_t *xs = reinterpret_cast<int8_t *>(region);
+            uint8_t *on = region + ch.pstride, *pi = on + round16((uint32_t)net.N);
+            run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, cj + 1, lane);
+        } else if (path == 2) {
+            RegPath<2, 4, kBatchD0, kBatchD1> P;
+            P.sm = sm;
+            P.codes = codes;
+            int8_t *xs = reinterpret_cast<int8_t *>(region);
+            uint8_t *on = region + ch.pstride, *pi = on + round16((uint32_t)net.N);
+            run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, cj + 1, lane);
+        } else if (path == 4) {
+            RegPath<4, 4, kBatchD0, kBatchD1> P;
+            P.sm = sm;
+            P.codes = codes;
+            int8_t *xs = reinterpret_cast<int8_t *>(region);
+            uint8_t *on = region + ch.pstride, *pi = on + round16((uint32_t)net.N);
+            run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, cj + 1, lane);
+        } else {
+            SmemPath P;
+            P.sm = sm;
+            P.codes = codes;
+            P.npl = net.npl;
+            const uint32_t lw = smem_path_lut_words(net.D, net.npl);
+            P.lut = reinterpret_cast<uint32_t *>(region);
+            P.node = P.lut + lw;
+            uint8_t *after = reinterpret_cast<uint8_t *>(P.node + net.npl * kF_N * 32);
+            int8_t *xs = reinterpret_cast<int8_t *>(after);
+            uint8_t *on = after + ch.pstride, *pi = on + round16((uint32_t)net.N);
+            run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, cj + 1, lane);
+        }
+    }
+}
+
+// Every network has advanced by `sweeps` steps.
+__global__ void advance_kernel(int64_t *g0, int32_t n_nets, int64_t sweeps)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_nets) g0[k] += sweeps;
+}
+
+bool batch_path_fits(int npl, int D0, int Drest)
+{
+    if (npl > kRegSlots) return false;
+    if (D0 > kBatchD0) return false;
+    return npl == 1 || Drest <= kBatchD1;
+}
+
+uint32_t batch_region_bytes(bool smem_path, const int *D, int npl, int pstride, int N)
+{
+    return warp_region(smem_path, D, npl, pstride, N).bytes;
+}
+
+cudaError_t batch_resident_warps(int wpb, uint32_t region_bytes, int sm_count, int *grid)
+{
+    const size_t smem = batch_head_bytes(wpb) + (size_t)wpb * region_bytes;
+    cudaError_t err = cudaFuncSetAttribute(anneal_batch_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, anneal_batch_kernel, wpb * 32,
+                                                        smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    *grid = sm_count * per_sm;
+    return cudaSuccess;
+}
+
+// Queue reset, the batched kernel and the step advance, in stream order (the
+// sequence that rn_anneal captures in a CUDA graph).
+cudaError_t launch_batch(const DevBatch &b, const DevSched &sc, int wpb, int grid,
+                         cudaStream_t st)
+{
+    const size_t smem = batch_head_bytes(wpb) + (size_t)wpb * b.region_bytes;
+    cudaError_t err = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned int), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(sc.done, 0, sizeof(int32_t) * (size_t)b.total, st);
+    if (err != cudaSuccess) return err;
+    anneal_batch_kernel<<<grid, wpb * 32, smem, st>>>(b, sc);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    advance_kernel<<<(b.n_nets + 127) / 128, 128, 0, st>>>(b.g0, b.n_nets, b.sweeps);
+    return cudaGetLastError();
+}
+
+}  // namespace rn

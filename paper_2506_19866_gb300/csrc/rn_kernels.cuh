@@ -450,17 +450,6 @@ __global__ void __launch_bounds__(128, (anneal_min_blocks<NPL, D0, D1>()))
     });
 }
 
-// One resident grid; with more chains than resident warps, the steps of every
-// chain are cut into chunks of 16 so that all warps stay busy to the end (the
-// last round costs at most one chunk).
-inline void plan_chunks(DevSched &s, int64_t n_chains, int64_t warps)
-{
-    const int64_t steps = s.g1 - s.g0;
-    s.chunk = n_chains > warps ? (steps < 16 ? steps : 16) : steps;
-    if (s.chunk < 1) s.chunk = 1;
-    s.n_chunks = (int32_t)((steps + s.chunk - 1) / s.chunk);
-}
-
 template <int NPL, int CG, int D0, int D1>
 cudaError_t launch_anneal_t(const DevNet &net, const DevChains &ch, const DevSched &sc,
                             int sm_count, cudaStream_t st)

@@ -9,6 +9,17 @@
 
 namespace rn {
 
+// One resident grid; with more chains than resident warps, the steps of every
+// chain are cut into chunks of 16 so that all warps stay busy to the end (the
+// last round costs at most one chunk).
+inline void plan_chunks(DevSched &s, int64_t n_chains, int64_t warps)
+{
+    const int64_t steps = s.g1 - s.g0;
+    s.chunk = n_chains > warps ? (steps < 16 ? steps : 16) : steps;
+    if (s.chunk < 1) s.chunk = 1;
+    s.n_chunks = (int32_t)((steps + s.chunk - 1) / s.chunk);
+}
+
 // Layouts compiled for the warp-per-chain kernels: 1, 2 or 4 nodes per lane
 // (N <= 128), 1 or 4 conditions per group, register capacity d0 for slot 0 and
 // d1 for the other slots (in-edges per node up to 16).
@@ -24,5 +35,24 @@ cudaError_t launch_anneal(const DevNet &net, int d0, int d1, const DevChains &ch
                           const DevSched &sc, int sm_count, cudaStream_t st);
 cudaError_t launch_init(const DevNet &net, const DevChains &ch, int32_t *status, cudaStream_t st);
 cudaError_t launch_level_sync(const DevChains &ch, int32_t *winner, cudaStream_t st);
+
+// Many networks in one persistent launch (rn_batch.cu).
+struct DevBatch {
+    int32_t n_nets, total;              // networks; chains over all networks
+    int64_t sweeps;                     // steps every chain advances
+    uint32_t region_bytes;              // shared memory of one warp region
+    const DevNet *nets;                 // [n_nets]
+    const DevChains *chains;            // [n_nets]
+    int64_t *g0;                        // [n_nets] next step of each network (advanced on device)
+    const int32_t *item_net;            // [total] network of global chain r
+    const int32_t *item_chain;          // [total] chain index within its network
+    const int32_t *path;                // [n_nets] 1, 2, 4: register tables; 0: shared memory
+};
+
+bool batch_path_fits(int npl, int D0, int Drest);
+uint32_t batch_region_bytes(bool smem_path, const int *D, int npl, int pstride, int N);
+cudaError_t batch_resident_warps(int wpb, uint32_t region_bytes, int sm_count, int *grid);
+cudaError_t launch_batch(const DevBatch &b, const DevSched &sc, int wpb, int grid,
+                         cudaStream_t st);
 
 }  // namespace rn

@@ -49,6 +49,7 @@ SIGNATURES = {
                                     _c_i64]),
     "rn_prepare_schedule": (_c_int, [_vp, ctypes.POINTER(rn_schedule), _c_i64]),
     "rn_launch_count": (_c_int, [_vp, _vp]),
+    "rn_batch_config": (_c_int, [_vp, _vp, _vp]),
     "rn_level_sync_noalloc": (_c_int, [_vp, _vp, _c_i32, _c_i64, _c_i32, _vp]),
     "rn_synchronize": (_c_int, [_vp]),
 }
@@ -211,6 +212,15 @@ def rn_launch_count(ctx):
     out = ctypes.c_int64(0)
     _check(ctx, load_library().rn_launch_count(ctx, ctypes.byref(out)))
     return out.value
+
+
+def rn_batch_config(ctx):
+    """(networks, warps per block, shared-memory-path networks, graph replay, trial ms)."""
+    info = np.zeros(4, np.int32)
+    ms = np.zeros(4, np.float64)
+    _check(ctx, load_library().rn_batch_config(ctx, _p(info), _p(ms)))
+    return dict(networks=int(info[0]), warps_per_block=int(info[1]),
+                shared_path_networks=int(info[2]), graph=bool(info[3]), trial_ms=ms.tolist())
 
 
 def rn_level_sync_noalloc(x_best_dev, d_best_dev, n_chains, row_bytes, n_params, stream=None):

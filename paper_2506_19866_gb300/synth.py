@@ -228,6 +228,36 @@ def make(name: str) -> Workload:
 WORKLOADS = ("n15_c3_t11", "n120_c8_t21", "hpg_9n_25e", "mtb_63n_178e")
 
 
+def make_batch(n_nets=256, total_chains=65536, seed=1003, n_min=10, n_max=300, max_indeg=16):
+    """Many independent networks of uneven size annealed together: node counts
+    log-uniform in [n_min, n_max], in-degree Poisson(4) (at least 1, at most
+    max_indeg), 2-12 conditions, 8-32 update steps, 20% observed entries, and
+    chains per network proportional to its parameter count (total_chains in
+    all, at least one each).  Returns a list of Workloads."""
+    rng = np.random.default_rng(seed)
+    nets = []
+    for b in range(n_nets):
+        N = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        cap = min(N - 1, max_indeg)
+        src, dst = random_digraph(N, np.clip(rng.poisson(4.0, size=N), 1, cap), rng)
+        fast = speed_classes(N, rng)
+        C = int(rng.integers(2, 13))
+        T = int(rng.integers(8, 33)) + 1
+        init, ko = conditions(N, C, rng)
+        obs = bernoulli_mask(C, T, N, 0.2, rng)
+        nets.append(Workload(f"batch{b}", src, dst, fast, init, ko, obs, T,
+                             planted_seed=20000 + b, noise_frac=0.0, noise_seed=30000 + b,
+                             chain_seed=b, n_chains=1, sweeps=2000, T0=10.0, alpha=0.995))
+    P = np.array([w.P for w in nets], dtype=np.float64)
+    share = np.maximum(1, np.floor(total_chains * P / P.sum())).astype(np.int64)
+    rest = total_chains - int(share.sum())
+    for b in np.argsort(-P)[:max(0, rest)]:
+        share[b] += 1
+    for w, n in zip(nets, share):
+        w.n_chains = int(n)
+    return nets
+
+
 def tiny(seed, n_nodes=4, indeg=2, n_cond=2, n_times=6, obs_frac=0.5):
     """A small random workload for parity and brute-force tests."""
     rng = np.random.default_rng(seed)

@@ -1,0 +1,88 @@
+"""Batched annealing of uneven networks in one persistent launch: every chain of
+every network must end bit-identical to annealing that network alone (which
+the single-network tests tie to the CPU oracle), through the autotuning trials
+and through CUDA-graph replays."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2506_19866_gb300 import rnanneal as R
+from paper_2506_19866_gb300 import synth
+from tests.gpu_util import Problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch():
+    nets = synth.make_batch(n_nets=7, total_chains=700, seed=11, n_min=8, n_max=300)
+    # one more network above 128 nodes (shared-memory tables) and a tiny one
+    extra = synth.make_batch(n_nets=2, total_chains=90, seed=3, n_min=200, n_max=260)
+    small = synth.make_batch(n_nets=1, total_chains=40, seed=4, n_min=10, n_max=12)
+    nets = nets + extra + small
+    sizes = [w.N for w in nets]
+    assert min(sizes) <= 32 and max(sizes) > 128
+    return nets
+
+
+def _state_all(ctx, probs, nets):
+    return [R.rn_get_chain_state(ctx, p.id, w.n_chains) for p, w in zip(probs, nets)]
+
+
+def test_batched_equals_separate_runs():
+    from paper_2506_19866_gb300 import build
+    build.build()
+    nets = _batch()
+    sched = R.schedule(6.0, 0.99)
+    sweeps = 24
+    ctx = R.rn_create(0)
+    try:
+        probs = [Problem(w, ctx) for w in nets]
+        for p, w in zip(probs, nets):
+            R.rn_init_chains(ctx, p.id, w.n_chains, w.chain_seed)
+        R.rn_prepare_schedule(ctx, sched, 4 * sweeps)
+        R.rn_anneal(ctx, sched, sweeps)           # tunes, then runs
+        cfg = R.rn_batch_config(ctx)
+        assert cfg["networks"] == len(nets) and cfg["warps_per_block"] in (2, 4)
+        assert all(t > 0 for t in cfg["trial_ms"])
+        R.rn_anneal(ctx, sched, sweeps)           # graph capture and replay
+        R.rn_anneal(ctx, sched, sweeps)
+        assert R.rn_batch_config(ctx)["graph"]
+        batched = _state_all(ctx, probs, nets)
+    finally:
+        R.rn_destroy(ctx)
+    for p, w, st in zip(probs, nets, batched):
+        c1 = R.rn_create(0)
+        try:
+            q = Problem(w, c1)
+            R.rn_init_chains(c1, q.id, w.n_chains, w.chain_seed)
+            R.rn_anneal(c1, sched, 3 * sweeps)
+            alone = R.rn_get_chain_state(c1, q.id, w.n_chains)
+        finally:
+            R.rn_destroy(c1)
+        for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"):
+            np.testing.assert_array_equal(st[k], alone[k], err_msg=f"{w.name} N={w.N} {k}")
+        assert st["step"] == alone["step"] == 3 * sweeps
+
+
+def test_batched_chain_matches_oracle():
+    # one chain of the largest network (shared-memory path in the batch)
+    from paper_2506_19866_gb300 import build
+    build.build()
+    nets = _batch()
+    big = max(range(len(nets)), key=lambda b: nets[b].N)
+    sched = R.schedule(6.0, 0.99)
+    ctx = R.rn_create(0)
+    try:
+        probs = [Problem(w, ctx) for w in nets]
+        for p, w in zip(probs, nets):
+            R.rn_init_chains(ctx, p.id, w.n_chains, w.chain_seed)
+        R.rn_anneal(ctx, sched, 12)
+        st = R.rn_get_chain_state(ctx, probs[big].id, nets[big].n_chains)
+    finally:
+        R.rn_destroy(ctx)
+    p, w = probs[big], nets[big]
+    ids = [0, w.n_chains - 1]
+    ch = O.start_chains(p.net, p.tc, w.chain_seed, len(ids), chain_ids=ids)
+    O.anneal(p.net, p.tc, O.Schedule(6.0, 0.99), w.chain_seed, ch, 0, 12, chain_ids=ids)
+    np.testing.assert_array_equal(st["x_cur"][ids], ch.x_cur)
+    np.testing.assert_array_equal(st["d_best"][ids], ch.d_best)
