@@ -55,13 +55,33 @@ def algorithmic_ops_per_eval(w):
     return w.C * (w.T - 1) * (2 * w.E + 12 * w.N) + 3 * int(w.observed.sum())
 
 
-def workload_config(w, sweeps_per_step):
-    return {"workload": w.name, "nodes": w.N, "edges": w.E, "params": w.P, "conditions": w.C,
-            "time_points": w.T, "chains": w.n_chains, "sweeps_per_step": sweeps_per_step,
-            "full_run_sweeps": w.sweeps, "schedule": f"geometric T0={w.T0} alpha={w.alpha:.10f}",
-            "noise_frac": w.noise_frac,
-            "l2": "working set (network tables + chain state, ~20 MB) is L2-resident by design; "
-                  "L2 flushed with a 512 MiB write between timed steps, outside the step events"}
+L2_NOTE = ("working set (network tables + chain state) is L2-resident by design; L2 flushed "
+           "with a 512 MiB write between timed steps, outside the step events")
+
+
+def workload_set(name):
+    """The networks of a benchmark workload: one, or the batch of 256 uneven ones."""
+    if name == "batch256":
+        return synth.make_batch()
+    return [synth.make(name)]
+
+
+def workload_config(ws, sweeps_per_step, name):
+    if len(ws) == 1:
+        w = ws[0]
+        return {"workload": w.name, "nodes": w.N, "edges": w.E, "params": w.P,
+                "conditions": w.C, "time_points": w.T, "chains": w.n_chains,
+                "sweeps_per_step": sweeps_per_step, "full_run_sweeps": w.sweeps,
+                "schedule": f"geometric T0={w.T0} alpha={w.alpha:.10f}",
+                "noise_frac": w.noise_frac, "l2": L2_NOTE}
+    N = np.array([w.N for w in ws])
+    return {"workload": name, "networks": len(ws),
+            "nodes": f"{N.min()}-{N.max()} (median {int(np.median(N))}, log-uniform 10-300)",
+            "edges_total": int(sum(w.E for w in ws)), "params_total": int(sum(w.P for w in ws)),
+            "conditions": "2-12", "time_points": "9-33",
+            "chains": int(sum(w.n_chains for w in ws)), "chains_per_network": "proportional to P",
+            "sweeps_per_step": sweeps_per_step,
+            "schedule": f"geometric T0={ws[0].T0} alpha={ws[0].alpha}", "l2": L2_NOTE}
 
 
 # ------------------------------------------------------------------ clocks --
@@ -188,7 +208,8 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": workload_config(w, args.sweeps_per_step),
+            "data": "synthetic",
+            "config": workload_config([w], args.sweeps_per_step, args.workload),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": samples[0] + f"; {args.steps} such steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -235,21 +256,25 @@ def run_ours(args, rank, world, local_rank):
     # library would read as "create your own"
     stream = torch.cuda.Stream(device=local_rank)
     torch.cuda.set_stream(stream)
-    w = synth.make(args.workload)
+    ws = workload_set(args.workload)
     S = args.sweeps_per_step
     ctx = R.rn_create(local_rank, stream.cuda_stream)
-    nid, ref = setup_problem(R, ctx, w)
-    seed = w.chain_seed + rank
-    R.rn_init_chains(ctx, nid, w.n_chains, seed)
-    sched = R.schedule(w.T0, w.alpha)
+    ids = [setup_problem(R, ctx, w)[0] for w in ws]
+    for nid, w in zip(ids, ws):   # every rank anneals its own replica of the chains
+        R.rn_init_chains(ctx, nid, w.n_chains, w.chain_seed + 1000003 * rank)
+    sched = R.schedule(ws[0].T0, ws[0].alpha)
     R.rn_prepare_schedule(ctx, sched, (args.warmup + args.steps) * S)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         R.rn_anneal(ctx, sched, S)
     R.rn_synchronize(ctx)
-    before = R.rn_get_chain_state(ctx, nid, w.n_chains)["counters"]
-    l0 = R.rn_launch_count(ctx)
 
+    def nulls_now():
+        return [int(R.rn_get_chain_state(ctx, nid, w.n_chains)["counters"][:, 2].sum())
+                for nid, w in zip(ids, ws)]
+
+    before = nulls_now()
+    l0 = R.rn_launch_count(ctx)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -274,9 +299,9 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     launches = R.rn_launch_count(ctx) - l0
     step_ms = [a.elapsed_time(b) for a, b in times]
-    after = R.rn_get_chain_state(ctx, nid, w.n_chains)["counters"]
-    nulls = int((after[:, 2] - before[:, 2]).sum())
-    evals = w.n_chains * S * args.steps - nulls
+    nulls = [a - b for a, b in zip(nulls_now(), before)]
+    evals_w = [w.n_chains * S * args.steps - z for w, z in zip(ws, nulls)]
+    evals = sum(evals_w)
     total_s = sum(step_ms) / 1000.0
 
     t_max, evals_all = total_s, evals
@@ -288,76 +313,85 @@ def run_ours(args, rank, world, local_rank):
         t_max, evals_all = float(t.item()), int(e.item())
     value = evals_all / t_max
 
-    # roofline of the anneal kernel (the only kernel of a step)
-    ops_eval = algorithmic_ops_per_eval(w)
-    per_launch_ops = ops_eval * evals / max(1, launches)
-    mean_launch_s = total_s / max(1, launches)
-    achieved = per_launch_ops / mean_launch_s
+    # roofline of the annealing kernel, the only kernel of a step (a batch step
+    # also runs a one-thread-per-network step-advance kernel)
+    ops = sum(algorithmic_ops_per_eval(w) * ev for w, ev in zip(ws, evals_w))
+    kernel_launches = args.steps
+    achieved = (ops / kernel_launches) / (total_s / kernel_launches)
     peaks = peak_int32(local_rank) if rank == 0 else {}
     sm_count = torch.cuda.get_device_properties(local_rank).multi_processor_count
     f_hz = (clk.get("sm_mhz") or 0.0) * 1e6
     alu_per_clk = peaks.get("alu", 0.0)
     peak = sm_count * alu_per_clk * f_hz if f_hz and alu_per_clk > 0 else None
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": None if peak is None else peak / 1e12,
-                "unit": "Tops/s", "frac": None if peak is None else achieved / peak,
-                "traffic": None,
-                "kernel": "anneal_kernel", "ops_per_eval": ops_eval,
+    roofline = {"bound": "alu", "achieved": achieved / 1e12,
+                "peak": None if peak is None else peak / 1e12, "unit": "Tops/s",
+                "frac": None if peak is None else achieved / peak, "traffic": None,
+                "kernel": "anneal_batch_kernel" if len(ws) > 1 else "anneal_kernel",
+                "ops_per_eval": (algorithmic_ops_per_eval(ws[0]) if len(ws) == 1
+                                 else "C (T-1) (2E + 12N) + 3 n_obs per network"),
                 "peak_basis": (f"{sm_count} SMs x {alu_per_clk:.1f} int32 ALU ops/clk/SM "
                                f"(measured, peaks.cu) x median SM clock {clk.get('sm_mhz')} MHz "
                                "sampled during the timed steps"),
                 "measured_issue_rates_per_sm_clk": peaks}
-
+    node_updates = sum(ev * w.C * (w.T - 1) * w.N for w, ev in zip(ws, evals_w)) / total_s
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": workload_config(w, S),
-            "node_updates_per_s": value * w.C * (w.T - 1) * w.N,
-            "null_moves_frac": nulls / (w.n_chains * S * args.steps),
+            "config": workload_config(ws, S, args.workload),
+            "node_updates_per_s": node_updates * evals_all / max(1, evals),
+            "null_moves_frac": sum(nulls) / (sum(w.n_chains for w in ws) * S * args.steps),
             "wall_s_timed_loop": t_wall,
             "roofline": roofline, "clocks": clk, "gpu_launches": launches}
-
+    if len(ws) > 1:
+        line["batch"] = R.rn_batch_config(ctx)
     if rank == 0 and not args.no_e2e:
-        line["e2e"] = e2e(args, R, w, local_rank, stream)
+        line["e2e"] = e2e(args, R, ws, local_rank, stream)
     R.rn_destroy(ctx)
-    if rank == 0 and not args.no_cpu_baseline and world == 1:
+    if rank == 0 and not args.no_cpu_baseline and world == 1 and len(ws) == 1:
         line["cpu_baseline"] = oracle_rate(args.workload, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def e2e(args, R, w, device, stream):
+def e2e(args, R, ws, device, stream):
     """Whole user path per step through the C ABI with host buffers: create a
-    context, load the network and the time courses, draw the chains, anneal
-    one step, read the best vector back."""
+    context, load the networks and their time courses, draw the chains, anneal
+    one step, read each network's best vector back."""
     import torch
-    nid_ref = None
+    refs = []
     ctx0 = R.rn_create(device, stream.cuda_stream)
-    _, ref = setup_problem(R, ctx0, w)
+    for w in ws:
+        refs.append(setup_problem(R, ctx0, w)[1])
     R.rn_destroy(ctx0)
     S = args.sweeps_per_step
-    h2d = (w.src.nbytes + w.dst.nbytes + w.fast.nbytes + w.init.nbytes + w.knockout.nbytes
-           + ref.nbytes + w.observed.nbytes)
-    d2h = w.P + 4 * w.n_chains + 8
+    h2d = sum(w.src.nbytes + w.dst.nbytes + w.fast.nbytes + w.init.nbytes + w.knockout.nbytes
+              + ref.nbytes + w.observed.nbytes for w, ref in zip(ws, refs))
+    d2h = sum(w.P + 4 * w.n_chains + 8 for w in ws)
     rates = []
     for _ in range(max(1, args.e2e_steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx = R.rn_create(device, stream.cuda_stream)
-        nid = R.rn_load_network(ctx, w.src, w.dst, w.fast)
-        R.rn_load_timecourse(ctx, nid, w.init, ref, w.observed, w.knockout)
-        R.rn_init_chains(ctx, nid, w.n_chains, w.chain_seed)
-        R.rn_anneal(ctx, R.schedule(w.T0, w.alpha), S)
-        x, score, chain = R.rn_get_best(ctx, nid)
+        ids = []
+        for w, ref in zip(ws, refs):
+            nid = R.rn_load_network(ctx, w.src, w.dst, w.fast)
+            R.rn_load_timecourse(ctx, nid, w.init, ref, w.observed, w.knockout)
+            R.rn_init_chains(ctx, nid, w.n_chains, w.chain_seed)
+            ids.append(nid)
+        R.rn_anneal(ctx, R.schedule(ws[0].T0, ws[0].alpha), S)
+        for nid in ids:
+            R.rn_get_best(ctx, nid)
         dt = time.perf_counter() - t0
-        nulls = int(R.rn_get_chain_state(ctx, nid, w.n_chains)["counters"][:, 2].sum())
+        nulls = sum(int(R.rn_get_chain_state(ctx, nid, w.n_chains)["counters"][:, 2].sum())
+                    for nid, w in zip(ids, ws))
         R.rn_destroy(ctx)
-        rates.append((w.n_chains * S - nulls) / dt)
+        rates.append((sum(w.n_chains for w in ws) * S - nulls) / dt)
     return {"value": float(np.median(rates)), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h),
-            "path": "rn_create + rn_load_network + rn_load_timecourse + rn_init_chains + "
-                    "rn_anneal(one step) + rn_get_best, host buffers, wall clock"}
-
+            "path": "rn_create + rn_load_network + rn_load_timecourse + rn_init_chains per "
+                    "network + rn_anneal(one step) + rn_get_best per network, host buffers, "
+                    "wall clock"}
 
 def main():
     args = parse()
