@@ -19,6 +19,8 @@
  *                       counter-based generator that replaces the paper's
  *                       per-thread xoroshiro128+ (Section 4.2)
  *   orc_bruteforce      exhaustive minimum over all valid parameter vectors
+ *   orc_mlp             the learned proposal screen (an MLP on the one-hot
+ *                       parameter vector) in FP64: forward, MSE loss, gradients
  *
  * Where the paper is silent or its extracted text is garbled, the readings
  * below are used (each is also stated at the function that applies it):
@@ -494,6 +496,111 @@ int32_t orc_anneal(const orc_net *net, const orc_tc *tc, const orc_schedule *sch
         }
     }
     return ORC_OK;
+}
+
+/* ------------------------------------------------------ screening MLP -- */
+
+/* One-hot input of the learned proposal screen: parameter j occupies
+ * |dom_j| consecutive positions from off[j]; value dom_j[i] sets position
+ * off[j] + i.  Returns D = off[P], the input width. */
+int32_t orc_onehot_offsets(const orc_net *net, int32_t *off)
+{
+    const int32_t P = orc_n_params(net);
+    off[0] = 0;
+    for (int32_t j = 0; j < P; j++) {
+        int8_t vals[6];
+        off[j + 1] = off[j] + orc_domain(net, j, vals);
+    }
+    return off[P];
+}
+
+static int32_t onehot_pos(const orc_net *net, const int32_t *off, int32_t j, int8_t v)
+{
+    int8_t vals[6];
+    int32_t n = orc_domain(net, j, vals);
+    for (int32_t k = 0; k < n; k++)
+        if (vals[k] == v) return off[j] + k;
+    return -1;
+}
+
+/* The screening MLP in FP64 over a batch of B vectors X[B][P]:
+ *   a1 = b1 + W1^T onehot(x)      h1 = relu(a1)          W1 [D][H1]
+ *   a2 = b2 + W2^T h1             h2 = relu(a2)          W2 [H1][H2]
+ *   y  = b3 + w3 . h2                                     w3 [H2]
+ * y[B] out.  With target t: loss = (1/B) sum_b (y_b - t_b)^2 and, where the
+ * output pointers are not NULL, its gradients (relu'(a) = [a > 0]). */
+int32_t orc_mlp(const orc_net *net, int32_t B, const int8_t *X, const double *target,
+                int32_t H1, int32_t H2, const double *W1, const double *b1, const double *W2,
+                const double *b2, const double *w3, double b3, double *y, double *loss,
+                double *gW1, double *gb1, double *gW2, double *gb2, double *gw3, double *gb3)
+{
+    const int32_t P = orc_n_params(net);
+    int32_t *off = malloc(sizeof(int32_t) * (size_t)(P + 1));
+    double *a1 = malloc(sizeof(double) * (size_t)H1), *a2 = malloc(sizeof(double) * (size_t)H2);
+    double *d2 = malloc(sizeof(double) * (size_t)H2), *d1 = malloc(sizeof(double) * (size_t)H1);
+    if (!off || !a1 || !a2 || !d2 || !d1) {
+        free(off); free(a1); free(a2); free(d2); free(d1);
+        return ORC_ENOMEM;
+    }
+    const int32_t D = orc_onehot_offsets(net, off);
+    const int grads = target != NULL;
+    if (grads) {
+        if (gW1) memset(gW1, 0, sizeof(double) * (size_t)D * H1);
+        if (gb1) memset(gb1, 0, sizeof(double) * (size_t)H1);
+        if (gW2) memset(gW2, 0, sizeof(double) * (size_t)H1 * H2);
+        if (gb2) memset(gb2, 0, sizeof(double) * (size_t)H2);
+        if (gw3) memset(gw3, 0, sizeof(double) * (size_t)H2);
+        if (gb3) *gb3 = 0.0;
+        if (loss) *loss = 0.0;
+    }
+    int32_t rc = ORC_OK;
+    for (int32_t b = 0; b < B && rc == ORC_OK; b++) {
+        const int8_t *x = X + (size_t)b * P;
+        for (int32_t i = 0; i < H1; i++) a1[i] = b1[i];
+        for (int32_t j = 0; j < P; j++) {
+            int32_t r = onehot_pos(net, off, j, x[j]);
+            if (r < 0) { rc = ORC_EINVAL; break; }
+            for (int32_t i = 0; i < H1; i++) a1[i] += W1[(size_t)r * H1 + i];
+        }
+        if (rc != ORC_OK) break;
+        for (int32_t k = 0; k < H2; k++) {
+            double s = b2[k];
+            for (int32_t i = 0; i < H1; i++)
+                s += (a1[i] > 0.0 ? a1[i] : 0.0) * W2[(size_t)i * H2 + k];
+            a2[k] = s;
+        }
+        double out = b3;
+        for (int32_t k = 0; k < H2; k++) out += w3[k] * (a2[k] > 0.0 ? a2[k] : 0.0);
+        y[b] = out;
+        if (!grads) continue;
+        const double diff = out - target[b];
+        if (loss) *loss += diff * diff / B;
+        const double dy = 2.0 * diff / B;
+        if (gb3) *gb3 += dy;
+        for (int32_t k = 0; k < H2; k++) {
+            const double h2 = a2[k] > 0.0 ? a2[k] : 0.0;
+            if (gw3) gw3[k] += dy * h2;
+            d2[k] = a2[k] > 0.0 ? dy * w3[k] : 0.0;
+            if (gb2) gb2[k] += d2[k];
+        }
+        for (int32_t i = 0; i < H1; i++) {
+            const double h1 = a1[i] > 0.0 ? a1[i] : 0.0;
+            double s = 0.0;
+            for (int32_t k = 0; k < H2; k++) {
+                if (gW2) gW2[(size_t)i * H2 + k] += h1 * d2[k];
+                s += d2[k] * W2[(size_t)i * H2 + k];
+            }
+            d1[i] = a1[i] > 0.0 ? s : 0.0;
+            if (gb1) gb1[i] += d1[i];
+        }
+        if (gW1)
+            for (int32_t j = 0; j < P; j++) {
+                const int32_t r = onehot_pos(net, off, j, x[j]);
+                for (int32_t i = 0; i < H1; i++) gW1[(size_t)r * H1 + i] += d1[i];
+            }
+    }
+    free(off); free(a1); free(a2); free(d2); free(d1);
+    return rc;
 }
 
 /* ---------------------------------------------------------- brute force -- */

@@ -85,6 +85,12 @@ int32_t orc_anneal(const orc_net *net, const orc_tc *tc, const orc_schedule *sch
 int64_t orc_bruteforce(const orc_net *net, const orc_tc *tc, int32_t *best_score,
                        int8_t *best_x);
 
+int32_t orc_onehot_offsets(const orc_net *net, int32_t *off);
+int32_t orc_mlp(const orc_net *net, int32_t B, const int8_t *X, const double *target,
+                int32_t H1, int32_t H2, const double *W1, const double *b1, const double *W2,
+                const double *b2, const double *w3, double b3, double *y, double *loss,
+                double *gW1, double *gb1, double *gW2, double *gb2, double *gw3, double *gb3);
+
 #ifdef __cplusplus
 }
 #endif

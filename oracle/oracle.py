@@ -91,6 +91,11 @@ def lib():
                                             ctypes.c_int64, P(_Chains)]),
             "orc_bruteforce": (ctypes.c_int64, [P(_Net), P(_TC), ctypes.c_void_p,
                                                 ctypes.c_void_p]),
+            "orc_onehot_offsets": (ctypes.c_int32, [P(_Net), ctypes.c_void_p]),
+            "orc_mlp": (ctypes.c_int32, [P(_Net), ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
+                        + [ctypes.c_void_p] * 5 + [ctypes.c_double]
+                        + [ctypes.c_void_p] * 8),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -272,6 +277,40 @@ def anneal(net, tc, sched, seed, chains, g0, sweeps, chain_ids=None):
     if rc != ORC_OK:
         raise RuntimeError(f"orc_anneal: {rc}")
     return chains
+
+
+def onehot_offsets(net):
+    off = np.zeros(net.P + 1, dtype=np.int32)
+    lib().orc_onehot_offsets(ctypes.byref(net.s), off.ctypes.data)
+    return off
+
+
+def mlp(net, X, params, target=None):
+    """FP64 screening MLP.  params: W1 [D][H1], b1, W2 [H1][H2], b2, w3, b3 (any
+    float arrays).  Returns y, and with a target also (loss, grads dict)."""
+    X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.int8)
+    B = X.shape[0]
+    f = {k: np.ascontiguousarray(params[k], dtype=np.float64) for k in ("W1", "b1", "W2", "b2", "w3")}
+    H1, H2 = f["W1"].shape[1], f["W2"].shape[1]
+    y = np.zeros(B, np.float64)
+    t = None if target is None else np.ascontiguousarray(target, dtype=np.float64)
+    g = {k: np.zeros_like(v) for k, v in f.items()}
+    gb3 = ctypes.c_double(0.0)
+    loss = ctypes.c_double(0.0)
+    grads = t is not None
+    rc = lib().orc_mlp(ctypes.byref(net.s), B, X.ctypes.data, _ptr(t), H1, H2,
+                       f["W1"].ctypes.data, f["b1"].ctypes.data, f["W2"].ctypes.data,
+                       f["b2"].ctypes.data, f["w3"].ctypes.data, float(params["b3"]),
+                       y.ctypes.data, ctypes.addressof(loss) if grads else None,
+                       *( [g[k].ctypes.data for k in ("W1", "b1", "W2", "b2", "w3")] if grads
+                          else [None] * 5),
+                       ctypes.addressof(gb3) if grads else None)
+    if rc != ORC_OK:
+        raise RuntimeError(f"orc_mlp: {rc}")
+    if not grads:
+        return y
+    g["b3"] = gb3.value
+    return y, loss.value, g
 
 
 def bruteforce(net, tc):
