@@ -235,6 +235,79 @@ int rn_batch_config(rn_ctx *ctx, int32_t info[4], double trial_ms[4]);
 int rn_level_sync_noalloc(int8_t *x_best, int32_t *d_best, int32_t n_chains, int64_t row_bytes,
                           int32_t n_params, void *stream);
 
+/* ---- Learned proposal screen ------------------------------------------------
+ * An addition of this library to the method of Table 1 (the paper has no
+ * surrogate): a small MLP on the one-hot encoding of x ranks K candidate moves
+ * per chain and step so that only the best-ranked few are simulated exactly.
+ * The exact simulator alone decides acceptance (Metropolis as in Table 1), so
+ * the surrogate changes which moves are tried, never what a move scores.
+ *
+ * Model: onehot(x) concatenates one block per parameter j of |dom_j| inputs
+ * (domains ascending as in Sections 2.1-2.2; width D = sum |dom_j|), and
+ *     a1 = b1 + W1^T onehot(x),  h1 = relu(a1)        W1 [D][H1]
+ *     a2 = b2 + W2^T h1,         h2 = relu(a2)        W2 [H1][H2]
+ *     y  = b3 + w3 . h2                               w3 [H2]
+ * FP32 master weights; the matrix products run on BF16 tensor-core GEMMs with
+ * FP32 accumulation (W1, W2 and h1 rounded to BF16, h2 and y in FP32).
+ * Training minimises mean (y - target)^2 with Adam on the FP32 masters. */
+
+/* Create the screen of a network: hidden widths h1, h2 (multiples of 256, at
+ * most 1024), a device training set of `capacity` pairs (>= 1).  Weights
+ * start at zero (rn_mlp_set_weights).  Out: *mlp_id, *onehot_width = D. */
+int rn_mlp_create(rn_ctx *ctx, int32_t net, int32_t h1, int32_t h2, int64_t capacity,
+                  int32_t *mlp_id, int32_t *onehot_width);
+
+/* FP32 weights, host arrays in the layouts above (W1 [D][h1] row-major, W2
+ * [h1][h2]); set resets the Adam state. */
+int rn_mlp_set_weights(rn_ctx *ctx, int32_t mlp, const float *W1, const float *b1,
+                       const float *W2, const float *b2, const float *w3, float b3);
+int rn_mlp_get_weights(rn_ctx *ctx, int32_t mlp, float *W1, float *b1, float *W2, float *b2,
+                       float *w3, float *b3);
+
+/* Predictions y[n] of the vectors x[n][P].  Here and in the calls below that
+ * take host vectors, every value must lie in its parameter's domain
+ * (RN_EINVAL otherwise); the constraints of Section 2.5.3 are not required. */
+int rn_mlp_forward(rn_ctx *ctx, int32_t mlp, int32_t n, const int8_t *x, float *y);
+
+/* Loss (mean squared error) and its gradients with respect to every weight,
+ * for the n (1 .. 65536) pairs (x[n][P], target[n]); output layouts as in
+ * rn_mlp_get_weights.  Any output may be NULL. */
+int rn_mlp_gradients(rn_ctx *ctx, int32_t mlp, int32_t n, const int8_t *x, const float *target,
+                     float *loss, float *gW1, float *gb1, float *gW2, float *gb2, float *gw3,
+                     float *gb3);
+
+/* Training set: append pairs from the host (targets as given), or the current
+ * state of every chain of the network (x_cur, target = delta_cur / n_obs with
+ * n_obs the observed entries of the time course).  The set is a ring: beyond
+ * its capacity the oldest pairs are overwritten.  *count (may be NULL) = pairs
+ * held after the call. */
+int rn_mlp_add_samples(rn_ctx *ctx, int32_t mlp, int32_t n, const int8_t *x, const float *target,
+                       int64_t *count);
+int rn_mlp_log_chains(rn_ctx *ctx, int32_t mlp, int64_t *count);
+
+/* `steps` Adam steps (learning rate lr, beta1 0.9, beta2 0.999, eps 1e-8) on
+ * minibatches of `batch` pairs (a multiple of 128, at most 65536) drawn
+ * uniformly with replacement from the training set by Philox4x32-10 keyed by
+ * `seed` (counter (step, 0, row, 8)).  *loss (may be NULL): mean loss of the
+ * last minibatch. */
+int rn_mlp_train(rn_ctx *ctx, int32_t mlp, int32_t steps, int32_t batch, float lr, uint64_t seed,
+                 float *loss);
+
+/* Screened annealing of the screen's network for `sweeps` steps (schedule as
+ * in rn_anneal; reset_to_best and global_sync are not supported here).  Step g
+ * of chain k draws K candidates: candidate 0 from Philox counter
+ * (g_lo, g_hi, k, 0) exactly as rn_anneal's proposal, candidate c >= 1 from
+ * (g_lo, g_hi, k, 16 + c) (words 0 and 1, GetCandidate of Table 1).  With
+ * probability eps (word 3 of counter tag 0 below eps * 2^32) only candidate 0
+ * is simulated; otherwise the `top` candidates of lowest predicted y (distinct
+ * moves, lowest index on ties) are simulated exactly and the one of lowest
+ * exact score (first on ties) goes to the Metropolis test of Table 1 with
+ * word 2 of counter tag 0.  A step with no candidate is a null move.  With
+ * eps = 1 the chains are bit-identical to rn_anneal's.  K: 1 .. 32;
+ * top: 1 .. 4 (<= K). */
+int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K, int32_t top,
+                       double eps, int64_t sweeps);
+
 /* Wait for all queued work on the context stream; reports device-side errors. */
 int rn_synchronize(rn_ctx *ctx);
 

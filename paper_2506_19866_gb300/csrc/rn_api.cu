@@ -20,181 +20,9 @@
 #include "../../include/rnanneal.h"
 #include "rn_launch.h"
 
-namespace {
+#include "rn_context.h"
 
-using namespace rn;
-
-// Device buffer owned by the context.
-template <typename T>
-struct DevBuf {
-    T *p = nullptr;
-    size_t n = 0;
-    DevBuf() = default;
-    DevBuf(const DevBuf &) = delete;
-    DevBuf &operator=(const DevBuf &) = delete;
-    ~DevBuf() { release(); }
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        n = 0;
-    }
-    cudaError_t alloc(size_t count)
-    {
-        release();
-        if (count == 0) count = 1;
-        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-        if (e != cudaSuccess) {
-            p = nullptr;
-            return e;
-        }
-        n = count;
-        return cudaSuccess;
-    }
-    cudaError_t reserve(size_t count)
-    {
-        return count <= n ? cudaSuccess : alloc(count);
-    }
-    cudaError_t upload(const std::vector<T> &v)
-    {
-        cudaError_t e = alloc(v.size());
-        if (e != cudaSuccess) return e;
-        if (v.empty()) return cudaSuccess;
-        return cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
-    }
-};
-
-struct Network {
-    int32_t N = 0, E = 0, P = 0;
-    std::vector<int32_t> src, dst;
-    std::vector<uint8_t> fast, frozen;
-    std::vector<int8_t> frozen_val;
-    bool has_frozen = false;
-    // lane / slot layout
-    int npl = 0, dtab = 0;
-    int D[kMaxSlots] = {};
-    std::vector<int32_t> node_q, edge_id, edge_pos, free_list, in_ptr, in_edges, out_ptr,
-        out_edges;
-    std::vector<int16_t> q_node;
-    std::vector<uint8_t> edge_q2;
-    bool supported = false;
-    // device copies
-    DevBuf<int32_t> d_edge_id, d_edge_pos, d_node_q, d_src, d_dst, d_free, d_in_ptr, d_in_edges,
-        d_out_ptr, d_out_edges;
-    DevBuf<int16_t> d_q_node;
-    DevBuf<uint8_t> d_edge_q2, d_fast, d_frozen;
-    DevBuf<int8_t> d_frozen_val;
-    // time course: conditions are simulated cg at a time, G groups
-    bool has_tc = false;
-    int32_t C = 0, T = 0, cg = 1, G = 0;
-    int d0 = -1, d1 = -1;               // register capacities of the anneal kernel
-    int64_t max_score = 0;
-    DevBuf<uint16_t> d_init_code, d_out_bits;
-    DevBuf<uint32_t> d_obs, d_init_s4, d_movable;
-    // chains
-    int32_t n_chains = 0;
-    int32_t pstride = 0;
-    uint64_t seed = 0;
-    int64_t step = 0;
-    bool chains_valid = false;
-    DevBuf<int8_t> d_x_cur, d_x_best;
-    DevBuf<int32_t> d_d_cur, d_d_best;
-    DevBuf<int64_t> d_cnt;
-
-    DevNet dev() const
-    {
-        DevNet n{};
-        n.N = N; n.E = E; n.P = P; n.n_free = (int32_t)free_list.size();
-        n.C = C; n.T = T; n.G = G;
-        n.npl = npl; n.cg = cg; n.dtab = dtab;
-        for (int k = 0; k < kMaxSlots; ++k) n.D[k] = D[k];
-        n.edge_id = d_edge_id.p; n.edge_q2 = d_edge_q2.p; n.edge_pos = d_edge_pos.p;
-        n.node_q = d_node_q.p; n.q_node = d_q_node.p; n.src = d_src.p; n.dst = d_dst.p;
-        n.fast = d_fast.p; n.free_list = d_free.p;
-        n.in_ptr = d_in_ptr.p; n.in_edges = d_in_edges.p;
-        n.out_ptr = d_out_ptr.p; n.out_edges = d_out_edges.p;
-        n.frozen = has_frozen ? d_frozen.p : nullptr;
-        n.frozen_val = has_frozen ? d_frozen_val.p : nullptr;
-        n.init_code = d_init_code.p; n.out_bits = d_out_bits.p; n.obs = d_obs.p;
-        n.init_s4 = d_init_s4.p; n.movable = d_movable.p;
-        return n;
-    }
-    DevChains chains() const
-    {
-        DevChains c{};
-        c.n = n_chains; c.pstride = pstride; c.seed = seed;
-        c.x_cur = d_x_cur.p; c.x_best = d_x_best.p;
-        c.d_cur = d_d_cur.p; c.d_best = d_d_best.p; c.cnt = d_cnt.p;
-        return c;
-    }
-};
-
-}  // namespace
-
-struct SchedCache {
-    bool valid = false;
-    double T0 = 0, alpha = 0;
-    int64_t iters = 0, l0 = 0, l1 = -1, cap = 0;
-    DevBuf<uint32_t> thr;
-    DevBuf<int32_t> off, len;
-};
-
-// Device descriptors of a batched launch over every network with chains, the
-// autotuned configuration, and the CUDA graph that replays the launch.
-struct BatchState {
-    bool valid = false;
-    uint64_t gen = 0;                 // context generation it was built for
-    std::vector<int> order;           // context network ids, most work per chain first
-    int32_t total = 0;
-    DevBuf<rn::DevNet> nets;
-    DevBuf<rn::DevChains> chains;
-    DevBuf<int64_t> g0;
-    DevBuf<int32_t> item_net, item_chain, path;
-    std::vector<int32_t> host_path;   // chosen table path per network (batch order)
-    uint32_t region_bytes = 0;
-    int wpb = 4, grid = 0;
-    bool tuned = false;
-    bool g0_synced = false;           // device g0 equals the host step counters
-    double tune_ms[4] = {0, 0, 0, 0}; // trial times of the candidate configurations
-    // graph of [queue reset, batched kernel, step advance]
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    int64_t graph_sweeps = -1;
-    void drop_graph()
-    {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        exec = nullptr;
-        graph = nullptr;
-        graph_sweeps = -1;
-    }
-    ~BatchState() { drop_graph(); }
-};
-
-struct rn_ctx {
-    int device = 0;
-    int64_t launches = 0;
-    uint64_t gen = 1;                 // bumped whenever networks or chains change
-    BatchState batch;
-    SchedCache cache;
-    int sm_count = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    std::string err;
-    std::vector<std::unique_ptr<Network>> nets;
-    DevBuf<uint32_t> thr;
-    DevBuf<int32_t> thr_off, thr_len;
-    DevBuf<int32_t> status;
-    DevBuf<int32_t> winner;
-    DevBuf<unsigned int> queue;   // work-item counter of the anneal kernel
-    DevBuf<int32_t> done;         // chunks finished per chain in the current launch
-    DevBuf<int32_t> dev_err;      // set by a kernel whose wait gave up
-    DevBuf<int8_t> xbuf;
-    DevBuf<int32_t> sbuf;
-    DevBuf<uint8_t> tbuf;
-};
-
-namespace {
+namespace rn {
 
 thread_local std::string g_create_error;
 
@@ -215,12 +43,6 @@ int cuda_fail(rn_ctx *ctx, cudaError_t e, const char *what)
     return fail(ctx, e == cudaErrorMemoryAllocation ? RN_ENOMEM : RN_ECUDA, "%s: %s", what,
                 cudaGetErrorString(e));
 }
-
-#define RN_CUDA(ctx, call)                                         \
-    do {                                                           \
-        cudaError_t e_ = (call);                                   \
-        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
-    } while (0)
 
 Network *get_net(rn_ctx *ctx, int32_t id)
 {
@@ -414,8 +236,10 @@ int check_device_flag(rn_ctx *ctx)
     if (!flag) return RN_OK;
     RN_CUDA(ctx, cudaMemset(ctx->dev_err.p, 0, sizeof flag));
     return fail(ctx, RN_ETIMEOUT,
-                "a device-side wait for another work item gave up; the chain state of the "
-                "last rn_anneal call is incomplete");
+                "a bounded device-side wait gave up (code %d: 1 = anneal work item, 2 = "
+                "tensor-core pipeline); results of the calls since the last check are "
+                "incomplete",
+                flag);
 }
 
 int require_supported(rn_ctx *ctx, const Network &n)
@@ -784,9 +608,6 @@ int anneal_batched(rn_ctx *ctx, const rn_schedule &s, int64_t sweeps)
     return RN_OK;
 }
 
-}  // namespace
-
-namespace rn {
 // Message of a failed call that has no context (read with rn_last_error(NULL)).
 void set_detached_error(const char *fmt, ...)
 {
@@ -798,6 +619,8 @@ void set_detached_error(const char *fmt, ...)
     g_create_error = buf;
 }
 }  // namespace rn
+
+using namespace rn;
 
 extern "C" {
 
@@ -945,7 +768,7 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     }
     // weight = observed * (|G| + 1), G from consecutive observed points (Section 2.3)
     std::vector<uint8_t> W(ctn, 0);
-    int64_t max_score = 0;
+    int64_t max_score = 0, n_obs = 0;
     for (int32_t c = 0; c < C; ++c)
         for (int32_t t = 0; t < T; ++t)
             for (int32_t i = 0; i < N; ++i) {
@@ -955,10 +778,12 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
                 if (t > 0 && observed[k - N]) g = std::abs((int)ref[k] - (int)ref[k - N]);
                 W[k] = (uint8_t)(g + 1);
                 max_score += 2 * W[k];
+                ++n_obs;
             }
     n->C = C;
     n->T = T;
     n->max_score = max_score;
+    n->n_obs = n_obs;
     n->has_tc = true;
     n->chains_valid = false;
     if (!n->supported) return RN_OK;

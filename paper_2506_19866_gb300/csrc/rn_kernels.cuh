@@ -191,6 +191,61 @@ __device__ __forceinline__ void count_constraints(const DevNet &net, const int8_
     }
 }
 
+// GetCandidate (Table 1) for a network with free parameters: the pick(r0)-th
+// free parameter j, then the pick(r1)-th of its domain values != x_j whose
+// single change keeps both constraints of Section 2.5.3 (counters out_nz,
+// pos_in of x).  Returns false for a null move (no such value).
+__device__ __forceinline__ bool get_candidate(const DevNet &net, const int8_t *xs,
+                                              const uint8_t *out_nz, const uint8_t *pos_in,
+                                              uint32_t r0, uint32_t r1, int &j, int &kind,
+                                              int &idx, int &cur, int &v)
+{
+    const int E = net.E, N = net.N;
+    j = net.free_list[pick(r0, (uint32_t)net.n_free)];
+    if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
+    else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
+    cur = xs[j];
+    int8_t vals[6];
+    const int nd = domain(kind, kind == 3 && net.fast[idx], vals);
+    bool blocked0 = false, blocked_all = false;
+    if (kind == 0 && cur != 0) {
+        const int a = net.src[idx], b = net.dst[idx];
+        blocked0 = out_nz[a] < 2 || (xs[E + idx] == 1 && pos_in[b] < 2);
+    } else if (kind == 1 && cur == 1 && xs[idx] != 0) {
+        blocked_all = pos_in[net.dst[idx]] < 2;
+    }
+    int8_t alts[6];
+    int n_alt = 0;
+    if (!blocked_all) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            if (k >= nd) break;
+            const int a = vals[k];
+            if (a == cur || (blocked0 && a == 0)) continue;
+            alts[n_alt++] = (int8_t)a;
+        }
+    }
+    if (n_alt == 0) return false;
+    v = alts[pick(r1, (uint32_t)n_alt)];
+    return true;
+}
+
+// Constraint counters after x_j: cur -> v (x still holds cur).
+__device__ __forceinline__ void apply_counters(const DevNet &net, const int8_t *xs,
+                                               uint8_t *out_nz, uint8_t *pos_in, int kind,
+                                               int idx, int cur, int v)
+{
+    const int E = net.E;
+    if (kind == 0 && (cur == 0) != (v == 0)) {
+        const int delta = v != 0 ? 1 : -1;
+        out_nz[net.src[idx]] += delta;
+        if (xs[E + idx] == 1) pos_in[net.dst[idx]] += delta;
+    } else if (kind == 1 && xs[idx] != 0) {
+        if (cur == 1) pos_in[net.dst[idx]] -= 1;
+        if (v == 1) pos_in[net.dst[idx]] += 1;
+    }
+}
+
 __device__ __forceinline__ void warp_copy16(void *dst, const void *src, int bytes, int lane)
 {
     uint4 *d = reinterpret_cast<uint4 *>(dst);
@@ -285,39 +340,11 @@ __device__ __forceinline__ void run_chunk(Path &P, const DevNet &net, const DevC
             ++n_null;
             continue;
         }
-        // GetCandidate: the pick(r0)-th free parameter ...
-        const int j = net.free_list[pick(r.x, (uint32_t)net.n_free)];
-        int kind, idx;
-        if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
-        else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
-        const int cur = xs[j];
-        int8_t vals[6];
-        const int nd = domain(kind, kind == 3 && net.fast[idx], vals);
-        // ... and the pick(r1)-th of its values != current that keep the
-        // constraints of Section 2.5.3
-        bool blocked0 = false, blocked_all = false;
-        if (kind == 0 && cur != 0) {
-            const int a = net.src[idx], b = net.dst[idx];
-            blocked0 = out_nz[a] < 2 || (xs[E + idx] == 1 && pos_in[b] < 2);
-        } else if (kind == 1 && cur == 1 && xs[idx] != 0) {
-            blocked_all = pos_in[net.dst[idx]] < 2;
-        }
-        int8_t alts[6];
-        int n_alt = 0;
-        if (!blocked_all) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                if (k >= nd) break;
-                const int v = vals[k];
-                if (v == cur || (blocked0 && v == 0)) continue;
-                alts[n_alt++] = (int8_t)v;
-            }
-        }
-        if (n_alt == 0) {
+        int j, kind, idx, cur, v;
+        if (!get_candidate(net, xs, out_nz, pos_in, r.x, r.y, j, kind, idx, cur, v)) {
             ++n_null;
             continue;
         }
-        const int v = alts[pick(r.y, (uint32_t)n_alt)];
 
         // apply the candidate to the owner lane's table entry
         int owner;
@@ -344,14 +371,7 @@ __device__ __forceinline__ void run_chunk(Path &P, const DevNet &net, const DevC
         }
         if (accept) {
             if (lane == 0) {
-                if (kind == 0 && (cur == 0) != (v == 0)) {
-                    const int delta = v != 0 ? 1 : -1;
-                    out_nz[net.src[idx]] += delta;
-                    if (xs[E + idx] == 1) pos_in[net.dst[idx]] += delta;
-                } else if (kind == 1 && xs[idx] != 0) {
-                    if (cur == 1) pos_in[net.dst[idx]] -= 1;
-                    if (v == 1) pos_in[net.dst[idx]] += 1;
-                }
+                apply_counters(net, xs, out_nz, pos_in, kind, idx, cur, v);
                 xs[j] = (int8_t)v;
             }
             __syncwarp();

@@ -1,0 +1,1010 @@
+// rn_mlp.cu -- the learned proposal screen: an MLP on the one-hot parameter
+// vector, trained on the GPU by its own forward/backward kernels and Adam, and
+// the screened annealing step that ranks K candidate moves per chain with it.
+//
+// Training batch of B rows (B a multiple of 128; D padded to Dp):
+//   onehot     OH [B][Dp] and OH^T [Dp][B] (bf16 0/1) from int8 vectors
+//   GEMM 1     h1 = relu(OH W1 + b1)                  bf16 [B][H1]
+//   GEMM 2     h2 = relu(h1 W2 + b2), partials of w3 . h2 per 64 columns
+//   head       y, dy = 2 (y - t) / n, dh2 = dy w3 [h2 > 0]
+//   GEMMs      dW2 = h1^T dh2,  dh1 = (dh2 W2^T) [h1 > 0],  dW1 = OH^T dh1
+//   colsums    db1, db2, dw3 = sum_b dy h2, db3 = sum_b dy
+//   Adam       on the FP32 masters, then the BF16 copies are refreshed
+// Screened step of C chains (M = C K candidate rows):
+//   propose    K candidates per chain (GetCandidate of Table 1) and their
+//              hidden rows relu(A1 + W1[new] - W1[old]) from the chain's
+//              layer-1 pre-activation A1 (sparse FP32 update: one parameter
+//              changes one row of the one-hot sum)
+//   GEMM 2     partials of w3 . relu(h1 W2 + b2)
+//   select     top candidates by predicted y, their vectors for exact scoring
+//   evaluate   Simulate + score of Table 1 (the exact kernel)
+//   commit     Metropolis test of Table 1 against the host threshold tables;
+//              x, delta, best, counters and A1 follow an accepted move
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "rn_context.h"
+#include "rn_gemm.cuh"
+#include "rn_kernels.cuh"
+#include "rn_umma.cuh"
+
+namespace rn {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+inline bf16 *bp(DevBuf<uint16_t> &b) { return reinterpret_cast<bf16 *>(b.p); }
+
+// ---------------------------------------------------------------- kernels --
+
+// Rows b < B: OH[b][row_base[j] + x_bj] = 1 and OHT[row][b] = 1 (buffers zeroed
+// before).  Row b reads vector idx[b] of X (idx null: vector b); padding rows
+// b >= n repeat the first vector.  A value whose row falls outside the
+// parameter's block [row_off[j], row_off[j + 1]) is skipped.
+__global__ void onehot_kernel(const int8_t *__restrict__ X, int64_t xstride,
+                              const int32_t *__restrict__ idx, int32_t n, int32_t P,
+                              const int32_t *__restrict__ row_base,
+                              const int32_t *__restrict__ row_off, bf16 *OH, int32_t ldo,
+                              bf16 *OHT, int32_t ldt)
+{
+    const int b = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P) return;
+    const int r0 = b < n ? b : 0;
+    const int64_t src = idx ? idx[r0] : r0;
+    const int r = row_base[j] + X[src * xstride + j];
+    if (r < row_off[j] || r >= row_off[j + 1]) return;
+    const bf16 one = __float2bfloat16(1.0f);
+    if (OH) OH[(size_t)b * ldo + r] = one;
+    if (OHT) OHT[(size_t)r * ldt + b] = one;
+}
+
+// out[c][r] = in[r][c] (R x C, both multiples of 32), 32 x 8 threads per tile.
+template <typename Tin>
+__global__ void transpose_kernel(const Tin *__restrict__ in, int ldi, bf16 *__restrict__ out,
+                                 int ldo)
+{
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const Tin v = in[(size_t)(r0 + k) * ldi + c0 + threadIdx.x];
+        if constexpr (sizeof(Tin) == 4) tile[k][threadIdx.x] = (float)v;
+        else tile[k][threadIdx.x] = __bfloat162float(v);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8)
+        out[(size_t)(c0 + k) * ldo + r0 + threadIdx.x] = __float2bfloat16(tile[threadIdx.x][k]);
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ in, bf16 *__restrict__ out, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16(in[i]);
+}
+
+// Warp per row b < B: y_b = b3 + sum of the layer-2 partials.  With targets:
+// dy_b = 2 (y_b - t_b) / n for b < n (0 for padding rows), the squared errors
+// summed into *sse, and dh2[b][k] = dy_b w3[k] [h2[b][k] > 0].
+__global__ void head_kernel(const float *__restrict__ part, int nparts, const float *__restrict__ b3,
+                            int32_t B, int32_t n, float *__restrict__ y,
+                            const float *__restrict__ tgt, float *__restrict__ dy,
+                            double *__restrict__ sse, const bf16 *__restrict__ h2,
+                            const float *__restrict__ w3, bf16 *__restrict__ dh2, int H2)
+{
+    const int lane = threadIdx.x & 31;
+    const int b = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (b >= B) return;
+    float s = lane < nparts ? part[(size_t)b * nparts + lane] : 0.f;
+#pragma unroll
+    for (int k = 16; k; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+    const float yb = *b3 + s;
+    if (lane == 0 && y) y[b] = yb;
+    if (!tgt) return;
+    const float e = b < n ? yb - tgt[b] : 0.f;
+    const float d = 2.f * e / (float)n;
+    if (lane == 0) {
+        dy[b] = d;
+        if (b < n) atomicAdd(sse, (double)e * (double)e);
+    }
+    for (int k = lane * 8; k < H2; k += 256) {
+        const uint4 hv = *reinterpret_cast<const uint4 *>(h2 + (size_t)b * H2 + k);
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&hv);
+        uint4 ov;
+        __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(&ov);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(h[q]);
+            o[q] = __floats2bfloat162_rn(f.x > 0.f ? d * w3[k + 2 * q] : 0.f,
+                                         f.y > 0.f ? d * w3[k + 2 * q + 1] : 0.f);
+        }
+        *reinterpret_cast<uint4 *>(dh2 + (size_t)b * H2 + k) = ov;
+    }
+}
+
+// part[s][c] = sum over the rows of split s of coef[r] A[r][c] (coef null: 1);
+// 32 x 8 threads, 64 columns per block, blockIdx.y = split.
+__global__ void colsum_kernel(const bf16 *__restrict__ A, int lda, int R,
+                              const float *__restrict__ coef, int rows_per_split,
+                              float *__restrict__ part, int C)
+{
+    __shared__ float red[8][64];
+    const int c = blockIdx.x * 64 + threadIdx.x * 2;
+    const int r0 = blockIdx.y * rows_per_split, r1 = min(R, r0 + rows_per_split);
+    float s0 = 0.f, s1 = 0.f;
+    for (int r = r0 + threadIdx.y; r < r1; r += 8) {
+        const float2 v =
+            __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(A + (size_t)r * lda + c));
+        const float w = coef ? coef[r] : 1.f;
+        s0 += w * v.x;
+        s1 += w * v.y;
+    }
+    red[threadIdx.y][threadIdx.x * 2] = s0;
+    red[threadIdx.y][threadIdx.x * 2 + 1] = s1;
+    __syncthreads();
+    if (threadIdx.y == 0) {
+        float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            t0 += red[k][threadIdx.x * 2];
+            t1 += red[k][threadIdx.x * 2 + 1];
+        }
+        part[(size_t)blockIdx.y * C + c] = t0;
+        part[(size_t)blockIdx.y * C + c + 1] = t1;
+    }
+}
+
+// out[c] = sum_s part[s][c]; with v != null also out[C] = sum_{r < nv} v[r]
+// (one extra thread block).
+__global__ void colsum_finish_kernel(const float *__restrict__ part, int S, int C,
+                                     float *__restrict__ out, const float *__restrict__ v, int nv)
+{
+    if (blockIdx.x == gridDim.x - 1 && v) {
+        __shared__ float red[256];
+        float s = 0.f;
+        for (int r = threadIdx.x; r < nv; r += blockDim.x) s += v[r];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[C] = red[0];
+        return;
+    }
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.f;
+    for (int k = 0; k < S; ++k) s += part[(size_t)k * C + c];
+    out[c] = s;
+}
+
+// Adam (Kingma & Ba, 2015) on the FP32 masters; c1 = 1 / (1 - beta1^t),
+// c2 = 1 / (1 - beta2^t).
+__global__ void adam_kernel(float *__restrict__ theta, const float *__restrict__ g,
+                            float *__restrict__ m, float *__restrict__ v, size_t n, float lr,
+                            float beta1, float beta2, float c1, float c2, float eps)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = beta1 * m[i] + (1.f - beta1) * gi;
+        const float vi = beta2 * v[i] + (1.f - beta2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        theta[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+// Minibatch rows: slot idx[b] of the training set, drawn uniformly from the
+// `count` held pairs by Philox counter (step, 0, b, 8); tgt[b] its target.
+__global__ void sample_kernel(uint64_t seed, uint32_t step, int32_t B, uint32_t count,
+                              const float *__restrict__ set_y, int32_t *__restrict__ idx,
+                              float *__restrict__ tgt)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const uint4 r = philox(seed, step, 0u, (uint32_t)b, 8u);
+    const uint32_t k = pick(r.x, count);
+    idx[b] = (int32_t)k;
+    tgt[b] = set_y[k];
+}
+
+// Warp per chain: its x_cur row and delta_cur * scale into ring slot
+// (head + chain) % cap.
+__global__ void log_chains_kernel(DevChains ch, int8_t *__restrict__ set_x,
+                                  float *__restrict__ set_y, int64_t head, int64_t cap,
+                                  float scale)
+{
+    const int lane = threadIdx.x & 31;
+    const int c = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (c >= ch.n) return;
+    const int64_t slot = (head + c) % cap;
+    warp_copy16(set_x + slot * ch.pstride, ch.x_cur + (size_t)c * ch.pstride, ch.pstride, lane);
+    if (lane == 0) set_y[slot] = (float)ch.d_cur[c] * scale;
+}
+
+// Block per chain: A1[c][h] = b1[h] + sum_j W1[row(j, x_j)][h] (the BF16
+// weights), h over the block's threads.
+__global__ void embed_chains_kernel(DevChains ch, int32_t P, const int32_t *__restrict__ row_base,
+                                    const bf16 *__restrict__ W1b, const float *__restrict__ b1,
+                                    int H1, float *__restrict__ A1)
+{
+    const int c = blockIdx.x;
+    const int8_t *x = ch.x_cur + (size_t)c * ch.pstride;
+    for (int h = threadIdx.x; h < H1; h += blockDim.x) {
+        float a = b1[h];
+        for (int j = 0; j < P; ++j)
+            a += __bfloat162float(W1b[(size_t)(row_base[j] + x[j]) * H1 + h]);
+        A1[(size_t)c * H1 + h] = a;
+    }
+}
+
+struct ScreenArgs {
+    DevNet net;
+    DevChains ch;
+    int64_t g;                          // global step
+    int32_t K, top, H1, nparts;
+    uint64_t eps_thr;                   // fallback iff word 3 < eps_thr (<= 2^32)
+    const int32_t *row_base;
+    const bf16 *W1b;                    // [Dp][H1]
+    const float *b3;
+    float *A1;                          // [chains][H1]
+    bf16 *hc;                           // [M][H1]
+    const float *pc;                    // [M][nparts]
+    int32_t *cand;                      // [chains][K]
+    int32_t *sel;                       // [chains][top]
+    int8_t *xe;                         // [chains * top][pstride]
+    const int32_t *se;                  // [chains * top]
+};
+
+constexpr int kScreenWarps = 4;
+constexpr int kMaxGroups = 4;           // H1 <= 4 * 256
+
+__device__ __forceinline__ uint4 step_draw(const DevChains &ch, int64_t g, int chain, uint32_t tag)
+{
+    return philox(ch.seed, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), (uint32_t)chain, tag);
+}
+
+// Warp per chain: K candidates (lane k draws candidate k), then the K hidden
+// rows relu(A1 + W1[new] - W1[old]) in BF16.  Shared memory per warp: x_cur,
+// out_nz[N], pos_in[N].
+__global__ void __launch_bounds__(kScreenWarps * 32) screen_propose_kernel(ScreenArgs a,
+                                                                           int region)
+{
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * kScreenWarps + warp;
+    if (c >= a.ch.n) return;
+    int8_t *xs = reinterpret_cast<int8_t *>(sm + warp * region);
+    uint8_t *out_nz = reinterpret_cast<uint8_t *>(xs) + a.ch.pstride;
+    uint8_t *pos_in = out_nz + ((a.net.N + 15) & ~15);
+    warp_copy16(xs, a.ch.x_cur + (size_t)c * a.ch.pstride, a.ch.pstride, lane);
+    __syncwarp();
+    count_constraints(a.net, xs, out_nz, pos_in, lane);
+    __syncwarp();
+    int j = 0, kind, idx, cur = 0, v = 0;
+    bool ok = false;
+    if (lane < a.K && a.net.n_free > 0) {
+        const uint4 r = step_draw(a.ch, a.g, c, lane == 0 ? 0u : 16u + (uint32_t)lane);
+        ok = get_candidate(a.net, xs, out_nz, pos_in, r.x, r.y, j, kind, idx, cur, v);
+    }
+    if (lane < a.K) a.cand[(size_t)c * a.K + lane] = ok ? (j << 8) | (v & 255) : -1;
+
+    const int groups = a.H1 >> 8;
+    float base[kMaxGroups][8];
+#pragma unroll
+    for (int q = 0; q < kMaxGroups; ++q) {
+        if (q >= groups) break;
+        const float4 *p = reinterpret_cast<const float4 *>(a.A1 + (size_t)c * a.H1 + q * 256 + lane * 8);
+        const float4 u0 = p[0], u1 = p[1];
+        base[q][0] = u0.x; base[q][1] = u0.y; base[q][2] = u0.z; base[q][3] = u0.w;
+        base[q][4] = u1.x; base[q][5] = u1.y; base[q][6] = u1.z; base[q][7] = u1.w;
+    }
+    for (int k = 0; k < a.K; ++k) {
+        const int okk = __shfl_sync(0xffffffffu, (int)ok, k);
+        const int jk = __shfl_sync(0xffffffffu, j, k);
+        const int rn = a.row_base[jk] + __shfl_sync(0xffffffffu, v, k);
+        const int ro = a.row_base[jk] + __shfl_sync(0xffffffffu, cur, k);
+        bf16 *out = a.hc + ((size_t)c * a.K + k) * a.H1;
+#pragma unroll
+        for (int q = 0; q < kMaxGroups; ++q) {
+            if (q >= groups) break;
+            const int col = q * 256 + lane * 8;
+            float h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) h[e] = base[q][e];
+            if (okk) {
+                const uint4 wn = *reinterpret_cast<const uint4 *>(a.W1b + (size_t)rn * a.H1 + col);
+                const uint4 wo = *reinterpret_cast<const uint4 *>(a.W1b + (size_t)ro * a.H1 + col);
+                const __nv_bfloat162 *pn = reinterpret_cast<const __nv_bfloat162 *>(&wn);
+                const __nv_bfloat162 *po = reinterpret_cast<const __nv_bfloat162 *>(&wo);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2 fn = __bfloat1622float2(pn[e]), fo = __bfloat1622float2(po[e]);
+                    h[2 * e] += fn.x - fo.x;
+                    h[2 * e + 1] += fn.y - fo.y;
+                }
+            }
+            uint4 ov;
+            __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(&ov);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                o[e] = __floats2bfloat162_rn(fmaxf(h[2 * e], 0.f), fmaxf(h[2 * e + 1], 0.f));
+            *reinterpret_cast<uint4 *>(out + col) = ov;
+        }
+    }
+}
+
+// Order-preserving key of a float (NaN: largest).
+__device__ __forceinline__ uint32_t float_key(float y)
+{
+    if (y != y) return 0xFFFFFFFEu;
+    const uint32_t u = __float_as_uint(y);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Warp per chain: the candidates to simulate (fallback: candidate 0 only;
+// otherwise the `top` distinct moves of lowest predicted y, lowest index on
+// ties) and their vectors x_cur with the move applied.
+__global__ void __launch_bounds__(kScreenWarps * 32) screen_select_kernel(ScreenArgs a)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * kScreenWarps + warp;
+    if (c >= a.ch.n) return;
+    const uint4 r = step_draw(a.ch, a.g, c, 0u);
+    const bool fallback = (uint64_t)r.w < a.eps_thr;
+    const int mv = lane < a.K ? a.cand[(size_t)c * a.K + lane] : -1;
+    uint32_t key = 0xFFFFFFFFu;
+    if (mv >= 0 && (!fallback || lane == 0)) {
+        if (fallback) {
+            key = 0;
+        } else {
+            float s = 0.f;
+            const float *p = a.pc + ((size_t)c * a.K + lane) * a.nparts;
+            for (int q = 0; q < a.nparts; ++q) s += p[q];
+            key = float_key(*a.b3 + s);
+        }
+    }
+    bool alive = key != 0xFFFFFFFFu;
+    for (int s = 0; s < a.top; ++s) {
+        const uint32_t m = __reduce_min_sync(0xffffffffu, alive ? key : 0xFFFFFFFFu);
+        int chosen = -1;
+        if (m != 0xFFFFFFFFu) {
+            const int w = __ffs(__ballot_sync(0xffffffffu, alive && key == m)) - 1;
+            chosen = __shfl_sync(0xffffffffu, mv, w);
+            if (mv == chosen) alive = false;   // the winner and its duplicates
+        }
+        if (lane == 0) a.sel[(size_t)c * a.top + s] = chosen;
+        int8_t *row = a.xe + ((size_t)c * a.top + s) * a.ch.pstride;
+        warp_copy16(row, a.ch.x_cur + (size_t)c * a.ch.pstride, a.ch.pstride, lane);
+        __syncwarp();
+        if (lane == 0 && chosen >= 0) row[chosen >> 8] = (int8_t)(chosen & 255);
+    }
+}
+
+// Warp per chain: the simulated candidate of lowest exact score (first slot on
+// ties) goes to the Metropolis test of Table 1 (host threshold tables, word 2
+// of the step draw).  An accepted move updates x_cur, delta_cur, the best
+// vector (strict improvement), the counters and A1.
+__global__ void __launch_bounds__(kScreenWarps * 32) screen_commit_kernel(ScreenArgs a, DevSched sc)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * kScreenWarps + warp;
+    if (c >= a.ch.n) return;
+    int best = -1;
+    int32_t d = 0;
+    for (int s = 0; s < a.top; ++s) {
+        const int mv = a.sel[(size_t)c * a.top + s];
+        if (mv < 0) continue;
+        const int32_t ds = a.se[(size_t)c * a.top + s];
+        if (best < 0 || ds < d) { best = mv; d = ds; }
+    }
+    int64_t *cnt = a.ch.cnt + 3 * (size_t)c;
+    if (best < 0) {
+        if (lane == 0) cnt[2] += 1;
+        return;
+    }
+    const int32_t d_cur = a.ch.d_cur[c], d_best = a.ch.d_best[c];
+    const int32_t dE = d - d_cur;
+    bool accept = dE <= 0;
+    if (!accept) {
+        const uint4 r = step_draw(a.ch, a.g, c, 0u);
+        const int64_t l = a.g / sc.iters - sc.level0;
+        if (dE <= sc.thr_len[l]) accept = r.z < sc.thr[sc.thr_off[l] + dE - 1];
+    }
+    if (!accept) return;
+    const int j = best >> 8;
+    const int v = (int8_t)(best & 255);
+    int8_t *x = a.ch.x_cur + (size_t)c * a.ch.pstride;
+    const int rn = a.row_base[j] + v, ro = a.row_base[j] + x[j];
+    __syncwarp();
+    if (lane == 0) {
+        x[j] = (int8_t)v;
+        a.ch.d_cur[c] = d;
+        cnt[0] += 1;
+        cnt[1] += dE > 0;
+    }
+    __syncwarp();
+    if (d < d_best) {
+        warp_copy16(a.ch.x_best + (size_t)c * a.ch.pstride, x, a.ch.pstride, lane);
+        if (lane == 0) a.ch.d_best[c] = d;
+    }
+    for (int h = lane; h < a.H1; h += 32)
+        a.A1[(size_t)c * a.H1 + h] += __bfloat162float(a.W1b[(size_t)rn * a.H1 + h]) -
+                                      __bfloat162float(a.W1b[(size_t)ro * a.H1 + h]);
+}
+
+// ------------------------------------------------------------------ host --
+
+Mlp *get_mlp(rn_ctx *ctx, int32_t id)
+{
+    if (!ctx || id < 0 || id >= (int32_t)ctx->mlps.size()) return nullptr;
+    return ctx->mlps[(size_t)id].get();
+}
+
+int lookup(rn_ctx *ctx, int32_t id, Mlp *&m, Network *&n)
+{
+    m = get_mlp(ctx, id);
+    if (!m) return fail(ctx, RN_EINVAL, "unknown screen %d", id);
+    n = get_net(ctx, m->net);
+    if (!n) return fail(ctx, RN_EINVAL, "the screen's network is gone");
+    return RN_OK;
+}
+
+int check_launch(rn_ctx *ctx, const char *what, int kernels = 1)
+{
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    ctx->launches += kernels;
+    return RN_OK;
+}
+
+// tcgen05 tensor-core GEMM where the shape allows (every shape of the screen:
+// widths are multiples of 256, Dp of 128, batches of 128), else mma.sync.
+int gemm(rn_ctx *ctx, int epi, const GemmArgs &g)
+{
+    const cudaError_t e = gemm_tc_supported(g)
+                              ? launch_gemm_tc(epi, g, ctx->dev_err.p, ctx->sm_count, ctx->stream)
+                              : launch_gemm(epi, g, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "BF16 GEMM");
+    ctx->launches += 1;
+    return RN_OK;
+}
+
+// Scratch of a batch of up to B rows (multiple of 128).
+int ensure_batch(rn_ctx *ctx, Mlp &m, int32_t B)
+{
+    if (B <= m.Bcap) return RN_OK;
+    const size_t Dp = (size_t)m.Dp, H1 = (size_t)m.H1, H2 = (size_t)m.H2, b = (size_t)B;
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    RN_CUDA(ctx, m.oh.alloc(b * Dp));
+    RN_CUDA(ctx, m.ohT.alloc(Dp * b));
+    RN_CUDA(ctx, m.h1.alloc(b * H1));
+    RN_CUDA(ctx, m.h1T.alloc(H1 * b));
+    RN_CUDA(ctx, m.h2.alloc(b * H2));
+    RN_CUDA(ctx, m.dh2.alloc(b * H2));
+    RN_CUDA(ctx, m.dh2T.alloc(H2 * b));
+    RN_CUDA(ctx, m.dh1.alloc(b * H1));
+    RN_CUDA(ctx, m.dh1T.alloc(H1 * b));
+    RN_CUDA(ctx, m.part.alloc(b * (H2 / 64)));
+    RN_CUDA(ctx, m.y.alloc(b));
+    RN_CUDA(ctx, m.dy.alloc(b));
+    RN_CUDA(ctx, m.tgt.alloc(b));
+    RN_CUDA(ctx, m.idx.alloc(b));
+    RN_CUDA(ctx, m.xrows.alloc(b * (size_t)m.pstride));
+    RN_CUDA(ctx, m.colpart.alloc(64 * std::max(H1, H2)));
+    m.Bcap = B;
+    return RN_OK;
+}
+
+// BF16 copies of W1 and W2 from the FP32 masters.
+int refresh_copies(rn_ctx *ctx, Mlp &m)
+{
+    const float *W1 = m.theta.p, *W2 = m.theta.p + m.off_W2();
+    const dim3 t(32, 8);
+    transpose_kernel<float><<<dim3(m.H1 / 32, m.Dp / 32), t, 0, ctx->stream>>>(W1, m.H1, bp(m.W1T), m.Dp);
+    transpose_kernel<float><<<dim3(m.H2 / 32, m.H1 / 32), t, 0, ctx->stream>>>(W2, m.H2, bp(m.W2T), m.H1);
+    to_bf16_kernel<<<512, 256, 0, ctx->stream>>>(W1, bp(m.W1b), (size_t)m.Dp * m.H1);
+    to_bf16_kernel<<<256, 256, 0, ctx->stream>>>(W2, bp(m.W2b), (size_t)m.H1 * m.H2);
+    m.a1_valid = false;
+    return check_launch(ctx, "weight copies", 4);
+}
+
+// Column sums of a bf16 [R][C] matrix (coef-weighted) into out[C] (and, with
+// v, out[C] = sum of v[0..nv)).
+int colsum(rn_ctx *ctx, Mlp &m, const bf16 *A, int R, int C, const float *coef, float *out,
+           const float *v = nullptr, int nv = 0)
+{
+    const int S = 64, rows = (R + S - 1) / S;
+    colsum_kernel<<<dim3(C / 64, S), dim3(32, 8), 0, ctx->stream>>>(A, C, R, coef, rows,
+                                                                     m.colpart.p, C);
+    const int blocks = (C + 255) / 256 + (v ? 1 : 0);
+    colsum_finish_kernel<<<blocks, 256, 0, ctx->stream>>>(m.colpart.p, S, C, out, v, nv);
+    return check_launch(ctx, "column sums", 2);
+}
+
+// One batch of B rows (n real): forward, and with targets the loss and every
+// gradient into m.grad.  Rows come from X (stride xstride) through idx (or in
+// order).
+int run_batch(rn_ctx *ctx, Mlp &m, const int8_t *X, int64_t xstride, const int32_t *idx,
+              int32_t n, int32_t B, const float *tgt)
+{
+    const bool train = tgt != nullptr;
+    const int Dp = m.Dp, H1 = m.H1, H2 = m.H2, P = m.P;
+    cudaStream_t st = ctx->stream;
+    RN_CUDA(ctx, cudaMemsetAsync(m.oh.p, 0, sizeof(uint16_t) * (size_t)B * Dp, st));
+    if (train) RN_CUDA(ctx, cudaMemsetAsync(m.ohT.p, 0, sizeof(uint16_t) * (size_t)B * Dp, st));
+    onehot_kernel<<<dim3((P + 255) / 256, B), 256, 0, st>>>(
+        X, xstride, idx, n, P, m.row_base.p, m.row_base.p + P, bp(m.oh), Dp,
+        train ? bp(m.ohT) : nullptr, B);
+    int rc = check_launch(ctx, "one-hot kernel");
+    if (rc) return rc;
+    const float *th = m.theta.p;
+    GemmArgs g{};
+    // h1 = relu(OH W1 + b1)
+    g.A = bp(m.oh); g.lda = Dp; g.B = bp(m.W1T); g.ldb = Dp;
+    g.M = B; g.N = H1; g.K = Dp; g.out_bf16 = bp(m.h1); g.ldc = H1; g.bias = th + m.off_b1();
+    if ((rc = gemm(ctx, kBiasReluBf16, g))) return rc;
+    // h2 = relu(h1 W2 + b2); partials of w3 . h2
+    g = GemmArgs{};
+    g.A = bp(m.h1); g.lda = H1; g.B = bp(m.W2T); g.ldb = H1;
+    g.M = B; g.N = H2; g.K = H1; g.out_bf16 = train ? bp(m.h2) : nullptr; g.ldc = H2;
+    g.bias = th + m.off_b2(); g.w = th + m.off_w3(); g.part = m.part.p;
+    if ((rc = gemm(ctx, kBiasReluDot, g))) return rc;
+    if (train) RN_CUDA(ctx, cudaMemsetAsync(m.loss.p, 0, sizeof(double), st));
+    head_kernel<<<(B + 7) / 8, 256, 0, st>>>(m.part.p, H2 / 64, th + m.off_b3(), B, n, m.y.p,
+                                             tgt, m.dy.p, m.loss.p, bp(m.h2),
+                                             th + m.off_w3(), bp(m.dh2), H2);
+    if ((rc = check_launch(ctx, "head kernel"))) return rc;
+    if (!train) return RN_OK;
+    float *gr = m.grad.p;
+    const dim3 t(32, 8);
+    // dW2 = h1^T dh2
+    transpose_kernel<bf16><<<dim3(H1 / 32, B / 32), t, 0, st>>>(bp(m.h1), H1, bp(m.h1T), B);
+    transpose_kernel<bf16><<<dim3(H2 / 32, B / 32), t, 0, st>>>(bp(m.dh2), H2, bp(m.dh2T), B);
+    if ((rc = check_launch(ctx, "transposes", 2))) return rc;
+    g = GemmArgs{};
+    g.A = bp(m.h1T); g.lda = B; g.B = bp(m.dh2T); g.ldb = B;
+    g.M = H1; g.N = H2; g.K = B; g.out_f32 = gr + m.off_W2(); g.ldc = H2;
+    if ((rc = gemm(ctx, kStoreF32, g))) return rc;
+    // dh1 = (dh2 W2^T) [h1 > 0]
+    g = GemmArgs{};
+    g.A = bp(m.dh2); g.lda = H2; g.B = bp(m.W2b); g.ldb = H2;
+    g.M = B; g.N = H1; g.K = H2; g.out_bf16 = bp(m.dh1); g.ldc = H1; g.mask = bp(m.h1);
+    if ((rc = gemm(ctx, kMaskBf16, g))) return rc;
+    // dW1 = OH^T dh1
+    transpose_kernel<bf16><<<dim3(H1 / 32, B / 32), t, 0, st>>>(bp(m.dh1), H1, bp(m.dh1T), B);
+    if ((rc = check_launch(ctx, "transpose"))) return rc;
+    g = GemmArgs{};
+    g.A = bp(m.ohT); g.lda = B; g.B = bp(m.dh1T); g.ldb = B;
+    g.M = Dp; g.N = H1; g.K = B; g.out_f32 = gr; g.ldc = H1;
+    if ((rc = gemm(ctx, kStoreF32, g))) return rc;
+    // bias and output-layer gradients
+    if ((rc = colsum(ctx, m, bp(m.dh1), B, H1, nullptr, gr + m.off_b1()))) return rc;
+    if ((rc = colsum(ctx, m, bp(m.dh2), B, H2, nullptr, gr + m.off_b2()))) return rc;
+    // dw3 = sum_b dy_b h2[b] and, in the slot after it, db3 = sum_b dy_b
+    return colsum(ctx, m, bp(m.h2), B, H2, m.dy.p, gr + m.off_w3(), m.dy.p, B);
+}
+
+int32_t round_up(int32_t v, int32_t k) { return (v + k - 1) / k * k; }
+
+// Every value inside its parameter's domain (the one-hot encoding needs no more).
+int check_domains(rn_ctx *ctx, const Network &n, const int8_t *x, int64_t which)
+{
+    for (int32_t j = 0; j < n.P; ++j) {
+        int8_t vals[6];
+        const int k = domain_of(n, j, vals);
+        bool in = false;
+        for (int a = 0; a < k; ++a) in |= vals[a] == x[j];
+        if (!in)
+            return fail(ctx, RN_EINVAL, "vector %lld: parameter %d = %d is outside its domain",
+                        (long long)which, j, (int)x[j]);
+    }
+    return RN_OK;
+}
+
+// Host vectors [n][P] into the staging rows (values checked against their domains).
+int stage_rows(rn_ctx *ctx, Mlp &m, const Network &net, const int8_t *x, int32_t n)
+{
+    std::vector<int8_t> rows((size_t)n * m.pstride, 0);
+    for (int32_t r = 0; r < n; ++r) {
+        const int8_t *xr = x + (size_t)r * m.P;
+        if (int rc = check_domains(ctx, net, xr, r)) return rc;
+        std::memcpy(&rows[(size_t)r * m.pstride], xr, (size_t)m.P);
+    }
+    RN_CUDA(ctx, cudaMemcpyAsync(m.xrows.p, rows.data(), rows.size(), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RN_OK;
+}
+
+int weights_io(rn_ctx *ctx, Mlp &m, bool set, float *W1, float *b1, float *W2, float *b2,
+               float *w3, float *b3)
+{
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<float> th(m.n_theta, 0.f);
+    if (!set)
+        RN_CUDA(ctx, cudaMemcpy(th.data(), m.theta.p, th.size() * sizeof(float),
+                                cudaMemcpyDeviceToHost));
+    const size_t D = (size_t)m.D, H1 = (size_t)m.H1, H2 = (size_t)m.H2;
+    struct Part { float *p; size_t off, n; } parts[] = {
+        {W1, 0, D * H1}, {b1, m.off_b1(), H1}, {W2, m.off_W2(), H1 * H2},
+        {b2, m.off_b2(), H2}, {w3, m.off_w3(), H2}, {b3, m.off_b3(), 1}};
+    for (auto &p : parts) {
+        if (!p.p) continue;
+        if (set) std::memcpy(&th[p.off], p.p, p.n * sizeof(float));
+        else std::memcpy(p.p, &th[p.off], p.n * sizeof(float));
+    }
+    if (!set) return RN_OK;
+    RN_CUDA(ctx, cudaMemcpy(m.theta.p, th.data(), th.size() * sizeof(float),
+                            cudaMemcpyHostToDevice));
+    RN_CUDA(ctx, cudaMemset(m.adam_m.p, 0, m.n_theta * sizeof(float)));
+    RN_CUDA(ctx, cudaMemset(m.adam_v.p, 0, m.n_theta * sizeof(float)));
+    m.adam_t = 0;
+    return refresh_copies(ctx, m);
+}
+
+// Candidate buffers of the screened step for the network's chains.
+int ensure_screen(rn_ctx *ctx, Mlp &m, const Network &n, int32_t K, int32_t top)
+{
+    if (m.chains == n.n_chains && m.K == K && m.top == top) return RN_OK;
+    const size_t C = (size_t)n.n_chains;
+    const size_t M = (size_t)round_up((int32_t)(C * K), 128);
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    RN_CUDA(ctx, m.A1.alloc(C * m.H1));
+    RN_CUDA(ctx, m.hc.alloc(M * m.H1));
+    RN_CUDA(ctx, cudaMemset(m.hc.p, 0, M * m.H1 * sizeof(uint16_t)));
+    RN_CUDA(ctx, m.pc.alloc(M * (m.H2 / 64)));
+    RN_CUDA(ctx, m.cand.alloc(C * K));
+    RN_CUDA(ctx, m.sel.alloc(C * top));
+    RN_CUDA(ctx, m.xe.alloc(C * top * (size_t)n.pstride));
+    RN_CUDA(ctx, m.se.alloc(C * top));
+    m.chains = n.n_chains;
+    m.K = K;
+    m.top = top;
+    m.a1_valid = false;
+    return RN_OK;
+}
+
+}  // namespace
+}  // namespace rn
+
+using namespace rn;
+
+extern "C" {
+
+int rn_mlp_create(rn_ctx *ctx, int32_t net, int32_t h1, int32_t h2, int64_t capacity,
+                  int32_t *mlp_id, int32_t *onehot_width)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Network *n = get_net(ctx, net);
+    if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
+    if (!mlp_id) return fail(ctx, RN_EINVAL, "mlp_id is NULL");
+    if (h1 < 256 || h1 > 1024 || h1 % 256 || h2 < 256 || h2 > 1024 || h2 % 256)
+        return fail(ctx, RN_EINVAL, "hidden widths must be 256, 512, 768 or 1024");
+    if (capacity < 1 || capacity > ((int64_t)1 << 31) - 1)
+        return fail(ctx, RN_EINVAL, "capacity must be in 1 .. 2^31 - 1");
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    auto m = std::make_unique<Mlp>();
+    m->net = net;
+    m->P = n->P;
+    m->pstride = (n->P + 15) & ~15;
+    m->H1 = h1;
+    m->H2 = h2;
+    // one-hot blocks: parameter j's value v sits at row_base[j] + v, inside
+    // [row_off[j], row_off[j + 1])
+    std::vector<int32_t> tab(2 * (size_t)n->P + 1);
+    int32_t D = 0;
+    for (int32_t j = 0; j < n->P; ++j) {
+        int8_t vals[6];
+        const int k = domain_of(*n, j, vals);
+        tab[(size_t)j] = D - vals[0];
+        tab[(size_t)n->P + j] = D;
+        D += k;
+    }
+    tab[2 * (size_t)n->P] = D;
+    m->D = D;
+    m->Dp = round_up(D, 128);
+    m->scale = n->n_obs > 0 ? 1.0 / (double)n->n_obs : 1.0;
+    RN_CUDA(ctx, m->row_base.upload(tab));
+    m->n_theta = m->off_b3() + 1;
+    RN_CUDA(ctx, m->theta.alloc(m->n_theta));
+    RN_CUDA(ctx, m->grad.alloc(m->n_theta));
+    RN_CUDA(ctx, m->adam_m.alloc(m->n_theta));
+    RN_CUDA(ctx, m->adam_v.alloc(m->n_theta));
+    for (DevBuf<float> *b : {&m->theta, &m->grad, &m->adam_m, &m->adam_v})
+        RN_CUDA(ctx, cudaMemset(b->p, 0, m->n_theta * sizeof(float)));
+    RN_CUDA(ctx, m->W1T.alloc((size_t)m->Dp * h1));
+    RN_CUDA(ctx, m->W1b.alloc((size_t)m->Dp * h1));
+    RN_CUDA(ctx, m->W2T.alloc((size_t)h1 * h2));
+    RN_CUDA(ctx, m->W2b.alloc((size_t)h1 * h2));
+    RN_CUDA(ctx, m->loss.alloc(1));
+    m->cap = capacity;
+    RN_CUDA(ctx, m->set_x.alloc((size_t)capacity * m->pstride));
+    RN_CUDA(ctx, m->set_y.alloc((size_t)capacity));
+    if (int rc = refresh_copies(ctx, *m)) return rc;
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->mlps.push_back(std::move(m));
+    *mlp_id = (int32_t)ctx->mlps.size() - 1;
+    if (onehot_width) *onehot_width = D;
+    return RN_OK;
+}
+
+int rn_mlp_set_weights(rn_ctx *ctx, int32_t mlp, const float *W1, const float *b1,
+                       const float *W2, const float *b2, const float *w3, float b3)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Mlp *m;
+    Network *n;
+    if (int rc = lookup(ctx, mlp, m, n)) return rc;
+    if (!W1 || !b1 || !W2 || !b2 || !w3) return fail(ctx, RN_EINVAL, "weight array is NULL");
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    float b3v = b3;
+    return weights_io(ctx, *m, true, const_cast<float *>(W1), const_cast<float *>(b1),
+                      const_cast<float *>(W2), const_cast<float *>(b2), const_cast<float *>(w3),
+                      &b3v);
+}
+
+int rn_mlp_get_weights(rn_ctx *ctx, int32_t mlp, float *W1, float *b1, float *W2, float *b2,
+                       float *w3, float *b3)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Mlp *m;
+    Network *n;
+    if (int rc = lookup(ctx, mlp, m, n)) return rc;
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    return weights_io(ctx, *m, false, W1, b1, W2, b2, w3, b3);
+}
+
+int rn_mlp_forward(rn_ctx *ctx, int32_t mlp, int32_t n_vec, const int8_t *x, float *y)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Mlp *m;
+    Network *n;
+    if (int rc = lookup(ctx, mlp, m, n)) return rc;
+    if (n_vec < 0 || (n_vec > 0 && (!x || !y))) return fail(ctx, RN_EINVAL, "bad vectors");
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int32_t chunk = 8192;
+    for (int32_t r0 = 0; r0 < n_vec; r0 += chunk) {
+        const int32_t k = std::min(chunk, n_vec - r0), B = round_up(k, 128);
+        int rc;
+        if ((rc = ensure_batch(ctx, *m, B))) return rc;
+        if ((rc = stage_rows(ctx, *m, *n, x + (size_t)r0 * m->P, k))) return rc;
+        if ((rc = run_batch(ctx, *m, m->xrows.p, m->pstride, nullptr, k, B, nullptr))) return rc;
+        RN_CUDA(ctx, cudaMemcpyAsync(y + r0, m->y.p, sizeof(float) * k, cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+        RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if ((rc = check_device_flag(ctx))) return rc;
+    }
+    return RN_OK;
+}
+
+int rn_mlp_gradients(rn_ctx *ctx, int32_t mlp, int32_t n_vec, const int8_t *x, const float *target,
+                     float *loss, float *gW1, float *gb1, float *gW2, float *gb2, float *gw3,
+                     float *gb3)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Mlp *m;
+    Network *n;
+    if (int rc = lookup(ctx, mlp, m, n)) return rc;
+    if (n_vec < 1 || n_vec > 65536 || !x || !target)
+        return fail(ctx, RN_EINVAL, "need 1 .. 65536 vectors and targets");
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int32_t B = round_up(n_vec, 128);
+    int rc;
+    if ((rc = ensure_batch(ctx, *m, B))) return rc;
+    if ((rc = stage_rows(ctx, *m, *n, x, n_vec))) return rc;
+    RN_CUDA(ctx, cudaMemcpyAsync(m->tgt.p, target, sizeof(float) * n_vec, cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    if ((rc = run_batch(ctx, *m, m->xrows.p, m->pstride, nullptr, n_vec, B, m->tgt.p))) return rc;
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if ((rc = check_device_flag(ctx))) return rc;
+    std::vector<float> g(m->n_theta);
+    RN_CUDA(ctx, cudaMemcpy(g.data(), m->grad.p, g.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    double sse = 0;
+    RN_CUDA(ctx, cudaMemcpy(&sse, m->loss.p, sizeof sse, cudaMemcpyDeviceToHost));
+    if (loss) *loss = (float)(sse / n_vec);
+    const size_t D = (size_t)m->D, H1 = (size_t)m->H1, H2 = (size_t)m->H2;
+    if (gW1) std::memcpy(gW1, &g[0], D * H1 * sizeof(float));
+    if (gb1) std::memcpy(gb1, &g[m->off_b1()], H1 * sizeof(float));
+    if (gW2) std::memcpy(gW2, &g[m->off_W2()], H1 * H2 * sizeof(float));
+    if (gb2) std::memcpy(gb2, &g[m->off_b2()], H2 * sizeof(float));
+    if (gw3) std::memcpy(gw3, &g[m->off_w3()], H2 * sizeof(float));
+    if (gb3) *gb3 = g[m->off_b3()];
+    return RN_OK;
+}
+
+int rn_mlp_add_samples(rn_ctx *ctx, int32_t mlp, int32_t n_vec, const int8_t *x,
+                       const float *target, int64_t *count)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Mlp *m;
+    Network *n;
+    if (int rc = lookup(ctx, mlp, m, n)) return rc;
+    if (n_vec < 0 || (n_vec > 0 && (!x || !target))) return fail(ctx, RN_EINVAL, "bad samples");
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    // the last min(n, cap) pairs survive; copied in at most two runs of the ring
+    const int64_t keep = std::min<int64_t>(n_vec, m->cap), first = n_vec - keep;
+    std::vector<int8_t> rows((size_t)keep * m->pstride, 0);
+    for (int64_t r = 0; r < keep; ++r) {
+        const int8_t *xr = x + (size_t)(first + r) * m->P;
+        if (int rc = check_domains(ctx, *n, xr, first + r)) return rc;
+        std::memcpy(&rows[(size_t)r * m->pstride], xr, (size_t)m->P);
+    }
+    m->head = (m->head + first) % m->cap;
+    for (int64_t r = 0; r < keep;) {
+        const int64_t run = std::min(keep - r, m->cap - m->head);
+        RN_CUDA(ctx, cudaMemcpy(m->set_x.p + m->head * m->pstride, &rows[(size_t)r * m->pstride],
+                                (size_t)run * m->pstride, cudaMemcpyHostToDevice));
+        RN_CUDA(ctx, cudaMemcpy(m->set_y.p + m->head, target + first + r, sizeof(float) * run,
+                                cudaMemcpyHostToDevice));
+        m->head = (m->head + run) % m->cap;
+        r += run;
+    }
+    m->count = std::min(m->count + n_vec, m->cap);
+    if (count) *count = m->count;
+    return RN_OK;
+}
+
+int rn_mlp_log_chains(rn_ctx *ctx, int32_t mlp, int64_t *count)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Mlp *m;
+    Network *n;
+    if (int rc = lookup(ctx, mlp, m, n)) return rc;
+    if (!n->chains_valid) return fail(ctx, RN_ESTATE, "the network has no chains");
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    const DevChains ch = n->chains();
+    log_chains_kernel<<<(ch.n + 7) / 8, 256, 0, ctx->stream>>>(ch, m->set_x.p, m->set_y.p,
+                                                               m->head, m->cap, (float)m->scale);
+    if (int rc = check_launch(ctx, "log kernel")) return rc;
+    m->head = (m->head + ch.n) % m->cap;
+    m->count = std::min(m->count + ch.n, m->cap);
+    if (count) *count = m->count;
+    return RN_OK;
+}
+
+int rn_mlp_train(rn_ctx *ctx, int32_t mlp, int32_t steps, int32_t batch, float lr, uint64_t seed,
+                 float *loss)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Mlp *m;
+    Network *n;
+    if (int rc = lookup(ctx, mlp, m, n)) return rc;
+    if (steps < 0 || batch < 128 || batch > 65536 || batch % 128)
+        return fail(ctx, RN_EINVAL, "batch must be a multiple of 128 in 128 .. 65536");
+    if (!(lr > 0.f) || !std::isfinite(lr)) return fail(ctx, RN_EINVAL, "bad learning rate");
+    if (m->count == 0) return fail(ctx, RN_ESTATE, "the training set is empty");
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    int rc;
+    if ((rc = ensure_batch(ctx, *m, batch))) return rc;
+    const double b1 = 0.9, b2 = 0.999;
+    for (int32_t s = 0; s < steps; ++s) {
+        sample_kernel<<<(batch + 255) / 256, 256, 0, ctx->stream>>>(
+            seed, (uint32_t)s, batch, (uint32_t)m->count, m->set_y.p, m->idx.p, m->tgt.p);
+        if ((rc = check_launch(ctx, "sample kernel"))) return rc;
+        if ((rc = run_batch(ctx, *m, m->set_x.p, m->pstride, m->idx.p, batch, batch, m->tgt.p)))
+            return rc;
+        m->adam_t += 1;
+        const double c1 = 1.0 / (1.0 - std::pow(b1, (double)m->adam_t));
+        const double c2 = 1.0 / (1.0 - std::pow(b2, (double)m->adam_t));
+        adam_kernel<<<1024, 256, 0, ctx->stream>>>(m->theta.p, m->grad.p, m->adam_m.p,
+                                                   m->adam_v.p, m->n_theta, lr, (float)b1,
+                                                   (float)b2, (float)c1, (float)c2, 1e-8f);
+        if ((rc = check_launch(ctx, "Adam kernel"))) return rc;
+        if ((rc = refresh_copies(ctx, *m))) return rc;
+    }
+    if (loss) {
+        double sse = 0;
+        RN_CUDA(ctx, cudaMemcpyAsync(&sse, m->loss.p, sizeof sse, cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+        RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if ((rc = check_device_flag(ctx))) return rc;
+        *loss = steps > 0 ? (float)(sse / batch) : 0.f;
+    }
+    return RN_OK;
+}
+
+int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K, int32_t top,
+                       double eps, int64_t sweeps)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Mlp *m;
+    Network *n;
+    if (int rc = lookup(ctx, mlp, m, n)) return rc;
+    if (!s) return fail(ctx, RN_EINVAL, "schedule is NULL");
+    if (K < 1 || K > 32 || top < 1 || top > 4 || top > K)
+        return fail(ctx, RN_EINVAL, "need 1 <= top <= 4, top <= K <= 32");
+    if (!(eps >= 0.0 && eps <= 1.0)) return fail(ctx, RN_EINVAL, "eps must be in [0, 1]");
+    if (sweeps < 0 || s->iters_per_level < 1) return fail(ctx, RN_EINVAL, "bad sweeps/schedule");
+    if (!(s->T0 > 0.0) || !(s->alpha > 0.0) || !std::isfinite(s->T0) || !std::isfinite(s->alpha))
+        return fail(ctx, RN_EINVAL, "T0 and alpha must be positive");
+    if (s->reset_to_best || s->global_sync)
+        return fail(ctx, RN_EUNSUPPORTED, "screened annealing runs without reset/global sync");
+    if (!n->chains_valid) return fail(ctx, RN_ESTATE, "no chains (call rn_init_chains)");
+    if (n->N > 4096 || n->pstride > 8192)
+        return fail(ctx, RN_EUNSUPPORTED, "screened annealing covers N <= 4096, P <= 8192");
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (sweeps == 0) return RN_OK;
+    int rc;
+    if ((rc = ensure_screen(ctx, *m, *n, K, top))) return rc;
+    ctx->batch.g0_synced = false;
+    const DevChains ch = n->chains();
+    const int blocks = (ch.n + kScreenWarps - 1) / kScreenWarps;
+    if (!m->a1_valid || m->a1_gen != ctx->gen || m->a1_step != n->step) {
+        embed_chains_kernel<<<ch.n, 256, 0, ctx->stream>>>(ch, m->P, m->row_base.p, bp(m->W1b),
+                                                           m->theta.p + m->off_b1(), m->H1,
+                                                           m->A1.p);
+        if ((rc = check_launch(ctx, "embed kernel"))) return rc;
+        m->a1_valid = true;
+        m->a1_gen = ctx->gen;
+    }
+    const int64_t iters = s->iters_per_level;
+    DevSched sc{};
+    bool cached = false;
+    if ((rc = thresholds_for(ctx, *s, n->step / iters, (n->step + sweeps - 1) / iters,
+                             n->max_score, sc, cached)))
+        return rc;
+    sc.iters = iters;
+    ScreenArgs a{};
+    a.net = n->dev();
+    a.ch = ch;
+    a.K = K;
+    a.top = top;
+    a.H1 = m->H1;
+    a.nparts = m->H2 / 64;
+    const double et = std::floor(eps * 4294967296.0);
+    a.eps_thr = et >= 4294967296.0 ? ((uint64_t)1 << 32) : (uint64_t)et;
+    a.row_base = m->row_base.p;
+    a.W1b = bp(m->W1b);
+    a.b3 = m->theta.p + m->off_b3();
+    a.A1 = m->A1.p;
+    a.hc = bp(m->hc);
+    a.pc = m->pc.p;
+    a.cand = m->cand.p;
+    a.sel = m->sel.p;
+    a.xe = m->xe.p;
+    a.se = m->se.p;
+    const int region = (int)(n->pstride + 2 * ((n->N + 15) & ~15));
+    const size_t smem = (size_t)kScreenWarps * region;
+    RN_CUDA(ctx, cudaFuncSetAttribute(screen_propose_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int32_t M = round_up(ch.n * K, 128);
+    GemmArgs g{};
+    g.A = a.hc; g.lda = m->H1; g.B = bp(m->W2T); g.ldb = m->H1;
+    g.M = M; g.N = m->H2; g.K = m->H1; g.ldc = m->H2;
+    g.bias = m->theta.p + m->off_b2(); g.w = m->theta.p + m->off_w3(); g.part = m->pc.p;
+    for (int64_t k = 0; k < sweeps; ++k) {
+        a.g = n->step + k;
+        screen_propose_kernel<<<blocks, kScreenWarps * 32, smem, ctx->stream>>>(a, region);
+        if ((rc = check_launch(ctx, "screen propose kernel"))) return rc;
+        if ((rc = gemm(ctx, kBiasReluDot, g))) return rc;
+        screen_select_kernel<<<blocks, kScreenWarps * 32, 0, ctx->stream>>>(a);
+        if ((rc = check_launch(ctx, "screen select kernel"))) return rc;
+        if ((rc = evaluate_device_impl(ctx, *n, ch.n * top, m->xe.p, n->pstride, m->se.p, nullptr,
+                                       nullptr)))
+            return rc;
+        screen_commit_kernel<<<blocks, kScreenWarps * 32, 0, ctx->stream>>>(a, sc);
+        if ((rc = check_launch(ctx, "screen commit kernel"))) return rc;
+    }
+    n->step += sweeps;
+    m->a1_step = n->step;
+    return RN_OK;
+}
+
+}  // extern "C"

@@ -51,6 +51,16 @@ SIGNATURES = {
     "rn_launch_count": (_c_int, [_vp, _vp]),
     "rn_batch_config": (_c_int, [_vp, _vp, _vp]),
     "rn_level_sync_noalloc": (_c_int, [_vp, _vp, _c_i32, _c_i64, _c_i32, _vp]),
+    "rn_mlp_create": (_c_int, [_vp, _c_i32, _c_i32, _c_i32, _c_i64, _vp, _vp]),
+    "rn_mlp_set_weights": (_c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp, ctypes.c_float]),
+    "rn_mlp_get_weights": (_c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "rn_mlp_forward": (_c_int, [_vp, _c_i32, _c_i32, _vp, _vp]),
+    "rn_mlp_gradients": (_c_int, [_vp, _c_i32, _c_i32, _vp, _vp] + [_vp] * 7),
+    "rn_mlp_add_samples": (_c_int, [_vp, _c_i32, _c_i32, _vp, _vp, _vp]),
+    "rn_mlp_log_chains": (_c_int, [_vp, _c_i32, _vp]),
+    "rn_mlp_train": (_c_int, [_vp, _c_i32, _c_i32, _c_i32, ctypes.c_float, _c_u64, _vp]),
+    "rn_anneal_screened": (_c_int, [_vp, _c_i32, ctypes.POINTER(rn_schedule), _c_i32, _c_i32,
+                                    ctypes.c_double, _c_i64]),
     "rn_synchronize": (_c_int, [_vp]),
 }
 
@@ -229,3 +239,84 @@ def rn_level_sync_noalloc(x_best_dev, d_best_dev, n_chains, row_bytes, n_params,
     _check(None, load_library().rn_level_sync_noalloc(_dev(x_best_dev), _dev(d_best_dev),
                                                       int(n_chains), int(row_bytes),
                                                       int(n_params), s))
+
+
+# ---- learned proposal screen -------------------------------------------------
+
+def rn_mlp_create(ctx, net, h1=512, h2=512, capacity=1 << 20):
+    """Returns (screen id, one-hot width D)."""
+    mid, D = ctypes.c_int32(-1), ctypes.c_int32(0)
+    _check(ctx, load_library().rn_mlp_create(ctx, int(net), int(h1), int(h2), int(capacity),
+                                             ctypes.byref(mid), ctypes.byref(D)))
+    return mid.value, D.value
+
+
+_WEIGHTS = ("W1", "b1", "W2", "b2", "w3")
+
+
+def rn_mlp_set_weights(ctx, mlp, params):
+    """params: dict W1 [D][h1], b1, W2 [h1][h2], b2, w3, b3."""
+    a = {k: _arr(params[k], np.float32) for k in _WEIGHTS}
+    _check(ctx, load_library().rn_mlp_set_weights(ctx, int(mlp), *[_p(a[k]) for k in _WEIGHTS],
+                                                  float(params["b3"])))
+
+
+def rn_mlp_get_weights(ctx, mlp, D, h1, h2):
+    out = dict(W1=np.zeros((D, h1), np.float32), b1=np.zeros(h1, np.float32),
+               W2=np.zeros((h1, h2), np.float32), b2=np.zeros(h2, np.float32),
+               w3=np.zeros(h2, np.float32))
+    b3 = np.zeros(1, np.float32)
+    _check(ctx, load_library().rn_mlp_get_weights(ctx, int(mlp), *[_p(out[k]) for k in _WEIGHTS],
+                                                  _p(b3)))
+    out["b3"] = float(b3[0])
+    return out
+
+
+def rn_mlp_forward(ctx, mlp, x):
+    x = _arr(np.atleast_2d(x), np.int8)
+    y = np.zeros(x.shape[0], np.float32)
+    _check(ctx, load_library().rn_mlp_forward(ctx, int(mlp), x.shape[0], _p(x), _p(y)))
+    return y
+
+
+def rn_mlp_gradients(ctx, mlp, x, target, D, h1, h2):
+    """Returns (loss, grads dict with the keys of rn_mlp_get_weights)."""
+    x = _arr(np.atleast_2d(x), np.int8)
+    t = _arr(target, np.float32)
+    g = dict(W1=np.zeros((D, h1), np.float32), b1=np.zeros(h1, np.float32),
+             W2=np.zeros((h1, h2), np.float32), b2=np.zeros(h2, np.float32),
+             w3=np.zeros(h2, np.float32))
+    loss, gb3 = ctypes.c_float(0), ctypes.c_float(0)
+    _check(ctx, load_library().rn_mlp_gradients(ctx, int(mlp), x.shape[0], _p(x), _p(t),
+                                                ctypes.byref(loss),
+                                                *[_p(g[k]) for k in _WEIGHTS],
+                                                ctypes.byref(gb3)))
+    g["b3"] = gb3.value
+    return loss.value, g
+
+
+def rn_mlp_add_samples(ctx, mlp, x, target):
+    x = _arr(np.atleast_2d(x), np.int8)
+    t = _arr(target, np.float32)
+    count = ctypes.c_int64(0)
+    _check(ctx, load_library().rn_mlp_add_samples(ctx, int(mlp), x.shape[0], _p(x), _p(t),
+                                                  ctypes.byref(count)))
+    return count.value
+
+
+def rn_mlp_log_chains(ctx, mlp):
+    count = ctypes.c_int64(0)
+    _check(ctx, load_library().rn_mlp_log_chains(ctx, int(mlp), ctypes.byref(count)))
+    return count.value
+
+
+def rn_mlp_train(ctx, mlp, steps, batch=4096, lr=1e-3, seed=0):
+    loss = ctypes.c_float(0)
+    _check(ctx, load_library().rn_mlp_train(ctx, int(mlp), int(steps), int(batch), float(lr),
+                                            int(seed), ctypes.byref(loss)))
+    return loss.value
+
+
+def rn_anneal_screened(ctx, mlp, sched: rn_schedule, sweeps, K=32, top=2, eps=0.0):
+    _check(ctx, load_library().rn_anneal_screened(ctx, int(mlp), ctypes.byref(sched), int(K),
+                                                  int(top), float(eps), int(sweeps)))

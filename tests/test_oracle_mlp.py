@@ -60,3 +60,15 @@ def test_mlp_gradients_match_finite_differences():
             num = (loss_at(flat[k] + eps) - loss_at(flat[k] - eps)) / (2 * eps)
             ana = np.reshape(grads[name], -1)[k] if shape else grads[name]
             assert abs(num - ana) <= 1e-6 * max(1.0, abs(num)), (name, k, num, ana)
+
+
+def test_bf16_rounding_pins():
+    # BF16 keeps 8 significant bits: spacing 2^-7 on [1, 2); ties go to the
+    # even neighbour
+    from tests.mlp_util import bf16
+    x = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -20, 3.0,
+                  -(1 + 3 * 2.0 ** -8), 2.0 ** -130], np.float32)
+    want = np.array([1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7, 3.0, -(1 + 2.0 ** -6), 0.0], np.float32)
+    np.testing.assert_array_equal(bf16(x)[:5], want[:5])
+    # subnormal input keeps its top bits (2^-130 is exact in BF16)
+    assert bf16(x)[5] == np.float32(2.0 ** -130)
