@@ -45,6 +45,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true",
+                    help="skip the time-to-target comparison (screened vs plain annealing)")
+    ap.add_argument("--ttt-seeds", type=int, default=3)
+    ap.add_argument("--screened", action="store_true",
+                    help="time screened steps (K = 32 candidates ranked by a seeded one-hot "
+                         "MLP, top 2 simulated exactly) instead of plain sweeps; value counts "
+                         "exact evaluations")
     return ap.parse_args()
 
 
@@ -54,6 +61,10 @@ def algorithmic_ops_per_eval(w):
     entry)."""
     return w.C * (w.T - 1) * (2 * w.E + 12 * w.N) + 3 * int(w.observed.sum())
 
+
+# DRAM bytes per annealing launch (read + write) from an ncu capture of the
+# current kernel: the chain state read once, independent of sweeps per launch.
+ANNEAL_TRAFFIC = {"n120_c8_t21": 9.26e6}
 
 L2_NOTE = ("working set (network tables + chain state) is L2-resident by design; L2 flushed "
            "with a 512 MiB write between timed steps, outside the step events")
@@ -265,8 +276,16 @@ def run_ours(args, rank, world, local_rank):
     sched = R.schedule(ws[0].T0, ws[0].alpha)
     R.rn_prepare_schedule(ctx, sched, (args.warmup + args.steps) * S)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    step = lambda: R.rn_anneal(ctx, sched, S)
+    top = 1
+    if args.screened:
+        if len(ws) != 1:
+            raise SystemExit("--screened runs one network")
+        mid = screen_for(R, ctx, ids[0], ws[0])
+        top = 2
+        step = lambda: R.rn_anneal_screened(ctx, mid, sched, S, K=32, top=top, eps=0.0)
     for _ in range(args.warmup):
-        R.rn_anneal(ctx, sched, S)
+        step()
     R.rn_synchronize(ctx)
 
     def nulls_now():
@@ -289,7 +308,7 @@ def run_ours(args, rank, world, local_rank):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        R.rn_anneal(ctx, sched, S)
+        step()
         e1.record(stream)
         times.append((e0, e1))
     torch.cuda.synchronize()
@@ -300,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
     launches = R.rn_launch_count(ctx) - l0
     step_ms = [a.elapsed_time(b) for a, b in times]
     nulls = [a - b for a, b in zip(nulls_now(), before)]
-    evals_w = [w.n_chains * S * args.steps - z for w, z in zip(ws, nulls)]
+    evals_w = [w.n_chains * S * args.steps * top - z for w, z in zip(ws, nulls)]
     evals = sum(evals_w)
     total_s = sum(step_ms) / 1000.0
 
@@ -323,9 +342,14 @@ def run_ours(args, rank, world, local_rank):
     f_hz = (clk.get("sm_mhz") or 0.0) * 1e6
     alu_per_clk = peaks.get("alu", 0.0)
     peak = sm_count * alu_per_clk * f_hz if f_hz and alu_per_clk > 0 else None
+    traffic = ANNEAL_TRAFFIC.get(args.workload) if len(ws) == 1 else None
     roofline = {"bound": "alu", "achieved": achieved / 1e12,
                 "peak": None if peak is None else peak / 1e12, "unit": "Tops/s",
-                "frac": None if peak is None else achieved / peak, "traffic": None,
+                "frac": None if peak is None else achieved / peak, "traffic": traffic,
+                "traffic_basis": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu "
+                                  "capture of this kernel (20 sweeps per launch): the chain "
+                                  "state read once per launch; everything else is L2-resident, "
+                                  "so it does not grow with sweeps per launch") if traffic else None,
                 "kernel": "anneal_batch_kernel" if len(ws) > 1 else "anneal_kernel",
                 "ops_per_eval": (algorithmic_ops_per_eval(ws[0]) if len(ws) == 1
                                  else "C (T-1) (2E + 12N) + 3 n_obs per network"),
@@ -345,8 +369,16 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline, "clocks": clk, "gpu_launches": launches}
     if len(ws) > 1:
         line["batch"] = R.rn_batch_config(ctx)
+    if args.screened:
+        line["config"]["step"] = ("screened: K = 32 candidates per chain ranked by a 512-512 "
+                                  "one-hot MLP (tcgen05 BF16 GEMM), top 2 simulated exactly")
+        line["roofline"] = {"bound": "tensor", "kernel": "gemm_tc_kernel (layer 2)",
+                            "flop_per_step": 2 * ws[0].n_chains * 32 * 512 * 512 * S,
+                            "note": "per-kernel split of a screened step: profiles/"}
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(args, R, ws, local_rank, stream)
+    if rank == 0 and not args.no_ttt and world == 1 and not args.screened:
+        line["time_to_target"] = time_to_target(args, R, local_rank, stream)
     R.rn_destroy(ctx)
     if rank == 0 and not args.no_cpu_baseline and world == 1 and len(ws) == 1:
         line["cpu_baseline"] = oracle_rate(args.workload, args.cpu_seconds)
@@ -392,6 +424,123 @@ def e2e(args, R, ws, device, stream):
             "path": "rn_create + rn_load_network + rn_load_timecourse + rn_init_chains per "
                     "network + rn_anneal(one step) + rn_get_best per network, host buffers, "
                     "wall clock"}
+
+def screen_for(R, ctx, nid, w, seed=13, h=512, capacity=1):
+    """A screen with seeded initial weights (a step's cost does not depend on them)."""
+    mid, D = R.rn_mlp_create(ctx, nid, h, h, capacity)
+    rng = np.random.default_rng(seed)
+    R.rn_mlp_set_weights(ctx, mid, dict(
+        W1=(rng.standard_normal((D, h)) * 0.5 / np.sqrt(w.P)).astype(np.float32),
+        b1=np.zeros(h, np.float32),
+        W2=(rng.standard_normal((h, h)) * np.sqrt(2 / h)).astype(np.float32),
+        b2=np.zeros(h, np.float32),
+        w3=(rng.standard_normal(h) / np.sqrt(h)).astype(np.float32), b3=0.0))
+    return mid
+
+
+def time_to_target(args, R, device, stream, name="mtb_63n_178e"):
+    """Wall-clock time until the best chain reaches the target score (planted
+    score + ceil(0.02 n_obs)), plain annealing against screened annealing (K = 32
+    candidates per chain and step ranked by the one-hot MLP, the top 2 simulated
+    exactly), same network, chains, schedule and seeds; median over seeds.  The
+    screen is trained beforehand (offline, timed separately) on 1.02M pairs
+    logged from an independent plain run of the same network."""
+    from scipy.stats import spearmanr
+    w = synth.make(name)
+    n_obs = int(w.observed.sum())
+    ctx = R.rn_create(device, stream.cuda_stream)
+    nid, ref = setup_problem(R, ctx, w)
+    R.rn_destroy(ctx)
+    # the planted vector scores 0 on noise-free data (its own trajectories)
+    target = 0 + math.ceil(0.02 * n_obs)
+    sched = R.schedule(w.T0, w.alpha)
+    cap = 30000
+    K, top, eps = 32, 2, 0.05
+
+    def fresh():
+        c = R.rn_create(device, stream.cuda_stream)
+        i = R.rn_load_network(c, w.src, w.dst, w.fast)
+        R.rn_load_timecourse(c, i, w.init, ref, w.observed, w.knockout)
+        R.rn_prepare_schedule(c, sched, cap)
+        return c, i
+
+    # screen: logged pairs from an independent plain run, then GPU training
+    ctx, nid = fresh()
+    mid = screen_for(R, ctx, nid, w, capacity=1 << 20)
+    R.rn_init_chains(ctx, nid, w.n_chains, 7)
+    t0 = time.perf_counter()
+    for _ in range(250):
+        R.rn_anneal(ctx, sched, 8)
+        pairs = R.rn_mlp_log_chains(ctx, mid)
+    R.rn_synchronize(ctx)
+    t_log = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    steps, batch = 3000, 4096
+    loss = R.rn_mlp_train(ctx, mid, steps, batch=batch, lr=1e-3, seed=3)
+    t_train = time.perf_counter() - t0
+    # held-out: states of another run at three stages
+    R.rn_init_chains(ctx, nid, 1024, 99)
+    Xh, yh = [], []
+    for s in (100, 1000, 4000):
+        R.rn_anneal(ctx, sched, s - R.rn_get_chain_state(ctx, nid, 1024)["step"])
+        st = R.rn_get_chain_state(ctx, nid, 1024)
+        Xh.append(st["x_cur"])
+        yh.append(st["d_cur"] / n_obs)
+    Xh, yh = np.concatenate(Xh), np.concatenate(yh)
+    pred = R.rn_mlp_forward(ctx, mid, Xh)
+    D = R.rn_mlp_create(ctx, nid, 512, 512, 1)[1]   # the one-hot width
+    weights = R.rn_mlp_get_weights(ctx, mid, D, 512, 512)
+    R.rn_destroy(ctx)
+
+    def run(seed, screened):
+        c, i = fresh()
+        m = None
+        if screened:
+            m, _ = R.rn_mlp_create(c, i, 512, 512, 1)
+            R.rn_mlp_set_weights(c, m, weights)
+        R.rn_init_chains(c, i, w.n_chains, seed)
+        R.rn_synchronize(c)
+        chunk = 20 if screened else 100
+        t0 = time.perf_counter()
+        done = 0
+        best = None
+        while done < cap:
+            if screened:
+                R.rn_anneal_screened(c, m, sched, chunk, K=K, top=top, eps=eps)
+            else:
+                R.rn_anneal(c, sched, chunk)
+            done += chunk
+            best = R.rn_get_best(c, i)[1]
+            if best <= target:
+                break
+        dt = time.perf_counter() - t0
+        R.rn_destroy(c)
+        return dict(seconds=dt, steps=done, best=int(best), reached=bool(best <= target),
+                    exact_evals=done * w.n_chains * (top if screened else 1))
+
+    seeds = [101 + k for k in range(max(1, args.ttt_seeds))]
+    run(seeds[0], False), run(seeds[0], True)            # warm-up (build, caches)
+    plain = [run(sd, False) for sd in seeds]
+    scr = [run(sd, True) for sd in seeds]
+    med = lambda rs: float(np.median([r["seconds"] for r in rs]))
+    return {"workload": name, "chains": w.n_chains, "target_score": target,
+            "target_rule": "planted score 0 + ceil(0.02 n_obs)", "n_obs": n_obs,
+            "schedule": {"T0": w.T0, "alpha": w.alpha, "iters_per_level": 1},
+            "plain_s": med(plain), "screened_s": med(scr),
+            "speedup": med(plain) / med(scr), "seeds": seeds,
+            "plain": plain, "screened": scr,
+            "screen": {"K": K, "top": top, "eps": eps, "hidden": [512, 512], "onehot_width": D,
+                       "dtype": "bf16 x bf16 -> fp32 (tcgen05)",
+                       "train_pairs": int(pairs), "train_steps": steps, "batch": batch,
+                       "log_s": t_log, "train_s": t_train, "last_loss": loss,
+                       "heldout_rmse": float(np.sqrt(np.mean((pred - yh) ** 2))),
+                       "heldout_target_std": float(np.std(yh)),
+                       "heldout_spearman": float(spearmanr(pred, yh).correlation),
+                       "heldout": "3072 states of an independent run after 100/1000/4000 sweeps",
+                       "tolerance": "held-out Spearman >= 0.3, RMSE <= 1.25 x target std"},
+            "timing": "wall clock, one host sync per chunk (plain 100 sweeps, screened 20 "
+                      "steps) to read the best score; screen training excluded (offline)"}
+
 
 def main():
     args = parse()
