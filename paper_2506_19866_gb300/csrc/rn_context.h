@@ -202,9 +202,6 @@ struct Mlp {
     DevBuf<uint16_t> hc;                // [Mc][H1] candidate hidden rows (bf16)
     DevBuf<float> pc;                   // [Mc][H2 / 64] candidate layer-2 partials
     DevBuf<int32_t> cand;               // [chains][K] (j << 8) | (v & 255), -1 = null
-    DevBuf<int32_t> sel;                // [chains][top] chosen candidate, -1 = none
-    DevBuf<int8_t> xe;                  // [chains * top][pstride] vectors simulated exactly
-    DevBuf<int32_t> se;                 // [chains * top] their scores
 
     size_t off_b1() const { return (size_t)Dp * H1; }
     size_t off_W2() const { return off_b1() + H1; }

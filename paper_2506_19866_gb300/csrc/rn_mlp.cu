@@ -16,10 +16,10 @@
 //              layer-1 pre-activation A1 (sparse FP32 update: one parameter
 //              changes one row of the one-hot sum)
 //   GEMM 2     partials of w3 . relu(h1 W2 + b2)
-//   select     top candidates by predicted y, their vectors for exact scoring
-//   evaluate   Simulate + score of Table 1 (the exact kernel)
-//   commit     Metropolis test of Table 1 against the host threshold tables;
-//              x, delta, best, counters and A1 follow an accepted move
+//   finish     top candidates by predicted y, each simulated exactly on the
+//              chain's tables (Table 1's Simulate and score), Metropolis test
+//              of Table 1 against the host threshold tables; x, delta, best,
+//              counters and A1 follow an accepted move
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -257,9 +257,6 @@ struct ScreenArgs {
     bf16 *hc;                           // [M][H1]
     const float *pc;                    // [M][nparts]
     int32_t *cand;                      // [chains][K]
-    int32_t *sel;                       // [chains][top]
-    int8_t *xe;                         // [chains * top][pstride]
-    const int32_t *se;                  // [chains * top]
 };
 
 constexpr int kScreenWarps = 4;
@@ -348,14 +345,22 @@ __device__ __forceinline__ uint32_t float_key(float y)
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// Warp per chain: the candidates to simulate (fallback: candidate 0 only;
-// otherwise the `top` distinct moves of lowest predicted y, lowest index on
-// ties) and their vectors x_cur with the move applied.
-__global__ void __launch_bounds__(kScreenWarps * 32) screen_select_kernel(ScreenArgs a)
+constexpr int kMaxTop = 4;
+
+// Warp per chain, after the layer-2 GEMM: the candidates to simulate
+// (fallback: candidate 0 only; otherwise the `top` distinct moves of lowest
+// predicted y, lowest candidate index on ties), each simulated exactly on the
+// chain's tables (change, Simulate, undo: Table 1's Simulate of x with one
+// parameter changed), the one of lowest exact score (first on ties) to the
+// Metropolis test of Table 1 against the host threshold tables (word 2 of the
+// step draw).  An accepted move updates x_cur, delta_cur, the best vector
+// (strict improvement), the counters and A1.  A step without a candidate is a
+// null move.
+template <class Path>
+__device__ __forceinline__ void screen_finish(const ScreenArgs &a, const DevSched &sc, Path &P,
+                                              int c, int lane)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.x * kScreenWarps + warp;
-    if (c >= a.ch.n) return;
+    const DevNet &net = a.net;
     const uint4 r = step_draw(a.ch, a.g, c, 0u);
     const bool fallback = (uint64_t)r.w < a.eps_thr;
     const int mv = lane < a.K ? a.cand[(size_t)c * a.K + lane] : -1;
@@ -371,56 +376,63 @@ __global__ void __launch_bounds__(kScreenWarps * 32) screen_select_kernel(Screen
         }
     }
     bool alive = key != 0xFFFFFFFFu;
-    for (int s = 0; s < a.top; ++s) {
+    int chosen[kMaxTop];
+#pragma unroll
+    for (int s = 0; s < kMaxTop; ++s) {
+        chosen[s] = -1;
+        if (s >= a.top) continue;
         const uint32_t m = __reduce_min_sync(0xffffffffu, alive ? key : 0xFFFFFFFFu);
-        int chosen = -1;
-        if (m != 0xFFFFFFFFu) {
-            const int w = __ffs(__ballot_sync(0xffffffffu, alive && key == m)) - 1;
-            chosen = __shfl_sync(0xffffffffu, mv, w);
-            if (mv == chosen) alive = false;   // the winner and its duplicates
-        }
-        if (lane == 0) a.sel[(size_t)c * a.top + s] = chosen;
-        int8_t *row = a.xe + ((size_t)c * a.top + s) * a.ch.pstride;
-        warp_copy16(row, a.ch.x_cur + (size_t)c * a.ch.pstride, a.ch.pstride, lane);
-        __syncwarp();
-        if (lane == 0 && chosen >= 0) row[chosen >> 8] = (int8_t)(chosen & 255);
-    }
-}
-
-// Warp per chain: the simulated candidate of lowest exact score (first slot on
-// ties) goes to the Metropolis test of Table 1 (host threshold tables, word 2
-// of the step draw).  An accepted move updates x_cur, delta_cur, the best
-// vector (strict improvement), the counters and A1.
-__global__ void __launch_bounds__(kScreenWarps * 32) screen_commit_kernel(ScreenArgs a, DevSched sc)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.x * kScreenWarps + warp;
-    if (c >= a.ch.n) return;
-    int best = -1;
-    int32_t d = 0;
-    for (int s = 0; s < a.top; ++s) {
-        const int mv = a.sel[(size_t)c * a.top + s];
-        if (mv < 0) continue;
-        const int32_t ds = a.se[(size_t)c * a.top + s];
-        if (best < 0 || ds < d) { best = mv; d = ds; }
+        if (m == 0xFFFFFFFFu) continue;
+        const int w = __ffs(__ballot_sync(0xffffffffu, alive && key == m)) - 1;
+        chosen[s] = __shfl_sync(0xffffffffu, mv, w);
+        if (mv == chosen[s]) alive = false;   // the winner and its duplicates
     }
     int64_t *cnt = a.ch.cnt + 3 * (size_t)c;
-    if (best < 0) {
+    if (chosen[0] < 0) {
         if (lane == 0) cnt[2] += 1;
         return;
+    }
+    int8_t *x = a.ch.x_cur + (size_t)c * a.ch.pstride;
+    P.load(net, x, lane);
+    __syncwarp();
+    const int E = net.E, N = net.N;
+    int best = -1;
+    int32_t d = 0;
+#pragma unroll
+    for (int s = 0; s < kMaxTop; ++s) {
+        const int move = chosen[s];
+        if (move < 0) continue;
+        const int j = move >> 8, v = (int8_t)(move & 255);
+        int kind, idx, owner;
+        if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
+        else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
+        if (kind < 3) {
+            const int pos = net.edge_pos[idx];
+            owner = pos >> 16;
+            int w = x[idx], p = x[E + idx], t = x[2 * E + idx];
+            if (kind == 0) w = v; else if (kind == 1) p = v; else t = v;
+            P.change_edge(net, lane, owner, pos, w, p, t, idx);
+        } else {
+            const int q = net.node_q[idx];
+            owner = q / net.npl;
+            P.change_node(lane, owner, q - owner * net.npl, kind, v);
+        }
+        __syncwarp();
+        const int32_t ds = P.simulate(net, lane, nullptr);
+        P.undo(lane, owner);
+        __syncwarp();
+        if (best < 0 || ds < d) { best = move; d = ds; }
     }
     const int32_t d_cur = a.ch.d_cur[c], d_best = a.ch.d_best[c];
     const int32_t dE = d - d_cur;
     bool accept = dE <= 0;
     if (!accept) {
-        const uint4 r = step_draw(a.ch, a.g, c, 0u);
         const int64_t l = a.g / sc.iters - sc.level0;
         if (dE <= sc.thr_len[l]) accept = r.z < sc.thr[sc.thr_off[l] + dE - 1];
     }
     if (!accept) return;
     const int j = best >> 8;
     const int v = (int8_t)(best & 255);
-    int8_t *x = a.ch.x_cur + (size_t)c * a.ch.pstride;
     const int rn = a.row_base[j] + v, ro = a.row_base[j] + x[j];
     __syncwarp();
     if (lane == 0) {
@@ -437,6 +449,57 @@ __global__ void __launch_bounds__(kScreenWarps * 32) screen_commit_kernel(Screen
     for (int h = lane; h < a.H1; h += 32)
         a.A1[(size_t)c * a.H1 + h] += __bfloat162float(a.W1b[(size_t)rn * a.H1 + h]) -
                                       __bfloat162float(a.W1b[(size_t)ro * a.H1 + h]);
+}
+
+// Register-table path (N <= 128), as evaluate_kernel: in-degree capacity 16.
+template <int NPL, int CG>
+__global__ void __launch_bounds__(kScreenWarps * 32) screen_finish_reg_kernel(ScreenArgs a,
+                                                                              DevSched sc)
+{
+    extern __shared__ __align__(256) uint8_t sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * kScreenWarps + warp;
+    if (c >= a.ch.n) return;
+    RegPath<NPL, CG, 16, 16> P;
+    P.sm = sm;
+    P.codes = (uint32_t)warp * kCodeBytesPerWarp;
+    screen_finish(a, sc, P, c, lane);
+}
+
+// Shared-memory-table path (129 .. 512 nodes).
+__global__ void __launch_bounds__(kScreenWarps * 32)
+    screen_finish_smem_kernel(ScreenArgs a, DevSched sc, uint32_t region_bytes, uint32_t lut_words)
+{
+    extern __shared__ __align__(256) uint8_t sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * kScreenWarps + warp;
+    if (c >= a.ch.n) return;
+    SmemPath P = make_smem_path(a.net, sm, warp, kScreenWarps, region_bytes, lut_words);
+    screen_finish(a, sc, P, c, lane);
+}
+
+cudaError_t launch_finish(const ScreenArgs &a, const DevSched &sc, cudaStream_t st)
+{
+    const int blocks = (a.ch.n + kScreenWarps - 1) / kScreenWarps;
+    if (a.net.npl > kRegSlots) {
+        const WarpRegion R = warp_region(true, a.net.D, a.net.npl, 0, 0);
+        const size_t smem = kScreenWarps * ((size_t)kCodeBytesPerWarp + R.bytes);
+        const cudaError_t e = cudaFuncSetAttribute(
+            screen_finish_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        screen_finish_smem_kernel<<<blocks, kScreenWarps * 32, smem, st>>>(a, sc, R.bytes,
+                                                                           R.lut_words);
+        return cudaGetLastError();
+    }
+    const size_t smem = kScreenWarps * (size_t)kCodeBytesPerWarp;
+#define RN_FIN(NPL_, CG_)                                                                      \
+    if (a.net.npl == NPL_ && a.net.cg == CG_) {                                                \
+        screen_finish_reg_kernel<NPL_, CG_><<<blocks, kScreenWarps * 32, smem, st>>>(a, sc);  \
+        return cudaGetLastError();                                                             \
+    }
+    RN_FIN(1, 1) RN_FIN(1, 4) RN_FIN(2, 1) RN_FIN(2, 4) RN_FIN(4, 1) RN_FIN(4, 4)
+#undef RN_FIN
+    return cudaErrorNotSupported;
 }
 
 // ------------------------------------------------------------------ host --
@@ -661,9 +724,6 @@ int ensure_screen(rn_ctx *ctx, Mlp &m, const Network &n, int32_t K, int32_t top)
     RN_CUDA(ctx, cudaMemset(m.hc.p, 0, M * m.H1 * sizeof(uint16_t)));
     RN_CUDA(ctx, m.pc.alloc(M * (m.H2 / 64)));
     RN_CUDA(ctx, m.cand.alloc(C * K));
-    RN_CUDA(ctx, m.sel.alloc(C * top));
-    RN_CUDA(ctx, m.xe.alloc(C * top * (size_t)n.pstride));
-    RN_CUDA(ctx, m.se.alloc(C * top));
     m.chains = n.n_chains;
     m.K = K;
     m.top = top;
@@ -977,9 +1037,6 @@ int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K
     a.hc = bp(m->hc);
     a.pc = m->pc.p;
     a.cand = m->cand.p;
-    a.sel = m->sel.p;
-    a.xe = m->xe.p;
-    a.se = m->se.p;
     const int region = (int)(n->pstride + 2 * ((n->N + 15) & ~15));
     const size_t smem = (size_t)kScreenWarps * region;
     RN_CUDA(ctx, cudaFuncSetAttribute(screen_propose_kernel,
@@ -994,13 +1051,9 @@ int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K
         screen_propose_kernel<<<blocks, kScreenWarps * 32, smem, ctx->stream>>>(a, region);
         if ((rc = check_launch(ctx, "screen propose kernel"))) return rc;
         if ((rc = gemm(ctx, kBiasReluDot, g))) return rc;
-        screen_select_kernel<<<blocks, kScreenWarps * 32, 0, ctx->stream>>>(a);
-        if ((rc = check_launch(ctx, "screen select kernel"))) return rc;
-        if ((rc = evaluate_device_impl(ctx, *n, ch.n * top, m->xe.p, n->pstride, m->se.p, nullptr,
-                                       nullptr)))
-            return rc;
-        screen_commit_kernel<<<blocks, kScreenWarps * 32, 0, ctx->stream>>>(a, sc);
-        if ((rc = check_launch(ctx, "screen commit kernel"))) return rc;
+        const cudaError_t e = launch_finish(a, sc, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "screen finish kernel");
+        ctx->launches += 1;
     }
     n->step += sweeps;
     m->a1_step = n->step;
