@@ -152,7 +152,10 @@ __device__ __forceinline__ void load_regs(Regs<NPL, D0, D1> &R, const DevNet &ne
 {
     const int E = net.E, N = net.N;
     for_each_word<NPL, D0, D1>(R, [&](int k, int d, uint32_t &word) {
-        uint32_t w = 0x00040404u | ((uint32_t)(2 * (lane * NPL + k)) << 24);   // padding: f = 0
+        // padding: f = 0, reading a valid state code (its nibbles select one of
+        // the three 4s): that of node 2 lane (one bank per lane) with two or
+        // more nodes per lane, the lane's own node with one
+        uint32_t w = 0x00040404u | ((uint32_t)((NPL == 1 ? 2 : 4) * lane) << 24);
         if (d < net.D[k]) {
             const int e = net.edge_id[(k * net.dtab + d) * 32 + lane];
             if (e >= 0) w = edge_word(x[e], x[E + e], x[2 * E + e], net.edge_q2[e]);
@@ -175,28 +178,31 @@ __device__ __forceinline__ void load_regs(Regs<NPL, D0, D1> &R, const DevNet &ne
     }
 }
 
+// Edges per slot rounded up to whole groups of 4; the table words past D are
+// neutral (every byte 4), so a group-of-4 gather adds exactly 4 per padding
+// word and condition.
+__host__ __device__ __forceinline__ int groups4(int D) { return (D + 3) & ~3; }
+
 // Biased image terms of the slot's node for the CG conditions, one byte each:
-// `acc` plus the sum over its D in-edges.  D is warp uniform: the jump into
-// the unrolled sequence does not diverge.
+// `acc` plus the sum over its first groups4(D) table words (4 per padding
+// word).  Edges go in groups of 4, the four shared-memory loads of a group
+// issued before their uses; D is warp uniform, so the groups do not diverge.
 template <int DC>
 __device__ __forceinline__ uint32_t image(const uint32_t (&lut)[DC], int D, uint32_t base,
                                           const uint8_t *sm, uint32_t acc = 0)
 {
-#define RN_EDGE(dd)                                                                    \
-    case (dd) + 1:                                                                     \
-        if constexpr (DC > (dd)) {                                                     \
-            const uint32_t a = __byte_perm(lut[dd], base, 0x7653u);                    \
-            acc += __byte_perm(lut[dd], 0u, (uint32_t)(*(const uint16_t *)(sm + a)));  \
-        }                                                                              \
-        [[fallthrough]];
-    switch (D) {
-        RN_EDGE(15) RN_EDGE(14) RN_EDGE(13) RN_EDGE(12) RN_EDGE(11) RN_EDGE(10) RN_EDGE(9)
-        RN_EDGE(8) RN_EDGE(7) RN_EDGE(6) RN_EDGE(5) RN_EDGE(4) RN_EDGE(3) RN_EDGE(2)
-        RN_EDGE(1) RN_EDGE(0)
-    default:
-        break;
+    static_assert(DC % 4 == 0, "table capacities are multiples of 4");
+#pragma unroll
+    for (int g = 0; g < DC; g += 4) {
+        if (g < D) {
+            uint32_t c[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                c[i] = *(const uint16_t *)(sm + __byte_perm(lut[g + i], base, 0x7653u));
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc += __byte_perm(lut[g + i], 0u, c[i]);
+        }
     }
-#undef RN_EDGE
     return acc;
 }
 
@@ -205,8 +211,10 @@ __device__ __forceinline__ void images(uint32_t (&acc)[NPL], const Regs<NPL, D0,
                                        const DevNet &net, uint32_t base, const uint8_t *sm)
 {
     acc[0] = image<D0>(R.lut0, net.D[0], base, sm);
+    if constexpr (NPL > 1) {
 #pragma unroll
-    for (int k = 1; k < NPL; ++k) acc[k] = image<D1>(R.lutr[k - 1], net.D[k], base, sm);
+        for (int k = 1; k < NPL; ++k) acc[k] = image<D1>(R.lutr[k - 1], net.D[k], base, sm);
+    }
 }
 
 // Byte-SIMD helpers: prmt with sign replication (selector nibble bit 3 set
@@ -317,11 +325,14 @@ __device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, co
         for (int tau = 0; tau < T; ++tau) {
             if (tau > 0) {
                 uint32_t acc[NPL];
-                acc[0] = image<D0>(R.lut0, net.D[0], base, sm, kH - 0x04040404u * net.D[0]);
+                acc[0] = image<D0>(R.lut0, net.D[0], base, sm,
+                                   kH - 0x04040404u * groups4(net.D[0]));
+                if constexpr (NPL > 1) {
 #pragma unroll
-                for (int k = 1; k < NPL; ++k)
-                    acc[k] = image<D1>(R.lutr[k - 1], net.D[k], base, sm,
-                                       kH - 0x04040404u * net.D[k]);
+                    for (int k = 1; k < NPL; ++k)
+                        acc[k] = image<D1>(R.lutr[k - 1], net.D[k], base, sm,
+                                           kH - 0x04040404u * groups4(net.D[k]));
+                }
                 uint32_t sn[NPL], pr01[NPL], pr23[NPL], elm[NPL];
                 uint32_t m01 = 0, m23 = 0;
 #pragma unroll
@@ -439,7 +450,7 @@ __device__ __forceinline__ int32_t simulate(const Regs<NPL, D0, D1> &R, const De
                     int32_t pr[NPL], sn[NPL], pmax = 0;
 #pragma unroll
                     for (int k = 0; k < NPL; ++k) {
-                        const int32_t lo = 4 * net.D[k];
+                        const int32_t lo = 4 * groups4(net.D[k]);
                         const int32_t kb = (int32_t)((acc[k] >> (8 * c)) & 0xffu);
                         const int32_t tgt = min(max(kb, lo), lo + 2) - lo;
                         const int32_t diff = tgt - s[k][c];
