@@ -64,7 +64,7 @@ def algorithmic_ops_per_eval(w):
 
 # DRAM bytes per annealing launch (read + write) from an ncu capture of the
 # current kernel: the chain state read once, independent of sweeps per launch.
-ANNEAL_TRAFFIC = {"n120_c8_t21": 9.26e6}
+ANNEAL_TRAFFIC = {"n120_c8_t21": 9.31e6}
 
 L2_NOTE = ("working set (network tables + chain state) is L2-resident by design; L2 flushed "
            "with a 512 MiB write between timed steps, outside the step events")
