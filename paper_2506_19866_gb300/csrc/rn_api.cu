@@ -383,18 +383,70 @@ bool batchable(rn_ctx *ctx, const rn_schedule &s)
     return k >= 2 && !s.global_sync;
 }
 
+// Global chain lists for the current table paths: the chains of networks on
+// the shared-memory tables first (the large-region warps' queue), then the
+// rest, each class in work order.
+int batch_items(rn_ctx *ctx, BatchState &B)
+{
+    std::vector<int32_t> item_net, item_chain;
+    int32_t big = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (size_t b = 0; b < B.order.size(); ++b) {
+            if ((B.host_path[b] == 0) != (pass == 0)) continue;
+            const Network &n = *ctx->nets[(size_t)B.order[b]];
+            for (int32_t c = 0; c < n.n_chains; ++c) {
+                item_net.push_back((int32_t)b);
+                item_chain.push_back(c);
+            }
+            if (pass == 0) big += n.n_chains;
+        }
+    B.total = (int32_t)item_net.size();
+    B.total_big = big;
+    RN_CUDA(ctx, B.item_net.upload(item_net));
+    RN_CUDA(ctx, B.item_chain.upload(item_chain));
+    return RN_OK;
+}
+
+// Item lists, warp regions (large: any network; small: register-table
+// networks), large-region warps per block (all when every network is on the
+// shared-memory tables, none without such networks, otherwise their share of
+// the work rounded up) and the resident grid of the current configuration.
 int batch_region(rn_ctx *ctx, BatchState &B)
 {
-    B.region_bytes = 0;
+    int rc = batch_items(ctx, B);
+    if (rc) return rc;
+    B.region_bytes = 16;
+    B.region_small = 16;
+    double work_big = 0, work_all = 0;
     for (size_t b = 0; b < B.order.size(); ++b) {
         const Network &n = *ctx->nets[(size_t)B.order[b]];
-        B.region_bytes = std::max(B.region_bytes, batch_region_bytes(B.host_path[b] == 0, n.D,
-                                                                     n.npl, n.pstride, n.N));
+        const bool big = B.host_path[b] == 0;
+        const uint32_t r = batch_region_bytes(big, n.D, n.npl, n.pstride, n.N);
+        B.region_bytes = std::max(B.region_bytes, r);
+        if (!big) B.region_small = std::max(B.region_small, r);
+        const double w = (double)n.n_chains * n.C * std::max(1, n.T - 1) * (n.N + n.E);
+        work_all += w;
+        if (big) work_big += w;
     }
+    if (B.total_big == 0) B.large = 0;
+    else if (B.total_big == B.total) B.large = B.wpb;
+    else
+        B.large = std::min(B.wpb - 1,
+                           std::max(1, (int)std::ceil(B.wpb * work_big / std::max(work_all, 1.0))));
     RN_CUDA(ctx, B.path.upload(B.host_path));
-    const cudaError_t e = batch_resident_warps(B.wpb, B.region_bytes, ctx->sm_count, &B.grid);
+    const size_t smem = batch_smem_bytes(B.wpb, B.large, B.region_bytes, B.region_small);
+    const cudaError_t e = batch_resident_warps(B.wpb, smem, ctx->sm_count, &B.grid);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batched kernel configuration");
     return RN_OK;
+}
+
+// Chunks of the batched launch: always 16-step chunks when the two classes
+// split the warps (a class may hold more chains than its warps), else as for
+// one network.
+void plan_batch_chunks(const BatchState &B, DevSched &sc)
+{
+    const bool split = B.large > 0 && B.large < B.wpb;
+    plan_chunks(sc, B.total, split ? 1 : (int64_t)B.grid * B.wpb);
 }
 
 int upload_batch_steps(rn_ctx *ctx, BatchState &B)
@@ -427,8 +479,8 @@ int build_batch(rn_ctx *ctx)
                      [&](int a, int b) { return work(a) > work(b); });
     std::vector<DevNet> nets;
     std::vector<DevChains> chains;
-    std::vector<int32_t> item_net, item_chain;
     B.host_path.clear();
+    int64_t total = 0;
     for (size_t b = 0; b < B.order.size(); ++b) {
         const Network &n = *ctx->nets[(size_t)B.order[b]];
         nets.push_back(n.dev());
@@ -436,18 +488,13 @@ int build_batch(rn_ctx *ctx)
         int drest = 0;
         for (int k = 1; k < n.npl; ++k) drest = std::max(drest, n.D[k]);
         B.host_path.push_back(batch_path_fits(n.npl, n.D[0], drest) ? n.npl : 0);
-        for (int32_t c = 0; c < n.n_chains; ++c) {
-            item_net.push_back((int32_t)b);
-            item_chain.push_back(c);
-        }
+        total += n.n_chains;
     }
-    B.total = (int32_t)item_net.size();
+    if (total > INT32_MAX / 2) return fail(ctx, RN_EINVAL, "too many chains in the batch");
     RN_CUDA(ctx, B.nets.upload(nets));
     RN_CUDA(ctx, B.chains.upload(chains));
-    RN_CUDA(ctx, B.item_net.upload(item_net));
-    RN_CUDA(ctx, B.item_chain.upload(item_chain));
     RN_CUDA(ctx, B.g0.alloc(B.order.size()));
-    RN_CUDA(ctx, ctx->done.reserve((size_t)B.total));
+    RN_CUDA(ctx, ctx->done.reserve((size_t)total));
     int rc = batch_region(ctx, B);
     if (rc) return rc;
     if ((rc = upload_batch_steps(ctx, B))) return rc;
@@ -462,8 +509,11 @@ DevBatch batch_desc(const BatchState &B, int64_t sweeps)
     DevBatch d{};
     d.n_nets = (int32_t)B.order.size();
     d.total = B.total;
+    d.total_big = B.total_big;
+    d.large = B.large;
     d.sweeps = sweeps;
     d.region_bytes = B.region_bytes;
+    d.region_small = B.region_small;
     d.nets = B.nets.p;
     d.chains = B.chains.p;
     d.g0 = B.g0.p;
@@ -521,7 +571,7 @@ int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
         DevSched sc = sc0;
         sc.g0 = 0;
         sc.g1 = trial;
-        plan_chunks(sc, B.total, (int64_t)B.grid * B.wpb);
+        plan_batch_chunks(B, sc);
         const DevBatch d = batch_desc(B, trial);
         cudaEventRecord(e0, ctx->stream);
         const cudaError_t e = launch_batch(d, sc, B.wpb, B.grid, ctx->stream);
@@ -582,7 +632,7 @@ int anneal_batched(rn_ctx *ctx, const rn_schedule &s, int64_t sweeps)
     }
     sc.g0 = 0;
     sc.g1 = sweeps;
-    plan_chunks(sc, B.total, (int64_t)B.grid * B.wpb);
+    plan_batch_chunks(B, sc);
     const DevBatch d = batch_desc(B, sweeps);
     if (cached) {
         const bool same = B.exec && B.graph_sweeps == sweeps;
@@ -650,7 +700,7 @@ int rn_create(rn_ctx **out, int device, void *stream)
         ctx->own_stream = true;
     }
     if (ctx->status.alloc(1) != cudaSuccess || ctx->winner.alloc(1) != cudaSuccess ||
-        ctx->queue.alloc(1) != cudaSuccess || ctx->done.alloc(1) != cudaSuccess ||
+        ctx->queue.alloc(2) != cudaSuccess || ctx->done.alloc(1) != cudaSuccess ||
         ctx->dev_err.alloc(1) != cudaSuccess)
         return fail(nullptr, RN_ENOMEM, "cannot allocate context buffers");
     if (cudaMemset(ctx->dev_err.p, 0, sizeof(int32_t)) != cudaSuccess)

@@ -1,14 +1,23 @@
 // rn_batch.cu -- one persistent launch over the chains of many networks.
 //
-// Every chain of every network is one "global chain" r; global chains are
-// ordered by network, the network with the most work per chain first.  Work
-// item i is chunk i / total of global chain i % total, so that, as in the
+// Every chain of every network is one "global chain" r.  Global chains come
+// in two classes with a work queue each: first the chains of networks on the
+// shared-memory tables (r < total_big), then those on register tables; within
+// a class, the network with the most work per chain first.  Item i of a class
+// of n chains is chunk i / n of the class's chain i % n, so that, as in the
 // single-network kernel, the predecessor of an item (the previous chunk of the
-// same chain) was handed out `total` items earlier.  Each warp copies the
-// descriptors of its item's network into its shared memory and runs the chunk
-// with that network's table path: register tables with 1, 2 or 4 nodes per
-// lane, or the shared-memory tables.  Results are those of separate
-// single-network runs, bit for bit (same per-chain code, same Philox counters).
+// same chain) was handed out n items earlier from the same queue.
+//
+// Shared-memory tables need a large per-warp region, register tables a small
+// one.  The first `large` warps of a block get a large region and take items
+// of the first class, then help with the second; the other warps get a small
+// region and take only register-table items.  Sizing every warp for the
+// largest network would cut the resident warps several fold.
+//
+// Each warp copies the descriptors of its item's network into its shared
+// memory and runs the chunk with that network's table path.  Results are
+// those of separate single-network runs, bit for bit (same per-chain code,
+// same Philox counters).
 #include "rn_kernels.cuh"
 
 namespace rn {
@@ -33,7 +42,7 @@ __device__ __forceinline__ void warp_copy_words(void *dst, const void *src, int 
     for (int k = lane; k < bytes / 4; k += 32) d[k] = __ldcg(s + k);
 }
 
-__global__ void __launch_bounds__(128, 2) anneal_batch_kernel(DevBatch b, DevSched sc)
+__global__ void __launch_bounds__(128, 3) anneal_batch_kernel(DevBatch b, DevSched sc)
 {
     extern __shared__ __align__(256) uint8_t sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -42,16 +51,25 @@ __global__ void __launch_bounds__(128, 2) anneal_batch_kernel(DevBatch b, DevSch
     DevNet *net_s = reinterpret_cast<DevNet *>(desc) + warp;
     DevChains *ch_s =
         reinterpret_cast<DevChains *>(desc + (uint32_t)wpb * sizeof(DevNet)) + warp;
-    uint8_t *region = sm + batch_head_bytes(wpb) + (uint32_t)warp * b.region_bytes;
+    const bool large = warp < b.large;
+    uint8_t *region = sm + batch_head_bytes(wpb) +
+                      (large ? (uint32_t)warp * b.region_bytes
+                             : (uint32_t)b.large * b.region_bytes +
+                                   (uint32_t)(warp - b.large) * b.region_small);
     const uint32_t codes = (uint32_t)warp * kCodeBytesPerWarp;
-    const int64_t n_items = (int64_t)sc.n_chunks * b.total;
+    int cls = large && b.total_big > 0 ? 0 : 1;
     for (;;) {
+        const int n_cls = cls == 0 ? b.total_big : b.total - b.total_big;
+        const int64_t n_items = (int64_t)sc.n_chunks * n_cls;
         unsigned int item = 0;
-        if (lane == 0) item = atomicAdd(sc.queue, 1u);
+        if (lane == 0 && n_cls > 0) item = atomicAdd(sc.queue + cls, 1u);
         item = __shfl_sync(kFull, item, 0);
-        if ((int64_t)item >= n_items) break;
-        const int cj = (int)(item / (unsigned)b.total);
-        const int r = (int)(item - (unsigned)cj * (unsigned)b.total);
+        if (n_cls == 0 || (int64_t)item >= n_items) {
+            if (cls == 0) { cls = 1; continue; }
+            break;
+        }
+        const int cj = (int)(item / (unsigned)n_cls);
+        const int r = (cls == 0 ? 0 : b.total_big) + (int)(item - (unsigned)cj * (unsigned)n_cls);
         if (cj > 0 && !wait_for_chunk(sc.done + r, cj, sc.err, lane)) return;
         const int nb = __ldg(b.item_net + r), chain = __ldg(b.item_chain + r);
         warp_copy_words(net_s, b.nets + nb, (int)sizeof(DevNet), lane);
@@ -120,9 +138,13 @@ uint32_t batch_region_bytes(bool smem_path, const int *D, int npl, int pstride, 
     return warp_region(smem_path, D, npl, pstride, N).bytes;
 }
 
-cudaError_t batch_resident_warps(int wpb, uint32_t region_bytes, int sm_count, int *grid)
+size_t batch_smem_bytes(int wpb, int large, uint32_t region_big, uint32_t region_small)
 {
-    const size_t smem = batch_head_bytes(wpb) + (size_t)wpb * region_bytes;
+    return batch_head_bytes(wpb) + (size_t)large * region_big + (size_t)(wpb - large) * region_small;
+}
+
+cudaError_t batch_resident_warps(int wpb, size_t smem, int sm_count, int *grid)
+{
     cudaError_t err = cudaFuncSetAttribute(anneal_batch_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -140,8 +162,8 @@ cudaError_t batch_resident_warps(int wpb, uint32_t region_bytes, int sm_count, i
 cudaError_t launch_batch(const DevBatch &b, const DevSched &sc, int wpb, int grid,
                          cudaStream_t st)
 {
-    const size_t smem = batch_head_bytes(wpb) + (size_t)wpb * b.region_bytes;
-    cudaError_t err = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned int), st);
+    const size_t smem = batch_smem_bytes(wpb, b.large, b.region_bytes, b.region_small);
+    cudaError_t err = cudaMemsetAsync(sc.queue, 0, 2 * sizeof(unsigned int), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(sc.done, 0, sizeof(int32_t) * (size_t)b.total, st);
     if (err != cudaSuccess) return err;
     anneal_batch_kernel<<<grid, wpb * 32, smem, st>>>(b, sc);

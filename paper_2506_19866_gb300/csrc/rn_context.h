@@ -136,6 +136,9 @@ struct BatchState {
     uint64_t gen = 0;                 // context generation it was built for
     std::vector<int> order;           // context network ids, most work per chain first
     int32_t total = 0;
+    int32_t total_big = 0;            // chains of networks on the shared-memory tables
+    int32_t large = 0;                // large-region warps per block
+    uint32_t region_small = 0;        // region of a small (register-table) warp
     DevBuf<rn::DevNet> nets;
     DevBuf<rn::DevChains> chains;
     DevBuf<int64_t> g0;

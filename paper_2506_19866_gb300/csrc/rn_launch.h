@@ -39,8 +39,11 @@ cudaError_t launch_level_sync(const DevChains &ch, int32_t *winner, cudaStream_t
 // Many networks in one persistent launch (rn_batch.cu).
 struct DevBatch {
     int32_t n_nets, total;              // networks; chains over all networks
+    int32_t total_big;                  // global chains [0, total_big) use the shared-memory tables
+    int32_t large;                      // warps per block with a large region (first in the block)
     int64_t sweeps;                     // steps every chain advances
-    uint32_t region_bytes;              // shared memory of one warp region
+    uint32_t region_bytes;              // shared memory of a large warp region (any network)
+    uint32_t region_small;              // shared memory of a small region (register-table networks)
     const DevNet *nets;                 // [n_nets]
     const DevChains *chains;            // [n_nets]
     int64_t *g0;                        // [n_nets] next step of each network (advanced on device)
@@ -51,7 +54,9 @@ struct DevBatch {
 
 bool batch_path_fits(int npl, int D0, int Drest);
 uint32_t batch_region_bytes(bool smem_path, const int *D, int npl, int pstride, int N);
-cudaError_t batch_resident_warps(int wpb, uint32_t region_bytes, int sm_count, int *grid);
+// Block shared memory of a configuration, and the resident grid it allows.
+size_t batch_smem_bytes(int wpb, int large, uint32_t region_big, uint32_t region_small);
+cudaError_t batch_resident_warps(int wpb, size_t smem, int sm_count, int *grid);
 cudaError_t launch_batch(const DevBatch &b, const DevSched &sc, int wpb, int grid,
                          cudaStream_t st);
 

@@ -48,10 +48,11 @@ __host__ __device__ __forceinline__ uint32_t edge_word_s(int w, int p, int t, ui
 
 // Shared-memory footprint of one warp (bytes; multiple of 16) and of the
 // code region that precedes all warp regions in the block (1 KiB per warp).
+// Each slot's table has groups4(D_k) rows: the rows past D_k are neutral.
 __host__ __device__ inline uint32_t smem_path_lut_words(const int *D, int npl)
 {
     uint32_t s = 0;
-    for (int k = 0; k < npl; ++k) s += (uint32_t)D[k];
+    for (int k = 0; k < npl; ++k) s += (uint32_t)groups4(D[k]);
     return s * 32u;
 }
 
@@ -84,7 +85,7 @@ struct SmemPath {
     __device__ __forceinline__ int lut_row(const DevNet &net, int k, int d) const
     {
         int o = 0;
-        for (int kk = 0; kk < k; ++kk) o += net.D[kk];
+        for (int kk = 0; kk < k; ++kk) o += groups4(net.D[kk]);
         return o + d;
     }
 
@@ -104,7 +105,13 @@ struct SmemPath {
                     w = 0x04040000u | ((codes + (uint32_t)(-1 - e)) & 0xffffu);
                 lut[(o + d) * 32 + lane] = w;
             }
-            o += net.D[k];
+            // neutral rows up to a whole group of 4, reading a valid code: that
+            // of node 2 lane (one bank per lane) with two or more nodes per
+            // lane, the lane's own node with one
+            const uint32_t pad = codes + (npl == 1 ? 2u : 4u) * (uint32_t)lane;
+            for (int d = net.D[k]; d < groups4(net.D[k]); ++d)
+                lut[(o + d) * 32 + lane] = 0x04040000u | (pad & 0xffffu);
+            o += groups4(net.D[k]);
             const int i = net.q_node[lane * npl + k];
             uint32_t u = 1, m1 = 1, d2 = 0;
             if (i >= 0) {
@@ -187,15 +194,22 @@ struct SmemPath {
                     int o = 0;
                     for (int k = 0; k < npl; ++k) {
                         const int D = net.D[k];
-                        uint32_t acc = kH - 0x04040404u * (uint32_t)D;
+                        const int D4 = groups4(D);
+                        uint32_t acc = kH - 0x04040404u * (uint32_t)D4;
                         const uint32_t *lw = lut + o * 32 + lane;
-#pragma unroll 4
-                        for (int d = 0; d < D; ++d) {
-                            const uint32_t w = lw[d * 32];
-                            const uint32_t c = *reinterpret_cast<const uint16_t *>(sm + (w & 0xffffu));
-                            acc += prmt(w, 0x04040404u, c);
+                        // groups of 4 edges: four table words, then four codes,
+                        // then the sums, so that the loads overlap
+                        for (int d = 0; d < D4; d += 4) {
+                            uint32_t w[4], c[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) w[i] = lw[(d + i) * 32];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
                         }
-                        o += D;
+                        o += D4;
                         const uint32_t s4 = F(k, kF_S4, lane);
                         const uint32_t tgt = (((acc - kB1) >> 7) & kB1) + (((acc - 2 * kB1) >> 7) & kB1);
                         const uint32_t dp = tgt + 2 * kB1 - s4;
