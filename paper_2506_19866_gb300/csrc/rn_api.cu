@@ -112,9 +112,14 @@ uint32_t threshold(double T, int64_t dE)
 void build_layout(Network &n)
 {
     const int32_t N = n.N, E = n.E;
-    // 1, 2 or 4 nodes per lane for the register-table kernels; above 128
-    // nodes, ceil(N / 32) for the shared-memory path (up to 512 nodes)
-    n.npl = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : N <= 32 * kMaxSlots ? (N + 31) / 32 : 0;
+    // A chain is simulated by L = 32 lanes (one warp) up to 512 nodes: 1, 2 or
+    // 4 nodes per lane for the register-table kernels, ceil(N / 32) above 128
+    // nodes for the shared-memory path.  Above 512 nodes a block of L = 256
+    // threads holds the chain (block path), ceil(N / 256) nodes per thread, up
+    // to 4096 nodes.
+    const int L = N <= 32 * kMaxSlots ? 32 : kBlockLanes;
+    n.lanes = L;
+    n.npl = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : N <= L * kMaxSlots ? (N + L - 1) / L : 0;
     n.in_ptr.assign((size_t)N + 1, 0);
     n.out_ptr.assign((size_t)N + 1, 0);
     for (int32_t e = 0; e < E; ++e) {
@@ -149,11 +154,11 @@ void build_layout(Network &n)
                n.in_ptr[(size_t)b + 1] - n.in_ptr[(size_t)b];
     });
     n.node_q.assign((size_t)N, 0);
-    n.q_node.assign((size_t)32 * npl, (int16_t)-1);
+    n.q_node.assign((size_t)L * npl, (int16_t)-1);
     for (int k = 0; k < kMaxSlots; ++k) n.D[k] = 0;
     for (int32_t r = 0; r < N; ++r) {
         const int32_t i = order[(size_t)r];
-        const int slot = r / 32, lane = r % 32;
+        const int slot = r / L, lane = r % L;
         const int q = lane * npl + slot;
         n.node_q[(size_t)i] = q;
         n.q_node[(size_t)q] = (int16_t)i;
@@ -161,22 +166,27 @@ void build_layout(Network &n)
     }
     n.dtab = 1;
     for (int k = 0; k < npl; ++k) n.dtab = std::max(n.dtab, n.D[k]);
-    if (n.dtab > 16) return;
-    n.edge_id.assign((size_t)npl * n.dtab * 32, -1);
+    // in-degree capacity: 16 in registers (warp paths), 64 on the block path
+    if (n.dtab > (L == 32 ? 16 : 64)) return;
+    // the block path's shared memory must fit one block (227 KiB on sm_103)
+    if (L != 32 && block_path_smem_bytes(n.D, npl, N) > 232448u) return;
+    n.edge_id.assign((size_t)npl * n.dtab * L, -1);
     n.edge_q2.assign((size_t)E, 0);
     n.edge_pos.assign((size_t)E, 0);
     if (npl <= kRegSlots)   // one-byte code offsets of the register-table words
         for (int32_t e = 0; e < E; ++e)
             n.edge_q2[(size_t)e] = (uint8_t)(2 * n.node_q[(size_t)n.src[(size_t)e]]);
-    // Column d of slot k is read by the 32 lanes at once: each lane gathers the
-    // 2-byte state code of one source.  A shared-memory bank serves one 4-byte
-    // word per wavefront, so the in-edges of each lane are spread over the
-    // columns greedily such that no two lanes of a column read different words
-    // of one bank; a padding entry reads a word already read in its column.
-    for (int slot = 0; slot < npl; ++slot) {
+    // Column d of slot k is read by the 32 lanes of a warp at once: each lane
+    // gathers the 2-byte state code of one source.  A shared-memory bank serves
+    // one 4-byte word per wavefront, so the in-edges of each lane are spread over
+    // the columns greedily such that no two lanes of a warp read different words
+    // of one bank in a column; a padding entry reads a word already read in its
+    // column.  (The block path does this for each of its 8 warps.)
+    for (int slot = 0; slot < npl; ++slot)
+    for (int wg = 0; wg < L / 32; ++wg) {
         std::vector<std::vector<std::pair<int, int32_t>>> rem(32);   // (word, edge)
         for (int lane = 0; lane < 32; ++lane) {
-            const int i = n.q_node[(size_t)(lane * npl + slot)];
+            const int i = n.q_node[(size_t)((32 * wg + lane) * npl + slot)];
             if (i < 0) continue;
             for (int32_t k = n.in_ptr[(size_t)i]; k < n.in_ptr[(size_t)i + 1]; ++k) {
                 const int32_t e = n.in_edges[(size_t)k];
@@ -211,8 +221,8 @@ void build_layout(Network &n)
                 const int32_t e = r[(size_t)pick].second;
                 r.erase(r.begin() + pick);
                 if (used[word & 31] < 0) used[word & 31] = word;
-                n.edge_id[((size_t)slot * n.dtab + d) * 32 + lane] = e;
-                n.edge_pos[(size_t)e] = (lane << 16) | (slot << 8) | d;
+                n.edge_id[((size_t)slot * n.dtab + d) * L + 32 * wg + lane] = e;
+                n.edge_pos[(size_t)e] = ((32 * wg + lane) << 16) | (slot << 8) | d;
             }
             int pad_word = 0;
             for (int b = 0; b < 32; ++b)
@@ -221,7 +231,7 @@ void build_layout(Network &n)
                     break;
                 }
             for (int lane : padded)   // padding: -1 - (byte offset of a read code)
-                n.edge_id[((size_t)slot * n.dtab + d) * 32 + lane] = -1 - 4 * pad_word;
+                n.edge_id[((size_t)slot * n.dtab + d) * L + 32 * wg + lane] = -1 - 4 * pad_word;
         }
     }
     n.supported = true;
@@ -247,7 +257,7 @@ int require_supported(rn_ctx *ctx, const Network &n)
     if (!n.supported)
         return fail(ctx, RN_EUNSUPPORTED,
                     "network with %d nodes and maximum in-degree %d is outside the compiled "
-                    "kernels (N <= 512, in-degree <= 16)",
+                    "kernels (N <= 512 with in-degree <= 16, or N <= 4096 with in-degree <= 64)",
                     n.N, n.dtab);
     return RN_OK;
 }
@@ -372,14 +382,15 @@ int thresholds_for(rn_ctx *ctx, const rn_schedule &s, int64_t l0, int64_t l1, in
 
 // Networks annealed together in one launch: every network with chains, when
 // all of them use groups of 4 conditions (the batched kernel's update).
+// A network the batched kernel takes: chains, groups of 4 conditions, and a
+// warp per chain.  The others (one condition, or the block path) are annealed
+// by their own launches beside the batch.
+bool in_batch(const Network &n) { return n.chains_valid && n.cg == 4 && n.lanes == 32; }
+
 bool batchable(rn_ctx *ctx, const rn_schedule &s)
 {
     int k = 0;
-    for (auto &np : ctx->nets) {
-        if (!np->chains_valid) continue;
-        if (np->cg != 4) return false;
-        ++k;
-    }
+    for (auto &np : ctx->nets) k += in_batch(*np);
     return k >= 2 && !s.global_sync;
 }
 
@@ -470,7 +481,7 @@ int build_batch(rn_ctx *ctx)
     B.valid = false;
     B.order.clear();
     for (size_t id = 0; id < ctx->nets.size(); ++id)
-        if (ctx->nets[id]->chains_valid) B.order.push_back((int)id);
+        if (in_batch(*ctx->nets[id])) B.order.push_back((int)id);
     auto work = [&](int id) {
         const Network &n = *ctx->nets[(size_t)id];
         return (int64_t)n.C * std::max(1, n.T - 1) * (n.N + n.E);
@@ -837,24 +848,24 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     n->has_tc = true;
     n->chains_valid = false;
     if (!n->supported) return RN_OK;
-    const int npl = n->npl;
+    const int npl = n->npl, L = n->lanes;
     // 4 conditions per group (byte-SIMD) unless there is a single condition;
-    // the shared-memory path always uses groups of 4
-    const int cg = (C >= 2 || npl > kRegSlots) ? 4 : 1;
+    // the shared-memory and block paths always use groups of 4
+    const int cg = (C >= 2 || npl > kRegSlots || L != 32) ? 4 : 1;
     const int G = (C + cg - 1) / cg;
     int drest = 0;
     for (int k = 1; k < npl; ++k) drest = std::max(drest, n->D[k]);
     anneal_capacity(npl, n->D[0], drest, &n->d0, &n->d1);
     // error table of an entry: byte b = W |b - R| for b = 0, 1, 2
-    std::vector<uint32_t> obs((size_t)C * T * 32 * npl, 0u);
+    std::vector<uint32_t> obs((size_t)C * T * L * npl, 0u);
     // state codes: nibble c = initial state of condition g * cg + c; a node that
     // never moves in a condition (padding, knocked out, condition beyond C)
     // starts at 0 and has its bit k * cg + c set in out_bits
-    std::vector<uint16_t> init_code((size_t)G * 32 * npl, 0), out_bits((size_t)G * 32, 0);
+    std::vector<uint16_t> init_code((size_t)G * L * npl, 0), out_bits((size_t)G * L, 0);
     // the same per byte for the byte-SIMD path: initial states and "may move" bits
-    std::vector<uint32_t> init_s4((size_t)G * 32 * npl, 0), movable((size_t)G * 32 * npl, 0);
+    std::vector<uint32_t> init_s4((size_t)G * L * npl, 0), movable((size_t)G * L * npl, 0);
     for (int g = 0; g < G; ++g)
-        for (int q = 0; q < 32 * npl; ++q) {
+        for (int q = 0; q < L * npl; ++q) {
             const int i = n->q_node[(size_t)q];
             const int lane = q / npl, slot = q % npl;
             for (int c = 0; c < cg; ++c) {
@@ -862,17 +873,18 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
                 const bool out =
                     i < 0 || cc >= C || (knockout && knockout[(size_t)cc * N + i]);
                 if (out) {
-                    out_bits[(size_t)g * 32 + lane] |= (uint16_t)(1u << (slot * cg + c));
+                    if (slot * cg + c < 16)   // the scalar path's bits (at most 16 per lane)
+                        out_bits[(size_t)g * L + lane] |= (uint16_t)(1u << (slot * cg + c));
                     continue;
                 }
                 const uint32_t s0 = init[(size_t)cc * N + i];
-                init_code[(size_t)g * 32 * npl + q] |= (uint16_t)(s0 << (4 * c));
-                init_s4[(size_t)g * 32 * npl + q] |= s0 << (8 * c);
-                movable[(size_t)g * 32 * npl + q] |= 0x80u << (8 * c);
+                init_code[(size_t)g * L * npl + q] |= (uint16_t)(s0 << (4 * c));
+                init_s4[(size_t)g * L * npl + q] |= s0 << (8 * c);
+                movable[(size_t)g * L * npl + q] |= 0x80u << (8 * c);
             }
         }
     for (int32_t c = 0; c < C; ++c) {
-        for (int q = 0; q < 32 * npl; ++q) {
+        for (int q = 0; q < L * npl; ++q) {
             const int i = n->q_node[(size_t)q];
             const int lane = q / npl, slot = q % npl;
             if (i < 0) continue;
@@ -882,7 +894,7 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
                 uint32_t word = 0;
                 if (w)
                     for (int b = 0; b < 3; ++b) word |= (uint32_t)(w * std::abs(b - r)) << (8 * b);
-                obs[(((size_t)c * T + t) * 32 + lane) * npl + slot] = word;
+                obs[(((size_t)c * T + t) * L + lane) * npl + slot] = word;
             }
         }
     }
@@ -969,15 +981,20 @@ int rn_anneal(rn_ctx *ctx, const rn_schedule *s, int64_t sweeps)
     if (!any) return fail(ctx, RN_ESTATE, "no network has chains (call rn_init_chains)");
     RN_CUDA(ctx, cudaSetDevice(ctx->device));
     if (sweeps == 0) return RN_OK;
-    // several networks: one persistent launch over all of their chains
-    if (batchable(ctx, *s)) return anneal_batched(ctx, *s, sweeps);
-    ctx->batch.g0_synced = false;
+    // several networks: one persistent launch over all of their chains, and
+    // separate launches for the networks it cannot take
+    const bool batched = batchable(ctx, *s);
+    if (batched) {
+        if (int rc = anneal_batched(ctx, *s, sweeps)) return rc;
+    } else {
+        ctx->batch.g0_synced = false;
+    }
     const int64_t iters = s->iters_per_level;
     // at most this many threshold entries per launch segment
     const size_t budget = (size_t)1 << 24;
     for (auto &np : ctx->nets) {
         Network &n = *np;
-        if (!n.chains_valid) continue;
+        if (!n.chains_valid || (batched && in_batch(n))) continue;
         const DevNet dn = n.dev();
         const DevChains ch = n.chains();
         int64_t g = n.step;
@@ -1034,7 +1051,9 @@ int rn_anneal(rn_ctx *ctx, const rn_schedule *s, int64_t sweeps)
             sc.queue = ctx->queue.p;
             sc.done = ctx->done.p;
             sc.err = ctx->dev_err.p;
-            cudaError_t e = launch_anneal(dn, n.d0, n.d1, ch, sc, ctx->sm_count, ctx->stream);
+            cudaError_t e = n.lanes != 32
+                                ? launch_anneal_block(dn, ch, sc, ctx->sm_count, ctx->stream)
+                                : launch_anneal(dn, n.d0, n.d1, ch, sc, ctx->sm_count, ctx->stream);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "anneal kernel");
             ctx->launches += 1;
             if (s->global_sync && seg_end % iters == 0) {

@@ -1,0 +1,557 @@
+// rn_block.cu -- block-per-chain simulation for networks of 513 .. 4096 nodes.
+//
+// A warp no longer holds the chain: its nodes are spread over the 256 threads
+// of a block (node rank r -> slot r / 256, thread r % 256, internal index
+// q = thread * npl + slot, npl <= 16).  Everything else is the shared-memory
+// table path of rn_smem.cuh: table words and per-node byte-SIMD update state
+// in shared memory, laid out [..][256] so that each warp's accesses are
+// consecutive words, four conditions per group (Sections 2.1-2.3).  The
+// priority maximum of a time step is a block maximum (warp redux, then eight
+// warp values through shared memory), so each update step has two block
+// barriers.  The annealing loop (Table 1: GetCandidate, Simulate, Metropolis)
+// runs with thread 0 drawing and deciding and the owner thread of the changed
+// table entry applying or undoing it.  The chain's x stays in global memory,
+// read through L2 (another SM may have advanced the chain in the previous
+// chunk), so that the tables of a 2000-node network fit the block's shared
+// memory.  Work items (chunk, chain) come from the same queue scheme as the
+// warp kernels, with bounded waits.
+#include "rn_kernels.cuh"
+
+namespace rn {
+namespace {
+
+constexpr int kBT = 256;        // threads per chain
+constexpr int kBW = kBT / 32;   // warps per chain
+
+__device__ __forceinline__ int xcg(const int8_t *x, int j) { return (int)__ldcg(x + j); }
+
+// Shared memory: codes [kBT * npl] u16 at offset 0, then the table rows, the
+// per-node fields, the constraint counters and a small scratch area.
+struct BlockLayout {
+    uint32_t codes, lut, node, cnt, scratch, bytes;
+};
+
+__host__ __device__ inline uint32_t round256(uint32_t v) { return (v + 255u) & ~255u; }
+
+__host__ __device__ inline BlockLayout block_layout(const int *D, int npl, int N)
+{
+    BlockLayout L;
+    uint32_t rows = 0;
+    for (int k = 0; k < npl; ++k) rows += (uint32_t)groups4(D[k]);
+    L.codes = 0;
+    L.lut = round256(2u * kBT * (uint32_t)npl);
+    L.node = L.lut + rows * kBT * 4u;
+    L.cnt = L.node + (uint32_t)npl * kF_N * kBT * 4u;
+    L.scratch = L.cnt + round256(2u * (((uint32_t)N + 15u) & ~15u));
+    L.bytes = L.scratch + 256u;
+    return L;
+}
+
+// Broadcast area of the annealing loop (in the scratch region).
+struct Bcast {
+    uint32_t wmax[kBW][4];   // per-warp maxima of the four conditions' priorities
+    uint32_t wsum[kBW];      // per-warp score sums
+    uint32_t item;           // work item
+    uint32_t rz;             // acceptance word of the step
+    int32_t ok;              // a candidate exists (or: the wait succeeded)
+    int32_t j, kind, idx, cur, v;   // the candidate x_j: cur -> v (kind, index in its block)
+    int32_t owner, pos, w, p, t, slot;   // owner thread and the changed table entry
+};
+
+struct BlockPath {
+    uint8_t *sm;
+    uint16_t *code;
+    uint32_t *lut, *node;
+    uint8_t *out_nz, *pos_in;
+    Bcast *bc;
+    int npl;
+    uint32_t undo_addr, undo_val;
+    bool undo_lut;
+
+    __device__ __forceinline__ uint32_t &F(int k, int f, int t) const
+    {
+        return node[(k * kF_N + f) * kBT + t];
+    }
+
+    __device__ __forceinline__ int lut_row(const DevNet &net, int k, int d) const
+    {
+        int o = 0;
+        for (int kk = 0; kk < k; ++kk) o += groups4(net.D[kk]);
+        return o + d;
+    }
+
+    // Tables of x (read through L2 when `cg`).
+    __device__ void load(const DevNet &net, const int8_t *x, int t, bool cg)
+    {
+        auto X = [&](int j) { return cg ? xcg(x, j) : (int)x[j]; };
+        const int E = net.E, N = net.N;
+        int o = 0;
+        for (int k = 0; k < npl; ++k) {
+            for (int d = 0; d < net.D[k]; ++d) {
+                const int e = net.edge_id[(k * net.dtab + d) * kBT + t];
+                uint32_t w;
+                if (e >= 0)
+                    w = edge_word_s(X(e), X(E + e), X(2 * E + e),
+                                    2u * (uint32_t)net.node_q[net.src[e]]);
+                else
+                    w = 0x04040000u | ((uint32_t)(-1 - e) & 0xffffu);
+                lut[(o + d) * kBT + t] = w;
+            }
+            // neutral rows up to a whole group of 4: the code of node 2 t (one
+            // bank per lane; npl >= 3 on this path, so node 2 t exists)
+            for (int d = net.D[k]; d < groups4(net.D[k]); ++d)
+                lut[(o + d) * kBT + t] = 0x04040000u | (4u * (uint32_t)t);
+            o += groups4(net.D[k]);
+            const int i = net.q_node[t * npl + k];
+            uint32_t u = 1, m1 = 1, d2 = 0;
+            if (i >= 0) {
+                u = (uint32_t)X(3 * E + i);
+                m1 = (uint32_t)X(3 * E + N + i) + 1u;
+                d2 = X(3 * E + 2 * N + i) == 2 ? 0xffffffffu : 0u;
+            }
+            F(k, kF_U2, t) = u * 0x00010001u;
+            F(k, kF_CM, t) = (128u - m1) * kB1;
+            F(k, kF_D2, t) = d2;
+        }
+    }
+
+    // Constraint counters of Section 2.5.3 from x (global, through L2).
+    __device__ void count(const DevNet &net, const int8_t *x, int t)
+    {
+        for (int i = t; i < net.N; i += kBT) {
+            int o = 0, q = 0;
+            for (int k = net.out_ptr[i]; k < net.out_ptr[i + 1]; ++k)
+                o += xcg(x, net.out_edges[k]) != 0;
+            for (int k = net.in_ptr[i]; k < net.in_ptr[i + 1]; ++k) {
+                const int e = net.in_edges[k];
+                q += (xcg(x, e) != 0) && (xcg(x, net.E + e) == 1);
+            }
+            out_nz[i] = (uint8_t)min(o, 255);
+            pos_in[i] = (uint8_t)min(q, 255);
+        }
+    }
+
+    __device__ void change_edge(const DevNet &net, int t, int owner, int pos, int w, int p, int tt)
+    {
+        if (t != owner) return;
+        const int row = lut_row(net, (pos >> 8) & 0xff, pos & 0xff);
+        const uint32_t a = (uint32_t)(row * kBT + t);
+        undo_lut = true;
+        undo_addr = a;
+        undo_val = lut[a];
+        lut[a] = edge_word_s(w, p, tt, undo_val);
+    }
+
+    __device__ void change_node(int t, int owner, int k, int kind, int v)
+    {
+        if (t != owner) return;
+        const int f = kind == 3 ? kF_U2 : kind == 4 ? kF_CM : kF_D2;
+        const uint32_t a = (uint32_t)((k * kF_N + f) * kBT + t);
+        undo_lut = false;
+        undo_addr = a;
+        undo_val = node[a];
+        node[a] = kind == 3 ? (uint32_t)v * 0x00010001u
+                : kind == 4 ? (127u - (uint32_t)v) * kB1
+                            : (v == 2 ? 0xffffffffu : 0u);
+    }
+
+    __device__ void undo(int t, int owner)
+    {
+        if (t != owner) return;
+        if (undo_lut) lut[undo_addr] = undo_val;
+        else node[undo_addr] = undo_val;
+    }
+
+    // Simulate(x) of Table 1 over every condition and time step, scored
+    // against the entry tables (Section 2.3).  Returns y in every thread.
+    __device__ int32_t simulate(const DevNet &net, int t, uint8_t *traj)
+    {
+        const int T = net.T, lane = t & 31, warp = t >> 5;
+        uint32_t score = 0;
+        for (int g = 0; g < net.G; ++g) {
+            for (int k = 0; k < npl; ++k) {
+                const size_t q = (size_t)g * kBT * npl + t * npl + k;
+                const uint32_t s4 = __ldg(net.init_s4 + q);
+                F(k, kF_S4, t) = s4;
+                F(k, kF_CU, t) = 0;
+                F(k, kF_CD, t) = 0;
+                F(k, kF_UA01, t) = F(k, kF_U2, t);
+                F(k, kF_UA23, t) = F(k, kF_U2, t);
+                F(k, kF_MOV, t) = __ldg(net.movable + q);
+                code[t * npl + k] = SmemPath::code_of(s4);
+            }
+            __syncthreads();
+            const int ncg = min(net.C - 4 * g, 4);
+            for (int tau = 0; tau < T; ++tau) {
+                if (tau > 0) {
+                    uint32_t m01 = 0, m23 = 0;
+                    int o = 0;
+                    for (int k = 0; k < npl; ++k) {
+                        const int D4 = groups4(net.D[k]);
+                        uint32_t acc = kH - 0x04040404u * (uint32_t)D4;
+                        const uint32_t *lw = lut + o * kBT + t;
+                        for (int d = 0; d < D4; d += 4) {
+                            uint32_t w[4], c[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) w[i] = lw[(d + i) * kBT];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
+                        }
+                        o += D4;
+                        const uint32_t s4 = F(k, kF_S4, t);
+                        const uint32_t tgt = (((acc - kB1) >> 7) & kB1) + (((acc - 2 * kB1) >> 7) & kB1);
+                        const uint32_t dp = tgt + 2 * kB1 - s4;
+                        const uint32_t up = (dp + 0x7D7D7D7Du) & kH;
+                        const uint32_t dn = ~(dp + 0x7E7E7E7Eu) & kH;
+                        const uint32_t cu = (F(k, kF_CU, t) + kB1) & prmt(up, 0u, 0xBA98u);
+                        const uint32_t cd = (F(k, kF_CD, t) + kB1) & prmt(dn, 0u, 0xBA98u);
+                        F(k, kF_CU, t) = cu;
+                        F(k, kF_CD, t) = cd;
+                        const uint32_t cm = F(k, kF_CM, t);
+                        const uint32_t el = ((cu + cm) | (cd + cm)) & F(k, kF_MOV, t);
+                        const uint32_t d2 = F(k, kF_D2, t);
+                        const uint32_t step1 = s4 + (up >> 7) - (dn >> 7);
+                        F(k, kF_SN, t) = (tgt & d2) | (step1 & ~d2);
+                        F(k, kF_ELM, t) = prmt(el, 0u, 0xBA98u);
+                        const uint32_t p01 = F(k, kF_UA01, t) & prmt(el, 0u, 0x9988u);
+                        const uint32_t p23 = F(k, kF_UA23, t) & prmt(el, 0u, 0xBBAAu);
+                        F(k, kF_PR01, t) = p01;
+                        F(k, kF_PR23, t) = p23;
+                        m01 = max_u16x2(m01, p01);
+                        m23 = max_u16x2(m23, p23);
+                    }
+                    const uint32_t p0 = __reduce_max_sync(kFull, m01 & 0xffffu);
+                    const uint32_t p1 = __reduce_max_sync(kFull, m01 >> 16);
+                    const uint32_t p2 = __reduce_max_sync(kFull, m23 & 0xffffu);
+                    const uint32_t p3 = __reduce_max_sync(kFull, m23 >> 16);
+                    if (lane == 0) {
+                        bc->wmax[warp][0] = p0;
+                        bc->wmax[warp][1] = p1;
+                        bc->wmax[warp][2] = p2;
+                        bc->wmax[warp][3] = p3;
+                    }
+                    __syncthreads();
+                    uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+#pragma unroll
+                    for (int w = 0; w < kBW; ++w) {
+                        q0 = max(q0, bc->wmax[w][0]);
+                        q1 = max(q1, bc->wmax[w][1]);
+                        q2 = max(q2, bc->wmax[w][2]);
+                        q3 = max(q3, bc->wmax[w][3]);
+                    }
+                    const uint32_t P01 = prmt(q0, q1, 0x5410u), P23 = prmt(q2, q3, 0x5410u);
+                    for (int k = 0; k < npl; ++k) {
+                        const uint32_t nz01 = ((F(k, kF_PR01, t) ^ P01) + 0x7FFF7FFFu) & 0x80008000u;
+                        const uint32_t nz23 = ((F(k, kF_PR23, t) ^ P23) + 0x7FFF7FFFu) & 0x80008000u;
+                        const uint32_t upd = F(k, kF_ELM, t) & ~prmt(nz01, nz23, 0xFDB9u);
+                        const uint32_t s4 = (F(k, kF_S4, t) & ~upd) | (F(k, kF_SN, t) & upd);
+                        F(k, kF_S4, t) = s4;
+                        F(k, kF_CU, t) &= ~upd;
+                        F(k, kF_CD, t) &= ~upd;
+                        const uint32_t u2 = F(k, kF_U2, t);
+                        const uint32_t u01 = prmt(upd, 0u, 0x9988u), u23 = prmt(upd, 0u, 0xBBAAu);
+                        F(k, kF_UA01, t) = ((F(k, kF_UA01, t) + u2) & ~u01) | (u2 & u01);
+                        F(k, kF_UA23, t) = ((F(k, kF_UA23, t) + u2) & ~u23) | (u2 & u23);
+                        code[t * npl + k] = SmemPath::code_of(s4);
+                    }
+                    __syncthreads();
+                }
+                // error at this time point (entry tables: byte b = W |b - R|)
+                const size_t row = (size_t)T * kBT * npl;
+                const uint32_t *ob = net.obs + ((size_t)4 * g * T + tau) * kBT * npl + t * npl;
+                uint32_t acc = 0;
+                for (int k = 0; k < npl; ++k) {
+                    const uint32_t s4 = F(k, kF_S4, t);
+                    const uint32_t x = s4 | (s4 >> 4);
+                    const uint32_t sel01 = (x & 0xffu) + 0x3340u;
+                    const uint32_t sel23 = ((x >> 16) & 0xffu) + 0x3340u;
+                    const uint32_t w0 = __ldg(ob + k);
+                    const uint32_t w1 = ncg > 1 ? __ldg(ob + row + k) : 0u;
+                    const uint32_t w2 = ncg > 2 ? __ldg(ob + 2 * row + k) : 0u;
+                    const uint32_t w3 = ncg > 3 ? __ldg(ob + 3 * row + k) : 0u;
+                    acc += __byte_perm(w0, w1, sel01) + __byte_perm(w2, w3, sel23);
+                    if (traj) {
+                        const int i = net.q_node[t * npl + k];
+                        for (int c = 0; c < ncg; ++c)
+                            if (i >= 0)
+                                traj[((size_t)(4 * g + c) * T + tau) * net.N + i] =
+                                    (uint8_t)((s4 >> (8 * c)) & 0xffu);
+                    }
+                }
+                score += (acc & 0xffu) + (acc >> 8);
+            }
+            __syncthreads();
+        }
+        score = __reduce_add_sync(kFull, score);
+        if (lane == 0) bc->wsum[warp] = score;
+        __syncthreads();
+        uint32_t total = 0;
+#pragma unroll
+        for (int w = 0; w < kBW; ++w) total += bc->wsum[w];
+        __syncthreads();
+        return (int32_t)total;
+    }
+};
+
+__device__ __forceinline__ BlockPath make_block_path(const DevNet &net, uint8_t *sm)
+{
+    const BlockLayout L = block_layout(net.D, net.npl, net.N);
+    BlockPath P;
+    P.sm = sm;
+    P.code = reinterpret_cast<uint16_t *>(sm + L.codes);
+    P.lut = reinterpret_cast<uint32_t *>(sm + L.lut);
+    P.node = reinterpret_cast<uint32_t *>(sm + L.node);
+    P.out_nz = sm + L.cnt;
+    P.pos_in = P.out_nz + ((net.N + 15) & ~15);
+    P.bc = reinterpret_cast<Bcast *>(sm + L.scratch);
+    P.npl = net.npl;
+    return P;
+}
+
+__global__ void __launch_bounds__(kBT, 1)
+    evaluate_block_kernel(DevNet net, const int8_t *__restrict__ X, int64_t xstride, int32_t n,
+                          int32_t *__restrict__ score, int32_t *__restrict__ score2,
+                          uint8_t *__restrict__ traj)
+{
+    extern __shared__ __align__(256) uint8_t sm[];
+    BlockPath P = make_block_path(net, sm);
+    const int t = threadIdx.x;
+    for (int v = blockIdx.x; v < n; v += gridDim.x) {
+        P.load(net, X + (size_t)v * xstride, t, false);
+        __syncthreads();
+        uint8_t *tv = traj ? traj + (size_t)v * net.C * net.T * net.N : nullptr;
+        const int32_t y = P.simulate(net, t, tv);
+        if (t == 0) {
+            score[v] = y;
+            if (score2) score2[v] = y;
+        }
+        __syncthreads();
+    }
+}
+
+// Copy a P-byte row between global buffers through L2, block-wide.
+__device__ __forceinline__ void block_copy16(int8_t *dst, const int8_t *src, int bytes, int t)
+{
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    for (int k = t; k < (bytes >> 4); k += kBT) __stcg(d + k, __ldcg(s + k));
+}
+
+// Steps [g_lo, g_hi) of one chain (Table 1), then publish the chunk.
+__device__ void block_chunk(BlockPath &P, const DevNet &net, const DevChains &ch,
+                            const DevSched &sc, int chain, int64_t g_lo, int64_t g_hi,
+                            int done_value, int t)
+{
+    const int E = net.E;
+    int8_t *xg = ch.x_cur + (size_t)chain * ch.pstride;
+    int8_t *xb = ch.x_best + (size_t)chain * ch.pstride;
+    Bcast *bc = P.bc;
+    P.load(net, xg, t, true);
+    P.count(net, xg, t);
+    __syncthreads();
+    int32_t d_cur = __ldcg(ch.d_cur + chain), d_best = __ldcg(ch.d_best + chain);
+    int32_t n_acc = 0, n_up = 0, n_null = 0;
+    int64_t level = g_lo / sc.iters;
+    int64_t in_level = g_lo - level * sc.iters;
+    auto X = [&](int j) { return xcg(xg, j); };
+    for (int64_t g = g_lo; g < g_hi; ++g) {
+        if (in_level == sc.iters) {
+            in_level = 0;
+            ++level;
+        }
+        if (sc.reset_to_best && in_level == 0) {
+            // Table 1: every level starts from the chain's x_best
+            block_copy16(xg, xb, ch.pstride, t);
+            __threadfence_block();
+            __syncthreads();
+            P.load(net, xg, t, true);
+            P.count(net, xg, t);
+            __syncthreads();
+            d_cur = d_best;
+        }
+        ++in_level;
+        if (t == 0) {
+            const uint4 r = philox(ch.seed, (uint32_t)g, (uint32_t)((uint64_t)g >> 32),
+                                   (uint32_t)chain, 0u);
+            int j = 0, kind = 0, idx = 0, cur = 0, v = 0;
+            const bool ok = net.n_free > 0 &&
+                            get_candidate_x(net, X, P.out_nz, P.pos_in, r.x, r.y, j, kind, idx,
+                                            cur, v);
+            bc->ok = ok;
+            if (ok) {
+                bc->j = j;
+                bc->kind = kind;
+                bc->idx = idx;
+                bc->cur = cur;
+                bc->v = v;
+                bc->rz = r.z;
+                if (kind < 3) {
+                    const int pos = net.edge_pos[idx];
+                    int w = X(idx), p = X(E + idx), tt = X(2 * E + idx);
+                    if (kind == 0) w = v; else if (kind == 1) p = v; else tt = v;
+                    bc->owner = pos >> 16;
+                    bc->pos = pos;
+                    bc->w = w;
+                    bc->p = p;
+                    bc->t = tt;
+                } else {
+                    const int q = net.node_q[idx];
+                    bc->owner = q / P.npl;
+                    bc->slot = q - (q / P.npl) * P.npl;
+                }
+            }
+        }
+        __syncthreads();
+        if (!bc->ok) {
+            ++n_null;
+            __syncthreads();
+            continue;
+        }
+        const int owner = bc->owner, kind = bc->kind;
+        if (kind < 3) P.change_edge(net, t, owner, bc->pos, bc->w, bc->p, bc->t);
+        else P.change_node(t, owner, bc->slot, kind, bc->v);
+        const int j = bc->j, v = bc->v, cur = bc->cur, idx = bc->idx;
+        const uint32_t rz = bc->rz;
+        __syncthreads();
+        const int32_t d_cand = P.simulate(net, t, nullptr);
+        // Metropolis acceptance against the host-computed threshold table
+        const int32_t dE = d_cand - d_cur;
+        bool accept = dE <= 0;
+        if (!accept) {
+            const int64_t l = level - sc.level0;
+            if (dE <= sc.thr_len[l]) accept = rz < __ldg(sc.thr + sc.thr_off[l] + dE - 1);
+        }
+        if (accept) {
+            if (t == 0) {
+                apply_counters_x(net, X, P.out_nz, P.pos_in, kind, idx, cur, v);
+                __stcg(xg + j, (int8_t)v);
+            }
+            d_cur = d_cand;
+            ++n_acc;
+            n_up += dE > 0;
+            __syncthreads();
+            if (d_cand < d_best) {
+                d_best = d_cand;
+                block_copy16(xb, xg, ch.pstride, t);
+            }
+        } else {
+            P.undo(t, owner);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        __stcg(ch.d_cur + chain, d_cur);
+        __stcg(ch.d_best + chain, d_best);
+        int64_t *cnt = ch.cnt + 3 * (size_t)chain;
+        __stcg(cnt + 0, __ldcg(cnt + 0) + n_acc);
+        __stcg(cnt + 1, __ldcg(cnt + 1) + n_up);
+        __stcg(cnt + 2, __ldcg(cnt + 2) + n_null);
+    }
+    // publish: every thread's stores, then the chunk counter of the chain
+    __threadfence();
+    __syncthreads();
+    if (t == 0) atomicExch(sc.done + chain, done_value);
+}
+
+// Thread 0 waits (bounded) until chunk cj - 1 of the chain is published.
+__device__ __forceinline__ bool block_wait(int32_t *flag, int cj, int32_t *err)
+{
+    for (int k = 0; k < kWaitLimit; ++k) {
+        if (*(volatile int32_t *)err) return false;
+        if (atomicAdd(flag, 0) >= cj) {
+            __threadfence();
+            return true;
+        }
+        __nanosleep(256);
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
+__global__ void __launch_bounds__(kBT, 1) anneal_block_kernel(DevNet net, DevChains ch, DevSched sc)
+{
+    extern __shared__ __align__(256) uint8_t sm[];
+    BlockPath P = make_block_path(net, sm);
+    const int t = threadIdx.x;
+    const int64_t n_items = (int64_t)sc.n_chunks * ch.n;
+    for (;;) {
+        if (t == 0) P.bc->item = atomicAdd(sc.queue, 1u);
+        __syncthreads();
+        const unsigned int item = P.bc->item;
+        __syncthreads();
+        if ((int64_t)item >= n_items) break;
+        const int cj = (int)(item / (unsigned)ch.n);
+        const int chain = (int)(item - (unsigned)cj * (unsigned)ch.n);
+        if (cj > 0) {
+            if (t == 0) P.bc->ok = block_wait(sc.done + chain, cj, sc.err);
+            __syncthreads();
+            const bool ok = P.bc->ok;
+            __syncthreads();
+            if (!ok) return;
+        }
+        const int64_t g_lo = sc.g0 + (int64_t)cj * sc.chunk;
+        const int64_t g_hi = min(sc.g1, g_lo + sc.chunk);
+        block_chunk(P, net, ch, sc, chain, g_lo, g_hi, cj + 1, t);
+    }
+}
+
+cudaError_t block_smem(const DevNet &net, size_t *bytes)
+{
+    *bytes = block_layout(net.D, net.npl, net.N).bytes;
+    int dev = 0, limit = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    return *bytes <= (size_t)limit ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+}  // namespace
+
+size_t block_path_smem_bytes(const int *D, int npl, int N)
+{
+    return block_layout(D, npl, N).bytes;
+}
+
+cudaError_t launch_evaluate_block(const DevNet &net, const int8_t *X, int64_t xstride, int32_t n,
+                                  int32_t *score, int32_t *score2, uint8_t *traj, int sm_count,
+                                  cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    size_t smem = 0;
+    cudaError_t e = block_smem(net, &smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(evaluate_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = n < sm_count ? n : sm_count;
+    evaluate_block_kernel<<<grid, kBT, smem, st>>>(net, X, xstride, n, score, score2, traj);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_anneal_block(const DevNet &net, const DevChains &ch, const DevSched &sc0,
+                                int sm_count, cudaStream_t st)
+{
+    size_t smem = 0;
+    cudaError_t e = block_smem(net, &smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(anneal_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, anneal_block_kernel, kBT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = sm_count * per_sm;
+    DevSched sc = sc0;
+    plan_chunks(sc, ch.n, grid);
+    e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc.done, 0, sizeof(int32_t) * (size_t)ch.n, st);
+    if (e != cudaSuccess) return e;
+    anneal_block_kernel<<<grid, kBT, smem, st>>>(net, ch, sc);
+    return cudaGetLastError();
+}
+
+}  // namespace rn

@@ -62,6 +62,7 @@ struct Network {
     bool has_frozen = false;
     // lane / slot layout
     int npl = 0, dtab = 0;
+    int lanes = 32;                     // threads per chain: 32, or kBlockLanes above 512 nodes
     int D[kMaxSlots] = {};
     std::vector<int32_t> node_q, edge_id, edge_pos, free_list, in_ptr, in_edges, out_ptr,
         out_edges;
@@ -97,7 +98,7 @@ struct Network {
         DevNet n{};
         n.N = N; n.E = E; n.P = P; n.n_free = (int32_t)free_list.size();
         n.C = C; n.T = T; n.G = G;
-        n.npl = npl; n.cg = cg; n.dtab = dtab;
+        n.npl = npl; n.cg = cg; n.dtab = dtab; n.lanes = lanes;
         for (int k = 0; k < kMaxSlots; ++k) n.D[k] = D[k];
         n.edge_id = d_edge_id.p; n.edge_q2 = d_edge_q2.p; n.edge_pos = d_edge_pos.p;
         n.node_q = d_node_q.p; n.q_node = d_q_node.p; n.src = d_src.p; n.dst = d_dst.p;

@@ -33,10 +33,13 @@ constexpr uint32_t kFull = 0xffffffffu;
 constexpr int32_t kOutUA = -(1 << 22);   // priority seed of a node that never moves
 
 // Network as the kernels see it (all pointers are device memory).
+constexpr int kBlockLanes = 256;        // threads of a chain on the block path (N > 512)
+
 struct DevNet {
     int32_t N, E, P, n_free;
     int32_t C, T, G;                    // conditions, time points, condition groups
     int32_t npl, cg, dtab;              // nodes per lane, conditions per group, table stride
+    int32_t lanes;                      // threads per chain: 32 (a warp) or kBlockLanes
     int32_t D[kMaxSlots];               // padded in-degree of each slot
     const int32_t *edge_id;             // [npl][dtab][32] edge index, or -1 - (code offset) for padding
     const uint8_t *edge_q2;             // [E] 2 * internal index of the edge's source

@@ -174,6 +174,8 @@ cudaError_t launch_evaluate(const DevNet &net, const int8_t *X, int64_t xstride,
                             cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
+    if (net.lanes != 32) return launch_evaluate_block(net, X, xstride, n, score, score2, traj,
+                                                      sm_count, st);
     int grid = (n + 3) / 4;
     if (grid > sm_count * 16) grid = sm_count * 16;
     if (net.npl > kRegSlots) {

@@ -194,24 +194,25 @@ __device__ __forceinline__ void count_constraints(const DevNet &net, const int8_
 // GetCandidate (Table 1) for a network with free parameters: the pick(r0)-th
 // free parameter j, then the pick(r1)-th of its domain values != x_j whose
 // single change keeps both constraints of Section 2.5.3 (counters out_nz,
-// pos_in of x).  Returns false for a null move (no such value).
-__device__ __forceinline__ bool get_candidate(const DevNet &net, const int8_t *xs,
-                                              const uint8_t *out_nz, const uint8_t *pos_in,
-                                              uint32_t r0, uint32_t r1, int &j, int &kind,
-                                              int &idx, int &cur, int &v)
+// pos_in of x).  Returns false for a null move (no such value).  `xr(j)`
+// reads x_j (shared memory, or global memory through L2).
+template <class XR>
+__device__ __forceinline__ bool get_candidate_x(const DevNet &net, XR xr, const uint8_t *out_nz,
+                                                const uint8_t *pos_in, uint32_t r0, uint32_t r1,
+                                                int &j, int &kind, int &idx, int &cur, int &v)
 {
     const int E = net.E, N = net.N;
     j = net.free_list[pick(r0, (uint32_t)net.n_free)];
     if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
     else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
-    cur = xs[j];
+    cur = xr(j);
     int8_t vals[6];
     const int nd = domain(kind, kind == 3 && net.fast[idx], vals);
     bool blocked0 = false, blocked_all = false;
     if (kind == 0 && cur != 0) {
         const int a = net.src[idx], b = net.dst[idx];
-        blocked0 = out_nz[a] < 2 || (xs[E + idx] == 1 && pos_in[b] < 2);
-    } else if (kind == 1 && cur == 1 && xs[idx] != 0) {
+        blocked0 = out_nz[a] < 2 || (xr(E + idx) == 1 && pos_in[b] < 2);
+    } else if (kind == 1 && cur == 1 && xr(idx) != 0) {
         blocked_all = pos_in[net.dst[idx]] < 2;
     }
     int8_t alts[6];
@@ -230,20 +231,37 @@ __device__ __forceinline__ bool get_candidate(const DevNet &net, const int8_t *x
     return true;
 }
 
-// Constraint counters after x_j: cur -> v (x still holds cur).
-__device__ __forceinline__ void apply_counters(const DevNet &net, const int8_t *xs,
-                                               uint8_t *out_nz, uint8_t *pos_in, int kind,
-                                               int idx, int cur, int v)
+__device__ __forceinline__ bool get_candidate(const DevNet &net, const int8_t *xs,
+                                              const uint8_t *out_nz, const uint8_t *pos_in,
+                                              uint32_t r0, uint32_t r1, int &j, int &kind,
+                                              int &idx, int &cur, int &v)
+{
+    return get_candidate_x(net, [&](int k) { return (int)xs[k]; }, out_nz, pos_in, r0, r1, j,
+                           kind, idx, cur, v);
+}
+
+// Constraint counters after x_j: cur -> v (x still holds cur); xr as above.
+template <class XR>
+__device__ __forceinline__ void apply_counters_x(const DevNet &net, XR xr, uint8_t *out_nz,
+                                                 uint8_t *pos_in, int kind, int idx, int cur,
+                                                 int v)
 {
     const int E = net.E;
     if (kind == 0 && (cur == 0) != (v == 0)) {
         const int delta = v != 0 ? 1 : -1;
         out_nz[net.src[idx]] += delta;
-        if (xs[E + idx] == 1) pos_in[net.dst[idx]] += delta;
-    } else if (kind == 1 && xs[idx] != 0) {
+        if (xr(E + idx) == 1) pos_in[net.dst[idx]] += delta;
+    } else if (kind == 1 && xr(idx) != 0) {
         if (cur == 1) pos_in[net.dst[idx]] -= 1;
         if (v == 1) pos_in[net.dst[idx]] += 1;
     }
+}
+
+__device__ __forceinline__ void apply_counters(const DevNet &net, const int8_t *xs,
+                                               uint8_t *out_nz, uint8_t *pos_in, int kind,
+                                               int idx, int cur, int v)
+{
+    apply_counters_x(net, [&](int k) { return (int)xs[k]; }, out_nz, pos_in, kind, idx, cur, v);
 }
 
 __device__ __forceinline__ void warp_copy16(void *dst, const void *src, int bytes, int lane)

@@ -34,6 +34,15 @@ cudaError_t launch_evaluate(const DevNet &net, const int8_t *X, int64_t xstride,
 cudaError_t launch_anneal(const DevNet &net, int d0, int d1, const DevChains &ch,
                           const DevSched &sc, int sm_count, cudaStream_t st);
 cudaError_t launch_init(const DevNet &net, const DevChains &ch, int32_t *status, cudaStream_t st);
+
+// Block path (rn_block.cu): networks of 513 .. 4096 nodes, a block of
+// kBlockLanes threads per chain.  Shared memory of one block:
+size_t block_path_smem_bytes(const int *D, int npl, int N);
+cudaError_t launch_evaluate_block(const DevNet &net, const int8_t *X, int64_t xstride, int32_t n,
+                                  int32_t *score, int32_t *score2, uint8_t *traj, int sm_count,
+                                  cudaStream_t st);
+cudaError_t launch_anneal_block(const DevNet &net, const DevChains &ch, const DevSched &sc,
+                                int sm_count, cudaStream_t st);
 cudaError_t launch_level_sync(const DevChains &ch, int32_t *winner, cudaStream_t st);
 
 // Many networks in one persistent launch (rn_batch.cu).

@@ -997,8 +997,9 @@ int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K
     if (s->reset_to_best || s->global_sync)
         return fail(ctx, RN_EUNSUPPORTED, "screened annealing runs without reset/global sync");
     if (!n->chains_valid) return fail(ctx, RN_ESTATE, "no chains (call rn_init_chains)");
-    if (n->N > 4096 || n->pstride > 8192)
-        return fail(ctx, RN_EUNSUPPORTED, "screened annealing covers N <= 4096, P <= 8192");
+    if (n->lanes != 32 || n->pstride > 8192)
+        return fail(ctx, RN_EUNSUPPORTED,
+                    "screened annealing covers networks of a warp per chain (N <= 512)");
     RN_CUDA(ctx, cudaSetDevice(ctx->device));
     if (sweeps == 0) return RN_OK;
     int rc;

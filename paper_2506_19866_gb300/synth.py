@@ -222,10 +222,24 @@ def make(name: str) -> Workload:
         return Workload(name, src, dst, fast, init, ko, obs, 20, planted_seed=2102,
                         noise_frac=0.0, noise_seed=4102, chain_seed=0, n_chains=4096,
                         sweeps=20_000, T0=10.0, alpha=plain_alpha(10.0, T_END_PLAIN, 20_000))
+    if name == "n2000_c16_t33":
+        # Scale-up network: 2000 nodes, in-degree Poisson(6) (floored at 1, capped
+        # at the block path's 64), 16 conditions, 32 update steps (T = 33 points
+        # with t0), 10% of entries observed, no noise; 16384 chains.
+        rng = np.random.default_rng(1005)
+        src, dst = random_digraph(2000, _poisson_indegree(2000, 6.0, 64, rng), rng)
+        fast = speed_classes(2000, rng)
+        init, ko = conditions(2000, 16, rng)
+        obs = bernoulli_mask(16, 33, 2000, 0.1, np.random.default_rng(3005))
+        return Workload(name, src, dst, fast, init, ko, obs, 33, planted_seed=2005,
+                        noise_frac=0.0, noise_seed=4005, chain_seed=0, n_chains=16384,
+                        sweeps=2000, T0=10.0, alpha=0.995)
     raise KeyError(name)
 
 
 WORKLOADS = ("n15_c3_t11", "n120_c8_t21", "hpg_9n_25e", "mtb_63n_178e")
+# networks above 512 nodes (a block of threads per chain)
+LARGE_WORKLOADS = ("n2000_c16_t33",)
 
 
 def make_batch(n_nets=256, total_chains=65536, seed=1003, n_min=10, n_max=300, max_indeg=16):

@@ -1,0 +1,138 @@
+"""Block path (513 .. 4096 nodes, a block of 256 threads per chain) against the
+CPU oracle through the C ABI: scores and trajectories of evaluated vectors,
+and whole annealing chains bit for bit, up to the 2000-node, 16-condition,
+33-time-point scale-up network; a batch that mixes a block-path network with
+warp-path networks equals separate runs."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2506_19866_gb300 import rnanneal as R
+from paper_2506_19866_gb300 import synth
+from tests.gpu_util import Problem, random_vectors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2506_19866_gb300 import build
+    build.build()
+
+
+@pytest.fixture
+def ctx(built):
+    h = R.rn_create(0)
+    yield h
+    R.rn_destroy(h)
+
+
+def _compare(st, ch, ids):
+    np.testing.assert_array_equal(st["x_cur"][ids], ch.x_cur)
+    np.testing.assert_array_equal(st["x_best"][ids], ch.x_best)
+    np.testing.assert_array_equal(st["d_cur"][ids], ch.d_cur)
+    np.testing.assert_array_equal(st["d_best"][ids], ch.d_best)
+    np.testing.assert_array_equal(st["counters"][ids][:, 0], ch.n_accept)
+    np.testing.assert_array_equal(st["counters"][ids][:, 1], ch.n_uphill)
+    np.testing.assert_array_equal(st["counters"][ids][:, 2], ch.n_null)
+
+
+@pytest.mark.parametrize("n_nodes,lam,cap,n_cond,n_times", [
+    (513, 4.0, 24, 3, 9), (777, 5.0, 24, 5, 7), (1300, 6.0, 24, 2, 12), (600, 20.0, 40, 2, 5),
+    (2900, 2.0, 8, 1, 4)])
+def test_evaluate_block_sizes(ctx, n_nodes, lam, cap, n_cond, n_times):
+    # slot and thread boundaries of the block layout (3 .. 12 nodes per thread),
+    # one to five conditions (a partial group of 4), an in-degree above the warp
+    # paths' 16, and a network near the shared-memory limit; trajectories
+    # included
+    w = synth.random_network(500 + n_nodes, n_nodes, lam=lam, cap=cap, n_cond=n_cond,
+                             n_times=n_times, obs_frac=0.3)
+    p = Problem(w, ctx)
+    X = np.concatenate([p.xs[None], O.init_chains(p.net, 3, 3), random_vectors(p.net, 3, 9)])
+    score, traj = R.rn_evaluate(ctx, p.id, X, traj_shape=p.shape)
+    for k in range(X.shape[0]):
+        y, t = O.objective(p.net, p.tc, X[k], return_traj=True)
+        np.testing.assert_array_equal(traj[k], t, err_msg=f"vector {k}")
+        assert score[k] == y, f"vector {k}"
+    assert score[0] == 0                        # the planted vector, noise-free data
+
+
+def test_anneal_block_chains_match_oracle(ctx):
+    w = synth.random_network(61, 700, lam=5.0, cap=20, n_cond=6, n_times=8, obs_frac=0.3)
+    p = Problem(w, ctx)
+    n = 300                                     # more chains than resident blocks: chunked
+    R.rn_init_chains(ctx, p.id, n, 5)
+    sched = R.schedule(3.0, 0.98)
+    R.rn_anneal(ctx, sched, 10)
+    R.rn_anneal(ctx, sched, 14)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    assert st["step"] == 24
+    ids = [0, 1, 151, 299]
+    ch = O.start_chains(p.net, p.tc, 5, n, ids)
+    O.anneal(p.net, p.tc, O.Schedule(3.0, 0.98), 5, ch, 0, 24, ids)
+    _compare(st, ch, ids)
+
+
+def test_anneal_block_paper_mode(ctx):
+    # reset to x_best at each level start and the global argmin at level end
+    w = synth.random_network(62, 600, lam=4.0, cap=20, n_cond=2, n_times=6, obs_frac=0.4)
+    p = Problem(w, ctx)
+    n = 40
+    R.rn_init_chains(ctx, p.id, n, 9)
+    sched = R.schedule(2.0, 0.9, iters_per_level=5, reset_to_best=True, global_sync=True)
+    R.rn_anneal(ctx, sched, 15)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    ids = list(range(n))
+    ch = O.start_chains(p.net, p.tc, 9, n)      # the global argmin needs every chain
+    O.anneal(p.net, p.tc, O.Schedule(2.0, 0.9, 5, True, True), 9, ch, 0, 15)
+    _compare(st, ch, ids)
+
+
+def test_scale_up_network_sampled(ctx):
+    # the 2000-node, 16-condition, 33-time-point network in the launch
+    # configuration of a full run (every chain resident): sampled chains and
+    # evaluated vectors against the oracle
+    w = synth.make("n2000_c16_t33")
+    p = Problem(w, ctx)
+    n = 2048
+    R.rn_init_chains(ctx, p.id, n, w.chain_seed)
+    sched = R.schedule(w.T0, w.alpha)
+    R.rn_anneal(ctx, sched, 3)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    ids = [0, 1777]
+    ch = O.start_chains(p.net, p.tc, w.chain_seed, n, ids)
+    O.anneal(p.net, p.tc, O.Schedule(w.T0, w.alpha), w.chain_seed, ch, 0, 3, ids)
+    _compare(st, ch, ids)
+    X = np.concatenate([p.xs[None], st["x_cur"][:2]])
+    score = R.rn_evaluate(ctx, p.id, X)
+    assert score[0] == 0
+    np.testing.assert_array_equal(score[1:], st["d_cur"][:2])
+
+
+def test_batch_with_block_network_equals_separate_runs(built):
+    nets = synth.make_batch(n_nets=3, total_chains=300, seed=21, n_min=20, n_max=200)
+    nets.append(synth.random_network(63, 640, lam=4.0, cap=20, n_cond=3, n_times=6,
+                                     obs_frac=0.3))
+    sched = R.schedule(4.0, 0.97)
+    ctx = R.rn_create(0)
+    try:
+        probs = [Problem(w, ctx) for w in nets]
+        for p, w in zip(probs, nets):
+            R.rn_init_chains(ctx, p.id, min(w.n_chains, 120), w.chain_seed)
+        R.rn_anneal(ctx, sched, 12)
+        R.rn_anneal(ctx, sched, 12)
+        assert R.rn_batch_config(ctx)["networks"] == 3
+        got = [R.rn_get_chain_state(ctx, p.id, min(w.n_chains, 120)) for p, w in zip(probs, nets)]
+    finally:
+        R.rn_destroy(ctx)
+    for w, st in zip(nets, got):
+        c1 = R.rn_create(0)
+        try:
+            q = Problem(w, c1)
+            R.rn_init_chains(c1, q.id, min(w.n_chains, 120), w.chain_seed)
+            R.rn_anneal(c1, sched, 24)
+            alone = R.rn_get_chain_state(c1, q.id, min(w.n_chains, 120))
+        finally:
+            R.rn_destroy(c1)
+        for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"):
+            np.testing.assert_array_equal(st[k], alone[k], err_msg=f"{w.name} {k}")

@@ -251,9 +251,10 @@ def test_rejects_bad_input(ctx):
     with pytest.raises(R.RNError) as e:
         R.rn_init_chains(ctx, net, 2, 0, x0)
     assert e.value.code == R.RN_ECONSTRAINT
-    big = synth.random_network(3, 600, lam=3.0, cap=8, n_cond=1, n_times=4, obs_frac=0.5)
+    # beyond the block path: more than 4096 nodes
+    big = synth.random_network(3, 5000, lam=3.0, cap=8, n_cond=1, n_times=4, obs_frac=0.5)
     bn = R.rn_load_network(ctx, big.src, big.dst, big.fast)
-    R.rn_load_timecourse(ctx, bn, big.init, np.zeros((1, 4, 600)), big.observed)
+    R.rn_load_timecourse(ctx, bn, big.init, np.zeros((1, 4, 5000)), big.observed)
     with pytest.raises(R.RNError) as e:
         R.rn_init_chains(ctx, bn, 2, 0)
     assert e.value.code == R.RN_EUNSUPPORTED
