@@ -94,7 +94,16 @@ const char *rn_last_error(const rn_ctx *ctx);
  * Rejected with RN_EINVAL: N < 1, E < 1, N > 65535, an index out of range,
  * a self-loop, a duplicate edge, a node without an in-edge or an out-edge
  * (the constraints of Section 2.5.3 could never hold), a fixed value outside
- * its domain.  On success *net_id receives the network's handle. */
+ * its domain.  On success *net_id receives the network's handle.
+ * Shapes the kernels cover (calls that need the device -- rn_init_chains,
+ * rn_evaluate, rn_anneal -- return RN_EUNSUPPORTED otherwise):
+ *   N <= 512, in-degree <= 16: a warp per chain (register tables up to 128
+ *     nodes, shared-memory tables above);
+ *   N <= 4096, in-degree <= 64: a block of 256 threads per chain, provided the
+ *     chain's tables and node state fit one block's shared memory (227 KiB:
+ *     about 4 KiB per 256 edges of the padded in-degree profile plus 52 bytes
+ *     per node, e.g. 2000 nodes at mean in-degree 6, or about 2900 nodes at
+ *     in-degree 2). */
 int rn_load_network(rn_ctx *ctx, int32_t n_nodes, int32_t n_edges, const int32_t *src,
                     const int32_t *dst, const uint8_t *fast, const uint8_t *frozen,
                     const int8_t *frozen_val, int32_t *net_id);
@@ -186,10 +195,12 @@ int rn_set_chain_state(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed
 /* Number of kernels this context has launched since rn_create. */
 int rn_launch_count(rn_ctx *ctx, int64_t *count);
 
-/* Batched annealing.  When two or more networks of a context have chains (and
- * the schedule has no global_sync), rn_anneal advances all of them in one
- * persistent launch over every chain; results are bit-identical to annealing
- * each network alone.  The first batched call tunes the launch on the real
+/* Batched annealing.  When two or more networks of a context have chains, a
+ * warp per chain and at least two conditions (and the schedule has no
+ * global_sync), rn_anneal advances all of them in one persistent launch over
+ * every chain; the other networks with chains (one condition, or above 512
+ * nodes) get their own launches in the same call.  Results are bit-identical
+ * to annealing each network alone.  The first batched call tunes the launch on the real
  * batch (table path per network -- register tables or shared-memory tables --
  * and warps per block), timing each candidate for a few steps from the current
  * state, which is restored afterwards.  With the threshold tables cached by
