@@ -101,9 +101,10 @@ const char *rn_last_error(const rn_ctx *ctx);
  *     nodes, shared-memory tables above);
  *   N <= 4096, in-degree <= 64: a block of 256 threads per chain, provided the
  *     chain's tables and node state fit one block's shared memory (227 KiB:
- *     about 4 KiB per 256 edges of the padded in-degree profile plus 52 bytes
- *     per node, e.g. 2000 nodes at mean in-degree 6, or about 2900 nodes at
- *     in-degree 2). */
+ *     52 bytes per node plus 1 KiB per table row, where nodes ranked by
+ *     in-degree fill slots of 256 and each slot has as many rows as its
+ *     largest in-degree rounded up to 4; e.g. 2000 nodes at mean in-degree 6,
+ *     or about 2900 nodes at in-degree 2). */
 int rn_load_network(rn_ctx *ctx, int32_t n_nodes, int32_t n_edges, const int32_t *src,
                     const int32_t *dst, const uint8_t *fast, const uint8_t *frozen,
                     const int8_t *frozen_val, int32_t *net_id);
