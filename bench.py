@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-ttt", action="store_true",
                     help="skip the time-to-target comparison (screened vs plain annealing)")
     ap.add_argument("--ttt-seeds", type=int, default=3)
+    ap.add_argument("--no-early-reject", action="store_true",
+                    help="skip the exact-early-rejection measurement late in the schedule")
     ap.add_argument("--screened", action="store_true",
                     help="time screened steps (K = 32 candidates ranked by a seeded one-hot "
                          "MLP, top 2 simulated exactly) instead of plain sweeps; value counts "
@@ -379,6 +381,9 @@ def run_ours(args, rank, world, local_rank):
         line["e2e"] = e2e(args, R, ws, local_rank, stream)
     if rank == 0 and not args.no_ttt and world == 1 and not args.screened:
         line["time_to_target"] = time_to_target(args, R, local_rank, stream)
+    if (rank == 0 and not args.no_early_reject and world == 1 and not args.screened and
+            len(ws) == 1):
+        line["early_reject"] = early_reject_gain(args, R, ws[0], local_rank, stream)
     R.rn_destroy(ctx)
     if rank == 0 and not args.no_cpu_baseline and world == 1 and len(ws) == 1:
         line["cpu_baseline"] = oracle_rate(args.workload, args.cpu_seconds)
@@ -436,6 +441,53 @@ def screen_for(R, ctx, nid, w, seed=13, h=512, capacity=1):
         b2=np.zeros(h, np.float32),
         w3=(rng.standard_normal(h) / np.sqrt(h)).astype(np.float32), b3=0.0))
     return mid
+
+
+def early_reject_gain(args, R, w, device, stream, g_late=60000):
+    """Proposals decided per second with and without exact early rejection,
+    late in the schedule (from step g_late, where most uphill candidates are
+    rejected), same chains and steps; the chain states must come out
+    identical."""
+    import torch
+    S = args.sweeps_per_step
+    ctx = R.rn_create(device, stream.cuda_stream)
+    nid, _ = setup_problem(R, ctx, w)
+    R.rn_init_chains(ctx, nid, w.n_chains, w.chain_seed)
+    full = R.schedule(w.T0, w.alpha)
+    R.rn_prepare_schedule(ctx, full, g_late + 4 * S)
+    R.rn_anneal(ctx, full, g_late)
+    st0 = R.rn_get_chain_state(ctx, nid, w.n_chains)
+    out = {}
+    states = []
+    for early in (False, True):
+        R.rn_set_chain_state(ctx, nid, w.chain_seed, st0)
+        sched = R.schedule(w.T0, w.alpha, early_reject=early)
+        R.rn_anneal(ctx, sched, S)                     # warm-up (same steps for both)
+        R.rn_set_chain_state(ctx, nid, w.chain_seed, st0)
+        R.rn_synchronize(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R.rn_anneal(ctx, sched, S)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = R.rn_get_chain_state(ctx, nid, w.n_chains)
+        states.append(st)
+        dec = w.n_chains * S - int((st["counters"][:, 2] - st0["counters"][:, 2]).sum())
+        acc = int((st["counters"][:, 0] - st0["counters"][:, 0]).sum())
+        ms = e0.elapsed_time(e1)
+        out["on" if early else "off"] = {"decisions_per_s": dec / (ms / 1000.0), "ms": ms,
+                                         "accept_frac": acc / max(dec, 1)}
+    R.rn_destroy(ctx)
+    same = all(np.array_equal(states[0][k], states[1][k])
+               for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"))
+    T = w.T0 * w.alpha ** g_late
+    out.update({"workload": w.name, "from_step": g_late, "sweeps": S, "temperature": T,
+                "speedup": out["on"]["decisions_per_s"] / out["off"]["decisions_per_s"],
+                "identical_chains": bool(same),
+                "note": "decisions = proposals decided (null moves excluded); with early "
+                        "rejection a rejected candidate is simulated only until its partial "
+                        "score exceeds the acceptance limit"})
+    return out
 
 
 def time_to_target(args, R, device, stream, name="mtb_63n_178e"):

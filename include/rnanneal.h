@@ -70,6 +70,15 @@ typedef struct {
     int64_t iters_per_level;
     int32_t reset_to_best;
     int32_t global_sync;
+    /* Exact early rejection (an addition to Table 1, off when 0): the
+     * acceptance word r is drawn before the simulation, so the largest
+     * acceptable dE is known up front (the thresholds do not increase with dE);
+     * a candidate's simulation stops once its partial score, which never
+     * decreases, exceeds delta_cur plus that dE.  Such a candidate would be
+     * rejected anyway: chains, scores and counters are bit-identical to the
+     * full simulation.  Networks above 512 nodes simulate in full. */
+    int32_t early_reject;
+    int32_t reserved;   /* 0 */
 } rn_schedule;
 
 /* Create a context on CUDA device `device`.  `stream` is a cudaStream_t the

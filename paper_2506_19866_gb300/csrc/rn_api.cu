@@ -630,6 +630,7 @@ int anneal_batched(rn_ctx *ctx, const rn_schedule &s, int64_t sweeps)
     if ((rc = thresholds_for(ctx, s, lmin, lmax, cap, sc, cached))) return rc;
     sc.iters = iters;
     sc.reset_to_best = s.reset_to_best;
+    sc.early_reject = s.early_reject;
     sc.queue = ctx->queue.p;
     sc.done = ctx->done.p;
     sc.err = ctx->dev_err.p;
@@ -646,7 +647,7 @@ int anneal_batched(rn_ctx *ctx, const rn_schedule &s, int64_t sweeps)
     plan_batch_chunks(B, sc);
     const DevBatch d = batch_desc(B, sweeps);
     if (cached) {
-        const bool same = B.exec && B.graph_sweeps == sweeps;
+        const bool same = B.exec && B.graph_sweeps == sweeps && B.graph_early == s.early_reject;
         if (!same) {
             B.drop_graph();
             RN_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
@@ -658,6 +659,7 @@ int anneal_batched(rn_ctx *ctx, const rn_schedule &s, int64_t sweeps)
             B.graph = g;
             RN_CUDA(ctx, cudaGraphInstantiate(&B.exec, B.graph, 0));
             B.graph_sweeps = sweeps;
+            B.graph_early = s.early_reject;
         }
         RN_CUDA(ctx, cudaGraphLaunch(B.exec, ctx->stream));
     } else {
@@ -1047,6 +1049,7 @@ int rn_anneal(rn_ctx *ctx, const rn_schedule *s, int64_t sweeps)
             sc.g1 = seg_end;
             sc.iters = iters;
             sc.reset_to_best = s->reset_to_best;
+            sc.early_reject = s->early_reject;
             RN_CUDA(ctx, ctx->done.reserve((size_t)ch.n));
             sc.queue = ctx->queue.p;
             sc.done = ctx->done.p;

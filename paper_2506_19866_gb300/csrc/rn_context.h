@@ -154,6 +154,7 @@ struct BatchState {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t graph_sweeps = -1;
+    int32_t graph_early = 0;          // early_reject flag the graph was captured with
     void drop_graph()
     {
         if (exec) cudaGraphExecDestroy(exec);

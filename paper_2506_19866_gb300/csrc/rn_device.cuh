@@ -79,6 +79,7 @@ struct DevSched {
     int64_t iters;                      // proposals per level
     int64_t level0;                     // level of thr_off[0]
     int32_t reset_to_best;
+    int32_t early_reject;               // stop simulating candidates that cannot be accepted
     int64_t chunk;                      // steps per work item
     int32_t n_chunks;
     const int32_t *thr_off;             // [levels] start of the level's table
@@ -299,7 +300,7 @@ __device__ __forceinline__ void load_obs(uint32_t (&w)[NPL], const uint32_t *ob)
 template <int NPL, int D0, int D1>
 __device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, const DevNet &net,
                                                   uint8_t *sm, uint32_t base, int lane,
-                                                  uint8_t *traj)
+                                                  uint8_t *traj, int32_t limit)
 {
     const int T = net.T;
     uint8_t *my_codes = sm + base + 2 * lane * NPL;
@@ -396,6 +397,11 @@ __device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, co
                 t += __byte_perm(w0[k], w1[k], sel01) + __byte_perm(w2[k], w3[k], sel23);
             }
             score += (t & 0xffu) + (t >> 8);
+            if (limit != INT32_MAX && (tau & 3) == 3) {
+                // exact early rejection: the partial score never decreases
+                const uint32_t tot = __reduce_add_sync(kFull, score);
+                if (tot > (uint32_t)limit) return (int32_t)tot;
+            }
             if (traj) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -420,11 +426,14 @@ __device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, co
 // step (Sections 2.1-2.2), scored against the entry tables (Section 2.3).
 // Returns y in every lane.  With traj != null, writes S to traj[C][T][N].
 // `base` is the warp's 256-byte-aligned offset of its state codes in `sm`.
+// With limit < INT32_MAX the simulation may stop early and return any value
+// above `limit` once the partial score (which never decreases) exceeds it.
 template <int NPL, int CG, int D0, int D1>
 __device__ __forceinline__ int32_t simulate(const Regs<NPL, D0, D1> &R, const DevNet &net,
-                                            uint8_t *sm, uint32_t base, int lane, uint8_t *traj)
+                                            uint8_t *sm, uint32_t base, int lane, uint8_t *traj,
+                                            int32_t limit = INT32_MAX)
 {
-    if constexpr (CG == 4) return simulate_swar4<NPL, D0, D1>(R, net, sm, base, lane, traj);
+    if constexpr (CG == 4) return simulate_swar4<NPL, D0, D1>(R, net, sm, base, lane, traj, limit);
     const int T = net.T;
     uint8_t *my_codes = sm + base + 2 * lane * NPL;
     uint32_t score = 0;
@@ -502,6 +511,11 @@ __device__ __forceinline__ int32_t simulate(const Regs<NPL, D0, D1> &R, const De
                         if (i >= 0) traj[((size_t)cc * T + tau) * net.N + i] = (uint8_t)s[k][c];
                     }
                 }
+            }
+            if (limit != INT32_MAX && (tau & 3) == 3) {
+                // exact early rejection: the partial score never decreases
+                const uint32_t tot = __reduce_add_sync(kFull, score);
+                if (tot > (uint32_t)limit) return (int32_t)tot;
             }
         }
         __syncwarp();

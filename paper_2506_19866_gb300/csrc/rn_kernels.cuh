@@ -110,9 +110,10 @@ struct RegPath {
         }
     }
 
-    __device__ int32_t simulate(const DevNet &net, int lane, uint8_t *traj)
+    __device__ int32_t simulate(const DevNet &net, int lane, uint8_t *traj,
+                                int32_t limit = INT32_MAX)
     {
-        return rn::simulate<NPL, CG, D0, D1>(R, net, sm, codes, lane, traj);
+        return rn::simulate<NPL, CG, D0, D1>(R, net, sm, codes, lane, traj, limit);
     }
 };
 
@@ -264,6 +265,21 @@ __device__ __forceinline__ void apply_counters(const DevNet &net, const int8_t *
     apply_counters_x(net, [&](int k) { return (int)xs[k]; }, out_nz, pos_in, kind, idx, cur, v);
 }
 
+// Largest dE the acceptance word r accepts at level l (Table 1: r < thr(T_l,
+// dE)); the thresholds do not increase with dE, so the accepted dE >= 1 form
+// a prefix of the level's table.  0 if r accepts no uphill move.
+__device__ __forceinline__ int32_t max_accepted_dE(const DevSched &sc, int64_t l, uint32_t r)
+{
+    const uint32_t *t = sc.thr + sc.thr_off[l];   // t[dE - 1]
+    int lo = 0, hi = sc.thr_len[l];
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (r < __ldg(t + mid - 1)) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ void warp_copy16(void *dst, const void *src, int bytes, int lane)
 {
     uint4 *d = reinterpret_cast<uint4 *>(dst);
@@ -378,13 +394,16 @@ __device__ __forceinline__ void run_chunk(Path &P, const DevNet &net, const DevC
             P.change_node(lane, owner, q - owner * net.npl, kind, v);
         }
         __syncwarp();
-        const int32_t d_cand = P.simulate(net, lane, nullptr);
+        const int64_t l = level - sc.level0;
+        // with exact early rejection the simulation may stop once the candidate
+        // cannot be accepted: above d_cur + the largest dE this draw accepts
+        const int32_t limit = sc.early_reject ? d_cur + max_accepted_dE(sc, l, r.z) : INT32_MAX;
+        const int32_t d_cand = P.simulate(net, lane, nullptr, limit);
 
         // Metropolis acceptance against the host-computed threshold table
         const int32_t dE = d_cand - d_cur;
         bool accept = dE <= 0;
         if (!accept) {
-            const int64_t l = level - sc.level0;
             if (dE <= sc.thr_len[l]) accept = r.z < __ldg(sc.thr + sc.thr_off[l] + dE - 1);
         }
         if (accept) {

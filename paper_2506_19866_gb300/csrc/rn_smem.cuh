@@ -170,7 +170,8 @@ struct SmemPath {
 
     // Simulate(x) of Table 1 (Sections 2.1-2.3), 4 conditions per group, the
     // byte-SIMD update of simulate_swar4 with its state in shared memory.
-    __device__ int32_t simulate(const DevNet &net, int lane, uint8_t *traj)
+    __device__ int32_t simulate(const DevNet &net, int lane, uint8_t *traj,
+                                int32_t limit = INT32_MAX)
     {
         const int T = net.T;
         uint16_t *code = reinterpret_cast<uint16_t *>(sm + codes);
@@ -278,6 +279,11 @@ struct SmemPath {
                     }
                 }
                 score += (t & 0xffu) + (t >> 8);
+                if (limit != INT32_MAX && (tau & 3) == 3) {
+                    // exact early rejection: the partial score never decreases
+                    const uint32_t tot = __reduce_add_sync(kFull, score);
+                    if (tot > (uint32_t)limit) return (int32_t)tot;
+                }
             }
             __syncwarp();
         }

@@ -29,7 +29,8 @@ _c_int, _c_i32, _c_i64, _c_u64, _vp = (ctypes.c_int, ctypes.c_int32, ctypes.c_in
 class rn_schedule(ctypes.Structure):
     _fields_ = [("T0", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("iters_per_level", ctypes.c_int64), ("reset_to_best", ctypes.c_int32),
-                ("global_sync", ctypes.c_int32)]
+                ("global_sync", ctypes.c_int32), ("early_reject", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 SIGNATURES = {
@@ -149,9 +150,10 @@ def rn_init_chains(ctx, net, n_chains, seed, x0=None):
     _check(ctx, load_library().rn_init_chains(ctx, int(net), int(n_chains), int(seed), _p(x0)))
 
 
-def schedule(T0, alpha, iters_per_level=1, reset_to_best=False, global_sync=False):
+def schedule(T0, alpha, iters_per_level=1, reset_to_best=False, global_sync=False,
+             early_reject=False):
     return rn_schedule(float(T0), float(alpha), int(iters_per_level), int(bool(reset_to_best)),
-                       int(bool(global_sync)))
+                       int(bool(global_sync)), int(bool(early_reject)), 0)
 
 
 def rn_anneal(ctx, sched: rn_schedule, sweeps):

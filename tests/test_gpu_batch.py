@@ -86,3 +86,24 @@ def test_batched_chain_matches_oracle():
     O.anneal(p.net, p.tc, O.Schedule(6.0, 0.99), w.chain_seed, ch, 0, 12, chain_ids=ids)
     np.testing.assert_array_equal(st["x_cur"][ids], ch.x_cur)
     np.testing.assert_array_equal(st["d_best"][ids], ch.d_best)
+
+
+def test_batched_early_reject_is_exact():
+    # the batched launch with exact early rejection: bit-identical chains
+    from paper_2506_19866_gb300 import build
+    build.build()
+    nets = _batch()
+    got = []
+    for early in (False, True):
+        ctx = R.rn_create(0)
+        try:
+            probs = [Problem(w, ctx) for w in nets]
+            for p, w in zip(probs, nets):
+                R.rn_init_chains(ctx, p.id, w.n_chains, w.chain_seed)
+            R.rn_anneal(ctx, R.schedule(0.4, 0.99, early_reject=early), 20)
+            got.append(_state_all(ctx, probs, nets))
+        finally:
+            R.rn_destroy(ctx)
+    for w, a, b in zip(nets, got[0], got[1]):
+        for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"):
+            np.testing.assert_array_equal(a[k], b[k], err_msg=f"{w.name} {k}")

@@ -258,3 +258,35 @@ def test_rejects_bad_input(ctx):
     with pytest.raises(R.RNError) as e:
         R.rn_init_chains(ctx, bn, 2, 0)
     assert e.value.code == R.RN_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("n_nodes,n_cond", [(100, 6), (40, 1), (200, 5)])
+def test_early_reject_is_exact(ctx, n_nodes, n_cond):
+    # register tables with 4 conditions per group, the single-condition scalar
+    # update, and the shared-memory tables; at a low temperature most
+    # candidates stop early, and the chains must not change at all
+    w = synth.random_network(900 + n_nodes, n_nodes, lam=4.0, cap=12, n_cond=n_cond,
+                             n_times=13, obs_frac=0.4)
+    p = Problem(w, ctx)
+    n, sweeps = 300, 40
+    runs = []
+    for early in (False, True):
+        c = R.rn_create(0)
+        try:
+            q = Problem(w, c)
+            R.rn_init_chains(c, q.id, n, 3)
+            R.rn_anneal(c, R.schedule(0.3, 0.99, early_reject=early), sweeps)
+            runs.append(R.rn_get_chain_state(c, q.id, n))
+        finally:
+            R.rn_destroy(c)
+    for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"):
+        np.testing.assert_array_equal(runs[0][k], runs[1][k], err_msg=k)
+    ids = [0, 7, 299]
+    ch = O.start_chains(p.net, p.tc, 3, n, ids)
+    O.anneal(p.net, p.tc, O.Schedule(0.3, 0.99), 3, ch, 0, sweeps, ids)
+    np.testing.assert_array_equal(runs[1]["x_cur"][ids], ch.x_cur)
+    np.testing.assert_array_equal(runs[1]["d_best"][ids], ch.d_best)
+    # the run decides many uphill candidates (rejections), the case that stops early
+    cnt = runs[1]["counters"]
+    rejected = n * sweeps - cnt[:, 0].sum() - cnt[:, 2].sum()
+    assert rejected > n * sweeps // 50
