@@ -120,6 +120,8 @@ void build_layout(Network &n)
     const int L = N <= 32 * kMaxSlots ? 32 : kBlockLanes;
     n.lanes = L;
     n.npl = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : N <= L * kMaxSlots ? (N + L - 1) / L : 0;
+    // 129 .. 256 nodes: 6 or 8 per lane, the hybrid path's compiled layouts
+    if (L == 32 && N > 128 && N <= 256) n.npl = N <= 192 ? 6 : 8;
     n.in_ptr.assign((size_t)N + 1, 0);
     n.out_ptr.assign((size_t)N + 1, 0);
     for (int32_t e = 0; e < E; ++e) {
@@ -403,7 +405,7 @@ int batch_items(rn_ctx *ctx, BatchState &B)
     int32_t big = 0;
     for (int pass = 0; pass < 2; ++pass)
         for (size_t b = 0; b < B.order.size(); ++b) {
-            if ((B.host_path[b] == 0) != (pass == 0)) continue;
+            if (batch_shared_tables(B.host_path[b]) != (pass == 0)) continue;
             const Network &n = *ctx->nets[(size_t)B.order[b]];
             for (int32_t c = 0; c < n.n_chains; ++c) {
                 item_net.push_back((int32_t)b);
@@ -431,8 +433,8 @@ int batch_region(rn_ctx *ctx, BatchState &B)
     double work_big = 0, work_all = 0;
     for (size_t b = 0; b < B.order.size(); ++b) {
         const Network &n = *ctx->nets[(size_t)B.order[b]];
-        const bool big = B.host_path[b] == 0;
-        const uint32_t r = batch_region_bytes(big, n.D, n.npl, n.pstride, n.N);
+        const bool big = batch_shared_tables(B.host_path[b]);
+        const uint32_t r = batch_region_bytes(B.host_path[b], n.D, n.npl, n.pstride, n.N);
         B.region_bytes = std::max(B.region_bytes, r);
         if (!big) B.region_small = std::max(B.region_small, r);
         const double w = (double)n.n_chains * n.C * std::max(1, n.T - 1) * (n.N + n.E);
@@ -1127,7 +1129,7 @@ int rn_batch_config(rn_ctx *ctx, int32_t info[4], double trial_ms[4])
     info[1] = on ? B.wpb : 0;
     int32_t shared = 0;
     if (on)
-        for (int32_t p : B.host_path) shared += p == 0;
+        for (int32_t p : B.host_path) shared += batch_shared_tables(p);
     info[2] = shared;
     info[3] = on && B.exec ? 1 : 0;
     if (trial_ms)

@@ -22,8 +22,11 @@
 
 namespace rn {
 
-// Register-table capacities of the batched kernel: slot 0 up to 16 in-edges,
-// the other slots up to 8; a network that needs more uses the shared-memory path.
+// Table paths of a network in the batch: 1, 2, 4 = register tables, capacities
+// slot 0 up to 16 in-edges and the other slots up to 8; 0 = the shared-memory
+// path (any layout).  The hybrid path of single-network launches (6 or 8
+// nodes per lane, rn_smemreg.cu) measured slower inside the batched kernel
+// than the shared-memory path, so the batch does not use it.
 constexpr int kBatchD0 = 16, kBatchD1 = 8;
 
 // Code region, then the per-warp copies of the item's DevNet and DevChains,
@@ -40,6 +43,41 @@ __device__ __forceinline__ void warp_copy_words(void *dst, const void *src, int 
     uint32_t *d = reinterpret_cast<uint32_t *>(dst);
     const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
     for (int k = lane; k < bytes / 4; k += 32) d[k] = __ldcg(s + k);
+}
+
+// One chunk of a chain on each table path.  Each is compiled as a function of
+// its own (not inlined into the kernel), so that the register allocation of
+// one path does not spill in the others.
+template <int NPL, int D0, int D1>
+__device__ __noinline__ void chunk_reg(const DevNet &net, const DevChains &ch, const DevSched &sc,
+                                       uint8_t *sm, uint32_t codes, uint8_t *region, int chain,
+                                       int64_t g_lo, int64_t g_hi, int32_t *flag, int done_value,
+                                       int lane)
+{
+    RegPath<NPL, 4, D0, D1> P;
+    P.sm = sm;
+    P.codes = codes;
+    int8_t *xs = reinterpret_cast<int8_t *>(region);
+    uint8_t *on = region + ch.pstride, *pi = on + round16((uint32_t)net.N);
+    run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, done_value, lane);
+}
+
+__device__ __noinline__ void chunk_smem(const DevNet &net, const DevChains &ch, const DevSched &sc,
+                                        uint8_t *sm, uint32_t codes, uint8_t *region, int chain,
+                                        int64_t g_lo, int64_t g_hi, int32_t *flag, int done_value,
+                                        int lane)
+{
+    SmemPath P;
+    P.sm = sm;
+    P.codes = codes;
+    P.npl = net.npl;
+    const uint32_t lw = smem_path_lut_words(net.D, net.npl);
+    P.lut = reinterpret_cast<uint32_t *>(region);
+    P.node = P.lut + lw;
+    uint8_t *after = reinterpret_cast<uint8_t *>(P.node + net.npl * kF_N * 32);
+    int8_t *xs = reinterpret_cast<int8_t *>(after);
+    uint8_t *on = after + ch.pstride, *pi = on + round16((uint32_t)net.N);
+    run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, done_value, lane);
 }
 
 __global__ void __launch_bounds__(128, 3) anneal_batch_kernel(DevBatch b, DevSched sc)
@@ -82,39 +120,23 @@ __global__ void __launch_bounds__(128, 3) anneal_batch_kernel(DevBatch b, DevSch
         const int64_t g_hi = min(g0 + b.sweeps, g_lo + sc.chunk);
         const int path = __ldg(b.path + nb);
         int32_t *flag = sc.done + r;
-        if (path == 1) {
-            RegPath<1, 4, kBatchD0, 1> P;
-            P.sm = sm;
-            P.codes = codes;
-            int8_t *xs = reinterpret_cast<int8_t *>(region);
-            uint8_t *on = region + ch.pstride, *pi = on + round16((uint32_t)net.N);
-            run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, cj + 1, lane);
-        } else if (path == 2) {
-            RegPath<2, 4, kBatchD0, kBatchD1> P;
-            P.sm = sm;
-            P.codes = codes;
-            int8_t *xs = reinterpret_cast<int8_t *>(region);
-            uint8_t *on = region + ch.pstride, *pi = on + round16((uint32_t)net.N);
-            run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, cj + 1, lane);
-        } else if (path == 4) {
-            RegPath<4, 4, kBatchD0, kBatchD1> P;
-            P.sm = sm;
-            P.codes = codes;
-            int8_t *xs = reinterpret_cast<int8_t *>(region);
-            uint8_t *on = region + ch.pstride, *pi = on + round16((uint32_t)net.N);
-            run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, cj + 1, lane);
-        } else {
-            SmemPath P;
-            P.sm = sm;
-            P.codes = codes;
-            P.npl = net.npl;
-            const uint32_t lw = smem_path_lut_words(net.D, net.npl);
-            P.lut = reinterpret_cast<uint32_t *>(region);
-            P.node = P.lut + lw;
-            uint8_t *after = reinterpret_cast<uint8_t *>(P.node + net.npl * kF_N * 32);
-            int8_t *xs = reinterpret_cast<int8_t *>(after);
-            uint8_t *on = after + ch.pstride, *pi = on + round16((uint32_t)net.N);
-            run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, cj + 1, lane);
+        const int dv = cj + 1;
+        switch (path) {
+        case 1:
+            chunk_reg<1, kBatchD0, 1>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv,
+                                      lane);
+            break;
+        case 2:
+            chunk_reg<2, kBatchD0, kBatchD1>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi,
+                                             flag, dv, lane);
+            break;
+        case 4:
+            chunk_reg<4, kBatchD0, kBatchD1>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi,
+                                             flag, dv, lane);
+            break;
+        default:
+            chunk_smem(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv, lane);
+            break;
         }
     }
 }
@@ -133,9 +155,9 @@ bool batch_path_fits(int npl, int D0, int Drest)
     return npl == 1 || Drest <= kBatchD1;
 }
 
-uint32_t batch_region_bytes(bool smem_path, const int *D, int npl, int pstride, int N)
+uint32_t batch_region_bytes(int path, const int *D, int npl, int pstride, int N)
 {
-    return warp_region(smem_path, D, npl, pstride, N).bytes;
+    return warp_region(path == 0, D, npl, pstride, N).bytes;
 }
 
 size_t batch_smem_bytes(int wpb, int large, uint32_t region_big, uint32_t region_small)

@@ -248,9 +248,18 @@ __device__ __forceinline__ void store_codes(uint8_t *p, const uint32_t (&code)[N
         *reinterpret_cast<uint16_t *>(p) = (uint16_t)code[0];
     } else if constexpr (NPL == 2) {
         *reinterpret_cast<uint32_t *>(p) = code[0] | (code[1] << 16);
-    } else {
+    } else if constexpr (NPL == 4) {
         *reinterpret_cast<uint2 *>(p) = make_uint2(code[0] | (code[1] << 16),
                                                    code[2] | (code[3] << 16));
+    } else if constexpr (NPL == 8) {
+        *reinterpret_cast<uint4 *>(p) =
+            make_uint4(code[0] | (code[1] << 16), code[2] | (code[3] << 16),
+                       code[4] | (code[5] << 16), code[6] | (code[7] << 16));
+    } else {
+        static_assert(NPL % 2 == 0, "codes are stored in pairs");
+#pragma unroll
+        for (int k = 0; k < NPL; k += 2)
+            reinterpret_cast<uint32_t *>(p)[k / 2] = code[k] | (code[k + 1] << 16);
     }
 }
 
@@ -272,9 +281,18 @@ __device__ __forceinline__ void load_codes(uint32_t (&code)[NPL], const uint16_t
 template <int NPL>
 __device__ __forceinline__ void load_obs(uint32_t (&w)[NPL], const uint32_t *ob)
 {
-    if constexpr (NPL == 4) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(ob));
-        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    if constexpr (NPL % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < NPL; k += 4) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(ob + k));
+            w[k] = v.x; w[k + 1] = v.y; w[k + 2] = v.z; w[k + 3] = v.w;
+        }
+    } else if constexpr (NPL % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < NPL; k += 2) {
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(ob + k));
+            w[k] = v.x; w[k + 1] = v.y;
+        }
     } else if constexpr (NPL == 2) {
         const uint2 v = __ldg(reinterpret_cast<const uint2 *>(ob));
         w[0] = v.x; w[1] = v.y;
@@ -297,23 +315,37 @@ __device__ __forceinline__ void load_obs(uint32_t (&w)[NPL], const uint32_t *ob)
 //   condition move to tgt (d = 2) or one level toward it (d = 1).
 // Byte values stay within their byte: a in [64, 192] for D <= 16, counters
 // below 128 for T <= 128, priorities below 2^15.
-template <int NPL, int D0, int D1>
-__device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, const DevNet &net,
-                                                  uint8_t *sm, uint32_t base, int lane,
-                                                  uint8_t *traj, int32_t limit)
+// 16-bit state code of a node's four conditions: nibble c = s_c for the
+// register-table words, 4 - s_c for the shared-memory words (rn_smem.cuh).
+template <bool SMEM_FMT>
+__device__ __forceinline__ uint32_t state_code(uint32_t s4)
+{
+    const uint32_t v = SMEM_FMT ? 4u * kB1 - s4 : s4;
+    return prmt(v | (v >> 4), 0u, 0x4420u);
+}
+
+// The byte-SIMD simulation, shared by the register-table and the
+// shared-memory-table instances; `gather(k)` returns slot k's biased image
+// bytes (128 + K per condition) from the instance's table words.
+template <int NPL, bool SMEM_FMT, bool EARLY, class Gather>
+__device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
+                                                       const int32_t (&m1)[NPL],
+                                                       const int32_t (&d2)[NPL],
+                                                       const DevNet &net, uint8_t *sm,
+                                                       uint32_t base, int lane, uint8_t *traj,
+                                                       int32_t limit, Gather gather)
 {
     const int T = net.T;
     uint8_t *my_codes = sm + base + 2 * lane * NPL;
     uint32_t U2[NPL], CM[NPL];
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
-        U2[k] = (uint32_t)R.u[k] * 0x00010001u;
-        CM[k] = (uint32_t)(128 - R.m1[k]) * kB1;
+        U2[k] = (uint32_t)u[k] * 0x00010001u;
+        CM[k] = (uint32_t)(128 - m1[k]) * kB1;
     }
     uint32_t score = 0;
     for (int g = 0; g < net.G; ++g) {
         uint32_t code[NPL], s4[NPL], cu[NPL], cd[NPL], ua01[NPL], ua23[NPL], mov[NPL];
-        load_codes<NPL>(code, net.init_code + (size_t)g * 32 * NPL + lane * NPL);
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
             const size_t q = (size_t)g * 32 * NPL + lane * NPL + k;
@@ -323,20 +355,15 @@ __device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, co
             cd[k] = 0;
             ua01[k] = U2[k];
             ua23[k] = U2[k];
+            code[k] = state_code<SMEM_FMT>(s4[k]);
         }
         store_codes<NPL>(my_codes, code);
         const int ncg = min(net.C - 4 * g, 4);
         for (int tau = 0; tau < T; ++tau) {
             if (tau > 0) {
                 uint32_t acc[NPL];
-                acc[0] = image<D0>(R.lut0, net.D[0], base, sm,
-                                   kH - 0x04040404u * groups4(net.D[0]));
-                if constexpr (NPL > 1) {
 #pragma unroll
-                    for (int k = 1; k < NPL; ++k)
-                        acc[k] = image<D1>(R.lutr[k - 1], net.D[k], base, sm,
-                                           kH - 0x04040404u * groups4(net.D[k]));
-                }
+                for (int k = 0; k < NPL; ++k) acc[k] = gather(k);
                 uint32_t sn[NPL], pr01[NPL], pr23[NPL], elm[NPL];
                 uint32_t m01 = 0, m23 = 0;
 #pragma unroll
@@ -350,7 +377,7 @@ __device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, co
                     cd[k] = (cd[k] + kB1) & prmt(dn, 0u, 0xBA98u);
                     const uint32_t el = ((cu[k] + CM[k]) | (cd[k] + CM[k])) & mov[k];
                     elm[k] = prmt(el, 0u, 0xBA98u);
-                    sn[k] = R.d2[k] ? tgt : s4[k] + (up >> 7) - (dn >> 7);
+                    sn[k] = d2[k] ? tgt : s4[k] + (up >> 7) - (dn >> 7);
                     pr01[k] = ua01[k] & prmt(el, 0u, 0x9988u);
                     pr23[k] = ua23[k] & prmt(el, 0u, 0xBBAAu);
                     m01 = max_u16x2(m01, pr01[k]);
@@ -372,8 +399,7 @@ __device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, co
                     const uint32_t u01 = prmt(upd, 0u, 0x9988u), u23 = prmt(upd, 0u, 0xBBAAu);
                     ua01[k] = ((ua01[k] + U2[k]) & ~u01) | (U2[k] & u01);
                     ua23[k] = ((ua23[k] + U2[k]) & ~u23) | (U2[k] & u23);
-                    const uint32_t x = s4[k] | (s4[k] >> 4);
-                    code[k] = prmt(x, 0u, 0x4420u);
+                    code[k] = state_code<SMEM_FMT>(s4[k]);
                 }
                 store_codes<NPL>(my_codes, code);
             }
@@ -392,12 +418,21 @@ __device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, co
             uint32_t t = 0;
 #pragma unroll
             for (int k = 0; k < NPL; ++k) {
-                const uint32_t sel01 = (code[k] & 0xffu) + 0x3340u;
-                const uint32_t sel23 = (code[k] >> 8) + 0x3340u;
+                // selector bytes: nibble c = s_c of conditions 0-1 and 2-3 (the
+                // register-format state code is exactly that)
+                uint32_t sel01, sel23;
+                if constexpr (SMEM_FMT) {
+                    const uint32_t x = s4[k] | (s4[k] >> 4);
+                    sel01 = (x & 0xffu) + 0x3340u;
+                    sel23 = ((x >> 16) & 0xffu) + 0x3340u;
+                } else {
+                    sel01 = (code[k] & 0xffu) + 0x3340u;
+                    sel23 = (code[k] >> 8) + 0x3340u;
+                }
                 t += __byte_perm(w0[k], w1[k], sel01) + __byte_perm(w2[k], w3[k], sel23);
             }
             score += (t & 0xffu) + (t >> 8);
-            if (limit != INT32_MAX && (tau & 3) == 3) {
+            if (EARLY && (tau & 3) == 3) {
                 // exact early rejection: the partial score never decreases
                 const uint32_t tot = __reduce_add_sync(kFull, score);
                 if (tot > (uint32_t)limit) return (int32_t)tot;
@@ -422,18 +457,37 @@ __device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, co
     return (int32_t)__reduce_add_sync(kFull, score);
 }
 
-// Simulate(x) of Table 1 for the warp's vector: every condition, every time
-// step (Sections 2.1-2.2), scored against the entry tables (Section 2.3).
-// Returns y in every lane.  With traj != null, writes S to traj[C][T][N].
-// `base` is the warp's 256-byte-aligned offset of its state codes in `sm`.
-// With limit < INT32_MAX the simulation may stop early and return any value
-// above `limit` once the partial score (which never decreases) exceeds it.
-template <int NPL, int CG, int D0, int D1>
-__device__ __forceinline__ int32_t simulate(const Regs<NPL, D0, D1> &R, const DevNet &net,
-                                            uint8_t *sm, uint32_t base, int lane, uint8_t *traj,
-                                            int32_t limit = INT32_MAX)
+// The register-table instance: table words in registers (rn_device.cuh format,
+// state-code nibble s), gathered in groups of 4 per slot.
+template <int NPL, int D0, int D1>
+__device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, const DevNet &net,
+                                                  uint8_t *sm, uint32_t base, int lane,
+                                                  uint8_t *traj, int32_t limit)
 {
-    if constexpr (CG == 4) return simulate_swar4<NPL, D0, D1>(R, net, sm, base, lane, traj, limit);
+    auto gather = [&](int k) -> uint32_t {
+        if (k == 0)
+            return image<D0>(R.lut0, net.D[0], base, sm, kH - 0x04040404u * groups4(net.D[0]));
+        if constexpr (NPL > 1)
+            return image<D1>(R.lutr[k - 1], net.D[k], base, sm,
+                             kH - 0x04040404u * groups4(net.D[k]));
+        return 0u;
+    };
+    // the early-rejection check lives only in the instance that needs it
+    if (limit == INT32_MAX)
+        return simulate_swar4_core<NPL, false, false>(R.u, R.m1, R.d2, net, sm, base, lane, traj,
+                                                      limit, gather);
+    return simulate_swar4_core<NPL, false, true>(R.u, R.m1, R.d2, net, sm, base, lane, traj,
+                                                 limit, gather);
+}
+
+// The scalar update (groups of CG conditions, one integer per node and
+// condition), used when a network has a single condition.  EARLY compiles the
+// early-rejection check against `limit`.
+template <int NPL, int CG, int D0, int D1, bool EARLY>
+__device__ __forceinline__ int32_t simulate_scalar(const Regs<NPL, D0, D1> &R, const DevNet &net,
+                                                   uint8_t *sm, uint32_t base, int lane,
+                                                   uint8_t *traj, int32_t limit)
+{
     const int T = net.T;
     uint8_t *my_codes = sm + base + 2 * lane * NPL;
     uint32_t score = 0;
@@ -512,7 +566,7 @@ __device__ __forceinline__ int32_t simulate(const Regs<NPL, D0, D1> &R, const De
                     }
                 }
             }
-            if (limit != INT32_MAX && (tau & 3) == 3) {
+            if (EARLY && (tau & 3) == 3) {
                 // exact early rejection: the partial score never decreases
                 const uint32_t tot = __reduce_add_sync(kFull, score);
                 if (tot > (uint32_t)limit) return (int32_t)tot;
@@ -521,6 +575,23 @@ __device__ __forceinline__ int32_t simulate(const Regs<NPL, D0, D1> &R, const De
         __syncwarp();
     }
     return (int32_t)__reduce_add_sync(kFull, score);
+}
+
+// Simulate(x) of Table 1 for the warp's vector: every condition, every time
+// step (Sections 2.1-2.2), scored against the entry tables (Section 2.3).
+// Returns y in every lane.  With traj != null, writes S to traj[C][T][N].
+// `base` is the warp's 256-byte-aligned offset of its state codes in `sm`.
+// With limit < INT32_MAX the simulation may stop early and return any value
+// above `limit` once the partial score (which never decreases) exceeds it.
+template <int NPL, int CG, int D0, int D1>
+__device__ __forceinline__ int32_t simulate(const Regs<NPL, D0, D1> &R, const DevNet &net,
+                                            uint8_t *sm, uint32_t base, int lane, uint8_t *traj,
+                                            int32_t limit = INT32_MAX)
+{
+    if constexpr (CG == 4) return simulate_swar4<NPL, D0, D1>(R, net, sm, base, lane, traj, limit);
+    if (limit == INT32_MAX)
+        return simulate_scalar<NPL, CG, D0, D1, false>(R, net, sm, base, lane, traj, limit);
+    return simulate_scalar<NPL, CG, D0, D1, true>(R, net, sm, base, lane, traj, limit);
 }
 
 }  // namespace rn

@@ -178,6 +178,8 @@ cudaError_t launch_evaluate(const DevNet &net, const int8_t *X, int64_t xstride,
                                                       sm_count, st);
     int grid = (n + 3) / 4;
     if (grid > sm_count * 16) grid = sm_count * 16;
+    if (smemreg_layout(net.npl))
+        return launch_evaluate_smemreg(net, X, xstride, n, score, score2, traj, grid, st);
     if (net.npl > kRegSlots) {
         const WarpRegion R = warp_region(true, net.D, net.npl, 0, 0);
         const size_t smem = 4 * ((size_t)kCodeBytesPerWarp + R.bytes);
@@ -254,6 +256,7 @@ cudaError_t launch_anneal(const DevNet &net, int d0, int d1, const DevChains &ch
                           const DevSched &sc, int sm_count, cudaStream_t st)
 {
     if (ch.n <= 0 || sc.g1 <= sc.g0) return cudaSuccess;
+    if (smemreg_layout(net.npl)) return launch_anneal_smemreg(net, ch, sc, sm_count, st);
     if (net.npl > kRegSlots) return launch_anneal_smem(net, ch, sc, sm_count, st);
     switch (net.npl) {
     case 1: return launch_anneal_npl1(net, d0, d1, ch, sc, sm_count, st);

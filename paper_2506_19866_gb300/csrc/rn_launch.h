@@ -35,6 +35,15 @@ cudaError_t launch_anneal(const DevNet &net, int d0, int d1, const DevChains &ch
                           const DevSched &sc, int sm_count, cudaStream_t st);
 cudaError_t launch_init(const DevNet &net, const DevChains &ch, int32_t *status, cudaStream_t st);
 
+// Hybrid path (rn_smemreg.cu): 6 or 8 nodes per lane, table words in shared
+// memory, node state in registers.
+bool smemreg_layout(int npl);
+cudaError_t launch_anneal_smemreg(const DevNet &net, const DevChains &ch, const DevSched &sc,
+                                  int sm_count, cudaStream_t st);
+cudaError_t launch_evaluate_smemreg(const DevNet &net, const int8_t *X, int64_t xstride,
+                                    int32_t n, int32_t *score, int32_t *score2, uint8_t *traj,
+                                    int grid, cudaStream_t st);
+
 // Block path (rn_block.cu): networks of 513 .. 4096 nodes, a block of
 // kBlockLanes threads per chain.  Shared memory of one block:
 size_t block_path_smem_bytes(const int *D, int npl, int N);
@@ -62,7 +71,9 @@ struct DevBatch {
 };
 
 bool batch_path_fits(int npl, int D0, int Drest);
-uint32_t batch_region_bytes(bool smem_path, const int *D, int npl, int pstride, int N);
+// Shared-table networks (path 0) run on the large-region warps.
+inline bool batch_shared_tables(int path) { return path == 0; }
+uint32_t batch_region_bytes(int path, const int *D, int npl, int pstride, int N);
 // Block shared memory of a configuration, and the resident grid it allows.
 size_t batch_smem_bytes(int wpb, int large, uint32_t region_big, uint32_t region_small);
 cudaError_t batch_resident_warps(int wpb, size_t smem, int sm_count, int *grid);

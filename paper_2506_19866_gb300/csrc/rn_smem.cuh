@@ -173,6 +173,15 @@ struct SmemPath {
     __device__ int32_t simulate(const DevNet &net, int lane, uint8_t *traj,
                                 int32_t limit = INT32_MAX)
     {
+        // the early-rejection check lives only in the instance that needs it
+        return limit == INT32_MAX ? simulate_t<false>(net, lane, traj, limit)
+                                  : simulate_t<true>(net, lane, traj, limit);
+    }
+
+    template <bool EARLY>
+    __device__ __forceinline__ int32_t simulate_t(const DevNet &net, int lane, uint8_t *traj,
+                                                  int32_t limit)
+    {
         const int T = net.T;
         uint16_t *code = reinterpret_cast<uint16_t *>(sm + codes);
         uint32_t score = 0;
@@ -279,7 +288,7 @@ struct SmemPath {
                     }
                 }
                 score += (t & 0xffu) + (t >> 8);
-                if (limit != INT32_MAX && (tau & 3) == 3) {
+                if (EARLY && (tau & 3) == 3) {
                     // exact early rejection: the partial score never decreases
                     const uint32_t tot = __reduce_add_sync(kFull, score);
                     if (tot > (uint32_t)limit) return (int32_t)tot;
@@ -288,6 +297,137 @@ struct SmemPath {
             __syncwarp();
         }
         return (int32_t)__reduce_add_sync(kFull, score);
+    }
+};
+
+// Hybrid path for 6 or 8 nodes per lane (129 .. 256 nodes): the table words of
+// the shared-memory path (16-bit code address, code nibble 4 - s) stay in the
+// warp's shared memory, gathered in groups of 4 rows, while the per-node
+// byte-SIMD update state lives in registers (the simulation of rn_device.cuh,
+// simulate_swar4_core), so that only the gather touches shared memory.
+constexpr int kSmemRegSlots[2] = {6, 8};
+
+__host__ __device__ inline uint32_t smem_reg_warp_bytes(uint32_t lut_words, int pstride, int N)
+{
+    const uint32_t cnt = 2u * (((uint32_t)N + 15u) & ~15u);
+    return lut_words * 4u + (uint32_t)pstride + cnt;
+}
+
+template <int NPL>
+struct SmemRegPath {
+    uint8_t *sm;         // dynamic shared memory of the block
+    uint32_t codes;      // offset of this warp's code array in sm
+    uint32_t *lut;       // [sum groups4(D_k)][32]
+    int32_t u[NPL], m1[NPL], d2[NPL];
+    uint32_t undo_addr, undo_val;
+    int undo_kind, undo_slot;
+
+    __device__ __forceinline__ int lut_row(const DevNet &net, int k, int d) const
+    {
+        int o = 0;
+        for (int kk = 0; kk < k; ++kk) o += groups4(net.D[kk]);
+        return o + d;
+    }
+
+    __device__ void load(const DevNet &net, const int8_t *x, int lane)
+    {
+        const int E = net.E, N = net.N;
+        const uint32_t pad = codes + 4u * (uint32_t)lane;   // the code of node 2 lane
+        int o = 0;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            for (int d = 0; d < net.D[k]; ++d) {
+                const int e = net.edge_id[(k * net.dtab + d) * 32 + lane];
+                uint32_t w;
+                if (e >= 0)
+                    w = edge_word_s(x[e], x[E + e], x[2 * E + e],
+                                    codes + 2u * (uint32_t)net.node_q[net.src[e]]);
+                else
+                    w = 0x04040000u | ((codes + (uint32_t)(-1 - e)) & 0xffffu);
+                lut[(o + d) * 32 + lane] = w;
+            }
+            for (int d = net.D[k]; d < groups4(net.D[k]); ++d)
+                lut[(o + d) * 32 + lane] = 0x04040000u | (pad & 0xffffu);
+            o += groups4(net.D[k]);
+            const int i = net.q_node[lane * NPL + k];
+            u[k] = i >= 0 ? x[3 * E + i] : 1;
+            m1[k] = i >= 0 ? x[3 * E + N + i] + 1 : 1;
+            d2[k] = i >= 0 ? x[3 * E + 2 * N + i] == 2 : 0;
+        }
+    }
+
+    __device__ void change_edge(const DevNet &net, int lane, int owner, int pos, int w, int p,
+                                int t, int)
+    {
+        if (lane != owner) return;
+        const uint32_t a = (uint32_t)(lut_row(net, (pos >> 8) & 0xff, pos & 0xff) * 32 + lane);
+        undo_kind = 0;
+        undo_addr = a;
+        undo_val = lut[a];
+        lut[a] = edge_word_s(w, p, t, undo_val);
+    }
+
+    __device__ void change_node(int lane, int owner, int slot, int kind, int v)
+    {
+        if (lane != owner) return;
+        undo_kind = kind;
+        undo_slot = slot;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            if (k != slot) continue;
+            if (kind == 3) { undo_val = (uint32_t)u[k]; u[k] = v; }
+            else if (kind == 4) { undo_val = (uint32_t)m1[k]; m1[k] = v + 1; }
+            else { undo_val = (uint32_t)d2[k]; d2[k] = v == 2; }
+        }
+    }
+
+    __device__ void undo(int lane, int owner)
+    {
+        if (lane != owner) return;
+        if (undo_kind == 0) {
+            lut[undo_addr] = undo_val;
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            if (k != undo_slot) continue;
+            if (undo_kind == 3) u[k] = (int32_t)undo_val;
+            else if (undo_kind == 4) m1[k] = (int32_t)undo_val;
+            else d2[k] = (int32_t)undo_val;
+        }
+    }
+
+    __device__ int32_t simulate(const DevNet &net, int lane, uint8_t *traj,
+                                int32_t limit = INT32_MAX)
+    {
+        int row0[NPL];
+        int o = 0;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            row0[k] = o;
+            o += groups4(net.D[k]);
+        }
+        auto gather = [&](int k) -> uint32_t {
+            const int D4 = groups4(net.D[k]);
+            uint32_t acc = kH - 0x04040404u * (uint32_t)D4;
+            const uint32_t *lw = lut + row0[k] * 32 + lane;
+            for (int d = 0; d < D4; d += 4) {
+                uint32_t w[4], c[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) w[i] = lw[(d + i) * 32];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
+            }
+            return acc;
+        };
+        if (limit == INT32_MAX)
+            return simulate_swar4_core<NPL, true, false>(u, m1, d2, net, sm, codes, lane, traj,
+                                                         limit, gather);
+        return simulate_swar4_core<NPL, true, true>(u, m1, d2, net, sm, codes, lane, traj, limit,
+                                                    gather);
     }
 };
 
