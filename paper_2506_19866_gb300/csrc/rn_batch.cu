@@ -59,7 +59,8 @@ __device__ __noinline__ void chunk_reg(const DevNet &net, const DevChains &ch, c
     P.codes = codes;
     int8_t *xs = reinterpret_cast<int8_t *>(region);
     uint8_t *on = region + ch.pstride, *pi = on + round16((uint32_t)net.N);
-    run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, done_value, lane);
+    run_chunk<decltype(P), false>(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, done_value,
+                                  lane);
 }
 
 __device__ __noinline__ void chunk_smem(const DevNet &net, const DevChains &ch, const DevSched &sc,
@@ -77,7 +78,8 @@ __device__ __noinline__ void chunk_smem(const DevNet &net, const DevChains &ch, 
     uint8_t *after = reinterpret_cast<uint8_t *>(P.node + net.npl * kF_N * 32);
     int8_t *xs = reinterpret_cast<int8_t *>(after);
     uint8_t *on = after + ch.pstride, *pi = on + round16((uint32_t)net.N);
-    run_chunk(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, done_value, lane);
+    run_chunk<decltype(P), false>(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, done_value,
+                                  lane);
 }
 
 __global__ void __launch_bounds__(128, 3) anneal_batch_kernel(DevBatch b, DevSched sc)

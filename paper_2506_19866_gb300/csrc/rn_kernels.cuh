@@ -333,7 +333,9 @@ __device__ __forceinline__ bool wait_for_chunk(const int32_t *done, int need, in
 
 // Steps [g_lo, g_hi) of one chain (Table 1 inner loop), its state in and out
 // of global memory through L2, then the chain's chunk counter is published.
-template <typename Path>
+// EARLY_OK compiles exact early rejection in; the batched kernel leaves it out
+// (one simulation instance per table path keeps that kernel's code small).
+template <typename Path, bool EARLY_OK = true>
 __device__ __forceinline__ void run_chunk(Path &P, const DevNet &net, const DevChains &ch,
                                           const DevSched &sc, int chain, int64_t g_lo,
                                           int64_t g_hi, int8_t *xs, uint8_t *out_nz,
@@ -397,7 +399,8 @@ __device__ __forceinline__ void run_chunk(Path &P, const DevNet &net, const DevC
         const int64_t l = level - sc.level0;
         // with exact early rejection the simulation may stop once the candidate
         // cannot be accepted: above d_cur + the largest dE this draw accepts
-        const int32_t limit = sc.early_reject ? d_cur + max_accepted_dE(sc, l, r.z) : INT32_MAX;
+        const int32_t limit =
+            EARLY_OK && sc.early_reject ? d_cur + max_accepted_dE(sc, l, r.z) : INT32_MAX;
         const int32_t d_cand = P.simulate(net, lane, nullptr, limit);
 
         // Metropolis acceptance against the host-computed threshold table
