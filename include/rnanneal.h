@@ -76,7 +76,8 @@ typedef struct {
      * a candidate's simulation stops once its partial score, which never
      * decreases, exceeds delta_cur plus that dE.  Such a candidate would be
      * rejected anyway: chains, scores and counters are bit-identical to the
-     * full simulation.  Networks above 512 nodes simulate in full. */
+     * full simulation.  Networks above 512 nodes and the batched launch
+     * (see rn_batch_config) simulate in full. */
     int32_t early_reject;
     int32_t reserved;   /* 0 */
 } rn_schedule;
