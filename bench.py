@@ -203,6 +203,23 @@ def oracle_rate(name, seconds, cores=None):
                       f"{wall:.1f} s wall incl. process start)"}
 
 
+def rank_seed(w, rank):
+    """Chain seed of a rank's replica: every rank anneals its own, independent
+    chains of the workload (replicas; no data exchange between ranks)."""
+    return w.chain_seed + 1000003 * rank
+
+
+def combine_ranks(evals, seconds, dist, device):
+    """Whole-job throughput inputs over the ranks: the evaluations of all ranks
+    and the slowest rank's time (barrier-bracketed steps)."""
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(evals)], dtype=torch.float64, device=device)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return int(e.item()), float(t.item())
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -274,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
     ctx = R.rn_create(local_rank, stream.cuda_stream)
     ids = [setup_problem(R, ctx, w)[0] for w in ws]
     for nid, w in zip(ids, ws):   # every rank anneals its own replica of the chains
-        R.rn_init_chains(ctx, nid, w.n_chains, w.chain_seed + 1000003 * rank)
+        R.rn_init_chains(ctx, nid, w.n_chains, rank_seed(w, rank))
     sched = R.schedule(ws[0].T0, ws[0].alpha)
     R.rn_prepare_schedule(ctx, sched, (args.warmup + args.steps) * S)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -327,11 +344,7 @@ def run_ours(args, rank, world, local_rank):
 
     t_max, evals_all = total_s, evals
     if dist is not None:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([evals], dtype=torch.float64, device="cuda")
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        t_max, evals_all = float(t.item()), int(e.item())
+        evals_all, t_max = combine_ranks(evals, total_s, dist, "cuda")
     value = evals_all / t_max
 
     # roofline of the annealing kernel, the only kernel of a step (a batch step
