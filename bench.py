@@ -509,7 +509,8 @@ def time_to_target(args, R, device, stream, name="mtb_63n_178e"):
     candidates per chain and step ranked by the one-hot MLP, the top 2 simulated
     exactly), same network, chains, schedule and seeds; median over seeds.  The
     screen is trained beforehand (offline, timed separately) on 1.02M pairs
-    logged from an independent plain run of the same network."""
+    logged from an independent plain run of the same network (another seed):
+    every chain's state every 32 sweeps over 8000 sweeps."""
     from scipy.stats import spearmanr
     w = synth.make(name)
     n_obs = int(w.observed.sum())
@@ -534,8 +535,9 @@ def time_to_target(args, R, device, stream, name="mtb_63n_178e"):
     mid = screen_for(R, ctx, nid, w, capacity=1 << 20)
     R.rn_init_chains(ctx, nid, w.n_chains, 7)
     t0 = time.perf_counter()
-    for _ in range(250):
-        R.rn_anneal(ctx, sched, 8)
+    log_sweeps, log_every = 8000, 32
+    for _ in range(log_sweeps // log_every):
+        R.rn_anneal(ctx, sched, log_every)
         pairs = R.rn_mlp_log_chains(ctx, mid)
     R.rn_synchronize(ctx)
     t_log = time.perf_counter() - t0
@@ -597,6 +599,8 @@ def time_to_target(args, R, device, stream, name="mtb_63n_178e"):
             "screen": {"K": K, "top": top, "eps": eps, "hidden": [512, 512], "onehot_width": D,
                        "dtype": "bf16 x bf16 -> fp32 (tcgen05)",
                        "train_pairs": int(pairs), "train_steps": steps, "batch": batch,
+                       "logged_from": f"plain run, chain seed 7, every {log_every} sweeps over "
+                                      f"{log_sweeps} sweeps",
                        "log_s": t_log, "train_s": t_train, "last_loss": loss,
                        "heldout_rmse": float(np.sqrt(np.mean((pred - yh) ** 2))),
                        "heldout_target_std": float(np.std(yh)),
