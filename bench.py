@@ -76,6 +76,8 @@ def workload_set(name):
     """The networks of a benchmark workload: one, or the batch of 256 uneven ones."""
     if name == "batch256":
         return synth.make_batch()
+    if name == "scaleup":
+        return synth.make_scaleup()
     return [synth.make(name)]
 
 
@@ -88,10 +90,12 @@ def workload_config(ws, sweeps_per_step, name):
                 "schedule": f"geometric T0={w.T0} alpha={w.alpha:.10f}",
                 "noise_frac": w.noise_frac, "l2": L2_NOTE}
     N = np.array([w.N for w in ws])
+    C = np.array([w.C for w in ws])
+    T = np.array([w.T for w in ws])
     return {"workload": name, "networks": len(ws),
-            "nodes": f"{N.min()}-{N.max()} (median {int(np.median(N))}, log-uniform 10-300)",
+            "nodes": f"{N.min()}-{N.max()} (median {int(np.median(N))})",
             "edges_total": int(sum(w.E for w in ws)), "params_total": int(sum(w.P for w in ws)),
-            "conditions": "2-12", "time_points": "9-33",
+            "conditions": f"{C.min()}-{C.max()}", "time_points": f"{T.min()}-{T.max()}",
             "chains": int(sum(w.n_chains for w in ws)), "chains_per_network": "proportional to P",
             "sweeps_per_step": sweeps_per_step,
             "schedule": f"geometric T0={ws[0].T0} alpha={ws[0].alpha}", "l2": L2_NOTE}
@@ -384,6 +388,8 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline, "clocks": clk, "gpu_launches": launches}
     if len(ws) > 1:
         line["batch"] = R.rn_batch_config(ctx)
+    free, total = torch.cuda.mem_get_info(local_rank)
+    line["device_memory_used_gb"] = (total - free) / 1e9
     if args.screened:
         line["config"]["step"] = ("screened: K = 32 candidates per chain ranked by a 512-512 "
                                   "one-hot MLP (tcgen05 BF16 GEMM), top 2 simulated exactly")

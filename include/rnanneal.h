@@ -109,7 +109,8 @@ const char *rn_last_error(const rn_ctx *ctx);
  * rn_evaluate, rn_anneal -- return RN_EUNSUPPORTED otherwise):
  *   N <= 512, in-degree <= 16: a warp per chain (register tables up to 128
  *     nodes, shared-memory tables above);
- *   N <= 4096, in-degree <= 64: a block of 256 threads per chain, provided the
+ *   otherwise N <= 4096, in-degree <= 64: a block of 256 threads per chain
+ *     (at least 2 nodes per thread), provided the
  *     chain's tables and node state fit one block's shared memory (227 KiB:
  *     52 bytes per node plus 1 KiB per table row, where nodes ranked by
  *     in-degree fill slots of 256 and each slot has as many rows as its

@@ -117,9 +117,18 @@ void build_layout(Network &n)
     // nodes for the shared-memory path.  Above 512 nodes a block of L = 256
     // threads holds the chain (block path), ceil(N / 256) nodes per thread, up
     // to 4096 nodes.
-    const int L = N <= 32 * kMaxSlots ? 32 : kBlockLanes;
+    // (the block path also takes networks of any size up to 4096 whose
+    // in-degree exceeds the warp paths' 16; it keeps at least 2 nodes per
+    // thread so that its padding rows can read the code of node 2 t)
+    std::vector<int32_t> indeg((size_t)N, 0);
+    for (int32_t e = 0; e < E; ++e) indeg[(size_t)n.dst[(size_t)e]]++;
+    const int32_t max_in = N ? *std::max_element(indeg.begin(), indeg.end()) : 0;
+    const int L = N <= 32 * kMaxSlots && max_in <= 16 ? 32 : kBlockLanes;
     n.lanes = L;
-    n.npl = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : N <= L * kMaxSlots ? (N + L - 1) / L : 0;
+    if (L == 32)
+        n.npl = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : (N + 31) / 32;
+    else
+        n.npl = N <= L * kMaxSlots ? std::max(2, (N + L - 1) / L) : 0;
     // 129 .. 256 nodes: 6 or 8 per lane, the hybrid path's compiled layouts
     if (L == 32 && N > 128 && N <= 256) n.npl = N <= 192 ? 6 : 8;
     n.in_ptr.assign((size_t)N + 1, 0);

@@ -1,8 +1,9 @@
-// rn_block.cu -- block-per-chain simulation for networks of 513 .. 4096 nodes.
+// rn_block.cu -- block-per-chain simulation for networks of 513 .. 4096 nodes
+// (and smaller ones whose in-degree exceeds the warp paths' 16).
 //
 // A warp no longer holds the chain: its nodes are spread over the 256 threads
 // of a block (node rank r -> slot r / 256, thread r % 256, internal index
-// q = thread * npl + slot, npl <= 16).  Everything else is the shared-memory
+// q = thread * npl + slot, 2 <= npl <= 16).  Everything else is the shared-memory
 // table path of rn_smem.cuh: table words and per-node byte-SIMD update state
 // in shared memory, laid out [..][256] so that each warp's accesses are
 // consecutive words, four conditions per group (Sections 2.1-2.3).  The
@@ -98,7 +99,7 @@ struct BlockPath {
                 lut[(o + d) * kBT + t] = w;
             }
             // neutral rows up to a whole group of 4: the code of node 2 t (one
-            // bank per lane; npl >= 3 on this path, so node 2 t exists)
+            // bank per lane; npl >= 2 on this path, so node 2 t exists)
             for (int d = net.D[k]; d < groups4(net.D[k]); ++d)
                 lut[(o + d) * kBT + t] = 0x04040000u | (4u * (uint32_t)t);
             o += groups4(net.D[k]);

@@ -242,10 +242,11 @@ WORKLOADS = ("n15_c3_t11", "n120_c8_t21", "hpg_9n_25e", "mtb_63n_178e")
 LARGE_WORKLOADS = ("n2000_c16_t33",)
 
 
-def make_batch(n_nets=256, total_chains=65536, seed=1003, n_min=10, n_max=300, max_indeg=16):
+def make_batch(n_nets=256, total_chains=65536, seed=1003, n_min=10, n_max=300, max_indeg=16,
+               lam=4.0, obs_frac=0.2):
     """Many independent networks of uneven size annealed together: node counts
-    log-uniform in [n_min, n_max], in-degree Poisson(4) (at least 1, at most
-    max_indeg), 2-12 conditions, 8-32 update steps, 20% observed entries, and
+    log-uniform in [n_min, n_max], in-degree Poisson(lam) (at least 1, at most
+    max_indeg), 2-12 conditions, 8-32 update steps, obs_frac observed entries, and
     chains per network proportional to its parameter count (total_chains in
     all, at least one each).  Returns a list of Workloads."""
     rng = np.random.default_rng(seed)
@@ -253,12 +254,12 @@ def make_batch(n_nets=256, total_chains=65536, seed=1003, n_min=10, n_max=300, m
     for b in range(n_nets):
         N = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
         cap = min(N - 1, max_indeg)
-        src, dst = random_digraph(N, np.clip(rng.poisson(4.0, size=N), 1, cap), rng)
+        src, dst = random_digraph(N, np.clip(rng.poisson(lam, size=N), 1, cap), rng)
         fast = speed_classes(N, rng)
         C = int(rng.integers(2, 13))
         T = int(rng.integers(8, 33)) + 1
         init, ko = conditions(N, C, rng)
-        obs = bernoulli_mask(C, T, N, 0.2, rng)
+        obs = bernoulli_mask(C, T, N, obs_frac, rng)
         nets.append(Workload(f"batch{b}", src, dst, fast, init, ko, obs, T,
                              planted_seed=20000 + b, noise_frac=0.0, noise_seed=30000 + b,
                              chain_seed=b, n_chains=1, sweeps=2000, T0=10.0, alpha=0.995))
@@ -270,6 +271,17 @@ def make_batch(n_nets=256, total_chains=65536, seed=1003, n_min=10, n_max=300, m
     for w, n in zip(nets, share):
         w.n_chains = int(n)
     return nets
+
+
+def make_scaleup():
+    """The scale-up set: the 2000-node, 16-condition network with its 16384
+    chains, and 63 networks of 100-1000 nodes (log-uniform, in-degree
+    Poisson(6), 10% observed, 2-12 conditions, 8-32 update steps) with 16384
+    chains in all, proportional to their parameter counts."""
+    big = make("n2000_c16_t33")
+    small = make_batch(n_nets=63, total_chains=16384, seed=1006, n_min=100, n_max=1000,
+                       max_indeg=24, lam=6.0, obs_frac=0.1)
+    return [big] + small
 
 
 def tiny(seed, n_nodes=4, indeg=2, n_cond=2, n_times=6, obs_frac=0.5):

@@ -39,12 +39,12 @@ def _compare(st, ch, ids):
 
 @pytest.mark.parametrize("n_nodes,lam,cap,n_cond,n_times", [
     (513, 4.0, 24, 3, 9), (777, 5.0, 24, 5, 7), (1300, 6.0, 24, 2, 12), (600, 20.0, 40, 2, 5),
-    (2900, 2.0, 8, 1, 4)])
+    (2900, 2.0, 8, 1, 4), (90, 24.0, 40, 3, 6)])
 def test_evaluate_block_sizes(ctx, n_nodes, lam, cap, n_cond, n_times):
-    # slot and thread boundaries of the block layout (3 .. 12 nodes per thread),
-    # one to five conditions (a partial group of 4), an in-degree above the warp
-    # paths' 16, and a network near the shared-memory limit; trajectories
-    # included
+    # slot and thread boundaries of the block layout (2 .. 12 nodes per thread),
+    # one to five conditions (a partial group of 4), in-degrees above the warp
+    # paths' 16 (also on a 90-node network, which the block path then takes),
+    # and a network near the shared-memory limit; trajectories included
     w = synth.random_network(500 + n_nodes, n_nodes, lam=lam, cap=cap, n_cond=n_cond,
                              n_times=n_times, obs_frac=0.3)
     p = Problem(w, ctx)
