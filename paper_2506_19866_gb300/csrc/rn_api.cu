@@ -115,8 +115,8 @@ void build_layout(Network &n)
     // A chain is simulated by L = 32 lanes (one warp) up to 512 nodes: 1, 2 or
     // 4 nodes per lane for the register-table kernels, ceil(N / 32) above 128
     // nodes for the shared-memory path.  Above 512 nodes a block of L = 256
-    // threads holds the chain (block path), ceil(N / 256) nodes per thread, up
-    // to 4096 nodes.
+    // threads holds the chain (block path), ceil(N / 256) nodes per thread
+    // (rounded up to an even number below 8), up to 4096 nodes.
     // (the block path also takes networks of any size up to 4096 whose
     // in-degree exceeds the warp paths' 16; it keeps at least 2 nodes per
     // thread so that its padding rows can read the code of node 2 t)
@@ -129,6 +129,9 @@ void build_layout(Network &n)
         n.npl = N <= 32 ? 1 : N <= 64 ? 2 : N <= 128 ? 4 : (N + 31) / 32;
     else
         n.npl = N <= L * kMaxSlots ? std::max(2, (N + L - 1) / L) : 0;
+    // up to 2048 nodes the block path keeps node state in registers, compiled
+    // for an even number of nodes per thread
+    if (L != 32 && n.npl > 0 && n.npl < 8) n.npl += n.npl & 1;
     // 129 .. 256 nodes: 6 or 8 per lane, the hybrid path's compiled layouts
     if (L == 32 && N > 128 && N <= 256) n.npl = N <= 192 ? 6 : 8;
     n.in_ptr.assign((size_t)N + 1, 0);

@@ -27,12 +27,19 @@ constexpr int kBW = kBT / 32;   // warps per chain
 __device__ __forceinline__ int xcg(const int8_t *x, int j) { return (int)__ldcg(x + j); }
 
 // Shared memory: codes [kBT * npl] u16 at offset 0, then the table rows, the
-// per-node fields, the constraint counters and a small scratch area.
+// per-node fields (not on the register variant), the constraint counters and a
+// small scratch area.
 struct BlockLayout {
     uint32_t codes, lut, node, cnt, scratch, bytes;
 };
 
 __host__ __device__ inline uint32_t round256(uint32_t v) { return (v + 255u) & ~255u; }
+
+// Node state in registers for these nodes per thread (at most 2048 nodes).
+__host__ __device__ inline bool block_reg_npl(int npl)
+{
+    return npl == 2 || npl == 4 || npl == 6 || npl == 8;
+}
 
 __host__ __device__ inline BlockLayout block_layout(const int *D, int npl, int N)
 {
@@ -42,7 +49,7 @@ __host__ __device__ inline BlockLayout block_layout(const int *D, int npl, int N
     L.codes = 0;
     L.lut = round256(2u * kBT * (uint32_t)npl);
     L.node = L.lut + rows * kBT * 4u;
-    L.cnt = L.node + (uint32_t)npl * kF_N * kBT * 4u;
+    L.cnt = L.node + (block_reg_npl(npl) ? 0u : (uint32_t)npl * kF_N * kBT * 4u);
     L.scratch = L.cnt + round256(2u * (((uint32_t)N + 15u) & ~15u));
     L.bytes = L.scratch + 256u;
     return L;
@@ -58,6 +65,23 @@ struct Bcast {
     int32_t j, kind, idx, cur, v;   // the candidate x_j: cur -> v (kind, index in its block)
     int32_t owner, pos, w, p, t, slot;   // owner thread and the changed table entry
 };
+
+// Constraint counters of Section 2.5.3 from x (global, through L2).
+__device__ void block_count(const DevNet &net, const int8_t *x, int t, uint8_t *out_nz,
+                            uint8_t *pos_in)
+{
+    for (int i = t; i < net.N; i += kBT) {
+        int o = 0, q = 0;
+        for (int k = net.out_ptr[i]; k < net.out_ptr[i + 1]; ++k)
+            o += xcg(x, net.out_edges[k]) != 0;
+        for (int k = net.in_ptr[i]; k < net.in_ptr[i + 1]; ++k) {
+            const int e = net.in_edges[k];
+            q += (xcg(x, e) != 0) && (xcg(x, net.E + e) == 1);
+        }
+        out_nz[i] = (uint8_t)min(o, 255);
+        pos_in[i] = (uint8_t)min(q, 255);
+    }
+}
 
 struct BlockPath {
     uint8_t *sm;
@@ -116,20 +140,9 @@ struct BlockPath {
         }
     }
 
-    // Constraint counters of Section 2.5.3 from x (global, through L2).
     __device__ void count(const DevNet &net, const int8_t *x, int t)
     {
-        for (int i = t; i < net.N; i += kBT) {
-            int o = 0, q = 0;
-            for (int k = net.out_ptr[i]; k < net.out_ptr[i + 1]; ++k)
-                o += xcg(x, net.out_edges[k]) != 0;
-            for (int k = net.in_ptr[i]; k < net.in_ptr[i + 1]; ++k) {
-                const int e = net.in_edges[k];
-                q += (xcg(x, e) != 0) && (xcg(x, net.E + e) == 1);
-            }
-            out_nz[i] = (uint8_t)min(o, 255);
-            pos_in[i] = (uint8_t)min(q, 255);
-        }
+        block_count(net, x, t, out_nz, pos_in);
     }
 
     __device__ void change_edge(const DevNet &net, int t, int owner, int pos, int w, int p, int tt)
@@ -312,13 +325,210 @@ __device__ __forceinline__ BlockPath make_block_path(const DevNet &net, uint8_t 
     return P;
 }
 
+// Block-wide reductions and barriers for simulate_swar4_core: warp redux, then
+// the eight warp values through the broadcast area.
+struct BlockSync {
+    Bcast *bc;
+    int lane, warp;
+
+    __device__ __forceinline__ void max4(uint32_t m01, uint32_t m23, uint32_t &P01,
+                                         uint32_t &P23) const
+    {
+        const uint32_t p0 = __reduce_max_sync(kFull, m01 & 0xffffu);
+        const uint32_t p1 = __reduce_max_sync(kFull, m01 >> 16);
+        const uint32_t p2 = __reduce_max_sync(kFull, m23 & 0xffffu);
+        const uint32_t p3 = __reduce_max_sync(kFull, m23 >> 16);
+        if (lane == 0)
+            *reinterpret_cast<uint4 *>(bc->wmax[warp]) = make_uint4(p0, p1, p2, p3);
+        __syncthreads();
+        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int w = 0; w < kBW; ++w) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(bc->wmax[w]);
+            q.x = max(q.x, v.x);
+            q.y = max(q.y, v.y);
+            q.z = max(q.z, v.z);
+            q.w = max(q.w, v.w);
+        }
+        P01 = prmt(q.x, q.y, 0x5410u);
+        P23 = prmt(q.z, q.w, 0x5410u);
+    }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ uint32_t sum(uint32_t v) const
+    {
+        v = __reduce_add_sync(kFull, v);
+        if (lane == 0) bc->wsum[warp] = v;
+        __syncthreads();
+        uint32_t total = 0;
+#pragma unroll
+        for (int w = 0; w < kBW; ++w) total += bc->wsum[w];
+        __syncthreads();
+        return total;
+    }
+};
+
+// Register variant for 2, 4, 6 or 8 nodes per thread (513 .. 2048 nodes, and
+// the small networks of high in-degree): the table rows stay in shared memory
+// as above, while each thread keeps its nodes' parameters and byte-SIMD update
+// state in registers (the warp paths' simulate_swar4_core, with block-wide
+// maxima), so that an update step touches shared memory only in the gather
+// and the state codes.
+template <int NPL>
+struct BlockRegPath {
+    uint8_t *sm;
+    uint32_t *lut;
+    uint8_t *out_nz, *pos_in;
+    Bcast *bc;
+    static constexpr int npl = NPL;
+    int32_t u[NPL], m1[NPL], d2[NPL];
+    uint32_t undo_addr, undo_val;
+    int undo_kind, undo_slot;
+
+    __device__ __forceinline__ int lut_row(const DevNet &net, int k, int d) const
+    {
+        int o = 0;
+        for (int kk = 0; kk < k; ++kk) o += groups4(net.D[kk]);
+        return o + d;
+    }
+
+    __device__ void load(const DevNet &net, const int8_t *x, int t, bool cg)
+    {
+        auto X = [&](int j) { return cg ? xcg(x, j) : (int)x[j]; };
+        const int E = net.E, N = net.N;
+        int o = 0;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            for (int d = 0; d < net.D[k]; ++d) {
+                const int e = net.edge_id[(k * net.dtab + d) * kBT + t];
+                lut[(o + d) * kBT + t] =
+                    e >= 0 ? edge_word_s(X(e), X(E + e), X(2 * E + e),
+                                         2u * (uint32_t)net.node_q[net.src[e]])
+                           : 0x04040000u | ((uint32_t)(-1 - e) & 0xffffu);
+            }
+            // neutral rows up to a whole group of 4: the code of node 2 t
+            for (int d = net.D[k]; d < groups4(net.D[k]); ++d)
+                lut[(o + d) * kBT + t] = 0x04040000u | (4u * (uint32_t)t);
+            o += groups4(net.D[k]);
+            const int i = net.q_node[t * NPL + k];
+            u[k] = i >= 0 ? X(3 * E + i) : 1;
+            m1[k] = i >= 0 ? X(3 * E + N + i) + 1 : 1;
+            d2[k] = i >= 0 ? X(3 * E + 2 * N + i) == 2 : 0;
+        }
+    }
+
+    __device__ void count(const DevNet &net, const int8_t *x, int t)
+    {
+        block_count(net, x, t, out_nz, pos_in);
+    }
+
+    __device__ void change_edge(const DevNet &net, int t, int owner, int pos, int w, int p, int tt)
+    {
+        if (t != owner) return;
+        const uint32_t a = (uint32_t)(lut_row(net, (pos >> 8) & 0xff, pos & 0xff) * kBT + t);
+        undo_kind = 0;
+        undo_addr = a;
+        undo_val = lut[a];
+        lut[a] = edge_word_s(w, p, tt, undo_val);
+    }
+
+    __device__ void change_node(int t, int owner, int slot, int kind, int v)
+    {
+        if (t != owner) return;
+        undo_kind = kind;
+        undo_slot = slot;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            if (k != slot) continue;
+            if (kind == 3) { undo_val = (uint32_t)u[k]; u[k] = v; }
+            else if (kind == 4) { undo_val = (uint32_t)m1[k]; m1[k] = v + 1; }
+            else { undo_val = (uint32_t)d2[k]; d2[k] = v == 2; }
+        }
+    }
+
+    __device__ void undo(int t, int owner)
+    {
+        if (t != owner) return;
+        if (undo_kind == 0) {
+            lut[undo_addr] = undo_val;
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            if (k != undo_slot) continue;
+            if (undo_kind == 3) u[k] = (int32_t)undo_val;
+            else if (undo_kind == 4) m1[k] = (int32_t)undo_val;
+            else d2[k] = (int32_t)undo_val;
+        }
+    }
+
+    // Simulate(x) of Table 1 (Sections 2.1-2.3); y in every thread.
+    __device__ int32_t simulate(const DevNet &net, int t, uint8_t *traj)
+    {
+        int row0[NPL];
+        int o = 0;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            row0[k] = o;
+            o += groups4(net.D[k]);
+        }
+        auto gather = [&](int k) -> uint32_t {
+            const int D4 = groups4(net.D[k]);
+            uint32_t acc = kH - 0x04040404u * (uint32_t)D4;
+            const uint32_t *lw = lut + row0[k] * kBT + t;
+            for (int d = 0; d < D4; d += 4) {
+                uint32_t w[4], c[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) w[i] = lw[(d + i) * kBT];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
+            }
+            return acc;
+        };
+        const BlockSync sync{bc, t & 31, t >> 5};
+        return simulate_swar4_core<NPL, true, false, kBT>(u, m1, d2, net, sm, 0u, t, traj,
+                                                          INT32_MAX, gather, sync);
+    }
+};
+
+template <int NPL>
+__device__ __forceinline__ BlockRegPath<NPL> make_block_reg_path(const DevNet &net, uint8_t *sm)
+{
+    const BlockLayout L = block_layout(net.D, NPL, net.N);
+    BlockRegPath<NPL> P;
+    P.sm = sm;
+    P.lut = reinterpret_cast<uint32_t *>(sm + L.lut);
+    P.out_nz = sm + L.cnt;
+    P.pos_in = P.out_nz + ((net.N + 15) & ~15);
+    P.bc = reinterpret_cast<Bcast *>(sm + L.scratch);
+    return P;
+}
+
+// make_path<Path>: the shared-memory layout of either variant.
+template <class Path> struct PathMaker;
+template <> struct PathMaker<BlockPath> {
+    static __device__ __forceinline__ BlockPath make(const DevNet &net, uint8_t *sm)
+    {
+        return make_block_path(net, sm);
+    }
+};
+template <int NPL> struct PathMaker<BlockRegPath<NPL>> {
+    static __device__ __forceinline__ BlockRegPath<NPL> make(const DevNet &net, uint8_t *sm)
+    {
+        return make_block_reg_path<NPL>(net, sm);
+    }
+};
+
+template <class Path>
 __global__ void __launch_bounds__(kBT, 1)
     evaluate_block_kernel(DevNet net, const int8_t *__restrict__ X, int64_t xstride, int32_t n,
                           int32_t *__restrict__ score, int32_t *__restrict__ score2,
                           uint8_t *__restrict__ traj)
 {
     extern __shared__ __align__(256) uint8_t sm[];
-    BlockPath P = make_block_path(net, sm);
+    Path P = PathMaker<Path>::make(net, sm);
     const int t = threadIdx.x;
     for (int v = blockIdx.x; v < n; v += gridDim.x) {
         P.load(net, X + (size_t)v * xstride, t, false);
@@ -342,7 +552,8 @@ __device__ __forceinline__ void block_copy16(int8_t *dst, const int8_t *src, int
 }
 
 // Steps [g_lo, g_hi) of one chain (Table 1), then publish the chunk.
-__device__ void block_chunk(BlockPath &P, const DevNet &net, const DevChains &ch,
+template <class Path>
+__device__ void block_chunk(Path &P, const DevNet &net, const DevChains &ch,
                             const DevSched &sc, int chain, int64_t g_lo, int64_t g_hi,
                             int done_value, int t)
 {
@@ -472,10 +683,11 @@ __device__ __forceinline__ bool block_wait(int32_t *flag, int cj, int32_t *err)
     return false;
 }
 
+template <class Path>
 __global__ void __launch_bounds__(kBT, 1) anneal_block_kernel(DevNet net, DevChains ch, DevSched sc)
 {
     extern __shared__ __align__(256) uint8_t sm[];
-    BlockPath P = make_block_path(net, sm);
+    Path P = PathMaker<Path>::make(net, sm);
     const int t = threadIdx.x;
     const int64_t n_items = (int64_t)sc.n_chunks * ch.n;
     for (;;) {
@@ -516,33 +728,43 @@ size_t block_path_smem_bytes(const int *D, int npl, int N)
     return block_layout(D, npl, N).bytes;
 }
 
-cudaError_t launch_evaluate_block(const DevNet &net, const int8_t *X, int64_t xstride, int32_t n,
-                                  int32_t *score, int32_t *score2, uint8_t *traj, int sm_count,
-                                  cudaStream_t st)
+namespace {
+
+template <class Path>
+cudaError_t evaluate_block_t(const DevNet &net, const int8_t *X, int64_t xstride, int32_t n,
+                             int32_t *score, int32_t *score2, uint8_t *traj, int sm_count,
+                             cudaStream_t st)
 {
-    if (n <= 0) return cudaSuccess;
     size_t smem = 0;
     cudaError_t e = block_smem(net, &smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(evaluate_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    e = cudaFuncSetAttribute(evaluate_block_kernel<Path>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = n < sm_count ? n : sm_count;
-    evaluate_block_kernel<<<grid, kBT, smem, st>>>(net, X, xstride, n, score, score2, traj);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_block_kernel<Path>, kBT,
+                                                      smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t cap = (int64_t)sm_count * per_sm;
+    const int grid = (int)(n < cap ? n : cap);
+    evaluate_block_kernel<Path><<<grid, kBT, smem, st>>>(net, X, xstride, n, score, score2, traj);
     return cudaGetLastError();
 }
 
-cudaError_t launch_anneal_block(const DevNet &net, const DevChains &ch, const DevSched &sc0,
-                                int sm_count, cudaStream_t st)
+template <class Path>
+cudaError_t anneal_block_t(const DevNet &net, const DevChains &ch, const DevSched &sc0,
+                           int sm_count, cudaStream_t st)
 {
     size_t smem = 0;
     cudaError_t e = block_smem(net, &smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(anneal_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    e = cudaFuncSetAttribute(anneal_block_kernel<Path>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, anneal_block_kernel, kBT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, anneal_block_kernel<Path>, kBT,
+                                                      smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int grid = sm_count * per_sm;
@@ -551,8 +773,36 @@ cudaError_t launch_anneal_block(const DevNet &net, const DevChains &ch, const De
     e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sc.done, 0, sizeof(int32_t) * (size_t)ch.n, st);
     if (e != cudaSuccess) return e;
-    anneal_block_kernel<<<grid, kBT, smem, st>>>(net, ch, sc);
+    anneal_block_kernel<Path><<<grid, kBT, smem, st>>>(net, ch, sc);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_evaluate_block(const DevNet &net, const int8_t *X, int64_t xstride, int32_t n,
+                                  int32_t *score, int32_t *score2, uint8_t *traj, int sm_count,
+                                  cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    switch (net.npl) {
+    case 2: return evaluate_block_t<BlockRegPath<2>>(net, X, xstride, n, score, score2, traj, sm_count, st);
+    case 4: return evaluate_block_t<BlockRegPath<4>>(net, X, xstride, n, score, score2, traj, sm_count, st);
+    case 6: return evaluate_block_t<BlockRegPath<6>>(net, X, xstride, n, score, score2, traj, sm_count, st);
+    case 8: return evaluate_block_t<BlockRegPath<8>>(net, X, xstride, n, score, score2, traj, sm_count, st);
+    default: return evaluate_block_t<BlockPath>(net, X, xstride, n, score, score2, traj, sm_count, st);
+    }
+}
+
+cudaError_t launch_anneal_block(const DevNet &net, const DevChains &ch, const DevSched &sc0,
+                                int sm_count, cudaStream_t st)
+{
+    switch (net.npl) {
+    case 2: return anneal_block_t<BlockRegPath<2>>(net, ch, sc0, sm_count, st);
+    case 4: return anneal_block_t<BlockRegPath<4>>(net, ch, sc0, sm_count, st);
+    case 6: return anneal_block_t<BlockRegPath<6>>(net, ch, sc0, sm_count, st);
+    case 8: return anneal_block_t<BlockRegPath<8>>(net, ch, sc0, sm_count, st);
+    default: return anneal_block_t<BlockPath>(net, ch, sc0, sm_count, st);
+    }
 }
 
 }  // namespace rn

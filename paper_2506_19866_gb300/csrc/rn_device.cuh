@@ -324,17 +324,41 @@ __device__ __forceinline__ uint32_t state_code(uint32_t s4)
     return prmt(v | (v >> 4), 0u, 0x4420u);
 }
 
+// Reductions and barriers of a chain simulated by one warp (simulate_swar4_core's
+// Sync policy; the block path has its own).
+struct WarpSync {
+    // the four conditions' priority maxima over the warp, as two 16-bit pairs
+    __device__ __forceinline__ void max4(uint32_t m01, uint32_t m23, uint32_t &P01,
+                                         uint32_t &P23) const
+    {
+        const uint32_t p0 = __reduce_max_sync(kFull, m01 & 0xffffu);
+        const uint32_t p1 = __reduce_max_sync(kFull, m01 >> 16);
+        const uint32_t p2 = __reduce_max_sync(kFull, m23 & 0xffffu);
+        const uint32_t p3 = __reduce_max_sync(kFull, m23 >> 16);
+        P01 = prmt(p0, p1, 0x5410u);
+        P23 = prmt(p2, p3, 0x5410u);
+    }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ uint32_t sum(uint32_t v) const { return __reduce_add_sync(kFull, v); }
+};
+
 // The byte-SIMD simulation, shared by the register-table and the
 // shared-memory-table instances; `gather(k)` returns slot k's biased image
-// bytes (128 + K per condition) from the instance's table words.
-template <int NPL, bool SMEM_FMT, bool EARLY, class Gather>
+// bytes (128 + K per condition) from the instance's table words.  A chain's
+// nodes sit on LANES threads (a warp, or the block of the block path), whose
+// maxima, barriers and score sum come from `sync`.  EARLY reduces over one
+// warp and is for LANES = 32 only.
+template <int NPL, bool SMEM_FMT, bool EARLY, int LANES = 32, class Gather,
+          class Sync = WarpSync>
 __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
                                                        const int32_t (&m1)[NPL],
                                                        const int32_t (&d2)[NPL],
                                                        const DevNet &net, uint8_t *sm,
                                                        uint32_t base, int lane, uint8_t *traj,
-                                                       int32_t limit, Gather gather)
+                                                       int32_t limit, Gather gather,
+                                                       Sync sync = Sync())
 {
+    static_assert(!EARLY || LANES == 32, "early rejection reduces over one warp");
     const int T = net.T;
     uint8_t *my_codes = sm + base + 2 * lane * NPL;
     uint32_t U2[NPL], CM[NPL];
@@ -348,7 +372,7 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
         uint32_t code[NPL], s4[NPL], cu[NPL], cd[NPL], ua01[NPL], ua23[NPL], mov[NPL];
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
-            const size_t q = (size_t)g * 32 * NPL + lane * NPL + k;
+            const size_t q = (size_t)g * LANES * NPL + lane * NPL + k;
             s4[k] = __ldg(net.init_s4 + q);
             mov[k] = __ldg(net.movable + q);
             cu[k] = 0;
@@ -383,11 +407,8 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
                     m01 = max_u16x2(m01, pr01[k]);
                     m23 = max_u16x2(m23, pr23[k]);
                 }
-                const uint32_t p0 = __reduce_max_sync(kFull, m01 & 0xffffu);
-                const uint32_t p1 = __reduce_max_sync(kFull, m01 >> 16);
-                const uint32_t p2 = __reduce_max_sync(kFull, m23 & 0xffffu);
-                const uint32_t p3 = __reduce_max_sync(kFull, m23 >> 16);
-                const uint32_t P01 = prmt(p0, p1, 0x5410u), P23 = prmt(p2, p3, 0x5410u);
+                uint32_t P01, P23;
+                sync.max4(m01, m23, P01, P23);   // the maxima over the chain's nodes
 #pragma unroll
                 for (int k = 0; k < NPL; ++k) {
                     const uint32_t nz01 = ((pr01[k] ^ P01) + 0x7FFF7FFFu) & 0x80008000u;
@@ -403,11 +424,11 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
                 }
                 store_codes<NPL>(my_codes, code);
             }
-            __syncwarp();
+            sync.sync();
             // error at this time point: PRMT of two conditions' entry tables
             // (byte b = W |b - R|) with a selector built from the state codes
-            const size_t row = (size_t)T * 32 * NPL;
-            const uint32_t *ob = net.obs + ((size_t)4 * g * T + tau) * 32 * NPL + lane * NPL;
+            const size_t row = (size_t)T * LANES * NPL;
+            const uint32_t *ob = net.obs + ((size_t)4 * g * T + tau) * LANES * NPL + lane * NPL;
             uint32_t w0[NPL], w1[NPL], w2[NPL], w3[NPL];
             load_obs<NPL>(w0, ob);
 #pragma unroll
@@ -452,9 +473,9 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
                 }
             }
         }
-        __syncwarp();
+        sync.sync();
     }
-    return (int32_t)__reduce_add_sync(kFull, score);
+    return (int32_t)sync.sum(score);
 }
 
 // The register-table instance: table words in registers (rn_device.cuh format,
