@@ -872,8 +872,8 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     int drest = 0;
     for (int k = 1; k < npl; ++k) drest = std::max(drest, n->D[k]);
     anneal_capacity(npl, n->D[0], drest, &n->d0, &n->d1);
-    // error table of an entry: byte b = W |b - R| for b = 0, 1, 2
-    std::vector<uint32_t> obs((size_t)C * T * L * npl, 0u);
+    // error table of an entry: byte b = W |b - R| for b = 0, 1, 2 (warp paths)
+    std::vector<uint32_t> obs((size_t)(L == 32 ? C : G) * T * L * npl, 0u);
     // state codes: nibble c = initial state of condition g * cg + c; a node that
     // never moves in a condition (padding, knocked out, condition beyond C)
     // starts at 0 and has its bit k * cg + c set in out_bits
@@ -899,20 +899,38 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
                 movable[(size_t)g * L * npl + q] |= 0x80u << (8 * c);
             }
         }
-    for (int32_t c = 0; c < C; ++c) {
-        for (int q = 0; q < L * npl; ++q) {
-            const int i = n->q_node[(size_t)q];
-            const int lane = q / npl, slot = q % npl;
-            if (i < 0) continue;
-            for (int32_t t = 0; t < T; ++t) {
-                const size_t k = ((size_t)c * T + t) * N + i;
-                const int w = W[k], r = ref[k];
-                uint32_t word = 0;
-                if (w)
-                    for (int b = 0; b < 3; ++b) word |= (uint32_t)(w * std::abs(b - r)) << (8 * b);
-                obs[(((size_t)c * T + t) * L + lane) * npl + slot] = word;
+    if (L == 32) {
+        for (int32_t c = 0; c < C; ++c) {
+            for (int q = 0; q < L * npl; ++q) {
+                const int i = n->q_node[(size_t)q];
+                const int lane = q / npl, slot = q % npl;
+                if (i < 0) continue;
+                for (int32_t t = 0; t < T; ++t) {
+                    const size_t k = ((size_t)c * T + t) * N + i;
+                    const int w = W[k], r = ref[k];
+                    uint32_t word = 0;
+                    if (w)
+                        for (int b = 0; b < 3; ++b)
+                            word |= (uint32_t)(w * std::abs(b - r)) << (8 * b);
+                    obs[(((size_t)c * T + t) * L + lane) * npl + slot] = word;
+                }
             }
         }
+    } else {
+        // block path: one compact word per group of 4 conditions, time point
+        // and node, byte c = R | W << 2 (W <= 3), [G][T][L][npl]
+        for (int g = 0; g < G; ++g)
+            for (int32_t t = 0; t < T; ++t)
+                for (int q = 0; q < L * npl; ++q) {
+                    const int i = n->q_node[(size_t)q];
+                    if (i < 0) continue;
+                    uint32_t word = 0;
+                    for (int c = 0; c < 4 && 4 * g + c < C; ++c) {
+                        const size_t k = ((size_t)(4 * g + c) * T + t) * N + i;
+                        if (W[k]) word |= (uint32_t)(ref[k] | W[k] << 2) << (8 * c);
+                    }
+                    obs[((size_t)g * T + t) * L * npl + (size_t)q] = word;
+                }
     }
     RN_CUDA(ctx, cudaSetDevice(ctx->device));
     RN_CUDA(ctx, n->d_obs.upload(obs));

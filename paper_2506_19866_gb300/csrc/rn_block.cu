@@ -66,6 +66,17 @@ struct Bcast {
     int32_t owner, pos, w, p, t, slot;   // owner thread and the changed table entry
 };
 
+// Error of a node's four conditions at one time point (Section 2.3) from its
+// compact entry word (byte c = R_c | W_c << 2, W = 0 where unobserved):
+// sum_c W_c |s_c - R_c|.  For s, R in 0..2, x = s ^ R is |s - R| except x = 3
+// (s, R = 1, 2), where |s - R| = 1 = x - 2; DP4A weights and sums the bytes.
+__device__ __forceinline__ uint32_t entry_error(uint32_t s4, uint32_t word, uint32_t acc)
+{
+    const uint32_t x = s4 ^ (word & 0x03030303u);
+    const uint32_t d = x - ((x & (x >> 1) & kB1) << 1);
+    return __dp4a(d, (word >> 2) & 0x03030303u, acc);
+}
+
 // Constraint counters of Section 2.5.3 from x (global, through L2).
 __device__ void block_count(const DevNet &net, const int8_t *x, int t, uint8_t *out_nz,
                             uint8_t *pos_in)
@@ -273,20 +284,11 @@ struct BlockPath {
                     }
                     __syncthreads();
                 }
-                // error at this time point (entry tables: byte b = W |b - R|)
-                const size_t row = (size_t)T * kBT * npl;
-                const uint32_t *ob = net.obs + ((size_t)4 * g * T + tau) * kBT * npl + t * npl;
-                uint32_t acc = 0;
+                // error at this time point (compact entry words)
+                const uint32_t *ob = net.obs + (((size_t)g * T + tau) * kBT + t) * npl;
                 for (int k = 0; k < npl; ++k) {
                     const uint32_t s4 = F(k, kF_S4, t);
-                    const uint32_t x = s4 | (s4 >> 4);
-                    const uint32_t sel01 = (x & 0xffu) + 0x3340u;
-                    const uint32_t sel23 = ((x >> 16) & 0xffu) + 0x3340u;
-                    const uint32_t w0 = __ldg(ob + k);
-                    const uint32_t w1 = ncg > 1 ? __ldg(ob + row + k) : 0u;
-                    const uint32_t w2 = ncg > 2 ? __ldg(ob + 2 * row + k) : 0u;
-                    const uint32_t w3 = ncg > 3 ? __ldg(ob + 3 * row + k) : 0u;
-                    acc += __byte_perm(w0, w1, sel01) + __byte_perm(w2, w3, sel23);
+                    score = entry_error(s4, __ldg(ob + k), score);
                     if (traj) {
                         const int i = net.q_node[t * npl + k];
                         for (int c = 0; c < ncg; ++c)
@@ -295,7 +297,6 @@ struct BlockPath {
                                     (uint8_t)((s4 >> (8 * c)) & 0xffu);
                     }
                 }
-                score += (acc & 0xffu) + (acc >> 8);
             }
             __syncthreads();
         }
@@ -326,10 +327,35 @@ __device__ __forceinline__ BlockPath make_block_path(const DevNet &net, uint8_t 
 }
 
 // Block-wide reductions and barriers for simulate_swar4_core: warp redux, then
-// the eight warp values through the broadcast area.
+// the eight warp values through the broadcast area.  A time point's compact
+// entry words (one per node, 4 conditions) are loaded at the start of its
+// update step, so that their latency overlaps the gather, the update and its
+// barriers (all warps of the block would otherwise wait on L2 at once).
+template <int NPL>
 struct BlockSync {
     Bcast *bc;
     int lane, warp;
+
+    struct Ahead {
+        uint32_t w[NPL];
+    };
+    template <int>
+    __device__ __forceinline__ Ahead fetch_obs(const DevNet &net, int g, int tau, int t) const
+    {
+        Ahead a;
+        load_obs<NPL>(a.w, net.obs + (((size_t)g * net.T + tau) * kBT + t) * NPL);
+        return a;
+    }
+    template <int, bool>
+    __device__ __forceinline__ uint32_t error(const Ahead &a, const uint32_t (&s4)[NPL],
+                                              const uint32_t (&)[NPL], const DevNet &, int, int,
+                                              int, int) const
+    {
+        uint32_t e = 0;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) e = entry_error(s4[k], a.w[k], e);
+        return e;
+    }
 
     __device__ __forceinline__ void max4(uint32_t m01, uint32_t m23, uint32_t &P01,
                                          uint32_t &P23) const
@@ -487,7 +513,7 @@ struct BlockRegPath {
             }
             return acc;
         };
-        const BlockSync sync{bc, t & 31, t >> 5};
+        const BlockSync<NPL> sync{bc, t & 31, t >> 5};
         return simulate_swar4_core<NPL, true, false, kBT>(u, m1, d2, net, sm, 0u, t, traj,
                                                           INT32_MAX, gather, sync);
     }

@@ -340,6 +340,48 @@ struct WarpSync {
     }
     __device__ __forceinline__ void sync() const { __syncwarp(); }
     __device__ __forceinline__ uint32_t sum(uint32_t v) const { return __reduce_add_sync(kFull, v); }
+    // Error of a time point (Section 2.3) from the entry tables, one word per
+    // condition and node (byte b = W |b - R|): a PRMT of two conditions' words
+    // with a selector built from the state codes.  The words are read where
+    // they are used (nothing is fetched ahead).
+    struct Ahead {};
+    template <int NPL>
+    __device__ __forceinline__ Ahead fetch_obs(const DevNet &, int, int, int) const
+    {
+        return {};
+    }
+    template <int NPL, bool SMEM_FMT>
+    __device__ __forceinline__ uint32_t error(const Ahead &, const uint32_t (&s4)[NPL],
+                                              const uint32_t (&code)[NPL], const DevNet &net,
+                                              int g, int tau, int lane, int ncg) const
+    {
+        const size_t row = (size_t)net.T * 32 * NPL;
+        const uint32_t *ob = net.obs + ((size_t)4 * g * net.T + tau) * 32 * NPL + lane * NPL;
+        uint32_t w0[NPL], w1[NPL], w2[NPL], w3[NPL];
+        load_obs<NPL>(w0, ob);
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) w1[k] = w2[k] = w3[k] = 0u;
+        if (ncg > 1) load_obs<NPL>(w1, ob + row);
+        if (ncg > 2) load_obs<NPL>(w2, ob + 2 * row);
+        if (ncg > 3) load_obs<NPL>(w3, ob + 3 * row);
+        uint32_t t = 0;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            // selector bytes: nibble c = s_c of conditions 0-1 and 2-3 (the
+            // register-format state code is exactly that)
+            uint32_t sel01, sel23;
+            if constexpr (SMEM_FMT) {
+                const uint32_t x = s4[k] | (s4[k] >> 4);
+                sel01 = (x & 0xffu) + 0x3340u;
+                sel23 = ((x >> 16) & 0xffu) + 0x3340u;
+            } else {
+                sel01 = (code[k] & 0xffu) + 0x3340u;
+                sel23 = (code[k] >> 8) + 0x3340u;
+            }
+            t += __byte_perm(w0[k], w1[k], sel01) + __byte_perm(w2[k], w3[k], sel23);
+        }
+        return (t & 0xffu) + (t >> 8);
+    }
 };
 
 // The byte-SIMD simulation, shared by the register-table and the
@@ -384,6 +426,9 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
         store_codes<NPL>(my_codes, code);
         const int ncg = min(net.C - 4 * g, 4);
         for (int tau = 0; tau < T; ++tau) {
+            // the entry words of this time point, fetched ahead of the update
+            // step where the policy does so
+            const auto ahead = sync.template fetch_obs<NPL>(net, g, tau, lane);
             if (tau > 0) {
                 uint32_t acc[NPL];
 #pragma unroll
@@ -425,34 +470,8 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
                 store_codes<NPL>(my_codes, code);
             }
             sync.sync();
-            // error at this time point: PRMT of two conditions' entry tables
-            // (byte b = W |b - R|) with a selector built from the state codes
-            const size_t row = (size_t)T * LANES * NPL;
-            const uint32_t *ob = net.obs + ((size_t)4 * g * T + tau) * LANES * NPL + lane * NPL;
-            uint32_t w0[NPL], w1[NPL], w2[NPL], w3[NPL];
-            load_obs<NPL>(w0, ob);
-#pragma unroll
-            for (int k = 0; k < NPL; ++k) w1[k] = w2[k] = w3[k] = 0u;
-            if (ncg > 1) load_obs<NPL>(w1, ob + row);
-            if (ncg > 2) load_obs<NPL>(w2, ob + 2 * row);
-            if (ncg > 3) load_obs<NPL>(w3, ob + 3 * row);
-            uint32_t t = 0;
-#pragma unroll
-            for (int k = 0; k < NPL; ++k) {
-                // selector bytes: nibble c = s_c of conditions 0-1 and 2-3 (the
-                // register-format state code is exactly that)
-                uint32_t sel01, sel23;
-                if constexpr (SMEM_FMT) {
-                    const uint32_t x = s4[k] | (s4[k] >> 4);
-                    sel01 = (x & 0xffu) + 0x3340u;
-                    sel23 = ((x >> 16) & 0xffu) + 0x3340u;
-                } else {
-                    sel01 = (code[k] & 0xffu) + 0x3340u;
-                    sel23 = (code[k] >> 8) + 0x3340u;
-                }
-                t += __byte_perm(w0[k], w1[k], sel01) + __byte_perm(w2[k], w3[k], sel23);
-            }
-            score += (t & 0xffu) + (t >> 8);
+            // error at this time point
+            score += sync.template error<NPL, SMEM_FMT>(ahead, s4, code, net, g, tau, lane, ncg);
             if (EARLY && (tau & 3) == 3) {
                 // exact early rejection: the partial score never decreases
                 const uint32_t tot = __reduce_add_sync(kFull, score);
