@@ -872,8 +872,10 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     int drest = 0;
     for (int k = 1; k < npl; ++k) drest = std::max(drest, n->D[k]);
     anneal_capacity(npl, n->D[0], drest, &n->d0, &n->d1);
-    // error table of an entry: byte b = W |b - R| for b = 0, 1, 2 (warp paths)
-    std::vector<uint32_t> obs((size_t)(L == 32 ? C : G) * T * L * npl, 0u);
+    // entry tables: per condition, byte b = W |b - R| for b = 0, 1, 2 (single
+    // conditions, cg = 1); per group of 4 conditions, one compact word per time
+    // point and node, byte c = R | W << 2 (W <= 3), [G][T][L][npl] (cg = 4)
+    std::vector<uint32_t> obs((size_t)(cg == 1 ? C : G) * T * L * npl, 0u);
     // state codes: nibble c = initial state of condition g * cg + c; a node that
     // never moves in a condition (padding, knocked out, condition beyond C)
     // starts at 0 and has its bit k * cg + c set in out_bits
@@ -899,7 +901,7 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
                 movable[(size_t)g * L * npl + q] |= 0x80u << (8 * c);
             }
         }
-    if (L == 32) {
+    if (cg == 1) {
         for (int32_t c = 0; c < C; ++c) {
             for (int q = 0; q < L * npl; ++q) {
                 const int i = n->q_node[(size_t)q];
@@ -917,8 +919,6 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
             }
         }
     } else {
-        // block path: one compact word per group of 4 conditions, time point
-        // and node, byte c = R | W << 2 (W <= 3), [G][T][L][npl]
         for (int g = 0; g < G; ++g)
             for (int32_t t = 0; t < T; ++t)
                 for (int q = 0; q < L * npl; ++q) {

@@ -66,17 +66,6 @@ struct Bcast {
     int32_t owner, pos, w, p, t, slot;   // owner thread and the changed table entry
 };
 
-// Error of a node's four conditions at one time point (Section 2.3) from its
-// compact entry word (byte c = R_c | W_c << 2, W = 0 where unobserved):
-// sum_c W_c |s_c - R_c|.  For s, R in 0..2, x = s ^ R is |s - R| except x = 3
-// (s, R = 1, 2), where |s - R| = 1 = x - 2; DP4A weights and sums the bytes.
-__device__ __forceinline__ uint32_t entry_error(uint32_t s4, uint32_t word, uint32_t acc)
-{
-    const uint32_t x = s4 ^ (word & 0x03030303u);
-    const uint32_t d = x - ((x & (x >> 1) & kB1) << 1);
-    return __dp4a(d, (word >> 2) & 0x03030303u, acc);
-}
-
 // Constraint counters of Section 2.5.3 from x (global, through L2).
 __device__ void block_count(const DevNet &net, const int8_t *x, int t, uint8_t *out_nz,
                             uint8_t *pos_in)

@@ -324,6 +324,18 @@ __device__ __forceinline__ uint32_t state_code(uint32_t s4)
     return prmt(v | (v >> 4), 0u, 0x4420u);
 }
 
+// Error of a node's four conditions at one time point (Section 2.3) from its
+// compact entry word (byte c = R_c | W_c << 2, W = 0 where unobserved), added
+// to acc: sum_c W_c |s_c - R_c|.  For s, R in 0..2, x = s ^ R equals |s - R|
+// except x = 3 (s, R = 1, 2), where |s - R| = 1 = x - 2; DP4A weights and sums
+// the four bytes.
+__device__ __forceinline__ uint32_t entry_error(uint32_t s4, uint32_t word, uint32_t acc)
+{
+    const uint32_t x = s4 ^ (word & 0x03030303u);
+    const uint32_t d = x - ((x & (x >> 1) & kB1) << 1);
+    return __dp4a(d, (word >> 2) & 0x03030303u, acc);
+}
+
 // Reductions and barriers of a chain simulated by one warp (simulate_swar4_core's
 // Sync policy; the block path has its own).
 struct WarpSync {
@@ -340,47 +352,25 @@ struct WarpSync {
     }
     __device__ __forceinline__ void sync() const { __syncwarp(); }
     __device__ __forceinline__ uint32_t sum(uint32_t v) const { return __reduce_add_sync(kFull, v); }
-    // Error of a time point (Section 2.3) from the entry tables, one word per
-    // condition and node (byte b = W |b - R|): a PRMT of two conditions' words
-    // with a selector built from the state codes.  The words are read where
-    // they are used (nothing is fetched ahead).
+    // Error of a time point (Section 2.3) from the compact entry words, read
+    // where they are used (nothing is fetched ahead).
     struct Ahead {};
     template <int NPL>
     __device__ __forceinline__ Ahead fetch_obs(const DevNet &, int, int, int) const
     {
         return {};
     }
-    template <int NPL, bool SMEM_FMT>
+    template <int NPL, bool>
     __device__ __forceinline__ uint32_t error(const Ahead &, const uint32_t (&s4)[NPL],
-                                              const uint32_t (&code)[NPL], const DevNet &net,
-                                              int g, int tau, int lane, int ncg) const
+                                              const uint32_t (&)[NPL], const DevNet &net, int g,
+                                              int tau, int lane, int) const
     {
-        const size_t row = (size_t)net.T * 32 * NPL;
-        const uint32_t *ob = net.obs + ((size_t)4 * g * net.T + tau) * 32 * NPL + lane * NPL;
-        uint32_t w0[NPL], w1[NPL], w2[NPL], w3[NPL];
-        load_obs<NPL>(w0, ob);
+        uint32_t w[NPL];
+        load_obs<NPL>(w, net.obs + (((size_t)g * net.T + tau) * 32 + lane) * NPL);
+        uint32_t e = 0;
 #pragma unroll
-        for (int k = 0; k < NPL; ++k) w1[k] = w2[k] = w3[k] = 0u;
-        if (ncg > 1) load_obs<NPL>(w1, ob + row);
-        if (ncg > 2) load_obs<NPL>(w2, ob + 2 * row);
-        if (ncg > 3) load_obs<NPL>(w3, ob + 3 * row);
-        uint32_t t = 0;
-#pragma unroll
-        for (int k = 0; k < NPL; ++k) {
-            // selector bytes: nibble c = s_c of conditions 0-1 and 2-3 (the
-            // register-format state code is exactly that)
-            uint32_t sel01, sel23;
-            if constexpr (SMEM_FMT) {
-                const uint32_t x = s4[k] | (s4[k] >> 4);
-                sel01 = (x & 0xffu) + 0x3340u;
-                sel23 = ((x >> 16) & 0xffu) + 0x3340u;
-            } else {
-                sel01 = (code[k] & 0xffu) + 0x3340u;
-                sel23 = (code[k] >> 8) + 0x3340u;
-            }
-            t += __byte_perm(w0[k], w1[k], sel01) + __byte_perm(w2[k], w3[k], sel23);
-        }
-        return (t & 0xffu) + (t >> 8);
+        for (int k = 0; k < NPL; ++k) e = entry_error(s4[k], w[k], e);
+        return e;
     }
 };
 

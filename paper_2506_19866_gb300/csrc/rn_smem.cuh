@@ -265,20 +265,11 @@ struct SmemPath {
                     }
                 }
                 __syncwarp();
-                // error at this time point (entry tables: byte b = W |b - R|)
-                const size_t row = (size_t)T * 32 * npl;
-                const uint32_t *ob = net.obs + ((size_t)4 * g * T + tau) * 32 * npl + lane * npl;
-                uint32_t t = 0;
+                // error at this time point (compact entry words)
+                const uint32_t *ob = net.obs + (((size_t)g * T + tau) * 32 + lane) * npl;
                 for (int k = 0; k < npl; ++k) {
                     const uint32_t s4 = F(k, kF_S4, lane);
-                    const uint32_t x = s4 | (s4 >> 4);
-                    const uint32_t sel01 = (x & 0xffu) + 0x3340u;
-                    const uint32_t sel23 = ((x >> 16) & 0xffu) + 0x3340u;
-                    const uint32_t w0 = __ldg(ob + k);
-                    const uint32_t w1 = ncg > 1 ? __ldg(ob + row + k) : 0u;
-                    const uint32_t w2 = ncg > 2 ? __ldg(ob + 2 * row + k) : 0u;
-                    const uint32_t w3 = ncg > 3 ? __ldg(ob + 3 * row + k) : 0u;
-                    t += __byte_perm(w0, w1, sel01) + __byte_perm(w2, w3, sel23);
+                    score = entry_error(s4, __ldg(ob + k), score);
                     if (traj) {
                         const int i = net.q_node[lane * npl + k];
                         for (int c = 0; c < ncg; ++c)
@@ -287,7 +278,6 @@ struct SmemPath {
                                     (uint8_t)((s4 >> (8 * c)) & 0xffu);
                     }
                 }
-                score += (t & 0xffu) + (t >> 8);
                 if (EARLY && (tau & 3) == 3) {
                     // exact early rejection: the partial score never decreases
                     const uint32_t tot = __reduce_add_sync(kFull, score);
