@@ -27,10 +27,10 @@ constexpr int kBW = kBT / 32;   // warps per chain
 __device__ __forceinline__ int xcg(const int8_t *x, int j) { return (int)__ldcg(x + j); }
 
 // Shared memory: codes [kBT * npl] u16 at offset 0, then the table rows, the
-// per-node fields (not on the register variant), the constraint counters and a
-// small scratch area.
+// per-node fields (not on the register variant), the constraint counters, a
+// small scratch area and, where it fits, the chain's x (xbytes, 0 for none).
 struct BlockLayout {
-    uint32_t codes, lut, node, cnt, scratch, bytes;
+    uint32_t codes, lut, node, cnt, scratch, x, bytes;
 };
 
 __host__ __device__ inline uint32_t round256(uint32_t v) { return (v + 255u) & ~255u; }
@@ -41,7 +41,8 @@ __host__ __device__ inline bool block_reg_npl(int npl)
     return npl == 2 || npl == 4 || npl == 6 || npl == 8;
 }
 
-__host__ __device__ inline BlockLayout block_layout(const int *D, int npl, int N)
+__host__ __device__ inline BlockLayout block_layout(const int *D, int npl, int N,
+                                                    uint32_t xbytes = 0)
 {
     BlockLayout L;
     uint32_t rows = 0;
@@ -51,7 +52,8 @@ __host__ __device__ inline BlockLayout block_layout(const int *D, int npl, int N
     L.node = L.lut + rows * kBT * 4u;
     L.cnt = L.node + (block_reg_npl(npl) ? 0u : (uint32_t)npl * kF_N * kBT * 4u);
     L.scratch = L.cnt + round256(2u * (((uint32_t)N + 15u) & ~15u));
-    L.bytes = L.scratch + 256u;
+    L.x = L.scratch + 256u;
+    L.bytes = L.x + xbytes;
     return L;
 }
 
@@ -66,17 +68,19 @@ struct Bcast {
     int32_t owner, pos, w, p, t, slot;   // owner thread and the changed table entry
 };
 
-// Constraint counters of Section 2.5.3 from x (global, through L2).
+// Constraint counters of Section 2.5.3 from x (global through L2 when `cg`,
+// else shared memory).
 __device__ void block_count(const DevNet &net, const int8_t *x, int t, uint8_t *out_nz,
-                            uint8_t *pos_in)
+                            uint8_t *pos_in, bool cg)
 {
+    auto X = [&](int j) { return cg ? xcg(x, j) : (int)x[j]; };
     for (int i = t; i < net.N; i += kBT) {
         int o = 0, q = 0;
         for (int k = net.out_ptr[i]; k < net.out_ptr[i + 1]; ++k)
-            o += xcg(x, net.out_edges[k]) != 0;
+            o += X(net.out_edges[k]) != 0;
         for (int k = net.in_ptr[i]; k < net.in_ptr[i + 1]; ++k) {
             const int e = net.in_edges[k];
-            q += (xcg(x, e) != 0) && (xcg(x, net.E + e) == 1);
+            q += (X(e) != 0) && (X(net.E + e) == 1);
         }
         out_nz[i] = (uint8_t)min(o, 255);
         pos_in[i] = (uint8_t)min(q, 255);
@@ -89,6 +93,7 @@ struct BlockPath {
     uint32_t *lut, *node;
     uint8_t *out_nz, *pos_in;
     Bcast *bc;
+    int8_t *xs;   // the chain's x in shared memory (when the launch reserved it)
     int npl;
     uint32_t undo_addr, undo_val;
     bool undo_lut;
@@ -140,9 +145,9 @@ struct BlockPath {
         }
     }
 
-    __device__ void count(const DevNet &net, const int8_t *x, int t)
+    __device__ void count(const DevNet &net, const int8_t *x, int t, bool cg)
     {
-        block_count(net, x, t, out_nz, pos_in);
+        block_count(net, x, t, out_nz, pos_in, cg);
     }
 
     __device__ void change_edge(const DevNet &net, int t, int owner, int pos, int w, int p, int tt)
@@ -311,6 +316,7 @@ __device__ __forceinline__ BlockPath make_block_path(const DevNet &net, uint8_t 
     P.out_nz = sm + L.cnt;
     P.pos_in = P.out_nz + ((net.N + 15) & ~15);
     P.bc = reinterpret_cast<Bcast *>(sm + L.scratch);
+    P.xs = reinterpret_cast<int8_t *>(sm + L.x);
     P.npl = net.npl;
     return P;
 }
@@ -394,6 +400,7 @@ struct BlockRegPath {
     uint32_t *lut;
     uint8_t *out_nz, *pos_in;
     Bcast *bc;
+    int8_t *xs;   // the chain's x in shared memory (when the launch reserved it)
     static constexpr int npl = NPL;
     int32_t u[NPL], m1[NPL], d2[NPL];
     uint32_t undo_addr, undo_val;
@@ -431,9 +438,9 @@ struct BlockRegPath {
         }
     }
 
-    __device__ void count(const DevNet &net, const int8_t *x, int t)
+    __device__ void count(const DevNet &net, const int8_t *x, int t, bool cg)
     {
-        block_count(net, x, t, out_nz, pos_in);
+        block_count(net, x, t, out_nz, pos_in, cg);
     }
 
     __device__ void change_edge(const DevNet &net, int t, int owner, int pos, int w, int p, int tt)
@@ -518,6 +525,7 @@ __device__ __forceinline__ BlockRegPath<NPL> make_block_reg_path(const DevNet &n
     P.out_nz = sm + L.cnt;
     P.pos_in = P.out_nz + ((net.N + 15) & ~15);
     P.bc = reinterpret_cast<Bcast *>(sm + L.scratch);
+    P.xs = reinterpret_cast<int8_t *>(sm + L.x);
     return P;
 }
 
@@ -558,16 +566,25 @@ __global__ void __launch_bounds__(kBT, 1)
     }
 }
 
-// Copy a P-byte row between global buffers through L2, block-wide.
+// Copy a row of `bytes` (a multiple of 16) block-wide; a global side is read
+// or written through L2 (another SM may run the chain's next chunk).
+template <bool SRC_GLOBAL, bool DST_GLOBAL>
 __device__ __forceinline__ void block_copy16(int8_t *dst, const int8_t *src, int bytes, int t)
 {
     uint4 *d = reinterpret_cast<uint4 *>(dst);
     const uint4 *s = reinterpret_cast<const uint4 *>(src);
-    for (int k = t; k < (bytes >> 4); k += kBT) __stcg(d + k, __ldcg(s + k));
+    for (int k = t; k < (bytes >> 4); k += kBT) {
+        const uint4 v = SRC_GLOBAL ? __ldcg(s + k) : s[k];
+        if (DST_GLOBAL) __stcg(d + k, v);
+        else d[k] = v;
+    }
 }
 
-// Steps [g_lo, g_hi) of one chain (Table 1), then publish the chunk.
-template <class Path>
+// Steps [g_lo, g_hi) of one chain (Table 1), then publish the chunk.  With XS
+// the chain's x is copied into shared memory for the chunk (one coalesced row
+// instead of scattered L2 reads by the table build, the constraint counters and
+// the proposals) and written back at its end.
+template <class Path, bool XS>
 __device__ void block_chunk(Path &P, const DevNet &net, const DevChains &ch,
                             const DevSched &sc, int chain, int64_t g_lo, int64_t g_hi,
                             int done_value, int t)
@@ -575,15 +592,21 @@ __device__ void block_chunk(Path &P, const DevNet &net, const DevChains &ch,
     const int E = net.E;
     int8_t *xg = ch.x_cur + (size_t)chain * ch.pstride;
     int8_t *xb = ch.x_best + (size_t)chain * ch.pstride;
+    int8_t *xr = xg;   // where x is read and written during the chunk
+    if constexpr (XS) {
+        xr = P.xs;
+        block_copy16<true, false>(xr, xg, ch.pstride, t);
+        __syncthreads();
+    }
     Bcast *bc = P.bc;
-    P.load(net, xg, t, true);
-    P.count(net, xg, t);
+    P.load(net, xr, t, !XS);
+    P.count(net, xr, t, !XS);
     __syncthreads();
     int32_t d_cur = __ldcg(ch.d_cur + chain), d_best = __ldcg(ch.d_best + chain);
     int32_t n_acc = 0, n_up = 0, n_null = 0;
     int64_t level = g_lo / sc.iters;
     int64_t in_level = g_lo - level * sc.iters;
-    auto X = [&](int j) { return xcg(xg, j); };
+    auto X = [&](int j) { return XS ? (int)xr[j] : xcg(xg, j); };
     for (int64_t g = g_lo; g < g_hi; ++g) {
         if (in_level == sc.iters) {
             in_level = 0;
@@ -591,11 +614,11 @@ __device__ void block_chunk(Path &P, const DevNet &net, const DevChains &ch,
         }
         if (sc.reset_to_best && in_level == 0) {
             // Table 1: every level starts from the chain's x_best
-            block_copy16(xg, xb, ch.pstride, t);
+            block_copy16<true, !XS>(xr, xb, ch.pstride, t);
             __threadfence_block();
             __syncthreads();
-            P.load(net, xg, t, true);
-            P.count(net, xg, t);
+            P.load(net, xr, t, !XS);
+            P.count(net, xr, t, !XS);
             __syncthreads();
             d_cur = d_best;
         }
@@ -654,7 +677,8 @@ __device__ void block_chunk(Path &P, const DevNet &net, const DevChains &ch,
         if (accept) {
             if (t == 0) {
                 apply_counters_x(net, X, P.out_nz, P.pos_in, kind, idx, cur, v);
-                __stcg(xg + j, (int8_t)v);
+                if (XS) xr[j] = (int8_t)v;
+                else __stcg(xg + j, (int8_t)v);
             }
             d_cur = d_cand;
             ++n_acc;
@@ -662,7 +686,7 @@ __device__ void block_chunk(Path &P, const DevNet &net, const DevChains &ch,
             __syncthreads();
             if (d_cand < d_best) {
                 d_best = d_cand;
-                block_copy16(xb, xg, ch.pstride, t);
+                block_copy16<!XS, true>(xb, xr, ch.pstride, t);
             }
         } else {
             P.undo(t, owner);
@@ -677,6 +701,7 @@ __device__ void block_chunk(Path &P, const DevNet &net, const DevChains &ch,
         __stcg(cnt + 1, __ldcg(cnt + 1) + n_up);
         __stcg(cnt + 2, __ldcg(cnt + 2) + n_null);
     }
+    if constexpr (XS) block_copy16<false, true>(xg, xr, ch.pstride, t);
     // publish: every thread's stores, then the chunk counter of the chain
     __threadfence();
     __syncthreads();
@@ -698,7 +723,7 @@ __device__ __forceinline__ bool block_wait(int32_t *flag, int cj, int32_t *err)
     return false;
 }
 
-template <class Path>
+template <class Path, bool XS>
 __global__ void __launch_bounds__(kBT, 1) anneal_block_kernel(DevNet net, DevChains ch, DevSched sc)
 {
     extern __shared__ __align__(256) uint8_t sm[];
@@ -722,16 +747,24 @@ __global__ void __launch_bounds__(kBT, 1) anneal_block_kernel(DevNet net, DevCha
         }
         const int64_t g_lo = sc.g0 + (int64_t)cj * sc.chunk;
         const int64_t g_hi = min(sc.g1, g_lo + sc.chunk);
-        block_chunk(P, net, ch, sc, chain, g_lo, g_hi, cj + 1, t);
+        block_chunk<Path, XS>(P, net, ch, sc, chain, g_lo, g_hi, cj + 1, t);
     }
+}
+
+cudaError_t smem_limit(int *limit)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return e;
 }
 
 cudaError_t block_smem(const DevNet &net, size_t *bytes)
 {
     *bytes = block_layout(net.D, net.npl, net.N).bytes;
-    int dev = 0, limit = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int limit = 0;
+    cudaError_t e = smem_limit(&limit);
     if (e != cudaSuccess) return e;
     return *bytes <= (size_t)limit ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
@@ -767,19 +800,16 @@ cudaError_t evaluate_block_t(const DevNet &net, const int8_t *X, int64_t xstride
     return cudaGetLastError();
 }
 
-template <class Path>
-cudaError_t anneal_block_t(const DevNet &net, const DevChains &ch, const DevSched &sc0,
-                           int sm_count, cudaStream_t st)
+template <class Path, bool XS>
+cudaError_t anneal_block_launch(const DevNet &net, const DevChains &ch, const DevSched &sc0,
+                                size_t smem, int sm_count, cudaStream_t st)
 {
-    size_t smem = 0;
-    cudaError_t e = block_smem(net, &smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(anneal_block_kernel<Path>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(anneal_block_kernel<Path, XS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, anneal_block_kernel<Path>, kBT,
-                                                      smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, anneal_block_kernel<Path, XS>,
+                                                      kBT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int grid = sm_count * per_sm;
@@ -788,8 +818,24 @@ cudaError_t anneal_block_t(const DevNet &net, const DevChains &ch, const DevSche
     e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sc.done, 0, sizeof(int32_t) * (size_t)ch.n, st);
     if (e != cudaSuccess) return e;
-    anneal_block_kernel<Path><<<grid, kBT, smem, st>>>(net, ch, sc);
+    anneal_block_kernel<Path, XS><<<grid, kBT, smem, st>>>(net, ch, sc);
     return cudaGetLastError();
+}
+
+// The chain's x is kept in shared memory where it fits beside the tables.
+template <class Path>
+cudaError_t anneal_block_t(const DevNet &net, const DevChains &ch, const DevSched &sc0,
+                           int sm_count, cudaStream_t st)
+{
+    size_t smem = 0;
+    cudaError_t e = block_smem(net, &smem);
+    if (e != cudaSuccess) return e;
+    int limit = 0;
+    if ((e = smem_limit(&limit)) != cudaSuccess) return e;
+    const size_t with_x = block_layout(net.D, net.npl, net.N, (uint32_t)ch.pstride).bytes;
+    if (with_x <= (size_t)limit)
+        return anneal_block_launch<Path, true>(net, ch, sc0, with_x, sm_count, st);
+    return anneal_block_launch<Path, false>(net, ch, sc0, smem, sm_count, st);
 }
 
 }  // namespace

@@ -57,8 +57,14 @@ def test_evaluate_block_sizes(ctx, n_nodes, lam, cap, n_cond, n_times):
     assert score[0] == 0                        # the planted vector, noise-free data
 
 
-def test_anneal_block_chains_match_oracle(ctx):
-    w = synth.random_network(61, 700, lam=5.0, cap=20, n_cond=6, n_times=8, obs_frac=0.3)
+@pytest.mark.parametrize("seed,n_nodes,lam,cap,n_cond,n_times", [
+    (61, 700, 5.0, 20, 6, 8), (64, 1000, 36.0, 48, 2, 5), (65, 2900, 2.0, 8, 1, 4)])
+def test_anneal_block_chains_match_oracle(ctx, seed, n_nodes, lam, cap, n_cond, n_times):
+    # 700 nodes: node state in registers, x in shared memory; 1000 nodes of
+    # in-degree up to 48: the tables leave no room for x, which stays in global
+    # memory; 2900 nodes: node state in shared memory (12 nodes per thread)
+    w = synth.random_network(seed, n_nodes, lam=lam, cap=cap, n_cond=n_cond, n_times=n_times,
+                             obs_frac=0.3)
     p = Problem(w, ctx)
     n = 300                                     # more chains than resident blocks: chunked
     R.rn_init_chains(ctx, p.id, n, 5)
