@@ -207,18 +207,7 @@ struct BlockPath {
                     int o = 0;
                     for (int k = 0; k < npl; ++k) {
                         const int D4 = groups4(net.D[k]);
-                        uint32_t acc = kH - 0x04040404u * (uint32_t)D4;
-                        const uint32_t *lw = lut + o * kBT + t;
-                        for (int d = 0; d < D4; d += 4) {
-                            uint32_t w[4], c[4];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) w[i] = lw[(d + i) * kBT];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
-                        }
+                        const uint32_t acc = gather_rows<kBT>(lut + o * kBT + t, D4, sm);
                         o += D4;
                         const uint32_t s4 = F(k, kF_S4, t);
                         const uint32_t tgt = (((acc - kB1) >> 7) & kB1) + (((acc - 2 * kB1) >> 7) & kB1);
@@ -494,20 +483,7 @@ struct BlockRegPath {
             o += groups4(net.D[k]);
         }
         auto gather = [&](int k) -> uint32_t {
-            const int D4 = groups4(net.D[k]);
-            uint32_t acc = kH - 0x04040404u * (uint32_t)D4;
-            const uint32_t *lw = lut + row0[k] * kBT + t;
-            for (int d = 0; d < D4; d += 4) {
-                uint32_t w[4], c[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) w[i] = lw[(d + i) * kBT];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
-#pragma unroll
-                for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
-            }
-            return acc;
+            return gather_rows<kBT>(lut + row0[k] * kBT + t, groups4(net.D[k]), sm);
         };
         const BlockSync<NPL> sync{bc, t & 31, t >> 5};
         return simulate_swar4_core<NPL, true, false, kBT>(u, m1, d2, net, sm, 0u, t, traj,

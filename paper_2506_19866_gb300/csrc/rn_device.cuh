@@ -241,6 +241,50 @@ __device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b)
 constexpr uint32_t kB1 = 0x01010101u;   // 1 in every byte
 constexpr uint32_t kH = 0x80808080u;    // top bit of every byte
 
+// Biased image bytes of one slot from its D4 = groups4(D) shared-memory table
+// rows at lw (row stride STRIDE words; word = code address | prmt selectors):
+// kH - 4 D4 per byte plus, per row, the source's state code picked into the
+// byte of each condition.  With PIPE the next group's four words are loaded
+// before the current group's codes are used, so that two groups are in flight
+// (measured faster with 8 nodes per lane, slower with 6).
+template <int STRIDE, bool PIPE = true>
+__device__ __forceinline__ uint32_t gather_rows(const uint32_t *lw, int D4, const uint8_t *sm)
+{
+    uint32_t acc = kH - 0x04040404u * (uint32_t)D4;
+    if constexpr (!PIPE) {
+        for (int d = 0; d < D4; d += 4) {
+            uint32_t w[4], c[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[i] = lw[(d + i) * STRIDE];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
+        }
+        return acc;
+    }
+    if (D4 == 0) return acc;
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i] = lw[i * STRIDE];
+    for (int d = 0; d < D4; d += 4) {
+        uint32_t c[4], wn[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
+        if (d + 4 < D4) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) wn[i] = lw[(d + 4 + i) * STRIDE];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = wn[i];
+    }
+    return acc;
+}
+
 template <int NPL>
 __device__ __forceinline__ void store_codes(uint8_t *p, const uint32_t (&code)[NPL])
 {

@@ -203,22 +203,8 @@ struct SmemPath {
                     uint32_t m01 = 0, m23 = 0;
                     int o = 0;
                     for (int k = 0; k < npl; ++k) {
-                        const int D = net.D[k];
-                        const int D4 = groups4(D);
-                        uint32_t acc = kH - 0x04040404u * (uint32_t)D4;
-                        const uint32_t *lw = lut + o * 32 + lane;
-                        // groups of 4 edges: four table words, then four codes,
-                        // then the sums, so that the loads overlap
-                        for (int d = 0; d < D4; d += 4) {
-                            uint32_t w[4], c[4];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) w[i] = lw[(d + i) * 32];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i)
-                                c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
-                        }
+                        const int D4 = groups4(net.D[k]);
+                        const uint32_t acc = gather_rows<32>(lut + o * 32 + lane, D4, sm);
                         o += D4;
                         const uint32_t s4 = F(k, kF_S4, lane);
                         const uint32_t tgt = (((acc - kB1) >> 7) & kB1) + (((acc - 2 * kB1) >> 7) & kB1);
@@ -398,20 +384,7 @@ struct SmemRegPath {
             o += groups4(net.D[k]);
         }
         auto gather = [&](int k) -> uint32_t {
-            const int D4 = groups4(net.D[k]);
-            uint32_t acc = kH - 0x04040404u * (uint32_t)D4;
-            const uint32_t *lw = lut + row0[k] * 32 + lane;
-            for (int d = 0; d < D4; d += 4) {
-                uint32_t w[4], c[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) w[i] = lw[(d + i) * 32];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
-#pragma unroll
-                for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
-            }
-            return acc;
+            return gather_rows<32, (NPL > 6)>(lut + row0[k] * 32 + lane, groups4(net.D[k]), sm);
         };
         if (limit == INT32_MAX)
             return simulate_swar4_core<NPL, true, false>(u, m1, d2, net, sm, codes, lane, traj,
