@@ -79,7 +79,12 @@ typedef struct {
      * full simulation.  Networks above 512 nodes and the batched launch
      * (see rn_batch_config) simulate in full. */
     int32_t early_reject;
-    int32_t reserved;   /* 0 */
+    /* Grouped level synchronisation (the group-wise reduction that Section 4.5
+     * proposes in place of one reduction over all threads): with global_sync,
+     * chains k*sync_group .. (k+1)*sync_group - 1 form group k (the last group
+     * may be shorter), and the level-end argmin and broadcast run within each
+     * group.  0 means one group of all the network's chains. */
+    int32_t sync_group;
 } rn_schedule;
 
 /* Create a context on CUDA device `device`.  `stream` is a cudaStream_t the

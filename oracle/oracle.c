@@ -443,6 +443,7 @@ int32_t orc_anneal(const orc_net *net, const orc_tc *tc, const orc_schedule *sch
     const int64_t n_iter = sched->iters_per_level;
     if (n_iter <= 0 || n_chains < 0 || sweeps < 0 || g0 < 0) return ORC_EINVAL;
     if (sched->global_sync && chain_ids) return ORC_EINVAL;
+    if (sched->sync_group < 0) return ORC_EINVAL;
     int64_t level = g0 / n_iter;
     double T = orc_level_temperature(sched->T0, sched->alpha, level);
 
@@ -485,13 +486,19 @@ int32_t orc_anneal(const orc_net *net, const orc_tc *tc, const orc_schedule *sch
             }
         }
         if (sched->global_sync && (g + 1) % n_iter == 0 && n_chains > 0) {
-            int32_t b = 0;
-            for (int32_t k = 1; k < n_chains; k++)
-                if (st->d_best[k] < st->d_best[b]) b = k;
-            for (int32_t k = 0; k < n_chains; k++) {
-                if (k == b) continue;
-                memcpy(st->x_best + (size_t)k * P, st->x_best + (size_t)b * P, (size_t)P);
-                st->d_best[k] = st->d_best[b];
+            /* one argmin over all chains, or one per group of sync_group
+             * consecutive chains (Section 4.5) */
+            const int32_t G = sched->sync_group > 0 ? sched->sync_group : n_chains;
+            for (int32_t first = 0; first < n_chains; first += G) {
+                const int32_t end = first + G < n_chains ? first + G : n_chains;
+                int32_t b = first;
+                for (int32_t k = first + 1; k < end; k++)
+                    if (st->d_best[k] < st->d_best[b]) b = k;
+                for (int32_t k = first; k < end; k++) {
+                    if (k == b) continue;
+                    memcpy(st->x_best + (size_t)k * P, st->x_best + (size_t)b * P, (size_t)P);
+                    st->d_best[k] = st->d_best[b];
+                }
             }
         }
     }

@@ -51,6 +51,8 @@ typedef struct {
     int64_t iters_per_level;    /* proposals per temperature level */
     int32_t reset_to_best;      /* Table 1: each level restarts from x_best */
     int32_t global_sync;        /* Table 1: argmin over chains + broadcast */
+    int32_t sync_group;         /* Section 4.5: argmin within groups of this many
+                                   consecutive chains (0: one group of all) */
 } orc_schedule;
 
 typedef struct {

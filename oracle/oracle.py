@@ -47,7 +47,7 @@ class _TC(ctypes.Structure):
 class _Sched(ctypes.Structure):
     _fields_ = [("T0", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("iters_per_level", ctypes.c_int64), ("reset_to_best", ctypes.c_int32),
-                ("global_sync", ctypes.c_int32)]
+                ("global_sync", ctypes.c_int32), ("sync_group", ctypes.c_int32)]
 
 
 class _Chains(ctypes.Structure):
@@ -230,12 +230,14 @@ def init_chains(net, seed, n_chains, chain_ids=None):
 
 
 class Schedule:
-    def __init__(self, T0, alpha, iters_per_level=1, reset_to_best=False, global_sync=False):
+    def __init__(self, T0, alpha, iters_per_level=1, reset_to_best=False, global_sync=False,
+                 sync_group=0):
         self.T0, self.alpha = float(T0), float(alpha)
         self.iters_per_level = int(iters_per_level)
         self.reset_to_best, self.global_sync = bool(reset_to_best), bool(global_sync)
+        self.sync_group = int(sync_group)
         self.s = _Sched(self.T0, self.alpha, self.iters_per_level, int(self.reset_to_best),
-                        int(self.global_sync))
+                        int(self.global_sync), self.sync_group)
 
 
 class Chains:

@@ -1008,6 +1008,7 @@ int rn_anneal(rn_ctx *ctx, const rn_schedule *s, int64_t sweeps)
     if (!s) return fail(ctx, RN_EINVAL, "schedule is NULL");
     if (sweeps < 0) return fail(ctx, RN_EINVAL, "sweeps must be >= 0");
     if (s->iters_per_level < 1) return fail(ctx, RN_EINVAL, "iters_per_level must be >= 1");
+    if (s->sync_group < 0) return fail(ctx, RN_EINVAL, "sync_group must be >= 0");
     if (!(s->T0 > 0.0) || !(s->alpha > 0.0) || !std::isfinite(s->T0) || !std::isfinite(s->alpha))
         return fail(ctx, RN_EINVAL, "T0 and alpha must be positive");
     bool any = false;
@@ -1092,7 +1093,10 @@ int rn_anneal(rn_ctx *ctx, const rn_schedule *s, int64_t sweeps)
             if (e != cudaSuccess) return cuda_fail(ctx, e, "anneal kernel");
             ctx->launches += 1;
             if (s->global_sync && seg_end % iters == 0) {
-                e = launch_level_sync(ch, ctx->winner.p, ctx->stream);
+                // one winner per group of sync_group chains (one group: 0)
+                const int32_t G = s->sync_group > 0 ? s->sync_group : ch.n;
+                RN_CUDA(ctx, ctx->winner.reserve((size_t)((ch.n + G - 1) / G)));
+                e = launch_level_sync(ch, ctx->winner.p, s->sync_group, ctx->stream);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "level sync kernels");
                 ctx->launches += 2;
             }

@@ -88,11 +88,15 @@ __global__ void init_kernel(DevNet net, DevChains ch, int32_t *status)
 
 // Table 1, end of a level: the lowest delta_best over the chains (lowest chain
 // index on ties).  One block.
-__global__ void argmin_kernel(const int32_t *__restrict__ d_best, int32_t n, int32_t *out)
+__global__ void argmin_kernel(const int32_t *__restrict__ d_best, int32_t n, int32_t group,
+                              int32_t *out)
 {
+    // block b: the chains of group b, [b * group, min(n, (b + 1) * group))
     __shared__ unsigned long long best[32];
     unsigned long long b = ~0ull;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int first = blockIdx.x * group;
+    const int end = min(n, first + group);
+    for (int k = first + threadIdx.x; k < end; k += blockDim.x) {
         const unsigned long long key =
             ((unsigned long long)(uint32_t)d_best[k] << 32) | (uint32_t)k;
         b = min(b, key);
@@ -103,18 +107,19 @@ __global__ void argmin_kernel(const int32_t *__restrict__ d_best, int32_t n, int
     if (threadIdx.x < 32) {
         b = threadIdx.x < (blockDim.x >> 5) ? best[threadIdx.x] : ~0ull;
         for (int o = 16; o > 0; o >>= 1) b = min(b, __shfl_xor_sync(kFull, b, o));
-        if (threadIdx.x == 0) *out = (int32_t)(uint32_t)b;
+        if (threadIdx.x == 0) out[blockIdx.x] = (int32_t)(uint32_t)b;
     }
 }
 
-// ... and its broadcast into every chain's x_best.
-__global__ void broadcast_kernel(DevChains ch, const int32_t *win)
+// ... and its broadcast into every chain's x_best (from its group's winner).
+__global__ void broadcast_kernel(DevChains ch, const int32_t *win, int32_t group)
 {
-    const int w = *win;
     const int rows_per_block = blockDim.x / 32;
     const int lane = threadIdx.x & 31;
     const int chain = blockIdx.x * rows_per_block + (threadIdx.x >> 5);
-    if (chain >= ch.n || chain == w) return;
+    if (chain >= ch.n) return;
+    const int w = win[chain / group];
+    if (chain == w) return;
     warp_copy16(ch.x_best + (size_t)chain * ch.pstride, ch.x_best + (size_t)w * ch.pstride,
                 ch.pstride, lane);
     if (lane == 0) ch.d_best[chain] = ch.d_best[w];
@@ -272,10 +277,14 @@ cudaError_t launch_init(const DevNet &net, const DevChains &ch, int32_t *status,
     return cudaGetLastError();
 }
 
-cudaError_t launch_level_sync(const DevChains &ch, int32_t *winner, cudaStream_t st)
+cudaError_t launch_level_sync(const DevChains &ch, int32_t *winner, int32_t group,
+                              cudaStream_t st)
 {
-    argmin_kernel<<<1, 1024, 0, st>>>(ch.d_best, ch.n, winner);
-    broadcast_kernel<<<(ch.n + 7) / 8, 256, 0, st>>>(ch, winner);
+    const int G = group > 0 && group < ch.n ? group : ch.n;
+    const int groups = (ch.n + G - 1) / G;
+    const int threads = G >= 1024 ? 1024 : ((G + 31) / 32) * 32;
+    argmin_kernel<<<groups, threads, 0, st>>>(ch.d_best, ch.n, G, winner);
+    broadcast_kernel<<<(ch.n + 7) / 8, 256, 0, st>>>(ch, winner, G);
     return cudaGetLastError();
 }
 

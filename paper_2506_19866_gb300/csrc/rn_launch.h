@@ -52,7 +52,11 @@ cudaError_t launch_evaluate_block(const DevNet &net, const int8_t *X, int64_t xs
                                   cudaStream_t st);
 cudaError_t launch_anneal_block(const DevNet &net, const DevChains &ch, const DevSched &sc,
                                 int sm_count, cudaStream_t st);
-cudaError_t launch_level_sync(const DevChains &ch, int32_t *winner, cudaStream_t st);
+// Level-end argmin of d_best and broadcast of the winner's x_best, within groups
+// of `group` consecutive chains (0: one group of all chains); winner holds one
+// entry per group.
+cudaError_t launch_level_sync(const DevChains &ch, int32_t *winner, int32_t group,
+                              cudaStream_t st);
 
 // Many networks in one persistent launch (rn_batch.cu).
 struct DevBatch {

@@ -30,7 +30,7 @@ class rn_schedule(ctypes.Structure):
     _fields_ = [("T0", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("iters_per_level", ctypes.c_int64), ("reset_to_best", ctypes.c_int32),
                 ("global_sync", ctypes.c_int32), ("early_reject", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("sync_group", ctypes.c_int32)]
 
 
 SIGNATURES = {
@@ -151,9 +151,9 @@ def rn_init_chains(ctx, net, n_chains, seed, x0=None):
 
 
 def schedule(T0, alpha, iters_per_level=1, reset_to_best=False, global_sync=False,
-             early_reject=False):
+             early_reject=False, sync_group=0):
     return rn_schedule(float(T0), float(alpha), int(iters_per_level), int(bool(reset_to_best)),
-                       int(bool(global_sync)), int(bool(early_reject)), 0)
+                       int(bool(global_sync)), int(bool(early_reject)), int(sync_group))
 
 
 def rn_anneal(ctx, sched: rn_schedule, sweeps):

@@ -79,18 +79,21 @@ def test_anneal_block_chains_match_oracle(ctx, seed, n_nodes, lam, cap, n_cond, 
     _compare(st, ch, ids)
 
 
-def test_anneal_block_paper_mode(ctx):
-    # reset to x_best at each level start and the global argmin at level end
+@pytest.mark.parametrize("group", [0, 16])
+def test_anneal_block_paper_mode(ctx, group):
+    # reset to x_best at each level start and the argmin at level end, over all
+    # chains or within groups of 16 (the last of 8)
     w = synth.random_network(62, 600, lam=4.0, cap=20, n_cond=2, n_times=6, obs_frac=0.4)
     p = Problem(w, ctx)
     n = 40
     R.rn_init_chains(ctx, p.id, n, 9)
-    sched = R.schedule(2.0, 0.9, iters_per_level=5, reset_to_best=True, global_sync=True)
+    sched = R.schedule(2.0, 0.9, iters_per_level=5, reset_to_best=True, global_sync=True,
+                       sync_group=group)
     R.rn_anneal(ctx, sched, 15)
     st = R.rn_get_chain_state(ctx, p.id, n)
     ids = list(range(n))
-    ch = O.start_chains(p.net, p.tc, 9, n)      # the global argmin needs every chain
-    O.anneal(p.net, p.tc, O.Schedule(2.0, 0.9, 5, True, True), 9, ch, 0, 15)
+    ch = O.start_chains(p.net, p.tc, 9, n)      # the argmin needs every chain
+    O.anneal(p.net, p.tc, O.Schedule(2.0, 0.9, 5, True, True, sync_group=group), 9, ch, 0, 15)
     _compare(st, ch, ids)
 
 

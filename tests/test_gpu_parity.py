@@ -183,6 +183,24 @@ def test_anneal_paper_mode(ctx):
     _compare(st, ch, list(range(n)))
 
 
+@pytest.mark.parametrize("group", [1, 6, 40])
+def test_anneal_paper_mode_grouped(ctx, group):
+    # level-end argmin within groups of consecutive chains (Section 4.5); 40
+    # chains in groups of 6 leave a last group of 4
+    w = synth.make("hpg_9n_25e")
+    p = Problem(w, ctx)
+    n = 40
+    R.rn_init_chains(ctx, p.id, n, 78)
+    sched = R.schedule(50.0, 0.9, iters_per_level=7, reset_to_best=True, global_sync=True,
+                       sync_group=group)
+    R.rn_anneal(ctx, sched, 25)
+    R.rn_anneal(ctx, sched, 24)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    ch = _oracle_run(p, 78, n, O.Schedule(50.0, 0.9, 7, True, True, sync_group=group), 0, 49)
+    _compare(st, ch, list(range(n)))
+    np.testing.assert_array_equal(st["d_best"], ch.d_best)
+
+
 def test_checkpoint_resume(ctx):
     w = synth.make("mtb_63n_178e")
     p = Problem(w, ctx)

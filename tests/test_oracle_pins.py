@@ -342,3 +342,43 @@ def test_paper_mode_levels():
     # sync requires every chain
     with pytest.raises(RuntimeError):
         O.anneal(net, tc, sched, 2, ch, 30, 10, chain_ids=[0, 1, 2, 3, 4])
+
+
+def test_grouped_level_sync():
+    # Section 4.5's group-wise reduction: the level-end argmin runs within groups
+    # of consecutive chains.  Within a level the chains are independent, so one
+    # level with groups of 3 over 7 chains ({0,1,2}, {3,4,5}, {6}) is the plain
+    # run followed by each group's argmin (lowest chain on ties) copied into the
+    # group's x_best.
+    w = synth.tiny(9, n_nodes=5, indeg=2)
+    net, tc, xs, _ = oracle_problem(w)
+    L, n = 12, 7
+    plain = O.start_chains(net, tc, 4, n)
+    O.anneal(net, tc, O.Schedule(6.0, 0.9, iters_per_level=L), 4, plain, 0, L)
+    grouped = O.start_chains(net, tc, 4, n)
+    O.anneal(net, tc, O.Schedule(6.0, 0.9, L, False, True, sync_group=3), 4, grouped, 0, L)
+    np.testing.assert_array_equal(grouped.x_cur, plain.x_cur)
+    np.testing.assert_array_equal(grouped.d_cur, plain.d_cur)
+    for first in range(0, n, 3):
+        rows = list(range(first, min(n, first + 3)))
+        b = rows[int(np.argmin(plain.d_best[rows]))]   # first index of the minimum
+        for k in rows:
+            np.testing.assert_array_equal(grouped.x_best[k], plain.x_best[b])
+            assert grouped.d_best[k] == plain.d_best[b]
+    assert len(set(plain.d_best.tolist())) > 1          # the groups had something to do
+    # groups of one chain: no exchange at all, over several levels with resets
+    a = O.start_chains(net, tc, 4, n)
+    O.anneal(net, tc, O.Schedule(6.0, 0.9, 5, True, True, sync_group=1), 4, a, 0, 40)
+    b = O.start_chains(net, tc, 4, n)
+    O.anneal(net, tc, O.Schedule(6.0, 0.9, 5, True, False), 4, b, 0, 40)
+    np.testing.assert_array_equal(a.x_best, b.x_best)
+    np.testing.assert_array_equal(a.x_cur, b.x_cur)
+    # one group of at least every chain: the global argmin
+    c = O.start_chains(net, tc, 4, n)
+    O.anneal(net, tc, O.Schedule(6.0, 0.9, 5, True, True, sync_group=n + 2), 4, c, 0, 40)
+    d = O.start_chains(net, tc, 4, n)
+    O.anneal(net, tc, O.Schedule(6.0, 0.9, 5, True, True), 4, d, 0, 40)
+    np.testing.assert_array_equal(c.x_best, d.x_best)
+    np.testing.assert_array_equal(c.x_cur, d.x_cur)
+    with pytest.raises(RuntimeError):
+        O.anneal(net, tc, O.Schedule(6.0, 0.9, 5, True, True, sync_group=-1), 4, d, 40, 5)
