@@ -65,8 +65,23 @@ def algorithmic_ops_per_eval(w):
 
 
 # DRAM bytes per annealing launch (read + write) from an ncu capture of the
-# current kernel: the chain state read once, independent of sweeps per launch.
-ANNEAL_TRAFFIC = {"n120_c8_t21": 9.31e6}
+# current kernel on the workload: the chain state read once (and, on the block
+# path, written back once) per launch, independent of sweeps per launch.
+ANNEAL_TRAFFIC = {"n120_c8_t21": 9.25e6}
+
+
+def block_path(w):
+    """Networks above 512 nodes or with an in-degree above 16 run on the block
+    path (a block of 256 threads per chain); the others on a warp per chain."""
+    return w.N > 512 or int(np.bincount(w.dst, minlength=w.N).max()) > 16
+
+
+def kernel_label(ws):
+    if len(ws) == 1:
+        return "anneal_block_kernel" if block_path(ws[0]) else "anneal_kernel"
+    n_blk = sum(block_path(w) for w in ws)
+    return ("anneal_batch_kernel" +
+            (f" + anneal_block_kernel ({n_blk} networks)" if n_blk else "") + ", whole step")
 
 L2_NOTE = ("working set (network tables + chain state) is L2-resident by design; L2 flushed "
            "with a 512 MiB write between timed steps, outside the step events")
@@ -366,10 +381,10 @@ def run_ours(args, rank, world, local_rank):
                 "peak": None if peak is None else peak / 1e12, "unit": "Tops/s",
                 "frac": None if peak is None else achieved / peak, "traffic": traffic,
                 "traffic_basis": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu "
-                                  "capture of this kernel (20 sweeps per launch): the chain "
-                                  "state read once per launch; everything else is L2-resident, "
-                                  "so it does not grow with sweeps per launch") if traffic else None,
-                "kernel": "anneal_batch_kernel" if len(ws) > 1 else "anneal_kernel",
+                                  "capture of this kernel on this workload: the chain state "
+                                  "moves once per launch; everything else is L2-resident, so it "
+                                  "does not grow with sweeps per launch") if traffic else None,
+                "kernel": kernel_label(ws),
                 "ops_per_eval": (algorithmic_ops_per_eval(ws[0]) if len(ws) == 1
                                  else "C (T-1) (2E + 12N) + 3 n_obs per network"),
                 "peak_basis": (f"{sm_count} SMs x {alu_per_clk:.1f} int32 ALU ops/clk/SM "

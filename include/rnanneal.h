@@ -218,18 +218,29 @@ int rn_launch_count(rn_ctx *ctx, int64_t *count);
  * every chain; the other networks with chains (one condition, or above 512
  * nodes) get their own launches in the same call.  Results are bit-identical
  * to annealing each network alone.  The first batched call tunes the launch on the real
- * batch (table path per network -- register tables or shared-memory tables --
- * and warps per block), timing each candidate for a few steps from the current
- * state, which is restored afterwards.  With the threshold tables cached by
- * rn_prepare_schedule, the launch is captured once in a CUDA graph and replayed.
- * This reports the configuration in use:
+ * batch (table path per network and warps per block), timing each candidate
+ * for a few steps from the current state, which is restored afterwards.
+ * Candidate c = 3 * w + p: table paths p = 0 register tables where they fit,
+ * shared-memory tables elsewhere; p = 1 the same with the hybrid path (table
+ * words in shared memory, node state in registers) for networks of 129-256
+ * nodes; p = 2 shared-memory tables for all; warps per block 4 (w = 0) or 2
+ * (w = 1).  With the threshold tables cached by rn_prepare_schedule, the
+ * launch is captured once in a CUDA graph and replayed.  This reports the
+ * configuration in use:
  *   info[0] networks in the batch (0: no batch yet)
  *   info[1] warps per block
- *   info[2] networks on the shared-memory table path
+ *   info[2] networks on a large warp region (shared-memory or hybrid tables)
  *   info[3] 1 if calls replay a CUDA graph
- *   trial_ms[4] (may be NULL) milliseconds of the tuning candidates
- *   (register tables where they fit / shared memory for all) x (4 / 2 warps). */
-int rn_batch_config(rn_ctx *ctx, int32_t info[4], double trial_ms[4]);
+ *   info[4] networks on the hybrid path
+ *   info[5] the candidate in use (-1: not tuned yet)
+ *   trial_ms[6] (may be NULL) milliseconds of the candidates' trials (0 when
+ *   the candidate was pinned by rn_batch_tune). */
+int rn_batch_config(rn_ctx *ctx, int32_t info[6], double trial_ms[6]);
+
+/* Pin the batched launch to candidate `config` (0 .. 5, see rn_batch_config)
+ * instead of timing the candidates, or return to autotuning with -1.  Takes
+ * effect at the next batched rn_anneal call.  RN_EINVAL outside -1 .. 5. */
+int rn_batch_tune(rn_ctx *ctx, int32_t config);
 
 /* For callers that cannot let a library allocate device memory -- an
  * application that owns every byte of the GPU through its own memory pool or

@@ -580,8 +580,31 @@ int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
         }
         return RN_OK;
     };
-    const std::vector<int32_t> best_fit = B.host_path;
-    std::vector<int32_t> all_smem(B.host_path.size(), 0);
+    // candidate c: table paths (c % 3: register tables where they fit and
+    // shared-memory tables elsewhere / the same with the hybrid path for 6 or 8
+    // nodes per lane / shared-memory tables for all) x warps per block (c / 3:
+    // 4 / 2)
+    std::vector<int32_t> best_fit(B.order.size(), 0), hybrid(B.order.size(), 0);
+    for (size_t b = 0; b < B.order.size(); ++b) {
+        const Network &n = *ctx->nets[(size_t)B.order[b]];
+        int drest = 0;
+        for (int k = 1; k < n.npl; ++k) drest = std::max(drest, n.D[k]);
+        best_fit[b] = batch_path_fits(n.npl, n.D[0], drest) ? n.npl : 0;
+        hybrid[b] = best_fit[b] == 0 && smemreg_layout(n.npl) ? n.npl : best_fit[b];
+    }
+    const std::vector<int32_t> all_smem(B.host_path.size(), 0);
+    auto apply = [&](int cfg) {
+        B.host_path = cfg % 3 == 0 ? best_fit : cfg % 3 == 1 ? hybrid : all_smem;
+        B.wpb = cfg / 3 == 0 ? 4 : 2;
+        B.cfg = cfg;
+    };
+    if (B.force >= 0) {
+        apply(B.force);
+        int rc = batch_region(ctx, B);
+        if (rc) return rc;
+        B.tuned = true;
+        return RN_OK;
+    }
     const int64_t trial = std::min<int64_t>(sweeps, 16);
     double best = 1e300;
     int best_cfg = 0;
@@ -589,9 +612,8 @@ int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
     RN_CUDA(ctx, cudaEventCreate(&e0));
     RN_CUDA(ctx, cudaEventCreate(&e1));
     int rc = copy_state(true);
-    for (int cfg = 0; cfg < 4 && !rc; ++cfg) {
-        B.host_path = (cfg & 1) ? all_smem : best_fit;
-        B.wpb = (cfg & 2) ? 2 : 4;
+    for (int cfg = 0; cfg < 6 && !rc; ++cfg) {
+        apply(cfg);
         if ((rc = batch_region(ctx, B))) break;
         DevSched sc = sc0;
         sc.g0 = 0;
@@ -616,8 +638,7 @@ int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
     if (rc) return rc;
     RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (int frc = check_device_flag(ctx)) return frc;
-    B.host_path = (best_cfg & 1) ? all_smem : best_fit;
-    B.wpb = (best_cfg & 2) ? 2 : 4;
+    apply(best_cfg);
     if ((rc = batch_region(ctx, B))) return rc;
     B.tuned = true;
     return RN_OK;
@@ -1154,20 +1175,36 @@ int rn_launch_count(rn_ctx *ctx, int64_t *count)
     return RN_OK;
 }
 
-int rn_batch_config(rn_ctx *ctx, int32_t info[4], double trial_ms[4])
+int rn_batch_config(rn_ctx *ctx, int32_t info[6], double trial_ms[6])
 {
     if (!ctx || !info) return RN_EINVAL;
     const BatchState &B = ctx->batch;
     const bool on = B.valid && B.gen == ctx->gen;
     info[0] = on ? (int32_t)B.order.size() : 0;
     info[1] = on ? B.wpb : 0;
-    int32_t shared = 0;
+    int32_t shared = 0, hybrid = 0;
     if (on)
-        for (int32_t p : B.host_path) shared += batch_shared_tables(p);
+        for (int32_t p : B.host_path) {
+            shared += batch_shared_tables(p);
+            hybrid += p > 4;
+        }
     info[2] = shared;
     info[3] = on && B.exec ? 1 : 0;
+    info[4] = hybrid;
+    info[5] = on && B.tuned ? B.cfg : -1;
     if (trial_ms)
-        for (int k = 0; k < 4; ++k) trial_ms[k] = B.tune_ms[k];
+        for (int k = 0; k < 6; ++k) trial_ms[k] = B.tune_ms[k];
+    return RN_OK;
+}
+
+int rn_batch_tune(rn_ctx *ctx, int32_t config)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    if (config < -1 || config > 5) return fail(ctx, RN_EINVAL, "config %d outside -1 .. 5", config);
+    ctx->batch.force = config;
+    ctx->batch.tuned = false;
+    ctx->batch.drop_graph();
     return RN_OK;
 }
 

@@ -24,9 +24,9 @@ namespace rn {
 
 // Table paths of a network in the batch: 1, 2, 4 = register tables, capacities
 // slot 0 up to 16 in-edges and the other slots up to 8; 0 = the shared-memory
-// path (any layout).  The hybrid path of single-network launches (6 or 8
-// nodes per lane, rn_smemreg.cu) measured slower inside the batched kernel
-// than the shared-memory path, so the batch does not use it.
+// path (any layout); 6, 8 = the hybrid path (table words in shared memory,
+// node state in registers) of 129-256-node networks.  Which of these a network
+// takes is chosen by the autotuner.
 constexpr int kBatchD0 = 16, kBatchD1 = 8;
 
 // Code region, then the per-warp copies of the item's DevNet and DevChains,
@@ -78,6 +78,23 @@ __device__ __noinline__ void chunk_smem(const DevNet &net, const DevChains &ch, 
     uint8_t *after = reinterpret_cast<uint8_t *>(P.node + net.npl * kF_N * 32);
     int8_t *xs = reinterpret_cast<int8_t *>(after);
     uint8_t *on = after + ch.pstride, *pi = on + round16((uint32_t)net.N);
+    run_chunk<decltype(P), false>(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, done_value,
+                                  lane);
+}
+
+template <int NPL>
+__device__ __noinline__ void chunk_smemreg(const DevNet &net, const DevChains &ch,
+                                           const DevSched &sc, uint8_t *sm, uint32_t codes,
+                                           uint8_t *region, int chain, int64_t g_lo, int64_t g_hi,
+                                           int32_t *flag, int done_value, int lane)
+{
+    SmemRegPath<NPL> P;
+    P.sm = sm;
+    P.codes = codes;
+    P.lut = reinterpret_cast<uint32_t *>(region);
+    const uint32_t lw = smem_path_lut_words(net.D, net.npl);
+    int8_t *xs = reinterpret_cast<int8_t *>(region + 4u * lw);
+    uint8_t *on = reinterpret_cast<uint8_t *>(xs) + ch.pstride, *pi = on + round16((uint32_t)net.N);
     run_chunk<decltype(P), false>(P, net, ch, sc, chain, g_lo, g_hi, xs, on, pi, flag, done_value,
                                   lane);
 }
@@ -136,6 +153,12 @@ __global__ void __launch_bounds__(128, 3) anneal_batch_kernel(DevBatch b, DevSch
             chunk_reg<4, kBatchD0, kBatchD1>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi,
                                              flag, dv, lane);
             break;
+        case 6:
+            chunk_smemreg<6>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv, lane);
+            break;
+        case 8:
+            chunk_smemreg<8>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv, lane);
+            break;
         default:
             chunk_smem(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv, lane);
             break;
@@ -159,6 +182,8 @@ bool batch_path_fits(int npl, int D0, int Drest)
 
 uint32_t batch_region_bytes(int path, const int *D, int npl, int pstride, int N)
 {
+    if (path == 6 || path == 8)
+        return round16(smem_reg_warp_bytes(smem_path_lut_words(D, npl), pstride, N));
     return warp_region(path == 0, D, npl, pstride, N).bytes;
 }
 

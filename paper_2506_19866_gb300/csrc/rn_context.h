@@ -149,7 +149,9 @@ struct BatchState {
     int wpb = 4, grid = 0;
     bool tuned = false;
     bool g0_synced = false;           // device g0 equals the host step counters
-    double tune_ms[4] = {0, 0, 0, 0}; // trial times of the candidate configurations
+    double tune_ms[6] = {0, 0, 0, 0, 0, 0};   // trial times of the candidate configurations
+    int32_t force = -1;               // candidate pinned by rn_batch_tune (-1: autotune)
+    int32_t cfg = 0;                  // candidate in use
     // graph of [queue reset, batched kernel, step advance]
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;

@@ -76,7 +76,9 @@ struct DevBatch {
 
 bool batch_path_fits(int npl, int D0, int Drest);
 // Shared-table networks (path 0) run on the large-region warps.
-inline bool batch_shared_tables(int path) { return path == 0; }
+// Table paths of a batched network: 1, 2, 4 register tables (small warp
+// region); 0 shared-memory tables, 6, 8 the hybrid layouts (large region).
+inline bool batch_shared_tables(int path) { return path == 0 || path > 4; }
 uint32_t batch_region_bytes(int path, const int *D, int npl, int pstride, int N);
 // Block shared memory of a configuration, and the resident grid it allows.
 size_t batch_smem_bytes(int wpb, int large, uint32_t region_big, uint32_t region_small);

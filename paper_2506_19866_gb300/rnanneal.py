@@ -51,6 +51,7 @@ SIGNATURES = {
     "rn_prepare_schedule": (_c_int, [_vp, ctypes.POINTER(rn_schedule), _c_i64]),
     "rn_launch_count": (_c_int, [_vp, _vp]),
     "rn_batch_config": (_c_int, [_vp, _vp, _vp]),
+    "rn_batch_tune": (_c_int, [_vp, _c_i32]),
     "rn_level_sync_noalloc": (_c_int, [_vp, _vp, _c_i32, _c_i64, _c_i32, _vp]),
     "rn_mlp_create": (_c_int, [_vp, _c_i32, _c_i32, _c_i32, _c_i64, _vp, _vp]),
     "rn_mlp_set_weights": (_c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp, ctypes.c_float]),
@@ -227,12 +228,19 @@ def rn_launch_count(ctx):
 
 
 def rn_batch_config(ctx):
-    """(networks, warps per block, shared-memory-path networks, graph replay, trial ms)."""
-    info = np.zeros(4, np.int32)
-    ms = np.zeros(4, np.float64)
+    """Networks, warps per block, large-region (shared-memory or hybrid) networks,
+    graph replay, hybrid networks, candidate in use, trial ms of the candidates."""
+    info = np.zeros(6, np.int32)
+    ms = np.zeros(6, np.float64)
     _check(ctx, load_library().rn_batch_config(ctx, _p(info), _p(ms)))
     return dict(networks=int(info[0]), warps_per_block=int(info[1]),
-                shared_path_networks=int(info[2]), graph=bool(info[3]), trial_ms=ms.tolist())
+                shared_path_networks=int(info[2]), graph=bool(info[3]),
+                hybrid_networks=int(info[4]), config=int(info[5]), trial_ms=ms.tolist())
+
+
+def rn_batch_tune(ctx, config):
+    """Pin the batched launch to candidate 0..5, or autotune again with -1."""
+    _check(ctx, load_library().rn_batch_tune(ctx, int(config)))
 
 
 def rn_level_sync_noalloc(x_best_dev, d_best_dev, n_chains, row_bytes, n_params, stream=None):

@@ -18,7 +18,9 @@ def _batch():
     # one more network above 128 nodes (shared-memory tables) and a tiny one
     extra = synth.make_batch(n_nets=2, total_chains=90, seed=3, n_min=200, n_max=260)
     small = synth.make_batch(n_nets=1, total_chains=40, seed=4, n_min=10, n_max=12)
-    nets = nets + extra + small
+    # and one of 129-192 nodes (6 nodes per lane on the hybrid path)
+    mid = synth.make_batch(n_nets=1, total_chains=60, seed=5, n_min=140, n_max=180)
+    nets = nets + extra + small + mid
     sizes = [w.N for w in nets]
     assert min(sizes) <= 32 and max(sizes) > 128
     return nets
@@ -28,7 +30,10 @@ def _state_all(ctx, probs, nets):
     return [R.rn_get_chain_state(ctx, p.id, w.n_chains) for p, w in zip(probs, nets)]
 
 
-def test_batched_equals_separate_runs():
+@pytest.mark.parametrize("pin", [None, 0, 1, 2, 4])
+def test_batched_equals_separate_runs(pin):
+    # autotuned, and each table-path candidate pinned (1 and 4: the hybrid path
+    # for the networks of 129-256 nodes, with 4 and 2 warps per block)
     from paper_2506_19866_gb300 import build
     build.build()
     nets = _batch()
@@ -40,10 +45,19 @@ def test_batched_equals_separate_runs():
         for p, w in zip(probs, nets):
             R.rn_init_chains(ctx, p.id, w.n_chains, w.chain_seed)
         R.rn_prepare_schedule(ctx, sched, 4 * sweeps)
-        R.rn_anneal(ctx, sched, sweeps)           # tunes, then runs
+        if pin is not None:
+            R.rn_batch_tune(ctx, pin)
+        R.rn_anneal(ctx, sched, sweeps)           # tunes (or takes the pinned one), then runs
         cfg = R.rn_batch_config(ctx)
         assert cfg["networks"] == len(nets) and cfg["warps_per_block"] in (2, 4)
-        assert all(t > 0 for t in cfg["trial_ms"])
+        if pin is None:
+            assert all(t > 0 for t in cfg["trial_ms"]) and 0 <= cfg["config"] <= 5
+        else:
+            assert cfg["config"] == pin
+            assert cfg["warps_per_block"] == (4 if pin < 3 else 2)
+            n_hybrid = sum(128 < w.N <= 256 for w in nets)
+            assert n_hybrid >= 2
+            assert cfg["hybrid_networks"] == (n_hybrid if pin % 3 == 1 else 0)
         R.rn_anneal(ctx, sched, sweeps)           # graph capture and replay
         R.rn_anneal(ctx, sched, sweeps)
         assert R.rn_batch_config(ctx)["graph"]
