@@ -114,7 +114,7 @@ const char *rn_last_error(const rn_ctx *ctx);
  * rn_evaluate, rn_anneal -- return RN_EUNSUPPORTED otherwise):
  *   N <= 512, in-degree <= 16: a warp per chain (register tables up to 128
  *     nodes, shared-memory tables above);
- *   otherwise N <= 4096, in-degree <= 64: a block of 256 threads per chain
+ *   otherwise N <= 4096, in-degree <= 31: a block of 256 threads per chain
  *     (at least 2 nodes per thread), provided the
  *     chain's tables and node state fit one block's shared memory (227 KiB:
  *     52 bytes per node plus 1 KiB per table row, where nodes ranked by
@@ -136,7 +136,8 @@ int rn_load_network(rn_ctx *ctx, int32_t n_nodes, int32_t n_edges, const int32_t
  * The weight of an entry is observed * (|G| + 1), with G the difference of R
  * to the previous time point of the same condition where both are observed
  * and 0 otherwise (0 in row t0).  Replaces earlier data and invalidates the
- * chains' objective values (call rn_init_chains again). */
+ * chains' objective values (call rn_init_chains again).  RN_EINVAL if the
+ * largest possible score, sum of 2 W over the entries, reaches 2^30. */
 int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times,
                        const uint8_t *init, const uint8_t *knockout, const uint8_t *ref,
                        const uint8_t *observed);

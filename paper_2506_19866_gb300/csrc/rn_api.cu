@@ -180,8 +180,11 @@ void build_layout(Network &n)
     }
     n.dtab = 1;
     for (int k = 0; k < npl; ++k) n.dtab = std::max(n.dtab, n.D[k]);
-    // in-degree capacity: 16 in registers (warp paths), 64 on the block path
-    if (n.dtab > (L == 32 ? 16 : 64)) return;
+    // in-degree capacity: 16 in registers (warp paths), 31 on the block path.
+    // The byte-SIMD image holds 127 + K_i in one byte per condition, exact for
+    // |K_i| <= 127; each edge adds at most 4 in magnitude (Section 2.1:
+    // (s // t) w p with s, w <= 2), so 31 in-edges are the most a byte holds.
+    if (n.dtab > (L == 32 ? 16 : 31)) return;
     // the block path's shared memory must fit one block (227 KiB on sm_103)
     if (L != 32 && block_path_smem_bytes(n.D, npl, N) > 232448u) return;
     n.edge_id.assign((size_t)npl * n.dtab * L, -1);
@@ -271,7 +274,7 @@ int require_supported(rn_ctx *ctx, const Network &n)
     if (!n.supported)
         return fail(ctx, RN_EUNSUPPORTED,
                     "network with %d nodes and maximum in-degree %d is outside the compiled "
-                    "kernels (N <= 512 with in-degree <= 16, or N <= 4096 with in-degree <= 64)",
+                    "kernels (N <= 512 with in-degree <= 16, or N <= 4096 with in-degree <= 31)",
                     n.N, n.dtab);
     return RN_OK;
 }
@@ -878,6 +881,9 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
                 max_score += 2 * W[k];
                 ++n_obs;
             }
+    // scores are summed in quarter units in 32 bits on the device
+    if (max_score >= ((int64_t)1 << 30))
+        return fail(ctx, RN_EINVAL, "maximum score %lld exceeds 2^30", (long long)max_score);
     n->C = C;
     n->T = T;
     n->max_score = max_score;

@@ -210,7 +210,7 @@ struct BlockPath {
                         const uint32_t acc = gather_rows<kBT>(lut + o * kBT + t, D4, sm);
                         o += D4;
                         const uint32_t s4 = F(k, kF_S4, t);
-                        const uint32_t tgt = (((acc - kB1) >> 7) & kB1) + (((acc - 2 * kB1) >> 7) & kB1);
+                        const uint32_t tgt = target4(acc);
                         const uint32_t dp = tgt + 2 * kB1 - s4;
                         const uint32_t up = (dp + 0x7D7D7D7Du) & kH;
                         const uint32_t dn = ~(dp + 0x7E7E7E7Eu) & kH;
@@ -290,7 +290,7 @@ struct BlockPath {
 #pragma unroll
         for (int w = 0; w < kBW; ++w) total += bc->wsum[w];
         __syncthreads();
-        return (int32_t)total;
+        return (int32_t)(total >> 2);   // quarter units (entry_error)
     }
 };
 

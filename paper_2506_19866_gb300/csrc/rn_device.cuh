@@ -241,6 +241,18 @@ __device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b)
 constexpr uint32_t kB1 = 0x01010101u;   // 1 in every byte
 constexpr uint32_t kH = 0x80808080u;    // top bit of every byte
 
+// Biased image bytes: a gather starts every byte at kImage0 - 4 D4 and adds
+// 4 + f per table word, so a byte ends at 127 + K_i (in 63 .. 191 for D <= 16,
+// and the block path's larger in-degrees stay inside the byte too).  Then bit
+// 7 of a byte is [K >= 1] and bit 7 of the byte minus 1 is [K >= 2], and their
+// sum is clamp(K, 0, 2), the target of Section 2.2 (reading 3).
+constexpr uint32_t kImage0 = kH - kB1;
+
+__device__ __forceinline__ uint32_t target4(uint32_t a)
+{
+    return ((a >> 7) & kB1) + (((a - kB1) >> 7) & kB1);
+}
+
 // Biased image bytes of one slot from its D4 = groups4(D) shared-memory table
 // rows at lw (row stride STRIDE words; word = code address | prmt selectors):
 // kH - 4 D4 per byte plus, per row, the source's state code picked into the
@@ -250,7 +262,7 @@ constexpr uint32_t kH = 0x80808080u;    // top bit of every byte
 template <int STRIDE, bool PIPE = true>
 __device__ __forceinline__ uint32_t gather_rows(const uint32_t *lw, int D4, const uint8_t *sm)
 {
-    uint32_t acc = kH - 0x04040404u * (uint32_t)D4;
+    uint32_t acc = kImage0 - 0x04040404u * (uint32_t)D4;
     if constexpr (!PIPE) {
         for (int d = 0; d < D4; d += 4) {
             uint32_t w[4], c[4];
@@ -370,14 +382,16 @@ __device__ __forceinline__ uint32_t state_code(uint32_t s4)
 
 // Error of a node's four conditions at one time point (Section 2.3) from its
 // compact entry word (byte c = R_c | W_c << 2, W = 0 where unobserved), added
-// to acc: sum_c W_c |s_c - R_c|.  For s, R in 0..2, x = s ^ R equals |s - R|
-// except x = 3 (s, R = 1, 2), where |s - R| = 1 = x - 2; DP4A weights and sums
-// the four bytes.
+// to acc in quarter units: 4 sum_c W_c |s_c - R_c|.  For s, R in 0..2, x = s ^ R
+// equals |s - R| except x = 3 (s, R = 1, 2), where |s - R| = 1 = x - 2; DP4A
+// weights the four bytes by 4 W (the word's bits 2-3 in place) and sums them.
+// Scores are below 2^30 (checked when the time course is loaded), so the
+// quarter-unit sums fit 32 bits; y = sum >> 2.
 __device__ __forceinline__ uint32_t entry_error(uint32_t s4, uint32_t word, uint32_t acc)
 {
     const uint32_t x = s4 ^ (word & 0x03030303u);
     const uint32_t d = x - ((x & (x >> 1) & kB1) << 1);
-    return __dp4a(d, (word >> 2) & 0x03030303u, acc);
+    return __dp4a(d, word & 0x0c0c0c0cu, acc);
 }
 
 // Reductions and barriers of a chain simulated by one warp (simulate_swar4_core's
@@ -472,7 +486,7 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
 #pragma unroll
                 for (int k = 0; k < NPL; ++k) {
                     const uint32_t a = acc[k];
-                    const uint32_t tgt = (((a - kB1) >> 7) & kB1) + (((a - 2 * kB1) >> 7) & kB1);
+                    const uint32_t tgt = target4(a);
                     const uint32_t dp = tgt + 2 * kB1 - s4[k];
                     const uint32_t up = (dp + 0x7D7D7D7Du) & kH;
                     const uint32_t dn = ~(dp + 0x7E7E7E7Eu) & kH;
@@ -508,7 +522,7 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
             score += sync.template error<NPL, SMEM_FMT>(ahead, s4, code, net, g, tau, lane, ncg);
             if (EARLY && (tau & 3) == 3) {
                 // exact early rejection: the partial score never decreases
-                const uint32_t tot = __reduce_add_sync(kFull, score);
+                const uint32_t tot = __reduce_add_sync(kFull, score) >> 2;
                 if (tot > (uint32_t)limit) return (int32_t)tot;
             }
             if (traj) {
@@ -528,7 +542,7 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
         }
         sync.sync();
     }
-    return (int32_t)sync.sum(score);
+    return (int32_t)(sync.sum(score) >> 2);   // quarter units (entry_error)
 }
 
 // The register-table instance: table words in registers (rn_device.cuh format,
@@ -540,10 +554,10 @@ __device__ __forceinline__ int32_t simulate_swar4(const Regs<NPL, D0, D1> &R, co
 {
     auto gather = [&](int k) -> uint32_t {
         if (k == 0)
-            return image<D0>(R.lut0, net.D[0], base, sm, kH - 0x04040404u * groups4(net.D[0]));
+            return image<D0>(R.lut0, net.D[0], base, sm, kImage0 - 0x04040404u * groups4(net.D[0]));
         if constexpr (NPL > 1)
             return image<D1>(R.lutr[k - 1], net.D[k], base, sm,
-                             kH - 0x04040404u * groups4(net.D[k]));
+                             kImage0 - 0x04040404u * groups4(net.D[k]));
         return 0u;
     };
     // the early-rejection check lives only in the instance that needs it

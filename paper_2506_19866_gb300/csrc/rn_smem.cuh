@@ -207,7 +207,7 @@ struct SmemPath {
                         const uint32_t acc = gather_rows<32>(lut + o * 32 + lane, D4, sm);
                         o += D4;
                         const uint32_t s4 = F(k, kF_S4, lane);
-                        const uint32_t tgt = (((acc - kB1) >> 7) & kB1) + (((acc - 2 * kB1) >> 7) & kB1);
+                        const uint32_t tgt = target4(acc);
                         const uint32_t dp = tgt + 2 * kB1 - s4;
                         const uint32_t up = (dp + 0x7D7D7D7Du) & kH;
                         const uint32_t dn = ~(dp + 0x7E7E7E7Eu) & kH;
@@ -266,13 +266,13 @@ struct SmemPath {
                 }
                 if (EARLY && (tau & 3) == 3) {
                     // exact early rejection: the partial score never decreases
-                    const uint32_t tot = __reduce_add_sync(kFull, score);
+                    const uint32_t tot = __reduce_add_sync(kFull, score) >> 2;
                     if (tot > (uint32_t)limit) return (int32_t)tot;
                 }
             }
             __syncwarp();
         }
-        return (int32_t)__reduce_add_sync(kFull, score);
+        return (int32_t)(__reduce_add_sync(kFull, score) >> 2);   // quarter units
     }
 };
 

@@ -38,8 +38,8 @@ def _compare(st, ch, ids):
 
 
 @pytest.mark.parametrize("n_nodes,lam,cap,n_cond,n_times", [
-    (513, 4.0, 24, 3, 9), (777, 5.0, 24, 5, 7), (1300, 6.0, 24, 2, 12), (600, 20.0, 40, 2, 5),
-    (2900, 2.0, 8, 1, 4), (90, 24.0, 40, 3, 6)])
+    (513, 4.0, 24, 3, 9), (777, 5.0, 24, 5, 7), (1300, 6.0, 24, 2, 12), (600, 20.0, 31, 2, 5),
+    (2900, 2.0, 8, 1, 4), (90, 24.0, 31, 3, 6)])
 def test_evaluate_block_sizes(ctx, n_nodes, lam, cap, n_cond, n_times):
     # slot and thread boundaries of the block layout (2 .. 12 nodes per thread),
     # one to five conditions (a partial group of 4), in-degrees above the warp
@@ -58,10 +58,10 @@ def test_evaluate_block_sizes(ctx, n_nodes, lam, cap, n_cond, n_times):
 
 
 @pytest.mark.parametrize("seed,n_nodes,lam,cap,n_cond,n_times", [
-    (61, 700, 5.0, 20, 6, 8), (64, 1000, 36.0, 48, 2, 5), (65, 2900, 2.0, 8, 1, 4)])
+    (61, 700, 5.0, 20, 6, 8), (64, 1200, 27.0, 31, 2, 5), (65, 2900, 2.0, 8, 1, 4)])
 def test_anneal_block_chains_match_oracle(ctx, seed, n_nodes, lam, cap, n_cond, n_times):
-    # 700 nodes: node state in registers, x in shared memory; 1000 nodes of
-    # in-degree up to 48: the tables leave no room for x, which stays in global
+    # 700 nodes: node state in registers, x in shared memory; 1200 nodes of
+    # in-degree up to 31: the tables leave no room for x, which stays in global
     # memory; 2900 nodes: node state in shared memory (12 nodes per thread)
     w = synth.random_network(seed, n_nodes, lam=lam, cap=cap, n_cond=n_cond, n_times=n_times,
                              obs_frac=0.3)
@@ -77,6 +77,40 @@ def test_anneal_block_chains_match_oracle(ctx, seed, n_nodes, lam, cap, n_cond, 
     ch = O.start_chains(p.net, p.tc, 5, n, ids)
     O.anneal(p.net, p.tc, O.Schedule(3.0, 0.98), 5, ch, 0, 24, ids)
     _compare(st, ch, ids)
+
+
+def test_image_byte_limits(ctx):
+    # in-degree 31, the block path's largest: every in-edge of one node
+    # activating at full strength (w = 2, p = +1, t = 1, sources in state 2 at
+    # t0: K = +124 at the first update) and of another inhibiting (p = -1:
+    # K = -124), the extremes one byte of the image holds (evaluation does not
+    # require the constraints of Section 2.5.3); in-degree 32 is refused
+    w = synth.random_network(66, 600, lam=20.0, cap=31, n_cond=2, n_times=4, obs_frac=0.5)
+    indeg = np.bincount(w.dst, minlength=w.N)
+    hubs = np.flatnonzero(indeg == 31)[:2]
+    assert len(hubs) == 2
+    w.init = w.init.copy()
+    w.knockout = np.zeros_like(w.knockout)
+    for h in hubs:
+        w.init[:, w.src[w.dst == h]] = 2
+    p = Problem(w, ctx)
+    E = w.E
+    x = p.xs.copy()
+    for h, sign in zip(hubs, (1, -1)):
+        e = np.flatnonzero(w.dst == h)
+        x[e], x[E + e], x[2 * E + e] = 2, sign, 1
+    X = np.stack([x, p.xs])
+    score, traj = R.rn_evaluate(ctx, p.id, X, traj_shape=p.shape)
+    for k in range(X.shape[0]):
+        y, t = O.objective(p.net, p.tc, X[k], return_traj=True)
+        np.testing.assert_array_equal(traj[k], t, err_msg=f"vector {k}")
+        assert score[k] == y
+    over = synth.random_network(67, 600, lam=24.0, cap=32, n_cond=1, n_times=4, obs_frac=0.5)
+    assert np.bincount(over.dst, minlength=over.N).max() == 32
+    q = Problem(over, ctx)
+    with pytest.raises(R.RNError) as e:
+        R.rn_init_chains(ctx, q.id, 2, 0)
+    assert e.value.code == R.RN_EUNSUPPORTED
 
 
 @pytest.mark.parametrize("group", [0, 16])
