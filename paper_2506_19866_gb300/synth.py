@@ -224,10 +224,11 @@ def make(name: str) -> Workload:
                         sweeps=20_000, T0=10.0, alpha=plain_alpha(10.0, T_END_PLAIN, 20_000))
     if name == "n2000_c16_t33":
         # Scale-up network: 2000 nodes, in-degree Poisson(6) (floored at 1, capped
-        # at the block path's 64), 16 conditions, 32 update steps (T = 33 points
-        # with t0), 10% of entries observed, no noise; 16384 chains.
+        # at the block path's 31, which this draw never reaches), 16 conditions,
+        # 32 update steps (T = 33 points with t0), 10% of entries observed, no
+        # noise; 16384 chains.
         rng = np.random.default_rng(1005)
-        src, dst = random_digraph(2000, _poisson_indegree(2000, 6.0, 64, rng), rng)
+        src, dst = random_digraph(2000, _poisson_indegree(2000, 6.0, 31, rng), rng)
         fast = speed_classes(2000, rng)
         init, ko = conditions(2000, 16, rng)
         obs = bernoulli_mask(16, 33, 2000, 0.1, np.random.default_rng(3005))
