@@ -67,7 +67,7 @@ def algorithmic_ops_per_eval(w):
 # DRAM bytes per annealing launch (read + write) from an ncu capture of the
 # current kernel on the workload: the chain state read once (and, on the block
 # path, written back once) per launch, independent of sweeps per launch.
-ANNEAL_TRAFFIC = {"n120_c8_t21": 9.25e6}
+ANNEAL_TRAFFIC = {"n120_c8_t21": 9.25e6, "n2000_c16_t33": 1.45e9}
 
 
 def block_path(w):
@@ -381,9 +381,10 @@ def run_ours(args, rank, world, local_rank):
                 "peak": None if peak is None else peak / 1e12, "unit": "Tops/s",
                 "frac": None if peak is None else achieved / peak, "traffic": traffic,
                 "traffic_basis": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu "
-                                  "capture of this kernel on this workload: the chain state "
-                                  "moves once per launch; everything else is L2-resident, so it "
-                                  "does not grow with sweeps per launch") if traffic else None,
+                                  "capture of this kernel on this workload (n120_c8_t21 at 20 "
+                                  "sweeps per launch, n2000_c16_t33 at 2): the chain state moves "
+                                  "once per launch and the tables stay in L2, so it does not grow "
+                                  "with sweeps per launch") if traffic else None,
                 "kernel": kernel_label(ws),
                 "ops_per_eval": (algorithmic_ops_per_eval(ws[0]) if len(ws) == 1
                                  else "C (T-1) (2E + 12N) + 3 n_obs per network"),
