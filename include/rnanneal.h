@@ -198,6 +198,16 @@ int rn_evaluate_device(rn_ctx *ctx, int32_t net, int32_t n, const int8_t *x_dev,
 /* Number of parameters P = 3E + 3N of a network. */
 int rn_n_params(rn_ctx *ctx, int32_t net, int32_t *n_params);
 
+/* Update scheme of a network (Section 2.2 names three): 0 = priority updating
+ * (the paper's, the default): only the eligible nodes of maximum priority
+ * u * (tau - last) move at a step; 1 = synchronous updating: every eligible
+ * node moves at every step (eligibility, memory m and step size d as before).
+ * Under scheme 1 the speeds u have no effect, so GetCandidate no longer
+ * proposes them (they keep their values).  The network's chains must be
+ * initialised again (RN_ESTATE until rn_init_chains).  The asynchronous scheme
+ * (random nodes updated) is not provided.  RN_EINVAL for another scheme. */
+int rn_set_update_scheme(rn_ctx *ctx, int32_t net, int32_t scheme);
+
 /* Checkpoint / parity access to the chain state of a network (host buffers,
  * each may be NULL): x_cur, x_best [n][P]; d_cur, d_best [n];
  * counters [n][3] = accepted moves, accepted uphill moves (dE > 0), null

@@ -88,6 +88,15 @@ int32_t orc_domain(const orc_net *net, int32_t j, int8_t vals[6])
 
 static int is_frozen(const orc_net *net, int32_t j) { return net->frozen && net->frozen[j]; }
 
+/* Parameters GetCandidate may pick: the free ones, less the speeds u under the
+ * synchronous scheme, where they have no effect. */
+static int is_proposable(const orc_net *net, int32_t j)
+{
+    int32_t idx;
+    if (is_frozen(net, j)) return 0;
+    return !(net->sync && kind_of(net, j, &idx) == K_U);
+}
+
 /* ------------------------------------------------------------ generator -- */
 
 /* Philox4x32-10: ten rounds of the Philox S-box on a 4x32-bit counter with a
@@ -135,7 +144,9 @@ static void draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t 
  *   cnt_i = consecutive steps told to move in the same direction    (2.2, m)
  *   eligible iff cnt_i >= m_i + 1; priority u_i * (tau - last_i)    (2.2)
  * All eligible nodes at the maximum priority then move by
- * min(d_i, |tgt_i - s_i|) toward tgt_i at the end of the step. */
+ * min(d_i, |tgt_i - s_i|) toward tgt_i at the end of the step.  Under the
+ * synchronous scheme (net->sync) every eligible node has the same priority,
+ * so all of them move. */
 int32_t orc_simulate(const orc_net *net, const orc_tc *tc, const int8_t *x, int32_t c, uint8_t *S)
 {
     const int32_t N = net->n_nodes, E = net->n_edges, T = tc->n_times;
@@ -178,7 +189,7 @@ int32_t orc_simulate(const orc_net *net, const orc_tc *tc, const int8_t *x, int3
             dir[i] = drv;
             if (cnt[i] >= m[i] + 1) {
                 int32_t mag = diff > 0 ? diff : -diff;
-                prio[i] = u[i] * (tau - last[i]);
+                prio[i] = net->sync ? 1 : u[i] * (tau - last[i]);
                 move[i] = drv * (d[i] < mag ? d[i] : mag);
             }
             if (prio[i] > pmax) pmax = prio[i];
@@ -296,12 +307,12 @@ int32_t orc_propose(const orc_net *net, const int8_t *x, uint32_t r0, uint32_t r
 {
     const int32_t P = orc_n_params(net);
     int32_t n_free = 0;
-    for (int32_t j = 0; j < P; j++) n_free += !is_frozen(net, j);
+    for (int32_t j = 0; j < P; j++) n_free += is_proposable(net, j);
     *j_out = -1;
     if (n_free == 0) return 0;
     int32_t want = (int32_t)pick(r0, (uint32_t)n_free), j = -1;
     for (int32_t k = 0, seen = 0; k < P; k++) {
-        if (is_frozen(net, k)) continue;
+        if (!is_proposable(net, k)) continue;
         if (seen++ == want) { j = k; break; }
     }
     *j_out = j;

@@ -34,6 +34,10 @@ typedef struct {
     const uint8_t *fast;        /* [N] 1 = fast node (u in {10,11,12}) */
     const uint8_t *frozen;      /* [P] 1 = parameter is fixed, or NULL */
     const int8_t *frozen_val;   /* [P] value of each fixed parameter, or NULL */
+    int32_t sync;               /* 1: synchronous update scheme (Section 2.2's
+                                   alternative to priority updating): every
+                                   eligible node moves at every step; u has no
+                                   effect and is never proposed */
 } orc_net;
 
 typedef struct {

@@ -35,7 +35,7 @@ class _Net(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("n_edges", ctypes.c_int32),
                 ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
                 ("fast", ctypes.c_void_p), ("frozen", ctypes.c_void_p),
-                ("frozen_val", ctypes.c_void_p)]
+                ("frozen_val", ctypes.c_void_p), ("sync", ctypes.c_int32)]
 
 
 class _TC(ctypes.Structure):
@@ -111,7 +111,7 @@ def _ptr(a):
 class Network:
     """Topology + speed classes (+ optional fixed parameters) as the oracle sees them."""
 
-    def __init__(self, src, dst, fast, frozen=None, frozen_val=None):
+    def __init__(self, src, dst, fast, frozen=None, frozen_val=None, sync=False):
         self.src = np.ascontiguousarray(src, dtype=np.int32)
         self.dst = np.ascontiguousarray(dst, dtype=np.int32)
         self.fast = np.ascontiguousarray(fast, dtype=np.uint8)
@@ -121,8 +121,9 @@ class Network:
         self.frozen = None if frozen is None else np.ascontiguousarray(frozen, dtype=np.uint8)
         self.frozen_val = (None if frozen_val is None
                            else np.ascontiguousarray(frozen_val, dtype=np.int8))
+        self.sync = bool(sync)
         self.s = _Net(self.N, self.E, _ptr(self.src), _ptr(self.dst), _ptr(self.fast),
-                      _ptr(self.frozen), _ptr(self.frozen_val))
+                      _ptr(self.frozen), _ptr(self.frozen_val), int(self.sync))
 
 
 class Timecourse:

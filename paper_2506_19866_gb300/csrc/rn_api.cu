@@ -156,7 +156,8 @@ void build_layout(Network &n)
     }
     n.free_list.clear();
     for (int32_t j = 0; j < n.P; ++j)
-        if (!(n.has_frozen && n.frozen[(size_t)j])) n.free_list.push_back(j);
+        if (!(n.has_frozen && n.frozen[(size_t)j]) && !(n.sync && j >= 3 * E && j < 3 * E + N))
+            n.free_list.push_back(j);   // (u has no effect under the synchronous scheme)
 
     n.supported = false;
     if (n.npl == 0) return;
@@ -968,6 +969,26 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     n->cg = cg;
     ctx->gen++;
     n->G = G;
+    return RN_OK;
+}
+
+int rn_set_update_scheme(rn_ctx *ctx, int32_t net, int32_t scheme)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Network *n = get_net(ctx, net);
+    if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
+    if (scheme != 0 && scheme != 1) return fail(ctx, RN_EINVAL, "scheme %d is not 0 or 1", scheme);
+    n->sync = scheme == 1;
+    const int32_t N = n->N, E = n->E;
+    n->free_list.clear();
+    for (int32_t j = 0; j < n->P; ++j)
+        if (!(n->has_frozen && n->frozen[(size_t)j]) && !(n->sync && j >= 3 * E && j < 3 * E + N))
+            n->free_list.push_back(j);
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    RN_CUDA(ctx, n->d_free.upload(n->free_list));
+    n->chains_valid = false;
+    ctx->gen++;
     return RN_OK;
 }
 

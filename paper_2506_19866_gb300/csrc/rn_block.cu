@@ -135,7 +135,7 @@ struct BlockPath {
             const int i = net.q_node[t * npl + k];
             uint32_t u = 1, m1 = 1, d2 = 0;
             if (i >= 0) {
-                u = (uint32_t)X(3 * E + i);
+                u = net.sync ? 0u : (uint32_t)X(3 * E + i);
                 m1 = (uint32_t)X(3 * E + N + i) + 1u;
                 d2 = X(3 * E + 2 * N + i) == 2 ? 0xffffffffu : 0u;
             }
@@ -421,7 +421,7 @@ struct BlockRegPath {
                 lut[(o + d) * kBT + t] = 0x04040000u | (4u * (uint32_t)t);
             o += groups4(net.D[k]);
             const int i = net.q_node[t * NPL + k];
-            u[k] = i >= 0 ? X(3 * E + i) : 1;
+            u[k] = i >= 0 ? (net.sync ? 0 : X(3 * E + i)) : 1;
             m1[k] = i >= 0 ? X(3 * E + N + i) + 1 : 1;
             d2[k] = i >= 0 ? X(3 * E + 2 * N + i) == 2 : 0;
         }

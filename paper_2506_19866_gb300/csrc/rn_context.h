@@ -60,6 +60,7 @@ struct Network {
     std::vector<uint8_t> fast, frozen;
     std::vector<int8_t> frozen_val;
     bool has_frozen = false;
+    bool sync = false;                // synchronous update scheme (rn_set_update_scheme)
     // lane / slot layout
     int npl = 0, dtab = 0;
     int lanes = 32;                     // threads per chain: 32, or kBlockLanes above 512 nodes
@@ -98,7 +99,7 @@ struct Network {
         DevNet n{};
         n.N = N; n.E = E; n.P = P; n.n_free = (int32_t)free_list.size();
         n.C = C; n.T = T; n.G = G;
-        n.npl = npl; n.cg = cg; n.dtab = dtab; n.lanes = lanes;
+        n.npl = npl; n.cg = cg; n.dtab = dtab; n.lanes = lanes; n.sync = sync ? 1 : 0;
         for (int k = 0; k < kMaxSlots; ++k) n.D[k] = D[k];
         n.edge_id = d_edge_id.p; n.edge_q2 = d_edge_q2.p; n.edge_pos = d_edge_pos.p;
         n.node_q = d_node_q.p; n.q_node = d_q_node.p; n.src = d_src.p; n.dst = d_dst.p;

@@ -40,6 +40,7 @@ struct DevNet {
     int32_t C, T, G;                    // conditions, time points, condition groups
     int32_t npl, cg, dtab;              // nodes per lane, conditions per group, table stride
     int32_t lanes;                      // threads per chain: 32 (a warp) or kBlockLanes
+    int32_t sync;                       // 1: synchronous update (every eligible node moves)
     int32_t D[kMaxSlots];               // padded in-degree of each slot
     const int32_t *edge_id;             // [npl][dtab][32] edge index, or -1 - (code offset) for padding
     const uint8_t *edge_q2;             // [E] 2 * internal index of the edge's source
@@ -171,7 +172,7 @@ __device__ __forceinline__ void load_regs(Regs<NPL, D0, D1> &R, const DevNet &ne
     for (int k = 0; k < NPL; ++k) {
         const int i = net.q_node[lane * NPL + k];
         if (i >= 0) {
-            R.u[k] = x[3 * E + i];
+            R.u[k] = net.sync ? 0 : x[3 * E + i];   // synchronous: every priority 0
             R.m1[k] = x[3 * E + N + i] + 1;
             R.d2[k] = x[3 * E + 2 * N + i] == 2;
         } else {
@@ -590,7 +591,8 @@ __device__ __forceinline__ int32_t simulate_scalar(const Regs<NPL, D0, D1> &R, c
             for (int c = 0; c < CG; ++c) {
                 s[k][c] = (code[k] >> (4 * c)) & 0xf;
                 run[k][c] = 0;
-                ua[k][c] = ((outb >> (k * CG + c)) & 1u) ? kOutUA : R.u[k];
+                // synchronous scheme: u = 0 and every eligible node at priority 1
+                ua[k][c] = ((outb >> (k * CG + c)) & 1u) ? kOutUA : (R.u[k] | net.sync);
             }
         store_codes<NPL>(my_codes, code);
         int ncg = net.C - g * CG;
@@ -621,7 +623,7 @@ __device__ __forceinline__ int32_t simulate_scalar(const Regs<NPL, D0, D1> &R, c
                         const bool upd = pr[k] == pmax && pr[k] > 0;
                         s[k][c] = upd ? sn[k] : s[k][c];
                         run[k][c] = upd ? 0 : run[k][c];
-                        ua[k][c] = upd ? R.u[k] : ua[k][c] + R.u[k];
+                        ua[k][c] = upd ? (R.u[k] | net.sync) : ua[k][c] + R.u[k];
                     }
                 }
 #pragma unroll

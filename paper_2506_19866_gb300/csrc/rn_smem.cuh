@@ -115,7 +115,7 @@ struct SmemPath {
             const int i = net.q_node[lane * npl + k];
             uint32_t u = 1, m1 = 1, d2 = 0;
             if (i >= 0) {
-                u = (uint32_t)x[3 * E + i];
+                u = net.sync ? 0u : (uint32_t)x[3 * E + i];
                 m1 = (uint32_t)x[3 * E + N + i] + 1u;
                 d2 = x[3 * E + 2 * N + i] == 2 ? 0xffffffffu : 0u;
             }
@@ -326,7 +326,7 @@ struct SmemRegPath {
                 lut[(o + d) * 32 + lane] = 0x04040000u | (pad & 0xffffu);
             o += groups4(net.D[k]);
             const int i = net.q_node[lane * NPL + k];
-            u[k] = i >= 0 ? x[3 * E + i] : 1;
+            u[k] = i >= 0 ? (net.sync ? 0 : x[3 * E + i]) : 1;
             m1[k] = i >= 0 ? x[3 * E + N + i] + 1 : 1;
             d2[k] = i >= 0 ? x[3 * E + 2 * N + i] == 2 : 0;
         }

@@ -52,6 +52,7 @@ SIGNATURES = {
     "rn_launch_count": (_c_int, [_vp, _vp]),
     "rn_batch_config": (_c_int, [_vp, _vp, _vp]),
     "rn_batch_tune": (_c_int, [_vp, _c_i32]),
+    "rn_set_update_scheme": (_c_int, [_vp, _c_i32, _c_i32]),
     "rn_level_sync_noalloc": (_c_int, [_vp, _vp, _c_i32, _c_i64, _c_i32, _vp]),
     "rn_mlp_create": (_c_int, [_vp, _c_i32, _c_i32, _c_i32, _c_i64, _vp, _vp]),
     "rn_mlp_set_weights": (_c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp, ctypes.c_float]),
@@ -236,6 +237,11 @@ def rn_batch_config(ctx):
     return dict(networks=int(info[0]), warps_per_block=int(info[1]),
                 shared_path_networks=int(info[2]), graph=bool(info[3]),
                 hybrid_networks=int(info[4]), config=int(info[5]), trial_ms=ms.tolist())
+
+
+def rn_set_update_scheme(ctx, net, scheme):
+    """0: priority updating (default); 1: synchronous updating (Section 2.2)."""
+    _check(ctx, load_library().rn_set_update_scheme(ctx, int(net), int(scheme)))
 
 
 def rn_batch_tune(ctx, config):

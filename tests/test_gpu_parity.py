@@ -201,6 +201,60 @@ def test_anneal_paper_mode_grouped(ctx, group):
     np.testing.assert_array_equal(st["d_best"], ch.d_best)
 
 
+@pytest.mark.parametrize("n_nodes,n_cond", [(40, 1), (100, 6), (200, 5), (300, 4), (700, 3)])
+def test_synchronous_scheme(ctx, n_nodes, n_cond):
+    # Section 2.2's synchronous updating (every eligible node moves at every
+    # step) on the scalar single-condition path, the register tables, the hybrid
+    # path, the shared-memory tables and the block path: evaluated scores and
+    # trajectories, and annealing chains (u is not proposed), against the oracle
+    w = synth.random_network(80 + n_nodes, n_nodes, lam=4.0, cap=14, n_cond=n_cond, n_times=9,
+                             obs_frac=0.3)
+    p = Problem(w, ctx, sync=True)
+    X = np.concatenate([p.xs[None], random_vectors(p.net, 4, 17)])
+    score, traj = R.rn_evaluate(ctx, p.id, X, traj_shape=p.shape)
+    for k in range(X.shape[0]):
+        y, t = O.objective(p.net, p.tc, X[k], return_traj=True)
+        np.testing.assert_array_equal(traj[k], t, err_msg=f"vector {k}")
+        assert score[k] == y
+    n = 96
+    R.rn_init_chains(ctx, p.id, n, 6)
+    sched = R.schedule(4.0, 0.98)
+    R.rn_anneal(ctx, sched, 30)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    ids = [0, 1, 50, 95]
+    ch = _oracle_run(p, 6, n, O.Schedule(4.0, 0.98), 0, 30, ids)
+    _compare(st, ch, ids)
+    E, N = w.E, w.N
+    x0 = O.init_chains(p.net, 6, n)
+    np.testing.assert_array_equal(st["x_cur"][:, 3 * E:3 * E + N], x0[:, 3 * E:3 * E + N])
+
+
+def test_synchronous_scheme_in_batch(ctx):
+    # a synchronous and a priority network annealed in one batched launch, each
+    # against the oracle under its own scheme; switching back restores the
+    # priority scheme and its proposals
+    ws = [synth.random_network(91, 60, lam=4.0, cap=12, n_cond=4, n_times=8, obs_frac=0.3),
+          synth.random_network(92, 150, lam=4.0, cap=12, n_cond=5, n_times=8, obs_frac=0.3)]
+    probs = [Problem(ws[0], ctx, sync=True), Problem(ws[1], ctx)]
+    for p in probs:
+        R.rn_init_chains(ctx, p.id, 64, 8)
+    sched = R.schedule(4.0, 0.98)
+    R.rn_anneal(ctx, sched, 20)
+    assert R.rn_batch_config(ctx)["networks"] == 2
+    for p in probs:
+        st = R.rn_get_chain_state(ctx, p.id, 64)
+        ids = [0, 33, 63]
+        ch = _oracle_run(p, 8, 64, O.Schedule(4.0, 0.98), 0, 20, ids)
+        _compare(st, ch, ids)
+    R.rn_set_update_scheme(ctx, probs[0].id, 0)
+    with pytest.raises(R.RNError) as e:
+        R.rn_get_best(ctx, probs[0].id)
+    assert e.value.code == R.RN_ESTATE
+    with pytest.raises(R.RNError) as e:
+        R.rn_set_update_scheme(ctx, probs[0].id, 2)
+    assert e.value.code == R.RN_EINVAL
+
+
 def test_checkpoint_resume(ctx):
     w = synth.make("mtb_63n_178e")
     p = Problem(w, ctx)

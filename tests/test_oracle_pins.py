@@ -344,6 +344,44 @@ def test_paper_mode_levels():
         O.anneal(net, tc, sched, 2, ch, 30, 10, chain_ids=[0, 1, 2, 3, 4])
 
 
+def test_synchronous_scheme_closed_form():
+    # Section 2.2's synchronous updating with m = 0 and d = 2: every node that is
+    # not at its target moves there at once, so each step is the textbook
+    # synchronous map S(tau) = clamp(K(S(tau - 1)), 0, 2) node by node, with
+    # K_i = sum over in-edges of (s // t) w p (Section 2.1) and knocked-out
+    # nodes held at 0.  The priority scheme differs on the same vector.
+    w = synth.tiny(21, n_nodes=7, indeg=3, n_cond=3, n_times=9)
+    net_s = O.Network(w.src, w.dst, w.fast, sync=True)
+    net_p = O.Network(w.src, w.dst, w.fast)
+    E, N, C, T = w.E, w.N, w.C, w.T
+    tc = O.Timecourse(w.init, np.zeros((C, T, N), np.uint8), w.observed, w.knockout)
+    ko = np.zeros((C, N), bool) if w.knockout is None else w.knockout.astype(bool)
+    differs = False
+    for seed in range(6):
+        x = O.init_chain(net_s, 30 + seed, 0).copy()
+        x[3 * E + N:3 * E + 2 * N] = 0                  # m = 0
+        x[3 * E + 2 * N:] = 2                            # d = 2
+        _, S = O.objective(net_s, tc, x, return_traj=True)
+        wv, pv, tv = x[:E].astype(int), x[E:2 * E].astype(int), x[2 * E:3 * E].astype(int)
+        for c in range(C):
+            for tau in range(1, T):
+                s = S[c, tau - 1].astype(int)
+                K = np.zeros(N, int)
+                np.add.at(K, w.dst, (s[w.src] // tv) * wv * pv)
+                want = np.clip(K, 0, 2)
+                want[ko[c]] = 0
+                np.testing.assert_array_equal(S[c, tau], want, err_msg=f"seed {seed} c {c} t {tau}")
+        _, Sp = O.objective(net_p, tc, x, return_traj=True)
+        differs |= bool((Sp != S).any())
+    assert differs
+    # the speeds u have no effect, so they are never proposed
+    ch = O.start_chains(net_s, tc, 3, 6)
+    u0 = ch.x_cur[:, 3 * E:3 * E + N].copy()
+    O.anneal(net_s, tc, O.Schedule(5.0, 0.99), 3, ch, 0, 300)
+    np.testing.assert_array_equal(ch.x_cur[:, 3 * E:3 * E + N], u0)
+    assert (ch.n_accept > 0).all()
+
+
 def test_grouped_level_sync():
     # Section 4.5's group-wise reduction: the level-end argmin runs within groups
     # of consecutive chains.  Within a level the chains are independent, so one
