@@ -17,6 +17,7 @@
 // memory.  Work items (chunk, chain) come from the same queue scheme as the
 // warp kernels, with bounded waits.
 #include "rn_kernels.cuh"
+#include "rn_screen.h"
 
 namespace rn {
 namespace {
@@ -66,7 +67,9 @@ struct Bcast {
     int32_t ok;              // a candidate exists (or: the wait succeeded)
     int32_t j, kind, idx, cur, v;   // the candidate x_j: cur -> v (kind, index in its block)
     int32_t owner, pos, w, p, t, slot;   // owner thread and the changed table entry
+    int32_t sel[kMaxTop];    // a screened step's moves to simulate
 };
+static_assert(sizeof(Bcast) <= 256, "the broadcast area is 256 bytes of the layout");
 
 // Constraint counters of Section 2.5.3 from x (global through L2 when `cg`,
 // else shared memory).
@@ -727,6 +730,105 @@ __global__ void __launch_bounds__(kBT, 1) anneal_block_kernel(DevNet net, DevCha
     }
 }
 
+// Finish of a screened step (the learned proposal screen) for block-path
+// networks, a block per chain: warp 0 selects the moves to simulate (as the
+// warp paths do), each is simulated exactly on the chain's tables (change,
+// Simulate, undo), and the one of lowest exact score (first on ties) goes to
+// the Metropolis test of Table 1; an accepted move updates x_cur, delta_cur,
+// the best vector (strict improvement), the counters and A1.
+template <class Path, bool XS>
+__global__ void __launch_bounds__(kBT, 1) screen_finish_block_kernel(ScreenArgs a, DevSched sc)
+{
+    extern __shared__ __align__(256) uint8_t sm[];
+    const DevNet &net = a.net;
+    Path P = PathMaker<Path>::make(net, sm);
+    Bcast *bc = P.bc;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int E = net.E, N = net.N;
+    for (int c = blockIdx.x; c < a.ch.n; c += gridDim.x) {
+        const uint4 r = step_draw(a.ch, a.g, c, 0u);
+        if (warp == 0) {
+            int chosen[kMaxTop];
+            select_candidates(a, c, lane, r, chosen);
+            if (lane == 0)
+                for (int s = 0; s < kMaxTop; ++s) bc->sel[s] = chosen[s];
+        }
+        __syncthreads();
+        int chosen[kMaxTop];
+#pragma unroll
+        for (int s = 0; s < kMaxTop; ++s) chosen[s] = bc->sel[s];
+        int64_t *cnt = a.ch.cnt + 3 * (size_t)c;
+        if (chosen[0] < 0) {
+            if (t == 0) cnt[2] += 1;
+            __syncthreads();
+            continue;
+        }
+        int8_t *xg = a.ch.x_cur + (size_t)c * a.ch.pstride;
+        int8_t *xr = xg;
+        if constexpr (XS) {
+            xr = P.xs;
+            block_copy16<true, false>(xr, xg, a.ch.pstride, t);
+            __syncthreads();
+        }
+        P.load(net, xr, t, false);
+        __syncthreads();
+        int best = -1;
+        int32_t d = 0;
+#pragma unroll
+        for (int s = 0; s < kMaxTop; ++s) {
+            const int move = chosen[s];
+            if (move < 0) continue;
+            const int j = move >> 8, v = (int8_t)(move & 255);
+            int kind, idx, owner;
+            if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
+            else { const int q = j - 3 * E; kind = 3 + q / N; idx = q - (kind - 3) * N; }
+            if (kind < 3) {
+                const int pos = net.edge_pos[idx];
+                owner = pos >> 16;
+                int w = xr[idx], p = xr[E + idx], tt = xr[2 * E + idx];
+                if (kind == 0) w = v; else if (kind == 1) p = v; else tt = v;
+                P.change_edge(net, t, owner, pos, w, p, tt);
+            } else {
+                const int q = net.node_q[idx];
+                owner = q / P.npl;
+                P.change_node(t, owner, q - owner * P.npl, kind, v);
+            }
+            __syncthreads();
+            const int32_t ds = P.simulate(net, t, nullptr);
+            P.undo(t, owner);
+            __syncthreads();
+            if (best < 0 || ds < d) { best = move; d = ds; }
+        }
+        const int32_t d_cur = a.ch.d_cur[c], d_best = a.ch.d_best[c];
+        const int32_t dE = d - d_cur;
+        bool accept = dE <= 0;
+        if (!accept) {
+            const int64_t l = a.g / sc.iters - sc.level0;
+            if (dE <= sc.thr_len[l]) accept = r.z < __ldg(sc.thr + sc.thr_off[l] + dE - 1);
+        }
+        if (accept) {
+            const int j = best >> 8, v = (int8_t)(best & 255);
+            const int rn = a.row_base[j] + v, ro = a.row_base[j] + xr[j];
+            __syncthreads();
+            if (t == 0) {
+                xg[j] = (int8_t)v;
+                a.ch.d_cur[c] = d;
+                cnt[0] += 1;
+                cnt[1] += dE > 0;
+            }
+            __syncthreads();
+            if (d < d_best) {
+                block_copy16<true, true>(a.ch.x_best + (size_t)c * a.ch.pstride, xg, a.ch.pstride, t);
+                if (t == 0) a.ch.d_best[c] = d;
+            }
+            for (int h = t; h < a.H1; h += kBT)
+                a.A1[(size_t)c * a.H1 + h] += __bfloat162float(a.W1b[(size_t)rn * a.H1 + h]) -
+                                              __bfloat162float(a.W1b[(size_t)ro * a.H1 + h]);
+        }
+        __syncthreads();
+    }
+}
+
 cudaError_t smem_limit(int *limit)
 {
     int dev = 0;
@@ -814,7 +916,50 @@ cudaError_t anneal_block_t(const DevNet &net, const DevChains &ch, const DevSche
     return anneal_block_launch<Path, false>(net, ch, sc0, smem, sm_count, st);
 }
 
+template <class Path, bool XS>
+cudaError_t finish_block_launch(const ScreenArgs &a, const DevSched &sc, size_t smem,
+                                int sm_count, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(screen_finish_block_kernel<Path, XS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, screen_finish_block_kernel<Path, XS>,
+                                                      kBT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t cap = (int64_t)sm_count * per_sm;
+    const int grid = (int)(a.ch.n < cap ? a.ch.n : cap);
+    screen_finish_block_kernel<Path, XS><<<grid, kBT, smem, st>>>(a, sc);
+    return cudaGetLastError();
+}
+
+template <class Path>
+cudaError_t finish_block_t(const ScreenArgs &a, const DevSched &sc, int sm_count, cudaStream_t st)
+{
+    size_t smem = 0;
+    cudaError_t e = block_smem(a.net, &smem);
+    if (e != cudaSuccess) return e;
+    int limit = 0;
+    if ((e = smem_limit(&limit)) != cudaSuccess) return e;
+    const size_t with_x = block_layout(a.net.D, a.net.npl, a.net.N, (uint32_t)a.ch.pstride).bytes;
+    if (with_x <= (size_t)limit) return finish_block_launch<Path, true>(a, sc, with_x, sm_count, st);
+    return finish_block_launch<Path, false>(a, sc, smem, sm_count, st);
+}
+
 }  // namespace
+
+cudaError_t launch_finish_block(const ScreenArgs &a, const DevSched &sc, int sm_count,
+                                cudaStream_t st)
+{
+    switch (a.net.npl) {
+    case 2: return finish_block_t<BlockRegPath<2>>(a, sc, sm_count, st);
+    case 4: return finish_block_t<BlockRegPath<4>>(a, sc, sm_count, st);
+    case 6: return finish_block_t<BlockRegPath<6>>(a, sc, sm_count, st);
+    case 8: return finish_block_t<BlockRegPath<8>>(a, sc, sm_count, st);
+    default: return finish_block_t<BlockPath>(a, sc, sm_count, st);
+    }
+}
 
 cudaError_t launch_evaluate_block(const DevNet &net, const int8_t *X, int64_t xstride, int32_t n,
                                   int32_t *score, int32_t *score2, uint8_t *traj, int sm_count,

@@ -210,6 +210,8 @@ struct Mlp {
     DevBuf<uint16_t> hc;                // [Mc][H1] candidate hidden rows (bf16)
     DevBuf<float> pc;                   // [Mc][H2 / 64] candidate layer-2 partials
     DevBuf<int32_t> cand;               // [chains][K] (j << 8) | (v & 255), -1 = null
+    DevBuf<uint16_t> emb_oh;            // [kEmbedRows][Dp] one-hot rows of chains (large P)
+    DevBuf<float> emb_out;              // [kEmbedRows][H1] their layer-1 products
 
     size_t off_b1() const { return (size_t)Dp * H1; }
     size_t off_W2() const { return off_b1() + H1; }

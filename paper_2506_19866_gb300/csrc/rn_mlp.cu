@@ -30,6 +30,7 @@
 #include "rn_context.h"
 #include "rn_gemm.cuh"
 #include "rn_kernels.cuh"
+#include "rn_screen.h"
 #include "rn_umma.cuh"
 
 namespace rn {
@@ -230,6 +231,15 @@ __global__ void log_chains_kernel(DevChains ch, int8_t *__restrict__ set_x,
 
 // Block per chain: A1[c][h] = b1[h] + sum_j W1[row(j, x_j)][h] (the BF16
 // weights), h over the block's threads.
+// A1 rows c0 .. c0 + n - 1 from the one-hot GEMM's rows: + b1.
+__global__ void embed_bias_kernel(const float *__restrict__ prod, int32_t n, int32_t H1,
+                                  const float *__restrict__ b1, float *__restrict__ A1)
+{
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)n * H1) return;
+    A1[k] = prod[k] + b1[k % H1];
+}
+
 __global__ void embed_chains_kernel(DevChains ch, int32_t P, const int32_t *__restrict__ row_base,
                                     const bf16 *__restrict__ W1b, const float *__restrict__ b1,
                                     int H1, float *__restrict__ A1)
@@ -244,29 +254,6 @@ __global__ void embed_chains_kernel(DevChains ch, int32_t P, const int32_t *__re
     }
 }
 
-struct ScreenArgs {
-    DevNet net;
-    DevChains ch;
-    int64_t g;                          // global step
-    int32_t K, top, H1, nparts;
-    uint64_t eps_thr;                   // fallback iff word 3 < eps_thr (<= 2^32)
-    const int32_t *row_base;
-    const bf16 *W1b;                    // [Dp][H1]
-    const float *b3;
-    float *A1;                          // [chains][H1]
-    bf16 *hc;                           // [M][H1]
-    const float *pc;                    // [M][nparts]
-    int32_t *cand;                      // [chains][K]
-};
-
-constexpr int kScreenWarps = 4;
-constexpr int kMaxGroups = 4;           // H1 <= 4 * 256
-
-__device__ __forceinline__ uint4 step_draw(const DevChains &ch, int64_t g, int chain, uint32_t tag)
-{
-    return philox(ch.seed, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), (uint32_t)chain, tag);
-}
-
 // Warp per chain: K candidates (lane k draws candidate k), then the K hidden
 // rows relu(A1 + W1[new] - W1[old]) in BF16.  Shared memory per warp: x_cur,
 // out_nz[N], pos_in[N].
@@ -275,7 +262,7 @@ __global__ void __launch_bounds__(kScreenWarps * 32) screen_propose_kernel(Scree
 {
     extern __shared__ __align__(16) uint8_t sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.x * kScreenWarps + warp;
+    const int c = blockIdx.x * (blockDim.x >> 5) + warp;
     if (c >= a.ch.n) return;
     int8_t *xs = reinterpret_cast<int8_t *>(sm + warp * region);
     uint8_t *out_nz = reinterpret_cast<uint8_t *>(xs) + a.ch.pstride;
@@ -337,16 +324,6 @@ __global__ void __launch_bounds__(kScreenWarps * 32) screen_propose_kernel(Scree
     }
 }
 
-// Order-preserving key of a float (NaN: largest).
-__device__ __forceinline__ uint32_t float_key(float y)
-{
-    if (y != y) return 0xFFFFFFFEu;
-    const uint32_t u = __float_as_uint(y);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-
-constexpr int kMaxTop = 4;
-
 // Warp per chain, after the layer-2 GEMM: the candidates to simulate
 // (fallback: candidate 0 only; otherwise the `top` distinct moves of lowest
 // predicted y, lowest candidate index on ties), each simulated exactly on the
@@ -362,31 +339,8 @@ __device__ __forceinline__ void screen_finish(const ScreenArgs &a, const DevSche
 {
     const DevNet &net = a.net;
     const uint4 r = step_draw(a.ch, a.g, c, 0u);
-    const bool fallback = (uint64_t)r.w < a.eps_thr;
-    const int mv = lane < a.K ? a.cand[(size_t)c * a.K + lane] : -1;
-    uint32_t key = 0xFFFFFFFFu;
-    if (mv >= 0 && (!fallback || lane == 0)) {
-        if (fallback) {
-            key = 0;
-        } else {
-            float s = 0.f;
-            const float *p = a.pc + ((size_t)c * a.K + lane) * a.nparts;
-            for (int q = 0; q < a.nparts; ++q) s += p[q];
-            key = float_key(*a.b3 + s);
-        }
-    }
-    bool alive = key != 0xFFFFFFFFu;
     int chosen[kMaxTop];
-#pragma unroll
-    for (int s = 0; s < kMaxTop; ++s) {
-        chosen[s] = -1;
-        if (s >= a.top) continue;
-        const uint32_t m = __reduce_min_sync(0xffffffffu, alive ? key : 0xFFFFFFFFu);
-        if (m == 0xFFFFFFFFu) continue;
-        const int w = __ffs(__ballot_sync(0xffffffffu, alive && key == m)) - 1;
-        chosen[s] = __shfl_sync(0xffffffffu, mv, w);
-        if (mv == chosen[s]) alive = false;   // the winner and its duplicates
-    }
+    select_candidates(a, c, lane, r, chosen);
     int64_t *cnt = a.ch.cnt + 3 * (size_t)c;
     if (chosen[0] < 0) {
         if (lane == 0) cnt[2] += 1;
@@ -713,6 +667,43 @@ int weights_io(rn_ctx *ctx, Mlp &m, bool set, float *W1, float *b1, float *W2, f
 }
 
 // Candidate buffers of the screened step for the network's chains.
+// A1 of every chain (the layer-1 pre-activation b1 + sum_j W1[onehot(x)_j]).
+// Small parameter vectors: a block per chain sums its P rows of W1 in order.
+// Large ones (the block path's thousands of parameters): one-hot rows of
+// kEmbedRows chains at a time times W1 on the tensor cores (FP32 accumulation,
+// so the rounding order differs from the per-chain sum).
+constexpr int kEmbedRows = 1024;
+
+int embed_chains(rn_ctx *ctx, Mlp &m, const DevChains &ch)
+{
+    cudaStream_t st = ctx->stream;
+    if ((int64_t)m.P * m.H1 <= ((int64_t)1 << 22)) {
+        embed_chains_kernel<<<ch.n, 256, 0, st>>>(ch, m.P, m.row_base.p, bp(m.W1b),
+                                                  m.theta.p + m.off_b1(), m.H1, m.A1.p);
+        return check_launch(ctx, "embed kernel");
+    }
+    const size_t Dp = (size_t)m.Dp, H1 = (size_t)m.H1;
+    RN_CUDA(ctx, m.emb_oh.reserve(kEmbedRows * Dp));
+    RN_CUDA(ctx, m.emb_out.reserve(kEmbedRows * H1));
+    for (int32_t c0 = 0; c0 < ch.n; c0 += kEmbedRows) {
+        const int32_t n = std::min(kEmbedRows, ch.n - c0);
+        RN_CUDA(ctx, cudaMemsetAsync(m.emb_oh.p, 0, sizeof(uint16_t) * kEmbedRows * Dp, st));
+        onehot_kernel<<<dim3((m.P + 255) / 256, kEmbedRows), 256, 0, st>>>(
+            ch.x_cur + (size_t)c0 * ch.pstride, ch.pstride, nullptr, n, m.P, m.row_base.p,
+            m.row_base.p + m.P, bp(m.emb_oh), m.Dp, nullptr, 0);
+        if (int rc = check_launch(ctx, "one-hot kernel")) return rc;
+        GemmArgs g{};
+        g.A = bp(m.emb_oh); g.lda = m.Dp; g.B = bp(m.W1T); g.ldb = m.Dp;
+        g.M = kEmbedRows; g.N = m.H1; g.K = m.Dp; g.out_f32 = m.emb_out.p; g.ldc = m.H1;
+        if (int rc = gemm(ctx, kStoreF32, g)) return rc;
+        const size_t cnt = (size_t)n * H1;
+        embed_bias_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(
+            m.emb_out.p, n, m.H1, m.theta.p + m.off_b1(), m.A1.p + (size_t)c0 * H1);
+        if (int rc = check_launch(ctx, "embed bias kernel")) return rc;
+    }
+    return RN_OK;
+}
+
 int ensure_screen(rn_ctx *ctx, Mlp &m, const Network &n, int32_t K, int32_t top)
 {
     if (m.chains == n.n_chains && m.K == K && m.top == top) return RN_OK;
@@ -997,21 +988,23 @@ int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K
     if (s->reset_to_best || s->global_sync)
         return fail(ctx, RN_EUNSUPPORTED, "screened annealing runs without reset/global sync");
     if (!n->chains_valid) return fail(ctx, RN_ESTATE, "no chains (call rn_init_chains)");
-    if (n->lanes != 32 || n->pstride > 8192)
-        return fail(ctx, RN_EUNSUPPORTED,
-                    "screened annealing covers networks of a warp per chain (N <= 512)");
+    // propose: a warp per chain, its x and constraint counters in shared memory
+    const int region = (int)(n->pstride + 2 * ((n->N + 15) & ~15));
+    int smem_limit = 0;
+    RN_CUDA(ctx, cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                        ctx->device));
+    const int pwarps = std::min(kScreenWarps, smem_limit / std::max(region, 1));
+    if (pwarps < 1)
+        return fail(ctx, RN_EUNSUPPORTED, "x of %d bytes is too large for the screened step",
+                    n->pstride);
     RN_CUDA(ctx, cudaSetDevice(ctx->device));
     if (sweeps == 0) return RN_OK;
     int rc;
     if ((rc = ensure_screen(ctx, *m, *n, K, top))) return rc;
     ctx->batch.g0_synced = false;
     const DevChains ch = n->chains();
-    const int blocks = (ch.n + kScreenWarps - 1) / kScreenWarps;
     if (!m->a1_valid || m->a1_gen != ctx->gen || m->a1_step != n->step) {
-        embed_chains_kernel<<<ch.n, 256, 0, ctx->stream>>>(ch, m->P, m->row_base.p, bp(m->W1b),
-                                                           m->theta.p + m->off_b1(), m->H1,
-                                                           m->A1.p);
-        if ((rc = check_launch(ctx, "embed kernel"))) return rc;
+        if ((rc = embed_chains(ctx, *m, ch))) return rc;
         m->a1_valid = true;
         m->a1_gen = ctx->gen;
     }
@@ -1038,10 +1031,10 @@ int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K
     a.hc = bp(m->hc);
     a.pc = m->pc.p;
     a.cand = m->cand.p;
-    const int region = (int)(n->pstride + 2 * ((n->N + 15) & ~15));
-    const size_t smem = (size_t)kScreenWarps * region;
+    const size_t smem = (size_t)pwarps * region;
     RN_CUDA(ctx, cudaFuncSetAttribute(screen_propose_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int pblocks = (ch.n + pwarps - 1) / pwarps;
     const int32_t M = round_up(ch.n * K, 128);
     GemmArgs g{};
     g.A = a.hc; g.lda = m->H1; g.B = bp(m->W2T); g.ldb = m->H1;
@@ -1049,10 +1042,11 @@ int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K
     g.bias = m->theta.p + m->off_b2(); g.w = m->theta.p + m->off_w3(); g.part = m->pc.p;
     for (int64_t k = 0; k < sweeps; ++k) {
         a.g = n->step + k;
-        screen_propose_kernel<<<blocks, kScreenWarps * 32, smem, ctx->stream>>>(a, region);
+        screen_propose_kernel<<<pblocks, pwarps * 32, smem, ctx->stream>>>(a, region);
         if ((rc = check_launch(ctx, "screen propose kernel"))) return rc;
         if ((rc = gemm(ctx, kBiasReluDot, g))) return rc;
-        const cudaError_t e = launch_finish(a, sc, ctx->stream);
+        const cudaError_t e = n->lanes == 32 ? launch_finish(a, sc, ctx->stream)
+                                             : launch_finish_block(a, sc, ctx->sm_count, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "screen finish kernel");
         ctx->launches += 1;
     }

@@ -253,6 +253,96 @@ def test_screened_anneal_invariants(ctx):
     assert np.all(st["counters"][:, 1] <= st["counters"][:, 0])
 
 
+def test_screened_block_path_eps1_is_plain_annealing(ctx):
+    """Block-path network (700 nodes, a block of threads per chain) with a
+    width-1024 screen: with eps = 1 the screened step simulates only the plain
+    proposal, so the chains are bit-identical to rn_anneal's."""
+    w = synth.random_network(71, 700, lam=4.0, cap=16, n_cond=3, n_times=6, obs_frac=0.3)
+    n, sweeps = 64, 12
+    sched = R.schedule(5.0, 0.97)
+    p = Problem(w, ctx)
+    mid, D, _ = _screen(ctx, p, 1024, 1024, 5)
+    R.rn_init_chains(ctx, p.id, n, 19)
+    R.rn_anneal_screened(ctx, mid, sched, 5, K=32, top=2, eps=1.0)
+    R.rn_anneal_screened(ctx, mid, sched, sweeps - 5, K=32, top=2, eps=1.0)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    ctx2 = R.rn_create(0)
+    try:
+        p2 = Problem(w, ctx2)
+        R.rn_init_chains(ctx2, p2.id, n, 19)
+        R.rn_anneal(ctx2, sched, sweeps)
+        ref = R.rn_get_chain_state(ctx2, p2.id, n)
+    finally:
+        R.rn_destroy(ctx2)
+    for k in ("x_cur", "d_cur", "x_best", "d_best", "counters"):
+        np.testing.assert_array_equal(st[k], ref[k], err_msg=k)
+
+
+def test_screened_block_path_step_selection(ctx):
+    """One greedy screened step on a block-path network with a width-1024
+    screen (its A1 from the one-hot GEMM, P x width above the per-chain
+    threshold): a moved chain took a move that can be among the top 2 predicted
+    (oracle prediction +- the derived bound) with exact dE <= 0; a chain that
+    stayed had no candidate surely among them with dE <= 0."""
+    w = synth.random_network(72, 600, lam=3.0, cap=12, n_cond=2, n_times=5, obs_frac=0.4)
+    p = Problem(w, ctx)
+    assert p.net.P * 1024 > (1 << 22)
+    mid, D, params = _screen(ctx, p, 1024, 1024, 6)
+    n, K, seed, g, top = 16, 32, 29, 0, 2
+    R.rn_init_chains(ctx, p.id, n, seed)
+    st0 = R.rn_get_chain_state(ctx, p.id, n)
+    R.rn_anneal_screened(ctx, mid, R.schedule(1e-9, 1.0), 1, K=K, top=top, eps=0.0)
+    st1 = R.rn_get_chain_state(ctx, p.id, n)
+    q = gpu_view(params)
+    moved = 0
+    for c in range(n):
+        x0 = st0["x_cur"][c]
+        d0 = int(st0["d_cur"][c])
+        moves = [m for m in dict.fromkeys(_candidates(p.net, x0, seed, c, g, K)) if m]
+        V = np.array([np.where(np.arange(p.net.P) == j, v, x0).astype(np.int8) for j, v in moves])
+        yp = O.mlp(p.net, V, q)
+        b = forward_bound(p.net, V, q)
+        dE = np.array([O.objective(p.net, p.tc, xv) for xv in V]) - d0
+        lo, hi = yp - b, yp + b
+        surely_beats = lo[None, :] > hi[:, None]
+        may_beat = lo[:, None] <= hi[None, :]
+        np.fill_diagonal(may_beat, False)
+        possible = surely_beats.sum(axis=0) < top
+        sure = may_beat.sum(axis=0) < top
+        x1 = st1["x_cur"][c]
+        diff = np.flatnonzero(x1 != x0)
+        assert len(diff) <= 1
+        if len(diff) == 1:
+            moved += 1
+            k = moves.index((int(diff[0]), int(x1[diff[0]])))
+            assert possible[k] and dE[k] <= 0
+            assert st1["d_cur"][c] == d0 + dE[k]
+        else:
+            assert not np.any(sure & (dE <= 0)), f"chain {c}"
+            assert st1["d_cur"][c] == d0
+    assert moved >= n // 4
+
+
+def test_screened_block_path_invariants(ctx):
+    """eps = 0.1 run on a block-path network: stored scores are exact, x_best
+    holds delta_best, the constraints hold, the counters add up."""
+    w = synth.random_network(73, 650, lam=4.0, cap=16, n_cond=2, n_times=6, obs_frac=0.3)
+    p = Problem(w, ctx)
+    mid, D, _ = _screen(ctx, p, 512, 512, 9)
+    n = 48
+    R.rn_init_chains(ctx, p.id, n, 37)
+    R.rn_anneal_screened(ctx, mid, R.schedule(2.0, 0.98), 10, K=32, top=2, eps=0.1)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    assert st["step"] == 10
+    np.testing.assert_array_equal(R.rn_evaluate(ctx, p.id, st["x_cur"]), st["d_cur"])
+    np.testing.assert_array_equal(R.rn_evaluate(ctx, p.id, st["x_best"]), st["d_best"])
+    assert np.all(st["d_best"] <= st["d_cur"])
+    for c in (0, 20, 47):
+        assert O.check_params(p.net, st["x_cur"][c]) == 0
+    assert np.all(st["counters"][:, 0] + st["counters"][:, 2] <= 10)
+    assert (st["counters"][:, 0] > 0).any()
+
+
 def test_trained_screen_beats_plain_at_equal_exact_evaluations(ctx):
     """What the learned screen gains: from the same mid-anneal state, 40
     screened steps (2 exact simulations each) against 80 plain steps (1 each):
