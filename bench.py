@@ -385,30 +385,45 @@ def run_ours(args, rank, world, local_rank):
     ws = workload_set(args.workload)
     S = args.sweeps_per_step
     ctx = R.rn_create(local_rank, stream.cuda_stream)
-    ids = [setup_problem(R, ctx, w)[0] for w in ws]
-    for nid, w in zip(ids, ws):   # every rank anneals its own replica of the chains
-        R.rn_init_chains(ctx, nid, w.n_chains, rank_seed(w, rank))
+    # with --screened on a set of networks ("both patterns"), the first network
+    # is annealed by the screened step in a context of its own and the others
+    # by the batched launch
+    both = args.screened and len(ws) > 1
+    ctx_main = R.rn_create(local_rank, stream.cuda_stream) if both else ctx
+    net_ctx = [ctx_main if (both and i == 0) else ctx for i in range(len(ws))]
+    ids = [setup_problem(R, c, w)[0] for c, w in zip(net_ctx, ws)]
+    for c, nid, w in zip(net_ctx, ids, ws):   # every rank anneals its own replica of the chains
+        R.rn_init_chains(c, nid, w.n_chains, rank_seed(w, rank))
     sched = R.schedule(ws[0].T0, ws[0].alpha)
-    R.rn_prepare_schedule(ctx, sched, (args.warmup + args.steps) * S)
+    for c in {id(x): x for x in net_ctx}.values():
+        R.rn_prepare_schedule(c, sched, (args.warmup + args.steps) * S)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     step = lambda: R.rn_anneal(ctx, sched, S)
-    top = 1
+    tops = [1] * len(ws)
+    screen_width = 1024 if any(block_path(w) for w in ws) else 512
     if args.screened:
-        if len(ws) != 1:
-            raise SystemExit("--screened runs one network")
-        mid = screen_for(R, ctx, ids[0], ws[0])
-        top = 2
-        step = lambda: R.rn_anneal_screened(ctx, mid, sched, S, K=32, top=top, eps=0.0)
+        mid = screen_for(R, ctx_main, ids[0], ws[0], h=screen_width)
+        tops[0] = 2
+        if both:
+            def step():
+                R.rn_anneal(ctx, sched, S)
+                R.rn_anneal_screened(ctx_main, mid, sched, S, K=32, top=2, eps=0.0)
+        else:
+            step = lambda: R.rn_anneal_screened(ctx, mid, sched, S, K=32, top=2, eps=0.0)
     for _ in range(args.warmup):
         step()
     R.rn_synchronize(ctx)
+    R.rn_synchronize(ctx_main)
 
     def nulls_now():
-        return [int(R.rn_get_chain_state(ctx, nid, w.n_chains)["counters"][:, 2].sum())
-                for nid, w in zip(ids, ws)]
+        return [int(R.rn_get_chain_state(c, nid, w.n_chains)["counters"][:, 2].sum())
+                for c, nid, w in zip(net_ctx, ids, ws)]
+
+    def launch_count():
+        return R.rn_launch_count(ctx) + (R.rn_launch_count(ctx_main) if both else 0)
 
     before = nulls_now()
-    l0 = R.rn_launch_count(ctx)
+    l0 = launch_count()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -431,10 +446,10 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     if dist is not None:
         dist.barrier()
-    launches = R.rn_launch_count(ctx) - l0
+    launches = launch_count() - l0
     step_ms = [a.elapsed_time(b) for a, b in times]
     nulls = [a - b for a, b in zip(nulls_now(), before)]
-    evals_w = [w.n_chains * S * args.steps * top - z for w, z in zip(ws, nulls)]
+    evals_w = [w.n_chains * S * args.steps * t - z for w, z, t in zip(ws, nulls, tops)]
     evals = sum(evals_w)
     total_s = sum(step_ms) / 1000.0
 
@@ -484,11 +499,18 @@ def run_ours(args, rank, world, local_rank):
     free, total = torch.cuda.mem_get_info(local_rank)
     line["device_memory_used_gb"] = (total - free) / 1e9
     if args.screened:
-        line["config"]["step"] = ("screened: K = 32 candidates per chain ranked by a 512-512 "
-                                  "one-hot MLP (tcgen05 BF16 GEMM), top 2 simulated exactly")
-        line["roofline"] = {"bound": "tensor", "kernel": "gemm_tc_kernel (layer 2)",
-                            "flop_per_step": 2 * ws[0].n_chains * 32 * 512 * 512 * S,
-                            "note": "per-kernel split of a screened step: profiles/"}
+        h = screen_width
+        line["config"]["step"] = (f"screened: K = 32 candidates per chain ranked by a {h}-{h} "
+                                  "one-hot MLP (tcgen05 BF16 GEMM), top 2 simulated exactly"
+                                  + ("; the first network screened, the others annealed by "
+                                     "the batched launch in the same step" if both else ""))
+        screen = {"kernel": "gemm_tc_kernel (layer 2)", "width": h,
+                  "flop_per_step": 2 * ws[0].n_chains * 32 * h * h * S}
+        if both:
+            line["screen"] = screen
+        else:
+            line["roofline"] = dict(bound="tensor", note="per-kernel split of a screened step: "
+                                    "profiles/", **screen)
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(args, R, ws, local_rank, stream)
     if rank == 0 and not args.no_ttt and world == 1 and not args.screened:
@@ -497,6 +519,8 @@ def run_ours(args, rank, world, local_rank):
             len(ws) == 1):
         line["early_reject"] = early_reject_gain(args, R, ws[0], local_rank, stream)
     R.rn_destroy(ctx)
+    if both:
+        R.rn_destroy(ctx_main)
     if rank == 0 and not args.no_cpu_baseline and world == 1 and len(ws) == 1:
         line["cpu_baseline"] = oracle_rate(args.workload, args.cpu_seconds)
     if rank == 0:

@@ -354,8 +354,9 @@ int rn_mlp_train(rn_ctx *ctx, int32_t mlp, int32_t steps, int32_t batch, float l
  * exact score (first on ties) goes to the Metropolis test of Table 1 with
  * word 2 of counter tag 0.  A step with no candidate is a null move.  With
  * eps = 1 the chains are bit-identical to rn_anneal's.  K: 1 .. 32;
- * top: 1 .. 4 (<= K).  Covers networks that a warp per chain holds (N <= 512,
- * in-degree <= 16, x of at most 8192 bytes); RN_EUNSUPPORTED otherwise. */
+ * top: 1 .. 4 (<= K).  Covers every network the annealing kernels cover (a
+ * warp or a block of threads per chain); RN_EUNSUPPORTED if one chain's x and
+ * constraint counters exceed a block's shared memory. */
 int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K, int32_t top,
                        double eps, int64_t sweeps);
 
