@@ -362,15 +362,15 @@ __device__ __forceinline__ void load_obs(uint32_t (&w)[NPL], const uint32_t *ob)
 // Section 2.2 done byte-SIMD within registers: byte c of every per-node word
 // belongs to condition c of the group.
 //
-//   a    = image byte 128 + K_i (the accumulator starts at (128 - 4 D) per byte)
-//   tgt  = [K >= 1] + [K >= 2] = clamp(K, 0, 2)      (bit 7 of a - 1 and a - 2)
+//   a    = image byte 127 + K_i (the accumulator starts at kImage0 - 4 D4 per byte)
+//   tgt  = [K >= 1] + [K >= 2] = clamp(K, 0, 2)      (bit 7 of a and of a - 1)
 //   dp   = tgt - s + 2 in [0, 4]; UP = dp >= 3, DN = dp <= 1 (told to move up/down)
 //   cu   = consecutive up drives, cd = consecutive down drives (reset by a move)
 //   EL   = cu >= m + 1 or cd >= m + 1, only where the node may move
 //   ua   = u * (steps since the last update), 16-bit lanes (two words)
 //   the nodes whose eligible priority equals the warp maximum of their
 //   condition move to tgt (d = 2) or one level toward it (d = 1).
-// Byte values stay within their byte: a in [64, 192] for D <= 16, counters
+// Byte values stay within their byte: a in [3, 251] for D <= 31, counters
 // below 128 for T <= 128, priorities below 2^15.
 // 16-bit state code of a node's four conditions: nibble c = s_c for the
 // register-table words, 4 - s_c for the shared-memory words (rn_smem.cuh).
