@@ -57,6 +57,13 @@ def parse():
                          "against time and acceptance rate per stretch of levels")
     ap.add_argument("--protocol-iters", type=int, default=100,
                     help="proposals per level for the thread-count sweep (the paper: 5000)")
+    ap.add_argument("--screen-gain", action="store_true",
+                    help="instead of the throughput line: train a width-1024 screen on the "
+                         "2000-node network (pairs logged from a plain run) and race plain "
+                         "against screened annealing for equal wall-clock time from the same "
+                         "start")
+    ap.add_argument("--gain-train-steps", type=int, default=1000,
+                    help="Adam steps of the --screen-gain training")
     ap.add_argument("--screened", action="store_true",
                     help="time screened steps (K = 32 candidates ranked by a seeded one-hot "
                          "MLP, top 2 simulated exactly) instead of plain sweeps; value counts "
@@ -381,6 +388,10 @@ def run_ours(args, rank, world, local_rank):
     if args.paper_protocol:
         if rank == 0:
             print(json.dumps(paper_protocol(args, R, local_rank, stream)), flush=True)
+        return
+    if args.screen_gain:
+        if rank == 0:
+            print(json.dumps(screen_gain(args, R, local_rank, stream)), flush=True)
         return
     ws = workload_set(args.workload)
     S = args.sweeps_per_step
@@ -732,6 +743,89 @@ def time_to_target(args, R, device, stream, name="mtb_63n_178e"):
                        "tolerance": "held-out Spearman >= 0.3, RMSE <= 1.25 x target std"},
             "timing": "wall clock, one host sync per chunk (plain 100 sweeps, screened 20 "
                       "steps) to read the best score; screen training excluded (offline)"}
+
+
+def screen_gain(args, R, device, stream, name="n2000_c16_t33", budget_s=20.0):
+    """What a trained screen of width 1024 gains on the 2000-node, 16-condition
+    network (42,000 parameters, one-hot width 117,000): pairs logged from a
+    plain run (chain seed 7, every 16 sweeps over 480 sweeps), Adam steps of
+    4096 on the GPU (--gain-train-steps), held-out rank correlation on an independent run, then
+    plain and screened annealing (K = 32, top 2, eps = 0.05) from the same
+    start (chain seed 101) for the same wall-clock budget, the best score read
+    after every chunk."""
+    from scipy.stats import spearmanr
+    w = synth.make(name)
+    n_obs = int(w.observed.sum())
+    ctx = R.rn_create(device, stream.cuda_stream)
+    try:
+        nid, _ = setup_problem(R, ctx, w)
+        sched = R.schedule(w.T0, w.alpha)
+        R.rn_prepare_schedule(ctx, sched, 4000)
+        h = 1024
+        mid = screen_for(R, ctx, nid, w, h=h, capacity=300000)
+        R.rn_init_chains(ctx, nid, w.n_chains, 7)
+        t0 = time.perf_counter()
+        for _ in range(30):
+            R.rn_anneal(ctx, sched, 16)
+            pairs = R.rn_mlp_log_chains(ctx, mid)
+        R.rn_synchronize(ctx)
+        t_log = time.perf_counter() - t0
+        steps, batch = args.gain_train_steps, 4096
+        t0 = time.perf_counter()
+        loss = R.rn_mlp_train(ctx, mid, steps, batch=batch, lr=1e-3, seed=3)
+        t_train = time.perf_counter() - t0
+        n_h = 2048
+        R.rn_init_chains(ctx, nid, n_h, 99)
+        Xh, yh = [], []
+        for s in (20, 100, 400):
+            R.rn_anneal(ctx, sched, s - R.rn_get_chain_state(ctx, nid, n_h)["step"])
+            st = R.rn_get_chain_state(ctx, nid, n_h)
+            Xh.append(st["x_cur"])
+            yh.append(st["d_cur"] / n_obs)
+        Xh, yh = np.concatenate(Xh), np.concatenate(yh)
+        pred = R.rn_mlp_forward(ctx, mid, Xh)
+
+        def race(screened):
+            R.rn_init_chains(ctx, nid, w.n_chains, 101)
+            R.rn_synchronize(ctx)
+            curve, done = [], 0
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < budget_s:
+                if screened:
+                    R.rn_anneal_screened(ctx, mid, sched, 2, K=32, top=2, eps=0.05)
+                    done += 2
+                else:
+                    R.rn_anneal(ctx, sched, 4)
+                    done += 4
+                best = R.rn_get_best(ctx, nid)[1]
+                curve.append([round(time.perf_counter() - t0, 3), done, int(best)])
+            return curve
+
+        race(False)                                       # warm-up of both paths
+        race(True)
+        plain, scr = race(False), race(True)
+        plain_final = plain[-1][2]
+        reach = next((c[0] for c in scr if c[2] <= plain_final), None)
+        return {"screen_gain": {
+            "workload": name, "chains": w.n_chains, "params": int(w.P), "n_obs": n_obs,
+            "width": h, "budget_s": budget_s,
+            "plain_final_best": plain_final, "screened_final_best": scr[-1][2],
+            "plain_steps": plain[-1][1], "screened_steps": scr[-1][1],
+            "screened_seconds_to_plain_final_best": reach,
+            "plain_curve": plain, "screened_curve": scr,
+            "screen": {"K": 32, "top": 2, "eps": 0.05, "train_pairs": int(pairs),
+                       "train_steps": steps, "batch": batch, "log_s": t_log,
+                       "train_s": t_train, "last_loss": loss,
+                       "heldout_spearman": float(spearmanr(pred, yh).correlation),
+                       "heldout_rmse": float(np.sqrt(np.mean((pred - yh) ** 2))),
+                       "heldout_target_std": float(np.std(yh)),
+                       "heldout": f"{3 * n_h} states of an independent run after 20/100/400 "
+                                  "sweeps"},
+            "schedule": {"T0": w.T0, "alpha": w.alpha},
+            "timing": "wall clock, one host read of the best score per chunk (plain 4 sweeps, "
+                      "screened 2 steps); training excluded"}}
+    finally:
+        R.rn_destroy(ctx)
 
 
 def main():
