@@ -231,11 +231,13 @@ int rn_launch_count(rn_ctx *ctx, int64_t *count);
  * to annealing each network alone.  The first batched call tunes the launch on the real
  * batch (table path per network and warps per block), timing each candidate
  * for a few steps from the current state, which is restored afterwards.
- * Candidate c = 3 * w + p: table paths p = 0 register tables where they fit,
- * shared-memory tables elsewhere; p = 1 the same with the hybrid path (table
- * words in shared memory, node state in registers) for networks of 129-256
- * nodes; p = 2 shared-memory tables for all; warps per block 4 (w = 0) or 2
- * (w = 1).  With the threshold tables cached by rn_prepare_schedule, the
+ * Candidate c = 3 * w + p (c < 6): table paths p = 0 register tables where
+ * they fit, shared-memory tables elsewhere; p = 1 the same with the hybrid
+ * path (table words in shared memory, node state in registers) for networks of
+ * 129-256 nodes; p = 2 shared-memory tables for all; warps per block 4 (w = 0)
+ * or 2 (w = 1); the warps with a region large enough for any network are the
+ * work share of those networks.  c = 6, 7: p = 0 with 4 / 2 warps per block,
+ * every warp with a large region.  With the threshold tables cached by rn_prepare_schedule, the
  * launch is captured once in a CUDA graph and replayed.  This reports the
  * configuration in use:
  *   info[0] networks in the batch (0: no batch yet)
@@ -244,13 +246,13 @@ int rn_launch_count(rn_ctx *ctx, int64_t *count);
  *   info[3] 1 if calls replay a CUDA graph
  *   info[4] networks on the hybrid path
  *   info[5] the candidate in use (-1: not tuned yet)
- *   trial_ms[6] (may be NULL) milliseconds of the candidates' trials (0 when
+ *   trial_ms[8] (may be NULL) milliseconds of the candidates' trials (0 when
  *   the candidate was pinned by rn_batch_tune). */
-int rn_batch_config(rn_ctx *ctx, int32_t info[6], double trial_ms[6]);
+int rn_batch_config(rn_ctx *ctx, int32_t info[6], double trial_ms[8]);
 
-/* Pin the batched launch to candidate `config` (0 .. 5, see rn_batch_config)
+/* Pin the batched launch to candidate `config` (0 .. 7, see rn_batch_config)
  * instead of timing the candidates, or return to autotuning with -1.  Takes
- * effect at the next batched rn_anneal call.  RN_EINVAL outside -1 .. 5. */
+ * effect at the next batched rn_anneal call.  RN_EINVAL outside -1 .. 7. */
 int rn_batch_tune(rn_ctx *ctx, int32_t config);
 
 /* For callers that cannot let a library allocate device memory -- an

@@ -458,7 +458,7 @@ int batch_region(rn_ctx *ctx, BatchState &B)
         if (big) work_big += w;
     }
     if (B.total_big == 0) B.large = 0;
-    else if (B.total_big == B.total) B.large = B.wpb;
+    else if (B.total_big == B.total || B.all_large) B.large = B.wpb;
     else
         B.large = std::min(B.wpb - 1,
                            std::max(1, (int)std::ceil(B.wpb * work_big / std::max(work_all, 1.0))));
@@ -584,10 +584,12 @@ int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
         }
         return RN_OK;
     };
-    // candidate c: table paths (c % 3: register tables where they fit and
+    // candidate c < 6: table paths (c % 3: register tables where they fit and
     // shared-memory tables elsewhere / the same with the hybrid path for 6 or 8
     // nodes per lane / shared-memory tables for all) x warps per block (c / 3:
-    // 4 / 2)
+    // 4 / 2), large-region warps by the work share; c = 6, 7: register tables
+    // where they fit, 4 / 2 warps per block, every warp with a large region
+    // (no warp idles once the register-table work is done)
     std::vector<int32_t> best_fit(B.order.size(), 0), hybrid(B.order.size(), 0);
     for (size_t b = 0; b < B.order.size(); ++b) {
         const Network &n = *ctx->nets[(size_t)B.order[b]];
@@ -598,8 +600,9 @@ int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
     }
     const std::vector<int32_t> all_smem(B.host_path.size(), 0);
     auto apply = [&](int cfg) {
-        B.host_path = cfg % 3 == 0 ? best_fit : cfg % 3 == 1 ? hybrid : all_smem;
-        B.wpb = cfg / 3 == 0 ? 4 : 2;
+        B.all_large = cfg >= 6;
+        B.host_path = cfg >= 6 || cfg % 3 == 0 ? best_fit : cfg % 3 == 1 ? hybrid : all_smem;
+        B.wpb = cfg >= 6 ? (cfg == 6 ? 4 : 2) : cfg / 3 == 0 ? 4 : 2;
         B.cfg = cfg;
     };
     if (B.force >= 0) {
@@ -616,7 +619,7 @@ int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
     RN_CUDA(ctx, cudaEventCreate(&e0));
     RN_CUDA(ctx, cudaEventCreate(&e1));
     int rc = copy_state(true);
-    for (int cfg = 0; cfg < 6 && !rc; ++cfg) {
+    for (int cfg = 0; cfg < 8 && !rc; ++cfg) {
         apply(cfg);
         if ((rc = batch_region(ctx, B))) break;
         DevSched sc = sc0;
@@ -1202,7 +1205,7 @@ int rn_launch_count(rn_ctx *ctx, int64_t *count)
     return RN_OK;
 }
 
-int rn_batch_config(rn_ctx *ctx, int32_t info[6], double trial_ms[6])
+int rn_batch_config(rn_ctx *ctx, int32_t info[6], double trial_ms[8])
 {
     if (!ctx || !info) return RN_EINVAL;
     const BatchState &B = ctx->batch;
@@ -1220,7 +1223,7 @@ int rn_batch_config(rn_ctx *ctx, int32_t info[6], double trial_ms[6])
     info[4] = hybrid;
     info[5] = on && B.tuned ? B.cfg : -1;
     if (trial_ms)
-        for (int k = 0; k < 6; ++k) trial_ms[k] = B.tune_ms[k];
+        for (int k = 0; k < 8; ++k) trial_ms[k] = B.tune_ms[k];
     return RN_OK;
 }
 
@@ -1228,7 +1231,7 @@ int rn_batch_tune(rn_ctx *ctx, int32_t config)
 {
     if (!ctx) return RN_EINVAL;
     ctx->err.clear();
-    if (config < -1 || config > 5) return fail(ctx, RN_EINVAL, "config %d outside -1 .. 5", config);
+    if (config < -1 || config > 7) return fail(ctx, RN_EINVAL, "config %d outside -1 .. 7", config);
     ctx->batch.force = config;
     ctx->batch.tuned = false;
     ctx->batch.drop_graph();

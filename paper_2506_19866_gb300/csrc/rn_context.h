@@ -140,6 +140,7 @@ struct BatchState {
     int32_t total = 0;
     int32_t total_big = 0;            // chains of networks on the shared-memory tables
     int32_t large = 0;                // large-region warps per block
+    bool all_large = false;           // every warp gets a large region (a tuning candidate)
     uint32_t region_small = 0;        // region of a small (register-table) warp
     DevBuf<rn::DevNet> nets;
     DevBuf<rn::DevChains> chains;
@@ -150,7 +151,7 @@ struct BatchState {
     int wpb = 4, grid = 0;
     bool tuned = false;
     bool g0_synced = false;           // device g0 equals the host step counters
-    double tune_ms[6] = {0, 0, 0, 0, 0, 0};   // trial times of the candidate configurations
+    double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // trial times of the candidates
     int32_t force = -1;               // candidate pinned by rn_batch_tune (-1: autotune)
     int32_t cfg = 0;                  // candidate in use
     // graph of [queue reset, batched kernel, step advance]

@@ -30,10 +30,11 @@ def _state_all(ctx, probs, nets):
     return [R.rn_get_chain_state(ctx, p.id, w.n_chains) for p, w in zip(probs, nets)]
 
 
-@pytest.mark.parametrize("pin", [None, 0, 1, 2, 4])
+@pytest.mark.parametrize("pin", [None, 0, 1, 2, 4, 6, 7])
 def test_batched_equals_separate_runs(pin):
     # autotuned, and each table-path candidate pinned (1 and 4: the hybrid path
-    # for the networks of 129-256 nodes, with 4 and 2 warps per block)
+    # for the networks of 129-256 nodes, with 4 and 2 warps per block; 6 and 7:
+    # every warp with a large region)
     from paper_2506_19866_gb300 import build
     build.build()
     nets = _batch()
@@ -54,10 +55,10 @@ def test_batched_equals_separate_runs(pin):
             assert all(t > 0 for t in cfg["trial_ms"]) and 0 <= cfg["config"] <= 5
         else:
             assert cfg["config"] == pin
-            assert cfg["warps_per_block"] == (4 if pin < 3 else 2)
+            assert cfg["warps_per_block"] == (4 if pin in (0, 1, 2, 6) else 2)
             n_hybrid = sum(128 < w.N <= 256 for w in nets)
             assert n_hybrid >= 2
-            assert cfg["hybrid_networks"] == (n_hybrid if pin % 3 == 1 else 0)
+            assert cfg["hybrid_networks"] == (n_hybrid if pin in (1, 4) else 0)
         R.rn_anneal(ctx, sched, sweeps)           # graph capture and replay
         R.rn_anneal(ctx, sched, sweeps)
         assert R.rn_batch_config(ctx)["graph"]
