@@ -201,12 +201,19 @@ int rn_n_params(rn_ctx *ctx, int32_t net, int32_t *n_params);
 /* Update scheme of a network (Section 2.2 names three): 0 = priority updating
  * (the paper's, the default): only the eligible nodes of maximum priority
  * u * (tau - last) move at a step; 1 = synchronous updating: every eligible
- * node moves at every step (eligibility, memory m and step size d as before).
- * Under scheme 1 the speeds u have no effect, so GetCandidate no longer
- * proposes them (they keep their values).  The network's chains must be
- * initialised again (RN_ESTATE until rn_init_chains).  The asynchronous scheme
- * (random nodes updated) is not provided.  RN_EINVAL for another scheme. */
-int rn_set_update_scheme(rn_ctx *ctx, int32_t net, int32_t scheme);
+ * node moves at every step; 2 = asynchronous updating: at step tau of condition
+ * c only node selected[c][tau] (-1: none) may move, if eligible (the others
+ * keep counting toward their memory m); eligibility, m and d as before.
+ *   selected  [C][T] node drawn by the caller for each step (entry tau = 0 is
+ *             unused), for scheme 2 only (else ignored); needs the time course
+ *             loaded first (RN_ESTATE), and groups of 4 conditions, i.e. not a
+ *             single-condition network of at most 128 nodes (RN_EUNSUPPORTED).
+ * Under schemes 1 and 2 the speeds u have no effect, so GetCandidate no longer
+ * proposes them (they keep their values).  A new rn_load_timecourse drops
+ * scheme 2 (back to 0).  The network's chains must be initialised again
+ * (RN_ESTATE until rn_init_chains).  RN_EINVAL for another scheme or a node
+ * outside -1 .. N-1. */
+int rn_set_update_scheme(rn_ctx *ctx, int32_t net, int32_t scheme, const int32_t *selected);
 
 /* Checkpoint / parity access to the chain state of a network (host buffers,
  * each may be NULL): x_cur, x_best [n][P]; d_cur, d_best [n];

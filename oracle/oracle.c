@@ -94,7 +94,7 @@ static int is_proposable(const orc_net *net, int32_t j)
 {
     int32_t idx;
     if (is_frozen(net, j)) return 0;
-    return !(net->sync && kind_of(net, j, &idx) == K_U);
+    return !((net->sync || net->async_sel) && kind_of(net, j, &idx) == K_U);
 }
 
 /* ------------------------------------------------------------ generator -- */
@@ -146,10 +146,12 @@ static void draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t 
  * All eligible nodes at the maximum priority then move by
  * min(d_i, |tgt_i - s_i|) toward tgt_i at the end of the step.  Under the
  * synchronous scheme (net->sync) every eligible node has the same priority,
- * so all of them move. */
+ * so all of them move; under the asynchronous scheme (net->async_sel) only the
+ * step's selected node may move (the others keep counting toward m). */
 int32_t orc_simulate(const orc_net *net, const orc_tc *tc, const int8_t *x, int32_t c, uint8_t *S)
 {
     const int32_t N = net->n_nodes, E = net->n_edges, T = tc->n_times;
+    if (net->async_sel && (c >= net->n_cond_sel || net->n_times_sel != T)) return ORC_EINVAL;
     const int8_t *w = x, *p = x + E, *t = x + 2 * E;
     const int8_t *u = x + 3 * E, *m = x + 3 * E + N, *d = x + 3 * E + 2 * N;
     const uint8_t *ko = tc->knockout ? tc->knockout + (size_t)c * N : NULL;
@@ -187,9 +189,11 @@ int32_t orc_simulate(const orc_net *net, const orc_tc *tc, const int8_t *x, int3
             int32_t drv = diff > 0 ? 1 : -1;
             cnt[i] = (drv == dir[i]) ? cnt[i] + 1 : 1;
             dir[i] = drv;
-            if (cnt[i] >= m[i] + 1) {
+            const int selected =
+                !net->async_sel || net->async_sel[(size_t)c * net->n_times_sel + tau] == i;
+            if (cnt[i] >= m[i] + 1 && selected) {
                 int32_t mag = diff > 0 ? diff : -diff;
-                prio[i] = net->sync ? 1 : u[i] * (tau - last[i]);
+                prio[i] = (net->sync || net->async_sel) ? 1 : u[i] * (tau - last[i]);
                 move[i] = drv * (d[i] < mag ? d[i] : mag);
             }
             if (prio[i] > pmax) pmax = prio[i];

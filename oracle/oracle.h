@@ -38,6 +38,12 @@ typedef struct {
                                    alternative to priority updating): every
                                    eligible node moves at every step; u has no
                                    effect and is never proposed */
+    int32_t n_cond_sel, n_times_sel;   /* shape of async_sel */
+    const int32_t *async_sel;   /* [C][T] or NULL: asynchronous update scheme
+                                   (Section 2.2's other alternative): at step tau
+                                   of condition c only node async_sel[c][tau]
+                                   (-1: none) may move, if eligible; u has no
+                                   effect and is never proposed */
 } orc_net;
 
 typedef struct {

@@ -35,7 +35,9 @@ class _Net(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("n_edges", ctypes.c_int32),
                 ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
                 ("fast", ctypes.c_void_p), ("frozen", ctypes.c_void_p),
-                ("frozen_val", ctypes.c_void_p), ("sync", ctypes.c_int32)]
+                ("frozen_val", ctypes.c_void_p), ("sync", ctypes.c_int32),
+                ("n_cond_sel", ctypes.c_int32), ("n_times_sel", ctypes.c_int32),
+                ("async_sel", ctypes.c_void_p)]
 
 
 class _TC(ctypes.Structure):
@@ -111,7 +113,7 @@ def _ptr(a):
 class Network:
     """Topology + speed classes (+ optional fixed parameters) as the oracle sees them."""
 
-    def __init__(self, src, dst, fast, frozen=None, frozen_val=None, sync=False):
+    def __init__(self, src, dst, fast, frozen=None, frozen_val=None, sync=False, async_sel=None):
         self.src = np.ascontiguousarray(src, dtype=np.int32)
         self.dst = np.ascontiguousarray(dst, dtype=np.int32)
         self.fast = np.ascontiguousarray(fast, dtype=np.uint8)
@@ -122,8 +124,13 @@ class Network:
         self.frozen_val = (None if frozen_val is None
                            else np.ascontiguousarray(frozen_val, dtype=np.int8))
         self.sync = bool(sync)
+        # asynchronous scheme: [C][T] node selected at each step (-1: none)
+        self.async_sel = (None if async_sel is None
+                          else np.ascontiguousarray(async_sel, dtype=np.int32))
+        C_sel, T_sel = (0, 0) if self.async_sel is None else self.async_sel.shape
         self.s = _Net(self.N, self.E, _ptr(self.src), _ptr(self.dst), _ptr(self.fast),
-                      _ptr(self.frozen), _ptr(self.frozen_val), int(self.sync))
+                      _ptr(self.frozen), _ptr(self.frozen_val), int(self.sync), C_sel, T_sel,
+                      _ptr(self.async_sel))
 
 
 class Timecourse:

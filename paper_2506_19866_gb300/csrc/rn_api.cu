@@ -156,8 +156,9 @@ void build_layout(Network &n)
     }
     n.free_list.clear();
     for (int32_t j = 0; j < n.P; ++j)
-        if (!(n.has_frozen && n.frozen[(size_t)j]) && !(n.sync && j >= 3 * E && j < 3 * E + N))
-            n.free_list.push_back(j);   // (u has no effect under the synchronous scheme)
+        if (!(n.has_frozen && n.frozen[(size_t)j]) &&
+            !((n.sync || n.async_) && j >= 3 * E && j < 3 * E + N))
+            n.free_list.push_back(j);   // (u has no effect without priorities)
 
     n.supported = false;
     if (n.npl == 0) return;
@@ -896,6 +897,17 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     // scores are summed in quarter units in 32 bits on the device
     if (max_score >= ((int64_t)1 << 30))
         return fail(ctx, RN_EINVAL, "maximum score %lld exceeds 2^30", (long long)max_score);
+    if (n->async_) {
+        // the selection table belongs to the previous time course: back to the
+        // priority scheme (u proposed again) until the scheme is set again
+        n->async_ = false;
+        n->free_list.clear();
+        for (int32_t j = 0; j < n->P; ++j)
+            if (!(n->has_frozen && n->frozen[(size_t)j]) &&
+                !(n->sync && j >= 3 * n->E && j < 3 * n->E + N))
+                n->free_list.push_back(j);
+        RN_CUDA(ctx, n->d_free.upload(n->free_list));
+    }
     n->C = C;
     n->T = T;
     n->max_score = max_score;
@@ -977,26 +989,56 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     RN_CUDA(ctx, n->d_out_bits.upload(out_bits));
     RN_CUDA(ctx, n->d_init_s4.upload(init_s4));
     RN_CUDA(ctx, n->d_movable.upload(movable));
+    n->movable_h = movable;
     n->cg = cg;
     ctx->gen++;
     n->G = G;
     return RN_OK;
 }
 
-int rn_set_update_scheme(rn_ctx *ctx, int32_t net, int32_t scheme)
+int rn_set_update_scheme(rn_ctx *ctx, int32_t net, int32_t scheme, const int32_t *selected)
 {
     if (!ctx) return RN_EINVAL;
     ctx->err.clear();
     Network *n = get_net(ctx, net);
     if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
-    if (scheme != 0 && scheme != 1) return fail(ctx, RN_EINVAL, "scheme %d is not 0 or 1", scheme);
-    n->sync = scheme == 1;
+    if (scheme < 0 || scheme > 2) return fail(ctx, RN_EINVAL, "scheme %d is not 0, 1 or 2", scheme);
     const int32_t N = n->N, E = n->E;
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (scheme == 2) {
+        if (!selected) return fail(ctx, RN_EINVAL, "the asynchronous scheme needs `selected`");
+        if (!n->has_tc) return fail(ctx, RN_ESTATE, "load the time course first");
+        if (!n->supported) return require_supported(ctx, *n);
+        if (n->cg != 4)
+            return fail(ctx, RN_EUNSUPPORTED,
+                        "the asynchronous scheme needs groups of 4 conditions (this network has "
+                        "one condition on the register-table path)");
+        const int32_t C = n->C, T = n->T, L = n->lanes, npl = n->npl, G = n->G;
+        for (size_t k = 0; k < (size_t)C * T; ++k)
+            if (selected[k] < -1 || selected[k] >= N)
+                return fail(ctx, RN_EINVAL, "selected node %d outside -1 .. N-1", selected[k]);
+        // per step: the static "may move" bits, only at the selected node
+        std::vector<uint32_t> mt((size_t)G * T * L * npl, 0u);
+        for (int g = 0; g < G; ++g)
+            for (int32_t t = 0; t < T; ++t)
+                for (int q = 0; q < L * npl; ++q) {
+                    const int i = n->q_node[(size_t)q];
+                    if (i < 0) continue;
+                    uint32_t w = 0;
+                    for (int c = 0; c < 4 && 4 * g + c < C; ++c)
+                        if (selected[(size_t)(4 * g + c) * T + t] == i)
+                            w |= n->movable_h[(size_t)g * L * npl + q] & (0xffu << (8 * c));
+                    mt[((size_t)g * T + t) * L * npl + q] = w;
+                }
+        RN_CUDA(ctx, n->d_movable_t.upload(mt));
+    }
+    n->sync = scheme == 1;
+    n->async_ = scheme == 2;
     n->free_list.clear();
     for (int32_t j = 0; j < n->P; ++j)
-        if (!(n->has_frozen && n->frozen[(size_t)j]) && !(n->sync && j >= 3 * E && j < 3 * E + N))
+        if (!(n->has_frozen && n->frozen[(size_t)j]) &&
+            !((n->sync || n->async_) && j >= 3 * E && j < 3 * E + N))
             n->free_list.push_back(j);
-    RN_CUDA(ctx, cudaSetDevice(ctx->device));
     RN_CUDA(ctx, n->d_free.upload(n->free_list));
     n->chains_valid = false;
     ctx->gen++;

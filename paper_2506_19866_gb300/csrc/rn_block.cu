@@ -206,6 +206,10 @@ struct BlockPath {
             const int ncg = min(net.C - 4 * g, 4);
             for (int tau = 0; tau < T; ++tau) {
                 if (tau > 0) {
+                    if (net.async) {   // only the step's selected node may move
+                        const uint32_t *mt = net.movable_t + ((size_t)(g * T + tau) * kBT + t) * npl;
+                        for (int k = 0; k < npl; ++k) F(k, kF_MOV, t) = __ldg(mt + k);
+                    }
                     uint32_t m01 = 0, m23 = 0;
                     int o = 0;
                     for (int k = 0; k < npl; ++k) {

@@ -84,6 +84,9 @@ struct Network {
     int64_t n_obs = 0;                  // observed entries of the time course
     DevBuf<uint16_t> d_init_code, d_out_bits;
     DevBuf<uint32_t> d_obs, d_init_s4, d_movable;
+    std::vector<uint32_t> movable_h;    // host copy of d_movable
+    bool async_ = false;                // asynchronous update scheme (rn_set_update_scheme)
+    DevBuf<uint32_t> d_movable_t;       // [G][T][lanes][npl]: the step's selected node
     // chains
     int32_t n_chains = 0;
     int32_t pstride = 0;
@@ -99,7 +102,10 @@ struct Network {
         DevNet n{};
         n.N = N; n.E = E; n.P = P; n.n_free = (int32_t)free_list.size();
         n.C = C; n.T = T; n.G = G;
-        n.npl = npl; n.cg = cg; n.dtab = dtab; n.lanes = lanes; n.sync = sync ? 1 : 0;
+        n.npl = npl; n.cg = cg; n.dtab = dtab; n.lanes = lanes;
+        n.sync = (sync || async_) ? 1 : 0;
+        n.async = async_ ? 1 : 0;
+        n.movable_t = async_ ? d_movable_t.p : nullptr;
         for (int k = 0; k < kMaxSlots; ++k) n.D[k] = D[k];
         n.edge_id = d_edge_id.p; n.edge_q2 = d_edge_q2.p; n.edge_pos = d_edge_pos.p;
         n.node_q = d_node_q.p; n.q_node = d_q_node.p; n.src = d_src.p; n.dst = d_dst.p;

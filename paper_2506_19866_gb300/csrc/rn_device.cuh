@@ -40,7 +40,9 @@ struct DevNet {
     int32_t C, T, G;                    // conditions, time points, condition groups
     int32_t npl, cg, dtab;              // nodes per lane, conditions per group, table stride
     int32_t lanes;                      // threads per chain: 32 (a warp) or kBlockLanes
-    int32_t sync;                       // 1: synchronous update (every eligible node moves)
+    int32_t sync;                       // 1: every eligible node has the same priority
+                                        //    (synchronous and asynchronous schemes)
+    int32_t async;                      // 1: asynchronous scheme, movable_t below
     int32_t D[kMaxSlots];               // padded in-degree of each slot
     const int32_t *edge_id;             // [npl][dtab][32] edge index, or -1 - (code offset) for padding
     const uint8_t *edge_q2;             // [E] 2 * internal index of the edge's source
@@ -58,6 +60,8 @@ struct DevNet {
     const uint16_t *out_bits;           // [G][32] bit (k * cg + c): never moves
     const uint32_t *init_s4;            // [G][32 * npl] byte c: initial state, condition c
     const uint32_t *movable;            // [G][32 * npl] bit 7 of byte c: may move in c
+    const uint32_t *movable_t;          // [G][T][lanes * npl] the same per step under the
+                                        // asynchronous scheme (only the selected node)
     const uint32_t *obs;                // [C][T][32][npl] error table of each entry
 };
 
@@ -478,6 +482,13 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
             // the entry words of this time point, fetched ahead of the update
             // step where the policy does so
             const auto ahead = sync.template fetch_obs<NPL>(net, g, tau, lane);
+            if (net.async && tau > 0) {
+                // asynchronous scheme: only the step's selected node may move
+                const uint32_t *mt =
+                    net.movable_t + ((size_t)(g * T + tau) * LANES + lane) * NPL;
+#pragma unroll
+                for (int k = 0; k < NPL; ++k) mov[k] = __ldg(mt + k);
+            }
             if (tau > 0) {
                 uint32_t acc[NPL];
 #pragma unroll

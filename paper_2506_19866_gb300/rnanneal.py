@@ -52,7 +52,7 @@ SIGNATURES = {
     "rn_launch_count": (_c_int, [_vp, _vp]),
     "rn_batch_config": (_c_int, [_vp, _vp, _vp]),
     "rn_batch_tune": (_c_int, [_vp, _c_i32]),
-    "rn_set_update_scheme": (_c_int, [_vp, _c_i32, _c_i32]),
+    "rn_set_update_scheme": (_c_int, [_vp, _c_i32, _c_i32, _vp]),
     "rn_level_sync_noalloc": (_c_int, [_vp, _vp, _c_i32, _c_i64, _c_i32, _vp]),
     "rn_mlp_create": (_c_int, [_vp, _c_i32, _c_i32, _c_i32, _c_i64, _vp, _vp]),
     "rn_mlp_set_weights": (_c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp, ctypes.c_float]),
@@ -239,9 +239,11 @@ def rn_batch_config(ctx):
                 hybrid_networks=int(info[4]), config=int(info[5]), trial_ms=ms.tolist())
 
 
-def rn_set_update_scheme(ctx, net, scheme):
-    """0: priority updating (default); 1: synchronous updating (Section 2.2)."""
-    _check(ctx, load_library().rn_set_update_scheme(ctx, int(net), int(scheme)))
+def rn_set_update_scheme(ctx, net, scheme, selected=None):
+    """0: priority updating (default); 1: synchronous updating; 2: asynchronous
+    updating with selected[C][T] the node that may move at each step (Section 2.2)."""
+    sel = None if selected is None else _arr(selected, np.int32)
+    _check(ctx, load_library().rn_set_update_scheme(ctx, int(net), int(scheme), _p(sel)))
 
 
 def rn_batch_tune(ctx, config):

@@ -7,18 +7,22 @@ from tests.helpers import oracle_problem
 
 
 class Problem:
-    def __init__(self, w, ctx, noise=True, frozen=None, frozen_val=None, sync=False):
+    def __init__(self, w, ctx, noise=True, frozen=None, frozen_val=None, sync=False,
+                 async_sel=None):
         self.w = w
         base, tc, xs, flipped = oracle_problem(w, noise=noise)
         self.xs = xs
         self.flipped = flipped
-        self.net = O.Network(w.src, w.dst, w.fast, frozen, frozen_val, sync=sync)
+        self.net = O.Network(w.src, w.dst, w.fast, frozen, frozen_val, sync=sync,
+                             async_sel=async_sel)
         self.tc = tc
         self.ctx = ctx
         self.id = R.rn_load_network(ctx, w.src, w.dst, w.fast, frozen, frozen_val)
+        R.rn_load_timecourse(ctx, self.id, w.init, tc.ref, w.observed, w.knockout)
         if sync:
             R.rn_set_update_scheme(ctx, self.id, 1)
-        R.rn_load_timecourse(ctx, self.id, w.init, tc.ref, w.observed, w.knockout)
+        if async_sel is not None:
+            R.rn_set_update_scheme(ctx, self.id, 2, async_sel)
 
     @property
     def shape(self):

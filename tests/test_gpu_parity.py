@@ -250,9 +250,78 @@ def test_synchronous_scheme_in_batch(ctx):
     with pytest.raises(R.RNError) as e:
         R.rn_get_best(ctx, probs[0].id)
     assert e.value.code == R.RN_ESTATE
+    for bad in ((3, None), (2, None)):     # no such scheme; asynchronous without a selection
+        with pytest.raises(R.RNError) as e:
+            R.rn_set_update_scheme(ctx, probs[0].id, *bad)
+        assert e.value.code == R.RN_EINVAL
+
+
+def _selection(w, seed):
+    rng = np.random.default_rng(seed)
+    sel = rng.integers(0, w.N, size=(w.C, w.T)).astype(np.int32)
+    sel[rng.random((w.C, w.T)) < 0.1] = -1
+    return sel
+
+
+@pytest.mark.parametrize("n_nodes,n_cond", [(100, 6), (200, 5), (300, 4), (700, 3)])
+def test_asynchronous_scheme(ctx, n_nodes, n_cond):
+    # Section 2.2's asynchronous updating (one node, drawn for each step, may
+    # move) on the register tables, the hybrid path, the shared-memory tables
+    # and the block path: scores, trajectories and chains against the oracle
+    w = synth.random_network(60 + n_nodes, n_nodes, lam=4.0, cap=14, n_cond=n_cond, n_times=9,
+                             obs_frac=0.3)
+    p = Problem(w, ctx, async_sel=_selection(w, n_nodes))
+    X = np.concatenate([p.xs[None], random_vectors(p.net, 4, 19)])
+    score, traj = R.rn_evaluate(ctx, p.id, X, traj_shape=p.shape)
+    for k in range(X.shape[0]):
+        y, t = O.objective(p.net, p.tc, X[k], return_traj=True)
+        np.testing.assert_array_equal(traj[k], t, err_msg=f"vector {k}")
+        assert score[k] == y
+    n = 96
+    R.rn_init_chains(ctx, p.id, n, 4)
+    sched = R.schedule(4.0, 0.98)
+    R.rn_anneal(ctx, sched, 30)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    ids = [0, 2, 47, 95]
+    ch = _oracle_run(p, 4, n, O.Schedule(4.0, 0.98), 0, 30, ids)
+    _compare(st, ch, ids)
+
+
+def test_asynchronous_scheme_in_batch_and_limits(ctx):
+    # an asynchronous and a priority network in one batched launch; a single
+    # condition on the register tables cannot take the scheme; a new time
+    # course drops it
+    ws = [synth.random_network(93, 80, lam=4.0, cap=12, n_cond=4, n_times=8, obs_frac=0.3),
+          synth.random_network(94, 150, lam=4.0, cap=12, n_cond=5, n_times=8, obs_frac=0.3)]
+    probs = [Problem(ws[0], ctx, async_sel=_selection(ws[0], 1)), Problem(ws[1], ctx)]
+    for p in probs:
+        R.rn_init_chains(ctx, p.id, 64, 9)
+    sched = R.schedule(4.0, 0.98)
+    R.rn_anneal(ctx, sched, 20)
+    assert R.rn_batch_config(ctx)["networks"] == 2
+    for p in probs:
+        st = R.rn_get_chain_state(ctx, p.id, 64)
+        ids = [0, 31, 63]
+        ch = _oracle_run(p, 9, 64, O.Schedule(4.0, 0.98), 0, 20, ids)
+        _compare(st, ch, ids)
+    one = synth.random_network(95, 40, lam=3.0, cap=8, n_cond=1, n_times=6, obs_frac=0.5)
+    q = Problem(one, ctx)
     with pytest.raises(R.RNError) as e:
-        R.rn_set_update_scheme(ctx, probs[0].id, 2)
+        R.rn_set_update_scheme(ctx, q.id, 2, _selection(one, 2))
+    assert e.value.code == R.RN_EUNSUPPORTED
+    bad = _selection(ws[0], 3)
+    bad[0, 1] = ws[0].N
+    with pytest.raises(R.RNError) as e:
+        R.rn_set_update_scheme(ctx, probs[0].id, 2, bad)
     assert e.value.code == R.RN_EINVAL
+    p0 = probs[0]
+    X = np.concatenate([p0.xs[None], random_vectors(p0.net, 3, 5)])
+    np.testing.assert_array_equal(
+        R.rn_evaluate(ctx, p0.id, X), [O.objective(p0.net, p0.tc, x) for x in X])
+    R.rn_load_timecourse(ctx, p0.id, ws[0].init, p0.tc.ref, ws[0].observed, ws[0].knockout)
+    prio = O.Network(ws[0].src, ws[0].dst, ws[0].fast)
+    np.testing.assert_array_equal(
+        R.rn_evaluate(ctx, p0.id, X), [O.objective(prio, p0.tc, x) for x in X])
 
 
 def test_checkpoint_resume(ctx):

@@ -382,6 +382,45 @@ def test_synchronous_scheme_closed_form():
     assert (ch.n_accept > 0).all()
 
 
+def test_asynchronous_scheme_closed_form():
+    # Section 2.2's asynchronous updating with the selected node of each step
+    # drawn beforehand: with m = 0 and d = 2, at each step only the selected node
+    # moves, straight to clamp(K) of the previous states; every other node keeps
+    # its state.  Steps whose selection is -1 change nothing.
+    w = synth.tiny(22, n_nodes=6, indeg=3, n_cond=2, n_times=12)
+    E, N, C, T = w.E, w.N, w.C, w.T
+    rng = np.random.default_rng(5)
+    sel = rng.integers(0, N, size=(C, T)).astype(np.int32)
+    sel[rng.random((C, T)) < 0.15] = -1
+    net_a = O.Network(w.src, w.dst, w.fast, async_sel=sel)
+    tc = O.Timecourse(w.init, np.zeros((C, T, N), np.uint8), w.observed, w.knockout)
+    ko = np.zeros((C, N), bool) if w.knockout is None else w.knockout.astype(bool)
+    moved = 0
+    for seed in range(5):
+        x = O.init_chain(net_a, 40 + seed, 0).copy()
+        x[3 * E + N:3 * E + 2 * N] = 0                  # m = 0
+        x[3 * E + 2 * N:] = 2                            # d = 2
+        _, S = O.objective(net_a, tc, x, return_traj=True)
+        wv, pv, tv = x[:E].astype(int), x[E:2 * E].astype(int), x[2 * E:3 * E].astype(int)
+        for c in range(C):
+            for tau in range(1, T):
+                s = S[c, tau - 1].astype(int)
+                K = np.zeros(N, int)
+                np.add.at(K, w.dst, (s[w.src] // tv) * wv * pv)
+                want = s.copy()
+                i = sel[c, tau]
+                if i >= 0 and not ko[c, i]:
+                    want[i] = min(max(K[i], 0), 2)
+                np.testing.assert_array_equal(S[c, tau], want, err_msg=f"seed {seed} c {c} t {tau}")
+                moved += int((S[c, tau] != S[c, tau - 1]).sum())
+    assert moved > 0
+    # u has no effect, so it is never proposed
+    ch = O.start_chains(net_a, tc, 3, 5)
+    u0 = ch.x_cur[:, 3 * E:3 * E + N].copy()
+    O.anneal(net_a, tc, O.Schedule(5.0, 0.99), 3, ch, 0, 200)
+    np.testing.assert_array_equal(ch.x_cur[:, 3 * E:3 * E + N], u0)
+
+
 def test_grouped_level_sync():
     # Section 4.5's group-wise reduction: the level-end argmin runs within groups
     # of consecutive chains.  Within a level the chains are independent, so one
