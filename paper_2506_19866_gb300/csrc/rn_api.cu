@@ -107,6 +107,19 @@ uint32_t threshold(double T, int64_t dE)
     return f >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)f;
 }
 
+// Parameters GetCandidate may pick (Table 1): every one that is not fixed,
+// less the speeds u when the update scheme has no priorities (synchronous or
+// asynchronous updating, Section 2.2), where u has no effect.
+void build_free_list(Network &n)
+{
+    const int32_t E = n.E, N = n.N;
+    n.free_list.clear();
+    for (int32_t j = 0; j < n.P; ++j)
+        if (!(n.has_frozen && n.frozen[(size_t)j]) &&
+            !((n.sync || n.async_) && j >= 3 * E && j < 3 * E + N))
+            n.free_list.push_back(j);
+}
+
 // Node placement: nodes ranked by in-degree (descending, then index); rank r
 // goes to slot r / 32, lane r % 32, internal index q = lane * npl + slot.
 void build_layout(Network &n)
@@ -154,11 +167,7 @@ void build_layout(Network &n)
             n.out_edges[(size_t)fo[(size_t)n.src[(size_t)e]]++] = e;
         }
     }
-    n.free_list.clear();
-    for (int32_t j = 0; j < n.P; ++j)
-        if (!(n.has_frozen && n.frozen[(size_t)j]) &&
-            !((n.sync || n.async_) && j >= 3 * E && j < 3 * E + N))
-            n.free_list.push_back(j);   // (u has no effect without priorities)
+    build_free_list(n);
 
     n.supported = false;
     if (n.npl == 0) return;
@@ -901,11 +910,7 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
         // the selection table belongs to the previous time course: back to the
         // priority scheme (u proposed again) until the scheme is set again
         n->async_ = false;
-        n->free_list.clear();
-        for (int32_t j = 0; j < n->P; ++j)
-            if (!(n->has_frozen && n->frozen[(size_t)j]) &&
-                !(n->sync && j >= 3 * n->E && j < 3 * n->E + N))
-                n->free_list.push_back(j);
+        build_free_list(*n);
         RN_CUDA(ctx, n->d_free.upload(n->free_list));
     }
     n->C = C;
@@ -1034,11 +1039,7 @@ int rn_set_update_scheme(rn_ctx *ctx, int32_t net, int32_t scheme, const int32_t
     }
     n->sync = scheme == 1;
     n->async_ = scheme == 2;
-    n->free_list.clear();
-    for (int32_t j = 0; j < n->P; ++j)
-        if (!(n->has_frozen && n->frozen[(size_t)j]) &&
-            !((n->sync || n->async_) && j >= 3 * E && j < 3 * E + N))
-            n->free_list.push_back(j);
+    build_free_list(*n);
     RN_CUDA(ctx, n->d_free.upload(n->free_list));
     n->chains_valid = false;
     ctx->gen++;
