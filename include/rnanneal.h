@@ -347,8 +347,13 @@ int rn_mlp_log_chains(rn_ctx *ctx, int32_t mlp, int64_t *count);
 /* `steps` Adam steps (learning rate lr, beta1 0.9, beta2 0.999, eps 1e-8) on
  * minibatches of `batch` pairs (a multiple of 128, at most 65536) drawn
  * uniformly with replacement from the training set by Philox4x32-10 keyed by
- * `seed` (counter (step, 0, row, 8)).  *loss (may be NULL): mean loss of the
- * last minibatch. */
+ * `seed` (counter (step, 0, row, 8)).  Where the training set's targets
+ * spread less than 1/16 of their mean level, they are standardised by their
+ * mean and standard deviation for the steps (the output layer w3, b3 is mapped
+ * to that scale before -- unless it has never been trained -- and back after,
+ * so predictions stay in the targets' units).  *loss (may be NULL): mean
+ * squared error of the last minibatch, on the standardised scale when the
+ * targets were standardised. */
 int rn_mlp_train(rn_ctx *ctx, int32_t mlp, int32_t steps, int32_t batch, float lr, uint64_t seed,
                  float *loss);
 

@@ -205,14 +205,22 @@ __global__ void adam_kernel(float *__restrict__ theta, const float *__restrict__
 // `count` held pairs by Philox counter (step, 0, b, 8); tgt[b] its target.
 __global__ void sample_kernel(uint64_t seed, uint32_t step, int32_t B, uint32_t count,
                               const float *__restrict__ set_y, int32_t *__restrict__ idx,
-                              float *__restrict__ tgt)
+                              float *__restrict__ tgt, float mu, float inv_sigma)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     const uint4 r = philox(seed, step, 0u, (uint32_t)b, 8u);
     const uint32_t k = pick(r.x, count);
     idx[b] = (int32_t)k;
-    tgt[b] = set_y[k];
+    tgt[b] = (set_y[k] - mu) * inv_sigma;
+}
+
+// Output layer w3 <- a w3, b3 <- a b3 + c (one block).
+__global__ void affine_head_kernel(float *__restrict__ w3, int H2, float *__restrict__ b3,
+                                   float a, float c)
+{
+    for (int k = threadIdx.x; k < H2; k += blockDim.x) w3[k] *= a;
+    if (threadIdx.x == 0) *b3 = *b3 * a + c;
 }
 
 // Warp per chain: its x_cur row and delta_cur * scale into ring slot
@@ -943,10 +951,36 @@ int rn_mlp_train(rn_ctx *ctx, int32_t mlp, int32_t steps, int32_t batch, float l
     RN_CUDA(ctx, cudaSetDevice(ctx->device));
     int rc;
     if ((rc = ensure_batch(ctx, *m, batch))) return rc;
+    // Where the targets' spread is small against their level (below 1/16 of
+    // it), they are standardised by the training set's mean and spread, so that
+    // the fit spends the BF16 activations' precision (2^-8 relative) on the
+    // differences between states rather than on their common level; the output
+    // layer is mapped to the standardised scale for the steps and back
+    // afterwards, so predictions stay in the targets' units.  An output layer
+    // that has never been trained is taken to be on the standardised scale
+    // already (mapping it would multiply its random outputs by 1 / sigma).
+    std::vector<float> ys((size_t)m->count);
+    RN_CUDA(ctx, cudaMemcpyAsync(ys.data(), m->set_y.p, sizeof(float) * ys.size(),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    double mean = 0, var = 0;
+    for (float v : ys) mean += v;
+    mean /= (double)ys.size();
+    for (float v : ys) var += ((double)v - mean) * ((double)v - mean);
+    const double sd = std::sqrt(var / (double)ys.size());
+    const bool standardise = sd > 1e-12 && sd < std::fabs(mean) / 16.0;
+    const double mu = standardise ? mean : 0.0, sigma = standardise ? sd : 1.0;
+    float *w3 = m->theta.p + m->off_w3(), *b3p = m->theta.p + m->off_b3();
+    if (standardise && m->adam_t > 0) {
+        affine_head_kernel<<<1, 256, 0, ctx->stream>>>(w3, m->H2, b3p, (float)(1.0 / sigma),
+                                                       (float)(-mu / sigma));
+        if ((rc = check_launch(ctx, "output-layer scaling"))) return rc;
+    }
     const double b1 = 0.9, b2 = 0.999;
     for (int32_t s = 0; s < steps; ++s) {
         sample_kernel<<<(batch + 255) / 256, 256, 0, ctx->stream>>>(
-            seed, (uint32_t)s, batch, (uint32_t)m->count, m->set_y.p, m->idx.p, m->tgt.p);
+            seed, (uint32_t)s, batch, (uint32_t)m->count, m->set_y.p, m->idx.p, m->tgt.p,
+            (float)mu, (float)(1.0 / sigma));
         if ((rc = check_launch(ctx, "sample kernel"))) return rc;
         if ((rc = run_batch(ctx, *m, m->set_x.p, m->pstride, m->idx.p, batch, batch, m->tgt.p)))
             return rc;
@@ -958,6 +992,10 @@ int rn_mlp_train(rn_ctx *ctx, int32_t mlp, int32_t steps, int32_t batch, float l
                                                    (float)b2, (float)c1, (float)c2, 1e-8f);
         if ((rc = check_launch(ctx, "Adam kernel"))) return rc;
         if ((rc = refresh_copies(ctx, *m))) return rc;
+    }
+    if (standardise) {
+        affine_head_kernel<<<1, 256, 0, ctx->stream>>>(w3, m->H2, b3p, (float)sigma, (float)mu);
+        if ((rc = check_launch(ctx, "output-layer scaling"))) return rc;
     }
     if (loss) {
         double sse = 0;
