@@ -324,6 +324,43 @@ def test_asynchronous_scheme_in_batch_and_limits(ctx):
         R.rn_evaluate(ctx, p0.id, X), [O.objective(prio, p0.tc, x) for x in X])
 
 
+def test_scheduling_argument_errors(ctx):
+    # out-of-range batch tuning candidates and group sizes are refused
+    w = synth.make("hpg_9n_25e")
+    p = Problem(w, ctx)
+    for bad in (-2, 8):
+        with pytest.raises(R.RNError) as e:
+            R.rn_batch_tune(ctx, bad)
+        assert e.value.code == R.RN_EINVAL
+    R.rn_init_chains(ctx, p.id, 8, 1)
+    with pytest.raises(R.RNError) as e:
+        R.rn_anneal(ctx, R.schedule(5.0, 0.9, iters_per_level=3, global_sync=True,
+                                    sync_group=-1), 3)
+    assert e.value.code == R.RN_EINVAL
+
+
+def test_screened_step_under_synchronous_scheme(ctx):
+    # the screen's exact simulations use the network's update scheme: with
+    # eps = 1 a synchronous network's screened chains equal its plain chains
+    w = synth.random_network(96, 90, lam=4.0, cap=12, n_cond=4, n_times=8, obs_frac=0.3)
+    p = Problem(w, ctx, sync=True)
+    mid, D = R.rn_mlp_create(ctx, p.id, 256, 256, 16)
+    rng = np.random.default_rng(2)
+    R.rn_mlp_set_weights(ctx, mid, dict(
+        W1=(0.05 * rng.standard_normal((D, 256))).astype(np.float32), b1=np.zeros(256, np.float32),
+        W2=(0.05 * rng.standard_normal((256, 256))).astype(np.float32),
+        b2=np.zeros(256, np.float32), w3=(0.05 * rng.standard_normal(256)).astype(np.float32),
+        b3=0.0))
+    n = 64
+    R.rn_init_chains(ctx, p.id, n, 12)
+    sched = R.schedule(5.0, 0.97)
+    R.rn_anneal_screened(ctx, mid, sched, 15, K=32, top=2, eps=1.0)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    ids = [0, 7, 63]
+    ch = _oracle_run(p, 12, n, O.Schedule(5.0, 0.97), 0, 15, ids)
+    _compare(st, ch, ids)
+
+
 def test_checkpoint_resume(ctx):
     w = synth.make("mtb_63n_178e")
     p = Problem(w, ctx)
