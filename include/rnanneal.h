@@ -206,8 +206,7 @@ int rn_n_params(rn_ctx *ctx, int32_t net, int32_t *n_params);
  * keep counting toward their memory m); eligibility, m and d as before.
  *   selected  [C][T] node drawn by the caller for each step (entry tau = 0 is
  *             unused), for scheme 2 only (else ignored); needs the time course
- *             loaded first (RN_ESTATE), and groups of 4 conditions, i.e. not a
- *             single-condition network of at most 128 nodes (RN_EUNSUPPORTED).
+ *             loaded first (RN_ESTATE).
  * Under schemes 1 and 2 the speeds u have no effect, so GetCandidate no longer
  * proposes them (they keep their values).  A new rn_load_timecourse drops
  * scheme 2 (back to 0).  The network's chains must be initialised again

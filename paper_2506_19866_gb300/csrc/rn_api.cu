@@ -1014,28 +1014,29 @@ int rn_set_update_scheme(rn_ctx *ctx, int32_t net, int32_t scheme, const int32_t
         if (!selected) return fail(ctx, RN_EINVAL, "the asynchronous scheme needs `selected`");
         if (!n->has_tc) return fail(ctx, RN_ESTATE, "load the time course first");
         if (!n->supported) return require_supported(ctx, *n);
-        if (n->cg != 4)
-            return fail(ctx, RN_EUNSUPPORTED,
-                        "the asynchronous scheme needs groups of 4 conditions (this network has "
-                        "one condition on the register-table path)");
         const int32_t C = n->C, T = n->T, L = n->lanes, npl = n->npl, G = n->G;
         for (size_t k = 0; k < (size_t)C * T; ++k)
             if (selected[k] < -1 || selected[k] >= N)
                 return fail(ctx, RN_EINVAL, "selected node %d outside -1 .. N-1", selected[k]);
-        // per step: the static "may move" bits, only at the selected node
-        std::vector<uint32_t> mt((size_t)G * T * L * npl, 0u);
-        for (int g = 0; g < G; ++g)
-            for (int32_t t = 0; t < T; ++t)
-                for (int q = 0; q < L * npl; ++q) {
-                    const int i = n->q_node[(size_t)q];
-                    if (i < 0) continue;
-                    uint32_t w = 0;
-                    for (int c = 0; c < 4 && 4 * g + c < C; ++c)
-                        if (selected[(size_t)(4 * g + c) * T + t] == i)
-                            w |= n->movable_h[(size_t)g * L * npl + q] & (0xffu << (8 * c));
-                    mt[((size_t)g * T + t) * L * npl + q] = w;
-                }
-        RN_CUDA(ctx, n->d_movable_t.upload(mt));
+        // the scalar single-condition path reads the selection itself
+        RN_CUDA(ctx, n->d_async_sel.upload(std::vector<int32_t>(selected, selected + (size_t)C * T)));
+        // groups of 4 conditions: per step, the static "may move" bits only at
+        // the selected node
+        if (n->cg == 4) {
+            std::vector<uint32_t> mt((size_t)G * T * L * npl, 0u);
+            for (int g = 0; g < G; ++g)
+                for (int32_t t = 0; t < T; ++t)
+                    for (int q = 0; q < L * npl; ++q) {
+                        const int i = n->q_node[(size_t)q];
+                        if (i < 0) continue;
+                        uint32_t w = 0;
+                        for (int c = 0; c < 4 && 4 * g + c < C; ++c)
+                            if (selected[(size_t)(4 * g + c) * T + t] == i)
+                                w |= n->movable_h[(size_t)g * L * npl + q] & (0xffu << (8 * c));
+                        mt[((size_t)g * T + t) * L * npl + q] = w;
+                    }
+            RN_CUDA(ctx, n->d_movable_t.upload(mt));
+        }
     }
     n->sync = scheme == 1;
     n->async_ = scheme == 2;

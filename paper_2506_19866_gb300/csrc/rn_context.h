@@ -87,6 +87,7 @@ struct Network {
     std::vector<uint32_t> movable_h;    // host copy of d_movable
     bool async_ = false;                // asynchronous update scheme (rn_set_update_scheme)
     DevBuf<uint32_t> d_movable_t;       // [G][T][lanes][npl]: the step's selected node
+    DevBuf<int32_t> d_async_sel;        // [C][T] the selection itself
     // chains
     int32_t n_chains = 0;
     int32_t pstride = 0;
@@ -106,6 +107,7 @@ struct Network {
         n.sync = (sync || async_) ? 1 : 0;
         n.async = async_ ? 1 : 0;
         n.movable_t = async_ ? d_movable_t.p : nullptr;
+        n.async_sel = async_ ? d_async_sel.p : nullptr;
         for (int k = 0; k < kMaxSlots; ++k) n.D[k] = D[k];
         n.edge_id = d_edge_id.p; n.edge_q2 = d_edge_q2.p; n.edge_pos = d_edge_pos.p;
         n.node_q = d_node_q.p; n.q_node = d_q_node.p; n.src = d_src.p; n.dst = d_dst.p;

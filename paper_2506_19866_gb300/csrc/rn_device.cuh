@@ -62,6 +62,7 @@ struct DevNet {
     const uint32_t *movable;            // [G][32 * npl] bit 7 of byte c: may move in c
     const uint32_t *movable_t;          // [G][T][lanes * npl] the same per step under the
                                         // asynchronous scheme (only the selected node)
+    const int32_t *async_sel;           // [C][T] the selected node of each step (scalar path)
     const uint32_t *obs;                // [C][T][32][npl] error table of each entry
 };
 
@@ -626,8 +627,16 @@ __device__ __forceinline__ int32_t simulate_scalar(const Regs<NPL, D0, D1> &R, c
                         run[k][c] = t * sg;
                         pr[k] = abs(run[k][c]) >= R.m1[k] ? ua[k][c] : 0;
                         sn[k] = R.d2[k] ? tgt : s[k][c] + sg;
-                        pmax = max(pmax, pr[k]);
                     }
+                    if (net.async && g * CG + c < net.C) {
+                        // asynchronous scheme: only the step's selected node may move
+                        const int sel = __ldg(net.async_sel + (size_t)(g * CG + c) * T + tau);
+#pragma unroll
+                        for (int k = 0; k < NPL; ++k)
+                            if (net.q_node[lane * NPL + k] != sel) pr[k] = 0;
+                    }
+#pragma unroll
+                    for (int k = 0; k < NPL; ++k) pmax = max(pmax, pr[k]);
                     pmax = __reduce_max_sync(kFull, pmax);
 #pragma unroll
                     for (int k = 0; k < NPL; ++k) {

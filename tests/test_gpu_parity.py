@@ -263,11 +263,12 @@ def _selection(w, seed):
     return sel
 
 
-@pytest.mark.parametrize("n_nodes,n_cond", [(100, 6), (200, 5), (300, 4), (700, 3)])
+@pytest.mark.parametrize("n_nodes,n_cond", [(40, 1), (100, 6), (200, 5), (300, 4), (700, 3)])
 def test_asynchronous_scheme(ctx, n_nodes, n_cond):
     # Section 2.2's asynchronous updating (one node, drawn for each step, may
-    # move) on the register tables, the hybrid path, the shared-memory tables
-    # and the block path: scores, trajectories and chains against the oracle
+    # move) on the single-condition scalar path, the register tables, the hybrid
+    # path, the shared-memory tables and the block path: scores, trajectories
+    # and chains against the oracle
     w = synth.random_network(60 + n_nodes, n_nodes, lam=4.0, cap=14, n_cond=n_cond, n_times=9,
                              obs_frac=0.3)
     p = Problem(w, ctx, async_sel=_selection(w, n_nodes))
@@ -288,9 +289,8 @@ def test_asynchronous_scheme(ctx, n_nodes, n_cond):
 
 
 def test_asynchronous_scheme_in_batch_and_limits(ctx):
-    # an asynchronous and a priority network in one batched launch; a single
-    # condition on the register tables cannot take the scheme; a new time
-    # course drops it
+    # an asynchronous and a priority network in one batched launch; a node
+    # outside the network is refused; a new time course drops the scheme
     ws = [synth.random_network(93, 80, lam=4.0, cap=12, n_cond=4, n_times=8, obs_frac=0.3),
           synth.random_network(94, 150, lam=4.0, cap=12, n_cond=5, n_times=8, obs_frac=0.3)]
     probs = [Problem(ws[0], ctx, async_sel=_selection(ws[0], 1)), Problem(ws[1], ctx)]
@@ -304,11 +304,6 @@ def test_asynchronous_scheme_in_batch_and_limits(ctx):
         ids = [0, 31, 63]
         ch = _oracle_run(p, 9, 64, O.Schedule(4.0, 0.98), 0, 20, ids)
         _compare(st, ch, ids)
-    one = synth.random_network(95, 40, lam=3.0, cap=8, n_cond=1, n_times=6, obs_frac=0.5)
-    q = Problem(one, ctx)
-    with pytest.raises(R.RNError) as e:
-        R.rn_set_update_scheme(ctx, q.id, 2, _selection(one, 2))
-    assert e.value.code == R.RN_EUNSUPPORTED
     bad = _selection(ws[0], 3)
     bad[0, 1] = ws[0].N
     with pytest.raises(R.RNError) as e:
