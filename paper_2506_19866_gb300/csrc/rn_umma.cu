@@ -1,5 +1,5 @@
 // rn_umma.cu -- host side of the tcgen05 GEMM: TMA tensor maps (encoded with
-// the driver's cuTensorMapEncodeTiled, resolved through the runtime so that
+// the CUDA driver API's cuTensorMapEncodeTiled, resolved through the runtime so that
 // the library needs no link against libcuda) and the persistent launch.
 #include <cudaTypedefs.h>
 
