@@ -115,12 +115,13 @@ const char *rn_last_error(const rn_ctx *ctx);
  *   N <= 512, in-degree <= 16: a warp per chain (register tables up to 128
  *     nodes, shared-memory tables above);
  *   otherwise N <= 4096, in-degree <= 31: a block of 256 threads per chain
- *     (at least 2 nodes per thread), provided the
- *     chain's tables and node state fit one block's shared memory (227 KiB:
- *     52 bytes per node plus 1 KiB per table row, where nodes ranked by
- *     in-degree fill slots of 256 and each slot has as many rows as its
- *     largest in-degree rounded up to 4; e.g. 2000 nodes at mean in-degree 6,
- *     or about 2900 nodes at in-degree 2). */
+ *     (at least 2 nodes per thread; node state in registers up to 2048
+ *     nodes), provided the chain's tables fit one block's shared memory
+ *     (227 KiB: 1 KiB per table row, where nodes ranked by in-degree fill
+ *     slots of 256 and each slot has as many rows as its largest in-degree
+ *     rounded up to 4, plus 4 bytes per node up to 2048 nodes and 52 above;
+ *     the chain's x joins them there when it fits; e.g. 2000 nodes at mean
+ *     in-degree 6, or about 2900 nodes at in-degree 2). */
 int rn_load_network(rn_ctx *ctx, int32_t n_nodes, int32_t n_edges, const int32_t *src,
                     const int32_t *dst, const uint8_t *fast, const uint8_t *frozen,
                     const int8_t *frozen_val, int32_t *net_id);
