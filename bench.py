@@ -83,6 +83,49 @@ def algorithmic_ops_per_eval(w):
 # path, written back once) per launch, independent of sweeps per launch.
 ANNEAL_TRAFFIC = {"n120_c8_t21": 9.26e6, "n2000_c16_t33": 1.45e9}
 
+# Shared-memory wavefronts per proposal step of one chain from the same
+# captures: 110.3e6 over 4096 chains x 20 steps, and 7.88e9 over 16,384
+# chains x 2 steps (null moves included, as in the captured launches).
+ANNEAL_SMEM_WAVEFRONTS = {"n120_c8_t21": 110.3e6 / (4096 * 20),
+                          "n2000_c16_t33": 7.88e9 / (16384 * 2)}
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU model (MEASURED_PEAKS.json beside
+    this file), else the fallback figure of 6800 GB/s; with its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6800.0, "fallback figure (no measured peak on this machine)"
+
+
+def side_rooflines(workload, proposals, launches, total_s, sm_count, f_hz, lds_per_clk):
+    """Shared-memory and DRAM throughput of the annealing kernel beside its ALU
+    roofline, from the per-proposal wavefronts and per-launch DRAM bytes of
+    one ncu capture (single-network workloads only)."""
+    out = {}
+    wf = ANNEAL_SMEM_WAVEFRONTS.get(workload)
+    if wf and f_hz:
+        # one conflict-free gather instruction = one wavefront; an SM issues at
+        # most 4 shared loads per clock, so a larger reading is a failed probe
+        measured = 0.0 < lds_per_clk <= 4.0
+        per_clk = lds_per_clk if measured else 1.0
+        a, p = wf * proposals / total_s, sm_count * per_clk * f_hz
+        out["smem"] = {"achieved": a / 1e9, "peak": p / 1e9, "unit": "G wavefronts/s",
+                       "frac": a / p, "wavefronts_per_proposal": wf,
+                       "peak_basis": (f"{sm_count} SMs x {per_clk:.3f} wavefronts/clk/SM "
+                                      + ("(measured conflict-free byte gather, peaks.cu)"
+                                         if measured else "(nominal: 32 banks x 4 B per clock)")
+                                      + " x median SM clock")}
+    traffic = ANNEAL_TRAFFIC.get(workload)
+    if traffic:
+        peak, basis = hbm_peak_gbs()
+        a = traffic * launches / total_s / 1e9
+        out["hbm"] = {"achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+                      "peak_basis": basis}
+    return out
+
 
 def block_path(w):
     """Networks above 512 nodes or with an in-degree above 16 run on the block
@@ -495,6 +538,10 @@ def run_ours(args, rank, world, local_rank):
                                f"(measured, peaks.cu) x median SM clock {clk.get('sm_mhz')} MHz "
                                "sampled during the timed steps"),
                 "measured_issue_rates_per_sm_clk": peaks}
+    if len(ws) == 1 and rank == 0:
+        roofline["secondary"] = side_rooflines(
+            args.workload, ws[0].n_chains * S * args.steps, kernel_launches, total_s, sm_count,
+            f_hz, peaks.get("lds", 0.0))
     node_updates = sum(ev * w.C * (w.T - 1) * w.N for w, ev in zip(ws, evals_w)) / total_s
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,

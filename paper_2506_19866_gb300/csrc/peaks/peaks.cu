@@ -92,16 +92,21 @@ __global__ void imad_kernel(uint32_t seed, uint32_t *sink, unsigned long long *r
 }
 
 // Byte loads from a 128-byte shared array at data-dependent addresses (the
-// gather pattern of the simulator): 8 independent chains per thread.
+// gather pattern of the simulator): 8 independent chains per thread.  A chain
+// of loads cannot be scheduled outside the timed span: the first addresses
+// take a term of the start stamp (zero in practice, unknown to the compiler)
+// and the end stamp, after the barrier, is read under a branch on the loaded
+// values (a warp reaches the barrier only after all but its last load).
 __global__ void lds_kernel(uint32_t seed, uint32_t *sink, unsigned long long *rec)
 {
     __shared__ uint8_t tab[128];
     if (threadIdx.x < 128) tab[threadIdx.x] = (uint8_t)((threadIdx.x * 37u + seed) & 127u);
     __syncthreads();
+    const unsigned long long t0 = stamp();
+    const uint32_t z = (uint32_t)(t0 >> 62);
     uint32_t a[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a[k] = (threadIdx.x * 5u + 11u * k) & 127u;
-    const unsigned long long t0 = stamp();
+    for (int k = 0; k < 8; ++k) a[k] = ((threadIdx.x * 5u + 11u * k) ^ z) & 127u;
 #pragma unroll 4
     for (int it = 0; it < kIters; ++it) {
 #pragma unroll
@@ -110,14 +115,17 @@ __global__ void lds_kernel(uint32_t seed, uint32_t *sink, unsigned long long *re
     uint32_t r = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) r ^= a[k];
-    if (r == 0x12345678u) sink[0] = r;
     __syncthreads();
-    record(rec, t0, stamp());
+    unsigned long long t1 = 0;
+    if (r != seed) t1 = stamp();   // always taken: r < 128 <= seed
+    else sink[0] = r;
+    record(rec, t0, t1);
 }
 
 }  // namespace
 
-// Runs one of the kernels (0: ALU, 1: IMAD, 2: shared byte loads) with
+// Runs one of the kernels (0: ALU, 1: IMAD, 2: shared byte loads; seed 12345,
+// at least 128 as the shared-load kernel requires) with
 // `blocks_per_sm` blocks of 256 threads per SM; returns the median over SMs of
 // operations per SM clock (ALU / IMAD: per-lane operations; shared loads:
 // warp-level load instructions), or a negative value on failure.

@@ -1,0 +1,50 @@
+"""Host arithmetic of bench.py's side rooflines (no GPU): shared-memory
+wavefronts against the measured or nominal issue rate, DRAM bytes against the
+measured or fallback copy bandwidth."""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture()
+def bench():
+    sys.path.insert(0, ROOT)
+    import bench as b
+    return b
+
+
+def test_smem_uses_a_plausible_measured_rate(bench):
+    wf = bench.ANNEAL_SMEM_WAVEFRONTS["n120_c8_t21"]
+    r = bench.side_rooflines("n120_c8_t21", 1000, 2, 0.5, 152, 2.0e9, 1.5)["smem"]
+    assert r["achieved"] == pytest.approx(wf * 1000 / 0.5 / 1e9)
+    assert r["peak"] == pytest.approx(152 * 1.5 * 2.0e9 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert "measured" in r["peak_basis"]
+
+
+@pytest.mark.parametrize("rate", [5309.0, 0.0, -3.0])
+def test_smem_falls_back_to_one_wavefront_per_clock(bench, rate):
+    # an SM issues at most 4 shared loads per clock: a larger (or failed)
+    # reading is not used as a peak
+    r = bench.side_rooflines("n2000_c16_t33", 10, 1, 1.0, 152, 2.0e9, rate)["smem"]
+    assert r["peak"] == pytest.approx(152 * 2.0e9 / 1e9)
+    assert "nominal" in r["peak_basis"]
+
+
+def test_hbm_per_launch_traffic(bench, tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    r = bench.side_rooflines("n2000_c16_t33", 10, 3, 0.6, 152, 0.0, 1.0)
+    assert "smem" not in r                      # no clock sample: no shared-memory figure
+    assert r["hbm"]["achieved"] == pytest.approx(1.45e9 * 3 / 0.6 / 1e9)
+    assert r["hbm"]["peak"] == 6800.0 and "fallback" in r["hbm"]["peak_basis"]
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6767.4}))
+    r = bench.side_rooflines("n2000_c16_t33", 10, 3, 0.6, 152, 0.0, 1.0)
+    assert r["hbm"]["peak"] == 6767.4 and "measured" in r["hbm"]["peak_basis"]
+
+
+def test_no_capture_no_side_figures(bench):
+    assert bench.side_rooflines("batch256", 10, 1, 1.0, 152, 2.0e9, 1.0) == {}
