@@ -81,6 +81,18 @@ def test_evaluate_time_lengths(ctx, T):
     _eval_parity(p, random_vectors(p.net, 6, T))
 
 
+@pytest.mark.parametrize("n_nodes,n_cond", [(40, 1), (40, 5), (100, 8), (200, 3), (400, 2),
+                                            (700, 3)])
+def test_evaluate_longest_time_course(ctx, n_nodes, n_cond):
+    # T = 128, the most accepted: drive counters and u * (steps since the last
+    # update) take their widest values on every table path (scalar, grouped
+    # conditions, shared-memory tables, hybrid, block)
+    w = synth.random_network(300 + n_nodes, n_nodes, lam=4.0, cap=12, n_cond=n_cond,
+                             n_times=128, obs_frac=0.3)
+    p = Problem(w, ctx)
+    _eval_parity(p, random_vectors(p.net, 6, n_nodes))
+
+
 def test_evaluate_high_degree(ctx):
     # in-degree up to 16 (the largest compiled slot capacity)
     w = synth.random_network(9, 60, lam=10.0, cap=16, n_cond=2, n_times=12, obs_frac=0.5)
