@@ -122,3 +122,46 @@ def test_batched_early_reject_is_exact():
     for w, a, b in zip(nets, got[0], got[1]):
         for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"):
             np.testing.assert_array_equal(a[k], b[k], err_msg=f"{w.name} {k}")
+
+
+def test_batch256_full_size_sampled():
+    # the 256-network batch (65,536 chains) in the launch configuration the
+    # benchmark times: threshold tables cached, the autotuned candidate, the
+    # launch replayed from a CUDA graph.  Sampled chains of the smallest, a
+    # median, a 129-256-node (hybrid-eligible) and the largest network
+    # (shared-memory tables) against the oracle, every field of their state.
+    from paper_2506_19866_gb300 import build
+    build.build()
+    nets = synth.make_batch()
+    T0, alpha = nets[0].T0, nets[0].alpha
+    sched = R.schedule(T0, alpha)
+    S, calls = 8, 3
+    order = sorted(range(len(nets)), key=lambda b: nets[b].N)
+    picks = [order[0], order[len(order) // 2],
+             next(b for b in order if 128 < nets[b].N <= 256), order[-1]]
+    ctx = R.rn_create(0)
+    try:
+        probs = [Problem(w, ctx) for w in nets]
+        for p, w in zip(probs, nets):
+            R.rn_init_chains(ctx, p.id, w.n_chains, w.chain_seed)
+        R.rn_prepare_schedule(ctx, sched, S * calls)
+        for _ in range(calls):
+            R.rn_anneal(ctx, sched, S)
+        cfg = R.rn_batch_config(ctx)
+        states = {b: R.rn_get_chain_state(ctx, probs[b].id, nets[b].n_chains) for b in picks}
+    finally:
+        R.rn_destroy(ctx)
+    assert cfg["networks"] == len(nets) and cfg["graph"] and cfg["config"] >= 0
+    assert sum(w.n_chains for w in nets) == 65536
+    for b in picks:
+        p, w, st = probs[b], nets[b], states[b]
+        ids = [0, w.n_chains // 2, w.n_chains - 1]
+        ch = O.start_chains(p.net, p.tc, w.chain_seed, len(ids), chain_ids=ids)
+        O.anneal(p.net, p.tc, O.Schedule(T0, alpha), w.chain_seed, ch, 0, S * calls,
+                 chain_ids=ids)
+        for k, want in (("x_cur", ch.x_cur), ("x_best", ch.x_best), ("d_cur", ch.d_cur),
+                        ("d_best", ch.d_best)):
+            np.testing.assert_array_equal(st[k][ids], want, err_msg=f"{w.name} N={w.N} {k}")
+        np.testing.assert_array_equal(st["counters"][ids, 0], ch.n_accept)
+        np.testing.assert_array_equal(st["counters"][ids, 1], ch.n_uphill)
+        np.testing.assert_array_equal(st["counters"][ids, 2], ch.n_null)

@@ -179,3 +179,45 @@ def test_batch_with_block_network_equals_separate_runs(built):
             R.rn_destroy(c1)
         for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"):
             np.testing.assert_array_equal(st[k], alone[k], err_msg=f"{w.name} {k}")
+
+
+def test_scaleup_full_size_sampled(built):
+    # the scale-up set (the 2000-node network with 16,384 chains and 63
+    # networks of 100-1000 nodes, 32,768 chains) in the launch configuration
+    # the benchmark times: one rn_anneal call runs the batched launch and the
+    # block-path launches, threshold tables cached.  Sampled chains of the
+    # 2000-node network, a 513-1000-node one, a block-path network by in-degree
+    # and the largest and smallest batched networks against the oracle.
+    nets = synth.make_scaleup()
+    T0, alpha = nets[0].T0, nets[0].alpha
+    sched = R.schedule(T0, alpha)
+    S, calls = 2, 2
+    indeg = [int(np.bincount(w.dst, minlength=w.N).max()) for w in nets]
+    blk = [b for b, w in enumerate(nets) if w.N > 512 or indeg[b] > 16]
+    warp = [b for b in range(len(nets)) if b not in blk]
+    mid = [b for b in blk if 512 < nets[b].N < 2000]
+    by_degree = [b for b in blk if nets[b].N <= 512]
+    assert nets[0].N == 2000 and mid and by_degree
+    picks = [0, mid[0], by_degree[0], max(warp, key=lambda b: nets[b].N),
+             min(warp, key=lambda b: nets[b].N)]
+    ctx = R.rn_create(0)
+    try:
+        probs = [Problem(w, ctx) for w in nets]
+        for p, w in zip(probs, nets):
+            R.rn_init_chains(ctx, p.id, w.n_chains, w.chain_seed)
+        R.rn_prepare_schedule(ctx, sched, S * calls)
+        for _ in range(calls):
+            R.rn_anneal(ctx, sched, S)
+        cfg = R.rn_batch_config(ctx)
+        states = {b: R.rn_get_chain_state(ctx, probs[b].id, nets[b].n_chains) for b in picks}
+    finally:
+        R.rn_destroy(ctx)
+    assert cfg["networks"] == len(warp)
+    assert sum(w.n_chains for w in nets) == 32768
+    for b in picks:
+        p, w, st = probs[b], nets[b], states[b]
+        ids = [0, w.n_chains - 1]
+        ch = O.start_chains(p.net, p.tc, w.chain_seed, len(ids), chain_ids=ids)
+        O.anneal(p.net, p.tc, O.Schedule(T0, alpha), w.chain_seed, ch, 0, S * calls,
+                 chain_ids=ids)
+        _compare(st, ch, ids)
