@@ -64,6 +64,9 @@ def parse():
                          "start")
     ap.add_argument("--gain-train-steps", type=int, default=1000,
                     help="Adam steps of the --screen-gain training")
+    ap.add_argument("--batch-candidate", type=int, default=None,
+                    help="pin the batched launch to one of the autotuner's candidates (0-7, "
+                         "see rn_batch_config) instead of timing them")
     ap.add_argument("--screened", action="store_true",
                     help="time screened steps (K = 32 candidates ranked by a seeded one-hot "
                          "MLP, top 2 simulated exactly) instead of plain sweeps; value counts "
@@ -448,6 +451,8 @@ def run_ours(args, rank, world, local_rank):
     ids = [setup_problem(R, c, w)[0] for c, w in zip(net_ctx, ws)]
     for c, nid, w in zip(net_ctx, ids, ws):   # every rank anneals its own replica of the chains
         R.rn_init_chains(c, nid, w.n_chains, rank_seed(w, rank))
+    if args.batch_candidate is not None:
+        R.rn_batch_tune(ctx, args.batch_candidate)
     sched = R.schedule(ws[0].T0, ws[0].alpha)
     for c in {id(x): x for x in net_ctx}.values():
         R.rn_prepare_schedule(c, sched, (args.warmup + args.steps) * S)
