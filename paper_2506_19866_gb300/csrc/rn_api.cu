@@ -424,19 +424,18 @@ bool batchable(rn_ctx *ctx, const rn_schedule &s)
 
 // Global chain lists for the current table paths: the chains of networks on
 // large regions first (shared-memory or hybrid tables: the large-region
-// warps' queue), then the rest, each class in work order -- the large class
-// grouped by table path first, so that the warps in flight mostly run one
-// path's code at a time.
+// warps' queue), then the rest.  Each class is grouped by table path
+// (descending: 8, 6, 0 and 4, 2, 1 nodes per lane, which also follows network
+// size), in work order within a path, so that the warps in flight mostly run
+// one path's code at a time.
 int batch_items(rn_ctx *ctx, BatchState &B)
 {
     std::vector<int32_t> item_net, item_chain;
     int32_t big = 0;
     std::vector<size_t> seq(B.order.size());
     std::iota(seq.begin(), seq.end(), 0);
-    std::stable_sort(seq.begin(), seq.end(), [&](size_t a, size_t b) {
-        const bool la = batch_shared_tables(B.host_path[a]), lb = batch_shared_tables(B.host_path[b]);
-        return la && lb && B.host_path[a] > B.host_path[b];
-    });
+    std::stable_sort(seq.begin(), seq.end(),
+                     [&](size_t a, size_t b) { return B.host_path[a] > B.host_path[b]; });
     for (int pass = 0; pass < 2; ++pass)
         for (size_t b : seq) {
             if (batch_shared_tables(B.host_path[b]) != (pass == 0)) continue;

@@ -3,7 +3,8 @@
 // Every chain of every network is one "global chain" r.  Global chains come
 // in two classes with a work queue each: first the chains of networks on the
 // shared-memory tables (r < total_big), then those on register tables; within
-// a class, the network with the most work per chain first.  Item i of a class
+// a class grouped by table path, and within a path the network with the most
+// work per chain first.  Item i of a class
 // of n chains is chunk i / n of the class's chain i % n, so that, as in the
 // single-network kernel, the predecessor of an item (the previous chunk of the
 // same chain) was handed out n items earlier from the same queue.
