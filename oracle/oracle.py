@@ -20,8 +20,12 @@ ORC_OK, ORC_EINVAL, ORC_ECONSTRAINT, ORC_ENOMEM = 0, -1, -2, -3
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (plain C, -O2, no vector intrinsics)."""
-    stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < max(
+    """Compile oracle.c into liboracle.so (plain C, -O2, no vector intrinsics).
+    ORC_LIB names a prebuilt library to load instead: the pin tests run against
+    oracle builds with a planted mistake that way (tests/test_oracle_mutants.py)."""
+    if os.environ.get("ORC_LIB"):
+        return os.environ["ORC_LIB"]
+    stale =(not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h")))
     if force or stale:
         tmp = _LIB + f".{os.getpid()}.tmp"

@@ -459,3 +459,101 @@ def test_grouped_level_sync():
     np.testing.assert_array_equal(c.x_cur, d.x_cur)
     with pytest.raises(RuntimeError):
         O.anneal(net, tc, O.Schedule(6.0, 0.9, 5, True, True, sync_group=-1), 4, d, 40, 5)
+
+
+def test_anneal_steps_follow_table1_one_at_a_time():
+    # Every step of orc_anneal against Table 1 rebuilt from its parts: r =
+    # Philox(seed; g_lo, g_hi, chain, 0) (the pinned generator); GetCandidate on
+    # words 0 and 1 (the pinned proposal), a null move when it finds no
+    # alternative; accept iff dE <= 0 or word 2 < min(floor(exp(-dE / T_l) 2^32),
+    # 2^32 - 1), T_l = T0 alpha^l by repeated multiplication; counters of
+    # accepted, accepted uphill (dE > 0) and null moves; x_best on strict
+    # improvement only.
+    w = synth.tiny(8, n_nodes=5, indeg=2)
+    net, tc, xs, _ = oracle_problem(w)
+    seed, chain, n_iter, T0, alpha = 13, 3, 7, 4.0, 0.9
+    sched = O.Schedule(T0, alpha, iters_per_level=n_iter)
+    ch = O.start_chains(net, tc, seed, 1, chain_ids=[chain])
+    x, d = ch.x_cur[0].copy(), int(ch.d_cur[0])
+    xb, db = x.copy(), d
+    n_acc = n_up = n_null = 0
+    kinds = set()
+    for g in range(400):
+        O.anneal(net, tc, sched, seed, ch, g, 1, chain_ids=[chain])
+        r = [int(v) for v in O.philox(seed, [g & 0xFFFFFFFF, g >> 32, chain, 0])]
+        T = T0
+        for _ in range(g // n_iter):
+            T *= alpha
+        moved, j, v = O.propose(net, x, r[0], r[1])
+        if not moved:
+            n_null += 1
+            kinds.add("null")
+        else:
+            y = x.copy()
+            y[j] = v
+            dc = O.objective(net, tc, y)
+            dE = dc - d
+            accept = dE <= 0 or r[2] < min(math.floor(math.exp(-dE / T) * 2.0 ** 32), 2 ** 32 - 1)
+            kinds.add(("down" if dE < 0 else "neutral" if dE == 0 else "up")
+                      + ("" if accept else " rejected"))
+            if accept:
+                x, d = y, dc
+                n_acc += 1
+                n_up += int(dE > 0)
+                if dc < db:
+                    xb, db = y.copy(), dc
+        np.testing.assert_array_equal(ch.x_cur[0], x, err_msg=f"step {g}")
+        np.testing.assert_array_equal(ch.x_best[0], xb, err_msg=f"step {g}")
+        assert (int(ch.d_cur[0]), int(ch.d_best[0])) == (d, db), g
+        assert (int(ch.n_accept[0]), int(ch.n_uphill[0]), int(ch.n_null[0])) == \
+            (n_acc, n_up, n_null), g
+    assert {"null", "down", "neutral", "up", "up rejected"} <= kinds
+
+
+def test_reset_to_best_starts_each_level_from_x_best():
+    # reset_to_best (Table 1): each level starts from the chain's x_best.  L
+    # levels run with the reset equal the same levels run one at a time without
+    # it, with x_cur and delta_cur set to x_best and delta_best by hand first.
+    w = synth.tiny(9, n_nodes=5, indeg=2)
+    net, tc, xs, _ = oracle_problem(w)
+    n, L, n_iter = 5, 6, 8
+    a = O.start_chains(net, tc, 7, n)
+    O.anneal(net, tc, O.Schedule(6.0, 0.8, n_iter, reset_to_best=True), 7, a, 0, L * n_iter)
+    b = O.start_chains(net, tc, 7, n)
+    plain = O.Schedule(6.0, 0.8, n_iter)
+    away = 0
+    for level in range(L):
+        away += int((b.x_cur != b.x_best).any())
+        b.x_cur[:] = b.x_best
+        b.d_cur[:] = b.d_best
+        O.anneal(net, tc, plain, 7, b, level * n_iter, n_iter)
+    for k in ("x_cur", "x_best", "d_cur", "d_best", "n_accept", "n_uphill", "n_null"):
+        np.testing.assert_array_equal(getattr(a, k), getattr(b, k), err_msg=k)
+    assert away > 0                       # some level did start away from x_best
+
+
+def test_global_argmin_takes_the_lowest_chain_on_ties():
+    # The level-end argmin of Table 1 with several chains at the minimum: the
+    # lowest chain index wins (the first minimum of a serial scan).  Chains 0-2
+    # hold three different vectors that all score 0 on noise-free data of the
+    # planted vector; no step can improve on 0, so after one step and the
+    # level-end exchange every chain holds chain 0's vector.
+    w = synth.tiny(9, n_nodes=5, indeg=2)
+    net, tc, xs, _ = oracle_problem(w, noise=False)
+    assert O.objective(net, tc, xs) == 0
+    zeros = [xs]
+    for j in range(net.P):
+        for v in O.domain(net, j):
+            y = xs.copy()
+            y[j] = v
+            if v != xs[j] and O.check_params(net, y) == 0 and O.objective(net, tc, y) == 0:
+                zeros.append(y)
+    assert len(zeros) >= 3
+    worse = O.init_chain(net, 5, 0)
+    X = np.stack([zeros[1], zeros[2], xs, worse])
+    ch = O.Chains(X, np.array([O.objective(net, tc, x) for x in X], np.int32))
+    assert list(ch.d_best[:3]) == [0, 0, 0] and ch.d_best[3] > 0
+    O.anneal(net, tc, O.Schedule(2.0, 0.9, iters_per_level=1, global_sync=True), 5, ch, 0, 1)
+    for k in range(4):
+        np.testing.assert_array_equal(ch.x_best[k], zeros[1])
+        assert ch.d_best[k] == 0
