@@ -129,7 +129,37 @@ MUTANTS = [
     ("init_repair_wrong_sign", "Sec. 2.5.3",
      "if (!is_frozen(net, E + e)) x[E + e] = 1;",
      "if (!is_frozen(net, E + e)) x[E + e] = -1;"),
+    ("pick_by_modulo", "Table 1, a uniform draw",
+     "return (uint32_t)(((uint64_t)r * n) >> 32); }",
+     "return r % n; }"),
+    ("proposal_index_off_by_one", "Table 1, GetCandidate",
+     "        if (seen++ == want) { j = k; break; }",
+     "        if (++seen == want) { j = k; break; }"),
+    ("threshold_without_cap", "Table 1, A = exp(-dE / T)",
+     "    if (f >= 4294967295.0) return 0xFFFFFFFFu;\n",
+     ""),
+    ("level_temperature_one_level_late", "Table 1, T <- rho T",
+     "for (int64_t l = 0; l < level; l++) T *= alpha;",
+     "for (int64_t l = 0; l <= level; l++) T *= alpha;"),
+    ("repair_weight_from_index_word", "Sec. 2.5.3",
+     "            x[e] = (int8_t)(1 + (r[1] & 1u));\n            break;",
+     "            x[e] = (int8_t)(1 + (r[0] & 1u));\n            break;"),
+    ("knockout_not_zero_at_t0", "Sec. 2.4, knockouts",
+     "s[i] = (ko && ko[i]) ? 0 : tc->init[(size_t)c * N + i];",
+     "s[i] = tc->init[(size_t)c * N + i];"),
+    ("knockout_node_updates", "Sec. 2.4, knockouts",
+     "            if (ko && ko[i]) continue;\n",
+     ""),
     # the screening MLP
+    ("mlp_drops_second_bias", "screen: a2 = b2 + W2^T h1",
+     "            double s = b2[k];",
+     "            double s = 0.0;"),
+    ("mlp_bias_gradient_without_relu_mask", "screen: dL/db1",
+     "            d1[i] = a1[i] > 0.0 ? s : 0.0;",
+     "            d1[i] = s;"),
+    ("mlp_output_bias_gradient_dropped", "screen: dL/db3",
+     "        if (gb3) *gb3 += dy;",
+     "        if (gb3) *gb3 += 0.0;"),
     ("mlp_drops_hidden_relu", "screen: h1 = relu(a1)",
      "s += (a1[i] > 0.0 ? a1[i] : 0.0) * W2[(size_t)i * H2 + k];",
      "s += a1[i] * W2[(size_t)i * H2 + k];"),

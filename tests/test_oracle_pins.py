@@ -155,6 +155,10 @@ def test_threshold_closed_form_and_bounds():
             assert abs(thr / 2 ** 32 - a) <= 2 ** -32 + 1e-15 * a
         # beyond 32 ln 2 * T the acceptance probability is below 2^-32
         assert O.threshold(T, int(32 * math.log(2) * T) + 2) == 0
+    # the cap min(., 2^32 - 1): where exp(-dE / T) * 2^32 reaches 2^32 (dE = 0, or
+    # dE / T below the double's resolution) the word is the largest, not 0
+    assert O.threshold(5.0, 0) == 2 ** 32 - 1
+    assert O.threshold(1e20, 1) == 2 ** 32 - 1
 
 
 def test_metropolis_acceptance_rate():
@@ -245,6 +249,46 @@ def test_init_valid_and_uniform():
         assert len(counts) == k and chi2 < 16.3  # p = 0.001 at <= 2 d.o.f.
     # distinct chains start from distinct vectors
     assert len({x.tobytes() for x in X}) == len(X)
+
+
+def _pick(r, n):
+    return (int(r) * n) >> 32
+
+
+def test_init_follows_the_documented_draws():
+    # The seeded sample-and-repair sampler as the library documents it, rebuilt
+    # from the pinned generator: each x_j = dom_j[pick(word j & 3 of Philox(seed;
+    # j >> 2, 0, chain, 1))]; then each node (in order) with no in-edge of p = +1,
+    # w != 0 gets the pick(r0)-th of its in-edges set to p = +1, w = 1 + (r1 & 1),
+    # r = Philox(seed; i, 0, chain, 3); then each node with no out-edge of w != 0
+    # gets the pick(r0)-th of its out-edges set to w = 1 + (r1 & 1), r = Philox(
+    # seed; i, 1, chain, 3).  pick(r, n) = floor(r n / 2^32).
+    w = synth.tiny(4, n_nodes=6, indeg=2)
+    net = O.Network(w.src, w.dst, w.fast)
+    E, N, seed = w.E, w.N, 21
+    repaired_in = repaired_out = 0
+    for chain in range(400):
+        x = np.zeros(net.P, np.int8)
+        for j in range(net.P):
+            dom = O.domain(net, j)
+            x[j] = dom[_pick(O.philox(seed, [j >> 2, 0, chain, 1])[j & 3], len(dom))]
+        for i in range(N):
+            ins = [e for e in range(E) if w.dst[e] == i]
+            if any(x[e] != 0 and x[E + e] == 1 for e in ins):
+                continue
+            r = O.philox(seed, [i, 0, chain, 3])
+            e = ins[_pick(r[0], len(ins))]
+            x[E + e], x[e] = 1, 1 + (int(r[1]) & 1)
+            repaired_in += 1
+        for i in range(N):
+            outs = [e for e in range(E) if w.src[e] == i]
+            if any(x[e] != 0 for e in outs):
+                continue
+            r = O.philox(seed, [i, 1, chain, 3])
+            x[outs[_pick(r[0], len(outs))]] = 1 + (int(r[1]) & 1)
+            repaired_out += 1
+        np.testing.assert_array_equal(O.init_chain(net, seed, chain), x, err_msg=f"chain {chain}")
+    assert repaired_in > 50 and repaired_out > 10
 
 
 def test_init_reports_unsatisfiable():
