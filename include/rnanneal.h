@@ -227,6 +227,18 @@ int rn_set_chain_state(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed
                        const int8_t *x_cur, const int32_t *d_cur, const int8_t *x_best,
                        const int32_t *d_best, const int64_t *counters, int64_t step);
 
+/* Annealing statistics of a network, for acceptance-rate profiles such as
+ * the paper's (Section 3):
+ *   stats[0] accepted moves, stats[1] accepted uphill moves (dE > 0),
+ *   stats[2] null moves, each summed over the network's chains since
+ *   rn_init_chains (or as restored by rn_set_chain_state);
+ *   stats[3] chains; stats[4] the next global step.
+ * A level's counts are the difference of two calls around the rn_anneal that
+ * runs it; its acceptance rate is accepted / (chains * steps - null).
+ * Synchronises the context stream.  RN_EINVAL for a NULL stats, RN_ESTATE if
+ * the network has no chains. */
+int rn_get_stats(rn_ctx *ctx, int32_t net, int64_t stats[5]);
+
 /* Number of kernels this context has launched since rn_create. */
 int rn_launch_count(rn_ctx *ctx, int64_t *count);
 

@@ -1396,6 +1396,28 @@ int rn_get_chain_state(rn_ctx *ctx, int32_t net, int8_t *x_cur, int32_t *d_cur, 
     return RN_OK;
 }
 
+int rn_get_stats(rn_ctx *ctx, int32_t net, int64_t stats[5])
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    if (!stats) return fail(ctx, RN_EINVAL, "stats is NULL");
+    Network *n = get_net(ctx, net);
+    if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
+    if (!n->chains_valid) return fail(ctx, RN_ESTATE, "network %d has no chains", net);
+    const int32_t n_chains = n->chains().n;
+    std::vector<int64_t> cnt((size_t)3 * (size_t)n_chains);
+    int64_t step = 0;
+    const int rc = rn_get_chain_state(ctx, net, nullptr, nullptr, nullptr, nullptr, cnt.data(), &step);
+    if (rc) return rc;
+    int64_t sum[3] = {0, 0, 0};
+    for (size_t c = 0; c < (size_t)n_chains; ++c)
+        for (int k = 0; k < 3; ++k) sum[k] += cnt[3 * c + (size_t)k];
+    for (int k = 0; k < 3; ++k) stats[k] = sum[k];
+    stats[3] = n_chains;
+    stats[4] = step;
+    return RN_OK;
+}
+
 int rn_set_chain_state(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed,
                        const int8_t *x_cur, const int32_t *d_cur, const int8_t *x_best,
                        const int32_t *d_best, const int64_t *counters, int64_t step)

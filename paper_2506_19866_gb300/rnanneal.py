@@ -49,6 +49,7 @@ SIGNATURES = {
     "rn_set_chain_state": (_c_int, [_vp, _c_i32, _c_i32, _c_u64, _vp, _vp, _vp, _vp, _vp,
                                     _c_i64]),
     "rn_prepare_schedule": (_c_int, [_vp, ctypes.POINTER(rn_schedule), _c_i64]),
+    "rn_get_stats": (_c_int, [_vp, _c_i32, _vp]),
     "rn_launch_count": (_c_int, [_vp, _vp]),
     "rn_batch_config": (_c_int, [_vp, _vp, _vp]),
     "rn_batch_tune": (_c_int, [_vp, _c_i32]),
@@ -220,6 +221,15 @@ def rn_synchronize(ctx):
 
 def rn_prepare_schedule(ctx, sched: rn_schedule, total_steps):
     _check(ctx, load_library().rn_prepare_schedule(ctx, ctypes.byref(sched), int(total_steps)))
+
+
+def rn_get_stats(ctx, net):
+    """Accepted, uphill (dE > 0) and null moves summed over a network's chains,
+    the number of chains and the next global step."""
+    s = np.zeros(5, np.int64)
+    _check(ctx, load_library().rn_get_stats(ctx, int(net), _p(s)))
+    return dict(accepted=int(s[0]), uphill=int(s[1]), null=int(s[2]), chains=int(s[3]),
+                step=int(s[4]))
 
 
 def rn_launch_count(ctx):

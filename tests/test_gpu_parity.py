@@ -163,6 +163,37 @@ def test_anneal_small_all_chains(ctx):
     np.testing.assert_array_equal(x, ch.x_best[chain])
 
 
+def test_stats_per_level(ctx):
+    # rn_get_stats: the three counters summed over the chains, the chain count
+    # and the next step; a level's counts are the difference around its call,
+    # equal to the oracle's over every chain
+    w = synth.make("n15_c3_t11")
+    p = Problem(w, ctx)
+    with pytest.raises(R.RNError) as e:
+        R.rn_get_stats(ctx, p.id)
+    assert e.value.code == R.RN_ESTATE
+    R.rn_init_chains(ctx, p.id, w.n_chains, w.chain_seed)
+    assert R.rn_get_stats(ctx, p.id) == dict(accepted=0, uphill=0, null=0,
+                                            chains=w.n_chains, step=0)
+    sched = R.schedule(w.T0, w.alpha, iters_per_level=100)
+    osched = O.Schedule(w.T0, w.alpha, iters_per_level=100)
+    ch = O.start_chains(p.net, p.tc, w.chain_seed, w.n_chains)
+    prev = R.rn_get_stats(ctx, p.id)
+    for level in range(3):
+        R.rn_anneal(ctx, sched, 100)
+        now = R.rn_get_stats(ctx, p.id)
+        before = (ch.n_accept.sum(), ch.n_uphill.sum(), ch.n_null.sum())
+        O.anneal(p.net, p.tc, osched, w.chain_seed, ch, 100 * level, 100)
+        after = (ch.n_accept.sum(), ch.n_uphill.sum(), ch.n_null.sum())
+        got = [now[k] - prev[k] for k in ("accepted", "uphill", "null")]
+        assert got == [int(a - b) for a, b in zip(after, before)], level
+        assert now["step"] == 100 * (level + 1) and now["chains"] == w.n_chains
+        prev = now
+    st = R.rn_get_chain_state(ctx, p.id, w.n_chains)
+    assert [prev[k] for k in ("accepted", "uphill", "null")] == \
+        st["counters"].sum(axis=0).tolist()
+
+
 def test_anneal_large_subset(ctx):
     # the 120-node configuration at its full chain count (4096), 16 chains compared
     w = synth.make("n120_c8_t21")
