@@ -129,6 +129,18 @@ MUTANTS = [
     ("init_repair_wrong_sign", "Sec. 2.5.3",
      "if (!is_frozen(net, E + e)) x[E + e] = 1;",
      "if (!is_frozen(net, E + e)) x[E + e] = -1;"),
+    ("asynchronous_scheme_proposes_speeds", "Sec. 2.2, asynchronous updating",
+     "return !((net->sync || net->async_sel) && kind_of(net, j, &idx) == K_U);",
+     "return !(net->sync && kind_of(net, j, &idx) == K_U);"),
+    ("out_edge_constraint_ignores_weight", "Sec. 2.5.3",
+     "if (net->src[e] == i && x[e] != 0) out_nz++;",
+     "if (net->src[e] == i) out_nz++;"),
+    ("conditions_share_one_trajectory", "Sec. 2.3, S per condition",
+     "int32_t rc = orc_simulate(net, tc, x, c, buf + (size_t)c * T * N);",
+     "int32_t rc = orc_simulate(net, tc, x, c, buf);"),
+    ("row_t0_not_recorded", "Sec. 2.3, S row t0",
+     "        S[i] = (uint8_t)s[i];\n",
+     ""),
     ("pick_by_modulo", "Table 1, a uniform draw",
      "return (uint32_t)(((uint64_t)r * n) >> 32); }",
      "return r % n; }"),
