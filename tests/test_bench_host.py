@@ -48,3 +48,11 @@ def test_hbm_per_launch_traffic(bench, tmp_path, monkeypatch):
 
 def test_no_capture_no_side_figures(bench):
     assert bench.side_rooflines("batch256", 10, 1, 1.0, 152, 2.0e9, 1.0) == {}
+
+
+def test_algorithmic_ops_per_evaluation(bench):
+    # C (T-1) (2E + 12N) + 3 n_obs, worked by hand: 8*20*(2*581 + 12*120) + 3*4057
+    # and 16*32*(2*12113 + 12*2000) + 3*105073 -- the figures the profiles quote
+    from paper_2506_19866_gb300 import synth
+    assert bench.algorithmic_ops_per_eval(synth.make("n120_c8_t21")) == 428491
+    assert bench.algorithmic_ops_per_eval(synth.make("n2000_c16_t33")) == 25006931
