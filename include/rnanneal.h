@@ -239,6 +239,18 @@ int rn_set_chain_state(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed
  * the network has no chains. */
 int rn_get_stats(rn_ctx *ctx, int32_t net, int64_t stats[5]);
 
+/* Self-test of the failure path of the device-side waits (an addition of this
+ * library; the paper has none).  The annealing kernels' work queue waits, with
+ * an iteration limit, for the previous chunk of a chain; a wait that gives up
+ * sets the context's device flag and its kernel returns, and the next call
+ * that checks the flag fails with RN_ETIMEOUT.  This call runs that same wait
+ * in one warp, with a short limit (4096 polls), on a counter that nothing
+ * advances, and returns what the flag check reports: RN_ETIMEOUT, with
+ * rn_last_error naming the wait, when the path works.  The flag is cleared, so
+ * the context stays usable.  RN_ECUDA if the wait did not give up and report
+ * it; an earlier failure on the context stream is reported first. */
+int rn_selftest_wait(rn_ctx *ctx);
+
 /* Number of kernels this context has launched since rn_create. */
 int rn_launch_count(rn_ctx *ctx, int64_t *count);
 

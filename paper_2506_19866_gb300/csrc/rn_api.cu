@@ -1249,6 +1249,30 @@ int rn_prepare_schedule(rn_ctx *ctx, const rn_schedule *s, int64_t total_steps)
     return RN_OK;
 }
 
+int rn_selftest_wait(rn_ctx *ctx)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int rc = check_device_flag(ctx);   // a failure of earlier work is reported as such
+    if (rc) return rc;
+    DevBuf<int32_t> buf;               // [0] the counter nothing advances, [1] the outcome
+    RN_CUDA(ctx, buf.alloc(2));
+    RN_CUDA(ctx, cudaMemsetAsync(buf.p, 0, 2 * sizeof(int32_t), ctx->stream));
+    RN_CUDA(ctx, launch_wait_selftest(buf.p, ctx->dev_err.p, buf.p + 1, ctx->stream));
+    ctx->launches += 1;
+    RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int32_t satisfied = 1;
+    RN_CUDA(ctx, cudaMemcpy(&satisfied, buf.p + 1, sizeof satisfied, cudaMemcpyDeviceToHost));
+    rc = check_device_flag(ctx);
+    if (satisfied || rc != RN_ETIMEOUT)
+        return fail(ctx, RN_ECUDA, "self-test: the wait on a counter nothing advances did not "
+                                   "give up and report it (satisfied %d, status %d)",
+                    satisfied, rc);
+    return RN_ETIMEOUT;
+}
+
 int rn_launch_count(rn_ctx *ctx, int64_t *count)
 {
     if (!ctx || !count) return RN_EINVAL;

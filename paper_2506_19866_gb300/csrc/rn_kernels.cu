@@ -277,6 +277,24 @@ cudaError_t launch_init(const DevNet &net, const DevChains &ch, int32_t *status,
     return cudaGetLastError();
 }
 
+// One warp runs the work queue's wait, with a short poll limit, on a counter
+// that nothing advances: the wait gives up, sets the error flag and returns,
+// without any fault.  out = 1 if the wait was (wrongly) satisfied, else 0.
+constexpr int kSelftestPolls = 1 << 12;
+
+__global__ void wait_selftest_kernel(const int32_t *never, int32_t *err, int32_t *out)
+{
+    const bool ok = wait_for_chunk<kSelftestPolls>(never, 1, err, (int)(threadIdx.x & 31));
+    if (threadIdx.x == 0) *out = ok ? 1 : 0;
+}
+
+cudaError_t launch_wait_selftest(const int32_t *never, int32_t *err, int32_t *out,
+                                 cudaStream_t st)
+{
+    wait_selftest_kernel<<<1, 32, 0, st>>>(never, err, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_level_sync(const DevChains &ch, int32_t *winner, int32_t group,
                               cudaStream_t st)
 {

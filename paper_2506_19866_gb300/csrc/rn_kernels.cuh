@@ -304,8 +304,10 @@ __device__ __forceinline__ void warp_store_cg(void *dst, const void *src, int by
     for (int k = lane; k < (bytes >> 4); k += 32) __stcg(d + k, s[k]);
 }
 
-// Wait (bounded) until `done` reaches `need`; false if the wait gave up or
-// another warp reported a failure.  One lane polls; the result is broadcast.
+// Wait (bounded: LIMIT polls) until `done` reaches `need`; false if the wait
+// gave up or another warp reported a failure.  One lane polls; the result is
+// broadcast.
+template <int LIMIT = kWaitLimit>
 __device__ __forceinline__ bool wait_for_chunk(const int32_t *done, int need, int32_t *err,
                                                int lane)
 {
@@ -319,7 +321,7 @@ __device__ __forceinline__ bool wait_for_chunk(const int32_t *done, int need, in
                 ok = 0;
                 break;
             }
-            if (++polls > kWaitLimit) {
+            if (++polls > LIMIT) {
                 ok = 0;
                 atomicExch(err, 1);
                 break;

@@ -57,6 +57,10 @@ cudaError_t launch_anneal_block(const DevNet &net, const DevChains &ch, const De
 // entry per group.
 cudaError_t launch_level_sync(const DevChains &ch, int32_t *winner, int32_t group,
                               cudaStream_t st);
+// One warp waits, with a short limit, on a counter nothing advances (*never = 0):
+// the wait gives up and sets *err; *out = 1 if it was satisfied instead.
+cudaError_t launch_wait_selftest(const int32_t *never, int32_t *err, int32_t *out,
+                                 cudaStream_t st);
 
 // Many networks in one persistent launch (rn_batch.cu).
 struct DevBatch {

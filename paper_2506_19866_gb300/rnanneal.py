@@ -50,6 +50,7 @@ SIGNATURES = {
                                     _c_i64]),
     "rn_prepare_schedule": (_c_int, [_vp, ctypes.POINTER(rn_schedule), _c_i64]),
     "rn_get_stats": (_c_int, [_vp, _c_i32, _vp]),
+    "rn_selftest_wait": (_c_int, [_vp]),
     "rn_launch_count": (_c_int, [_vp, _vp]),
     "rn_batch_config": (_c_int, [_vp, _vp, _vp]),
     "rn_batch_tune": (_c_int, [_vp, _c_i32]),
@@ -230,6 +231,12 @@ def rn_get_stats(ctx, net):
     _check(ctx, load_library().rn_get_stats(ctx, int(net), _p(s)))
     return dict(accepted=int(s[0]), uphill=int(s[1]), null=int(s[2]), chains=int(s[3]),
                 step=int(s[4]))
+
+
+def rn_selftest_wait(ctx):
+    """Run one device-side wait that must give up; raises RNError with
+    RN_ETIMEOUT when the failure path works (see the header)."""
+    _check(ctx, load_library().rn_selftest_wait(ctx))
 
 
 def rn_launch_count(ctx):

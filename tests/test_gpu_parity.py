@@ -194,6 +194,24 @@ def test_stats_per_level(ctx):
         st["counters"].sum(axis=0).tolist()
 
 
+def test_bounded_wait_gives_up_and_reports(ctx):
+    # The failure path of the work queue's bounded waits, without any fault: one
+    # warp waits (4096 polls) on a counter that nothing advances.  The host reads
+    # RN_ETIMEOUT, the flag is cleared, and the context keeps working bit-exactly.
+    w = synth.make("n15_c3_t11")
+    p = Problem(w, ctx)
+    R.rn_init_chains(ctx, p.id, 8, w.chain_seed)
+    n0 = R.rn_launch_count(ctx)
+    with pytest.raises(R.RNError) as e:
+        R.rn_selftest_wait(ctx)
+    assert e.value.code == R.RN_ETIMEOUT and "gave up" in str(e.value)
+    assert R.rn_launch_count(ctx) == n0 + 1
+    R.rn_anneal(ctx, R.schedule(w.T0, w.alpha), 30)
+    st = R.rn_get_chain_state(ctx, p.id, 8)
+    ch = _oracle_run(p, w.chain_seed, 8, O.Schedule(w.T0, w.alpha), 0, 30)
+    _compare(st, ch, list(range(8)))
+
+
 def test_anneal_large_subset(ctx):
     # the 120-node configuration at its full chain count (4096), 16 chains compared
     w = synth.make("n120_c8_t21")
