@@ -40,6 +40,10 @@ int fail(rn_ctx *ctx, int code, const char *fmt, ...)
 
 int cuda_fail(rn_ctx *ctx, cudaError_t e, const char *what)
 {
+    // The runtime also records the error for the next cudaGetLastError, which the
+    // launchers check after every launch; reported here, it is cleared, so that a
+    // recoverable failure (an allocation too large) does not fail a later call.
+    (void)cudaGetLastError();
     return fail(ctx, e == cudaErrorMemoryAllocation ? RN_ENOMEM : RN_ECUDA, "%s: %s", what,
                 cudaGetErrorString(e));
 }

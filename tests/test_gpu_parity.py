@@ -212,6 +212,21 @@ def test_bounded_wait_gives_up_and_reports(ctx):
     _compare(st, ch, list(range(8)))
 
 
+def test_out_of_memory_is_reported_and_recoverable(ctx):
+    # chains far beyond the device's memory (2^31 - 1 rows of 192 bytes): RN_ENOMEM,
+    # and the same context keeps working bit-exactly afterwards
+    w = synth.make("n15_c3_t11")
+    p = Problem(w, ctx)
+    with pytest.raises(R.RNError) as e:
+        R.rn_init_chains(ctx, p.id, 2 ** 31 - 1, w.chain_seed)
+    assert e.value.code == R.RN_ENOMEM
+    R.rn_init_chains(ctx, p.id, 8, w.chain_seed)
+    R.rn_anneal(ctx, R.schedule(w.T0, w.alpha), 30)
+    st = R.rn_get_chain_state(ctx, p.id, 8)
+    ch = _oracle_run(p, w.chain_seed, 8, O.Schedule(w.T0, w.alpha), 0, 30)
+    _compare(st, ch, list(range(8)))
+
+
 def test_anneal_large_subset(ctx):
     # the 120-node configuration at its full chain count (4096), 16 chains compared
     w = synth.make("n120_c8_t21")
