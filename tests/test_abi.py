@@ -2,6 +2,7 @@
 declared in include/rnanneal.h (no compute calls: runs without a GPU)."""
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -48,3 +49,26 @@ def test_create_reports_missing_device(lib):
         R.rn_create(0)
     assert ei.value.code == R.RN_ECUDA
     assert R.rn_last_error(None)
+
+
+def test_header_is_plain_c_and_cxx():
+    for cmd in (["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                 "-x", "c", HEADER],
+                ["g++", "-std=c++17", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                 "-x", "c++", HEADER]):
+        subprocess.check_call(cmd)
+
+
+def test_c_program_links_every_entry_point(lib, tmp_path):
+    # a C program that takes the address of every declared entry point links
+    # against the library: the names have C linkage and the declarations are C
+    names = declared_entry_points()
+    src = tmp_path / "abi_link.c"
+    src.write_text('#include "rnanneal.h"\nint main(void) {\n    void (*fns[])(void) = {\n'
+                   + ",\n".join(f"        (void (*)(void))&{n}" for n in names)
+                   + "\n    };\n    return (int)(sizeof fns / sizeof fns[0]) == %d ? 0 : 1;\n}\n"
+                   % len(names))
+    cuda_lib = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64")
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.dirname(HEADER),
+                           str(src), "-L", os.path.dirname(R.LIB_PATH), "-lrnanneal",
+                           f"-Wl,-rpath-link,{cuda_lib}", "-o", str(tmp_path / "abi_link")])
