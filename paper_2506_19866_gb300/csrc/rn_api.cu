@@ -1011,7 +1011,7 @@ int rn_set_update_scheme(rn_ctx *ctx, int32_t net, int32_t scheme, const int32_t
     Network *n = get_net(ctx, net);
     if (!n) return fail(ctx, RN_EINVAL, "unknown network %d", net);
     if (scheme < 0 || scheme > 2) return fail(ctx, RN_EINVAL, "scheme %d is not 0, 1 or 2", scheme);
-    const int32_t N = n->N, E = n->E;
+    const int32_t N = n->N;
     RN_CUDA(ctx, cudaSetDevice(ctx->device));
     if (scheme == 2) {
         if (!selected) return fail(ctx, RN_EINVAL, "the asynchronous scheme needs `selected`");

@@ -344,7 +344,7 @@ __device__ __forceinline__ void run_chunk(Path &P, const DevNet &net, const DevC
                                           uint8_t *pos_in, int32_t *done_flag, int done_value,
                                           int lane)
 {
-    const int E = net.E, N = net.N;
+    const int E = net.E;
     int8_t *xg = ch.x_cur + (size_t)chain * ch.pstride;
     int8_t *xb = ch.x_best + (size_t)chain * ch.pstride;
     warp_load_cg(xs, xg, ch.pstride, lane);
