@@ -106,7 +106,8 @@ const char *rn_last_error(const rn_ctx *ctx);
  *              proposed, or NULL (everything free).
  *   frozen_val [P] values of the fixed parameters (ignored where frozen = 0),
  *              or NULL iff frozen is NULL.
- * Rejected with RN_EINVAL: N < 1, E < 1, N > 65535, an index out of range,
+ * Rejected with RN_EINVAL: N < 1, E < 1, N > 65535, P = 3E + 3N above
+ * 2^31 - 1, an index out of range,
  * a self-loop, a duplicate edge, a node without an in-edge or an out-edge
  * (the constraints of Section 2.5.3 could never hold), a fixed value outside
  * its domain.  On success *net_id receives the network's handle.
@@ -138,7 +139,8 @@ int rn_load_network(rn_ctx *ctx, int32_t n_nodes, int32_t n_edges, const int32_t
  * to the previous time point of the same condition where both are observed
  * and 0 otherwise (0 in row t0).  Replaces earlier data and invalidates the
  * chains' objective values (call rn_init_chains again).  RN_EINVAL if the
- * largest possible score, sum of 2 W over the entries, reaches 2^30. */
+ * largest possible score, sum of 2 W over the entries, reaches 2^30, or if
+ * C * T * N exceeds 2^31. */
 int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times,
                        const uint8_t *init, const uint8_t *knockout, const uint8_t *ref,
                        const uint8_t *observed);

@@ -806,6 +806,8 @@ int rn_load_network(rn_ctx *ctx, int32_t n_nodes, int32_t n_edges, const int32_t
     if (!src || !dst || !fast || !net_id) return fail(ctx, RN_EINVAL, "NULL array");
     if (n_nodes < 1 || n_nodes > 65535) return fail(ctx, RN_EINVAL, "n_nodes %d out of range", n_nodes);
     if (n_edges < 1) return fail(ctx, RN_EINVAL, "n_edges %d out of range", n_edges);
+    if (3 * (int64_t)n_edges + 3 * (int64_t)n_nodes > INT32_MAX)
+        return fail(ctx, RN_EINVAL, "P = 3E + 3N exceeds 2^31 - 1");
     if ((frozen == nullptr) != (frozen_val == nullptr))
         return fail(ctx, RN_EINVAL, "frozen and frozen_val must both be given or both be NULL");
     auto n = std::make_unique<Network>();
@@ -883,6 +885,8 @@ int rn_load_timecourse(rn_ctx *ctx, int32_t net, int32_t n_cond, int32_t n_times
     if ((int64_t)n_times > 128)
         return fail(ctx, RN_EINVAL, "n_times %d exceeds 128", n_times);
     const int32_t N = n->N, C = n_cond, T = n_times;
+    if ((int64_t)C * T * N > ((int64_t)1 << 31))
+        return fail(ctx, RN_EINVAL, "the time course has more than 2^31 entries");
     const size_t ctn = (size_t)C * T * N;
     for (size_t k = 0; k < (size_t)C * N; ++k) {
         if (init[k] > 2) return fail(ctx, RN_EINVAL, "init value %d outside 0..2", init[k]);
