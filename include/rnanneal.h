@@ -176,7 +176,9 @@ int rn_prepare_schedule(rn_ctx *ctx, const rn_schedule *sched, int64_t total_ste
  * is simulated; otherwise the candidate is simulated over every condition and
  * scored, and accepted iff dE <= 0 or r2 < thr(T_l, dE).  x_best follows
  * strict improvements.  Asynchronous on the context stream except for the
- * small threshold-table upload; RN_ESTATE if a network has no chains. */
+ * small threshold-table upload.  Networks without chains are skipped;
+ * RN_ESTATE if no network of the context has chains.  RN_EINVAL for sweeps < 0,
+ * iters_per_level < 1, sync_group < 0, or T0 or alpha not positive and finite. */
 int rn_anneal(rn_ctx *ctx, const rn_schedule *sched, int64_t sweeps);
 
 /* Best vector over a network's chains: lowest delta_best, lowest chain index
