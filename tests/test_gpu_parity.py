@@ -194,6 +194,26 @@ def test_stats_per_level(ctx):
         st["counters"].sum(axis=0).tolist()
 
 
+def test_empty_inputs(ctx):
+    # zero vectors to evaluate (host and device entries) and zero sweeps: no
+    # work, no launch, the state unchanged
+    w = synth.make("n15_c3_t11")
+    p = Problem(w, ctx)
+    R.rn_init_chains(ctx, p.id, 8, w.chain_seed)
+    before = R.rn_get_chain_state(ctx, p.id, 8)
+    n0 = R.rn_launch_count(ctx)
+    score, traj = R.rn_evaluate(ctx, p.id, np.zeros((0, p.net.P), np.int8), traj_shape=p.shape)
+    assert score.shape == (0,) and traj.shape == (0, *p.shape)
+    R.rn_evaluate_device(ctx, p.id, 0, None, None)
+    R.rn_anneal(ctx, R.schedule(w.T0, w.alpha), 0)
+    R.rn_synchronize(ctx)
+    assert R.rn_launch_count(ctx) == n0
+    after = R.rn_get_chain_state(ctx, p.id, 8)
+    for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"):
+        np.testing.assert_array_equal(after[k], before[k])
+    assert after["step"] == before["step"] == 0
+
+
 def test_bounded_wait_gives_up_and_reports(ctx):
     # The failure path of the work queue's bounded waits, without any fault: one
     # warp waits (4096 polls) on a counter that nothing advances.  The host reads
