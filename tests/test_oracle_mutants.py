@@ -172,6 +172,15 @@ MUTANTS = [
     ("mlp_output_bias_gradient_dropped", "screen: dL/db3",
      "        if (gb3) *gb3 += dy;",
      "        if (gb3) *gb3 += 0.0;"),
+    ("mlp_first_gradient_overwritten", "screen: dL/dW1 sums over the batch",
+     "for (int32_t i = 0; i < H1; i++) gW1[(size_t)r * H1 + i] += d1[i];",
+     "for (int32_t i = 0; i < H1; i++) gW1[(size_t)r * H1 + i] = d1[i];"),
+    ("mlp_loss_absolute", "screen: mean (y - t)^2",
+     "if (loss) *loss += diff * diff / B;",
+     "if (loss) *loss += fabs(diff) / B;"),
+    ("mlp_output_gradient_without_relu", "screen: dL/dw3 = dy h2",
+     "if (gw3) gw3[k] += dy * h2;",
+     "if (gw3) gw3[k] += dy * a2[k];"),
     ("mlp_drops_hidden_relu", "screen: h1 = relu(a1)",
      "s += (a1[i] > 0.0 ? a1[i] : 0.0) * W2[(size_t)i * H2 + k];",
      "s += a1[i] * W2[(size_t)i * H2 + k];"),
