@@ -72,3 +72,22 @@ def test_c_program_links_every_entry_point(lib, tmp_path):
     subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.dirname(HEADER),
                            str(src), "-L", os.path.dirname(R.LIB_PATH), "-lrnanneal",
                            f"-Wl,-rpath-link,{cuda_lib}", "-o", str(tmp_path / "abi_link")])
+
+
+def test_product_never_loads_the_oracle():
+    # the package and its kernels hold no import, library name or symbol of the
+    # oracle: the product path cannot route through it
+    pkg = os.path.join(B.ROOT, "paper_2506_19866_gb300")
+    pattern = re.compile(r"import\s+oracle|from\s+oracle|liboracle|\borc_[a-z]")
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                with open(os.path.join(root, f)) as fh:
+                    assert not pattern.search(fh.read()), os.path.join(root, f)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no fallback: without the built library the binding raises
+    monkeypatch.setattr(R, "_lib", None)
+    with pytest.raises(ImportError):
+        R.load_library(str(tmp_path / "librnanneal.so"))
