@@ -196,7 +196,10 @@ int rn_evaluate(rn_ctx *ctx, int32_t net, int32_t n, const int8_t *x, int32_t *s
 /* As rn_evaluate with device pointers (x_dev [n][P], score_dev [n],
  * traj_dev [n][C][T][N] or NULL) and no host synchronisation: the work is
  * queued on the context stream.  Values outside a domain give undefined
- * scores (not checked). */
+ * scores (not checked).  Each buffer must be device (or managed) memory of the
+ * context's device holding its full size within one allocation; a host
+ * pointer, another device's memory or a short buffer is refused with
+ * RN_EINVAL before anything is launched. */
 int rn_evaluate_device(rn_ctx *ctx, int32_t net, int32_t n, const int8_t *x_dev,
                        int32_t *score_dev, uint8_t *traj_dev);
 
@@ -316,9 +319,14 @@ int rn_batch_tune(rn_ctx *ctx, int32_t config);
  * call shares the array and leaves its contents behind; nothing in it needs to
  * start at zero, because each call writes every slot before reading it.  Calls
  * whose work overlaps on the GPU (two streams, or two host threads) race on
- * the array: order them on one stream.  Errors: RN_EINVAL for a NULL pointer or
- * a size out of range, RN_ECUDA if the device cannot be used; the message is
- * rn_last_error(NULL). */
+ * the array: order them on one stream.  The resolved address is kept for the
+ * life of the process; after a cudaDeviceReset of that device it would be
+ * stale, so the call is not supported after such a reset.  Before launching,
+ * the call checks that x_best and d_best are device (or managed) memory of the
+ * current device spanning the bytes above within their allocations.  Errors:
+ * RN_EINVAL for a NULL pointer, a host pointer, another device's memory, a
+ * buffer shorter than its span or a size out of range; RN_ECUDA if the device
+ * cannot be used; the message is rn_last_error(NULL). */
 int rn_level_sync_noalloc(int8_t *x_best, int32_t *d_best, int32_t n_chains, int64_t row_bytes,
                           int32_t n_params, void *stream);
 

@@ -17,6 +17,8 @@
 #include <utility>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/rnanneal.h"
 #include "rn_launch.h"
 
@@ -744,6 +746,64 @@ void set_detached_error(const char *fmt, ...)
     va_end(ap);
     g_create_error = buf;
 }
+
+namespace {
+PFN_cuMemGetAddressRange_v3020 address_range_fn()
+{
+    static PFN_cuMemGetAddressRange_v3020 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 3020, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuMemGetAddressRange_v3020>(p);
+        else
+            (void)cudaGetLastError();
+    }
+    return fn;
+}
+}  // namespace
+
+// A caller's device buffer of at least `bytes` bytes from p: device memory of
+// `device` (or managed memory), with [p, p + bytes) inside one allocation.
+// Anything else -- a host pointer, another device's memory, a span past the
+// end of its allocation -- would make a kernel fault, so it is refused here,
+// before any launch.  Writes the reason to `why` and returns RN_EINVAL.
+int check_device_span(const void *p, size_t bytes, int device, const char *name, char *why,
+                      size_t why_len)
+{
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        snprintf(why, why_len, "%s: not a pointer the CUDA runtime knows (%s)", name,
+                 cudaGetErrorString(e));
+        return RN_EINVAL;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+        snprintf(why, why_len, "%s: host memory where device memory is required", name);
+        return RN_EINVAL;
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device != device) {
+        snprintf(why, why_len, "%s: memory of device %d, the call runs on device %d", name,
+                 a.device, device);
+        return RN_EINVAL;
+    }
+    PFN_cuMemGetAddressRange_v3020 range = address_range_fn();
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    if (range && range(&base, &size, (CUdeviceptr)(uintptr_t)p) == CUDA_SUCCESS) {
+        const uint64_t lo = (uint64_t)(uintptr_t)p, end = (uint64_t)base + size;
+        if (lo + bytes > end) {
+            snprintf(why, why_len,
+                     "%s: %zu bytes needed, %llu left in its allocation from that address",
+                     name, bytes, (unsigned long long)(end - lo));
+            return RN_EINVAL;
+        }
+    }
+    return RN_OK;
+}
 }  // namespace rn
 
 using namespace rn;
@@ -1396,6 +1456,18 @@ int rn_evaluate_device(rn_ctx *ctx, int32_t net, int32_t count, const int8_t *x_
     int rc = require_supported(ctx, *n);
     if (rc) return rc;
     RN_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (count > 0) {
+        char why[256];
+        const size_t c = (size_t)count;
+        if ((rc = check_device_span(x_dev, c * (size_t)n->P, ctx->device, "x_dev", why,
+                                    sizeof why)) ||
+            (rc = check_device_span(score_dev, c * sizeof(int32_t), ctx->device, "score_dev",
+                                    why, sizeof why)) ||
+            (traj_dev && (rc = check_device_span(traj_dev, c * (size_t)n->C * (size_t)n->T *
+                                                               (size_t)n->N,
+                                                 ctx->device, "traj_dev", why, sizeof why))))
+            return fail(ctx, rc, "%s", why);
+    }
     return evaluate_device_impl(ctx, *n, count, x_dev, n->P, score_dev, nullptr, traj_dev);
 }
 

@@ -16,6 +16,8 @@
 
 namespace rn {
 void set_detached_error(const char *fmt, ...);
+int check_device_span(const void *p, size_t bytes, int device, const char *name, char *why,
+                      size_t why_len);
 }
 
 namespace {
@@ -80,7 +82,9 @@ std::mutex g_mutex;
 unsigned long long *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, resolved on the
-// first call for that device.
+// first call for that device and kept for the life of the process.  A
+// cudaDeviceReset unloads the library's device code, so the kept address is
+// stale afterwards: the header rules out calls after a reset.
 int scratch_address(int dev, unsigned long long **out)
 {
     std::lock_guard<std::mutex> lock(g_mutex);
@@ -88,6 +92,7 @@ int scratch_address(int dev, unsigned long long **out)
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) {
+            (void)cudaGetLastError();   // not left behind for a later call's launch check
             rn::set_detached_error("cudaGetSymbolAddress(scratch) on device %d: %s", dev,
                                    cudaGetErrorString(e));
             return RN_ECUDA;
@@ -120,8 +125,18 @@ extern "C" int rn_level_sync_noalloc(int8_t *x_best, int32_t *d_best, int32_t n_
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        (void)cudaGetLastError();
         rn::set_detached_error("no usable current device");
         return RN_ECUDA;
+    }
+    char why[256];
+    if (rn::check_device_span(x_best, (size_t)(n_chains - 1) * (size_t)row_bytes +
+                                          (size_t)n_params,
+                              dev, "x_best", why, sizeof why) != RN_OK ||
+        rn::check_device_span(d_best, (size_t)n_chains * sizeof(int32_t), dev, "d_best", why,
+                              sizeof why) != RN_OK) {
+        rn::set_detached_error("%s", why);
+        return RN_EINVAL;
     }
     unsigned long long *scratch = nullptr;
     const int rc = scratch_address(dev, &scratch);

@@ -115,6 +115,23 @@ def _dev(t):
     return int(t) if isinstance(t, int) else int(t.data_ptr())
 
 
+def _dev_checked(t, dtype_name, min_numel, name):
+    """Device address of a torch CUDA tensor after checking its device, dtype,
+    contiguity and size (a raw integer address is passed through; the library
+    checks it against its allocation)."""
+    if t is None or isinstance(t, int):
+        return _dev(t)
+    if not getattr(t, "is_cuda", False):
+        raise RNError(RN_EINVAL, f"{name}: a CUDA tensor is required")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise RNError(RN_EINVAL, f"{name}: dtype {t.dtype}, expected torch.{dtype_name}")
+    if not t.is_contiguous():
+        raise RNError(RN_EINVAL, f"{name}: must be contiguous")
+    if t.numel() < min_numel:
+        raise RNError(RN_EINVAL, f"{name}: {t.numel()} elements, at least {min_numel} needed")
+    return int(t.data_ptr())
+
+
 def rn_create(device: int = 0, stream=None):
     h = _vp()
     s = None if stream is None else int(stream)
@@ -190,8 +207,14 @@ def rn_evaluate(ctx, net, x, traj_shape=None):
 
 
 def rn_evaluate_device(ctx, net, n, x_dev, score_dev, traj_dev=None):
-    _check(ctx, load_library().rn_evaluate_device(ctx, int(net), int(n), _dev(x_dev),
-                                                  _dev(score_dev), _dev(traj_dev)))
+    """x_dev [n][P] int8, score_dev [n] int32, traj_dev [n][C][T][N] uint8 or
+    None: torch CUDA tensors (checked here) or raw device addresses."""
+    n = int(n)
+    P = rn_n_params(ctx, net) if n > 0 else 0
+    x = _dev_checked(x_dev, "int8", n * P, "x_dev") if n > 0 else _dev(x_dev)
+    s = _dev_checked(score_dev, "int32", n, "score_dev") if n > 0 else _dev(score_dev)
+    t = _dev_checked(traj_dev, "uint8", n, "traj_dev") if n > 0 else _dev(traj_dev)
+    _check(ctx, load_library().rn_evaluate_device(ctx, int(net), n, x, s, t))
 
 
 def rn_get_chain_state(ctx, net, n_chains):
@@ -271,9 +294,11 @@ def rn_batch_tune(ctx, config):
 def rn_level_sync_noalloc(x_best_dev, d_best_dev, n_chains, row_bytes, n_params, stream=None):
     """Level-end argmin + broadcast on caller-owned device buffers; allocates nothing."""
     s = None if stream is None else int(stream)
-    _check(None, load_library().rn_level_sync_noalloc(_dev(x_best_dev), _dev(d_best_dev),
-                                                      int(n_chains), int(row_bytes),
-                                                      int(n_params), s))
+    n, row, P = int(n_chains), int(row_bytes), int(n_params)
+    span = (n - 1) * row + P if n > 0 else 0
+    x = _dev_checked(x_best_dev, "int8", span, "x_best")
+    d = _dev_checked(d_best_dev, "int32", max(n, 0), "d_best")
+    _check(None, load_library().rn_level_sync_noalloc(x, d, n, row, P, s))
 
 
 # ---- learned proposal screen -------------------------------------------------

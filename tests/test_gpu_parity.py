@@ -114,6 +114,32 @@ def test_evaluate_device_entry(ctx):
     np.testing.assert_array_equal(sd.cpu().numpy(), expect)
 
 
+def test_evaluate_device_refuses_bad_buffers(ctx):
+    # host memory, short buffers and tensors of the wrong kind are refused
+    # before any launch (the library checks raw addresses against their
+    # allocation; the binding checks tensors)
+    import torch
+    p = Problem(synth.make("n15_c3_t11"), ctx)
+    P = p.net.P
+    xd = torch.from_numpy(O.init_chains(p.net, 3, 4)).cuda()
+    sd = torch.full((4,), -7, dtype=torch.int32, device="cuda")
+    host = np.zeros(4 * P, np.int8)
+    n0 = R.rn_launch_count(ctx)
+    with pytest.raises(R.RNError) as e:
+        R.rn_evaluate_device(ctx, p.id, 4, host.ctypes.data, sd.data_ptr())
+    assert e.value.code == R.RN_EINVAL and "x_dev" in str(e.value)
+    small = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(R.RNError) as e:     # 2^22 vectors of P bytes: past the allocation
+        R.rn_evaluate_device(ctx, p.id, 1 << 22, xd.data_ptr(), small.data_ptr())
+    assert e.value.code == R.RN_EINVAL and "allocation" in str(e.value)
+    for bad in (xd[:3], xd.to(torch.int32), xd.cpu(), xd.t()):
+        with pytest.raises(R.RNError) as e:
+            R.rn_evaluate_device(ctx, p.id, 4, bad, sd)
+        assert e.value.code == R.RN_EINVAL
+    R.rn_synchronize(ctx)
+    assert R.rn_launch_count(ctx) == n0 and (sd.cpu().numpy() == -7).all()
+
+
 @pytest.mark.parametrize("name", ["n15_c3_t11", "n120_c8_t21", "mtb_63n_178e"])
 def test_init_chains(ctx, name):
     p = Problem(synth.make(name), ctx)
@@ -152,11 +178,13 @@ def test_anneal_small_all_chains(ctx):
     p = Problem(w, ctx)
     R.rn_init_chains(ctx, p.id, w.n_chains, w.chain_seed)
     sched = R.schedule(w.T0, w.alpha)
-    R.rn_anneal(ctx, sched, 300)
-    R.rn_anneal(ctx, sched, 200)
+    # the whole run of the configuration (2000 sweeps, T from 10 down to 4.4e-4),
+    # in calls of uneven length, every chain compared at the end
+    for k in (300, 200, 1000, 499, 1):
+        R.rn_anneal(ctx, sched, k)
     st = R.rn_get_chain_state(ctx, p.id, w.n_chains)
-    assert st["step"] == 500
-    ch = _oracle_run(p, w.chain_seed, w.n_chains, O.Schedule(w.T0, w.alpha), 0, 500)
+    assert st["step"] == w.sweeps == 2000
+    ch = _oracle_run(p, w.chain_seed, w.n_chains, O.Schedule(w.T0, w.alpha), 0, w.sweeps)
     _compare(st, ch, list(range(w.n_chains)))
     x, score, chain = R.rn_get_best(ctx, p.id)
     assert score == int(ch.d_best.min()) and chain == int(np.argmin(ch.d_best))
@@ -263,6 +291,80 @@ def test_anneal_large_subset(ctx):
     y = R.rn_evaluate(ctx, p.id, st["x_cur"][sample])
     np.testing.assert_array_equal(y, st["d_cur"][sample])
     assert (st["d_best"] <= st["d_cur"]).all()
+
+
+def _chains_of(st, ids):
+    """The oracle's view of the GPU chains `ids` at a hand-over point."""
+    c = st["counters"][ids]
+    return O.Chains(st["x_cur"][ids], st["d_cur"][ids], st["x_best"][ids], st["d_best"][ids],
+                    c[:, 0], c[:, 1], c[:, 2])
+
+
+def test_anneal_late_schedule_subset(ctx):
+    # The 120-node configuration where its runs spend their time: the GPU
+    # anneals all 4096 chains to step 60,000 (T = 0.024) and to step 99,900
+    # (T = 4.4e-4, the last 100 steps of the 10^5-step schedule) in 500-step
+    # calls from cached threshold tables, as the benchmark does.  At each point
+    # 16 chains' state goes to the oracle, and 100 more steps of both sides must
+    # agree element by element.  Here every uphill threshold is 0 (empty tables),
+    # the level index is large and T is the product of 60,000+ multiplications.
+    w = synth.make("n120_c8_t21")
+    p = Problem(w, ctx)
+    R.rn_init_chains(ctx, p.id, w.n_chains, w.chain_seed)
+    sched = R.schedule(w.T0, w.alpha)
+    R.rn_prepare_schedule(ctx, sched, w.sweeps)
+    osched = O.Schedule(w.T0, w.alpha)
+    ids = [0, 5, 77, 151, 600, 1023, 1024, 2047, 2048, 2500, 3000, 3333, 4000, 4093, 4094, 4095]
+    g = 0
+    for g_check in (60000, 99900):
+        while g < g_check:
+            k = min(500, g_check - g)
+            R.rn_anneal(ctx, sched, k)
+            g += k
+        st = R.rn_get_chain_state(ctx, p.id, w.n_chains)
+        assert st["step"] == g
+        assert O.threshold(O.level_temperature(w.T0, w.alpha, g), 1) == 0
+        ch = _chains_of(st, ids)
+        for k, c in enumerate(ids):    # stored objectives are those of the stored vectors
+            assert O.objective(p.net, p.tc, st["x_cur"][c]) == st["d_cur"][c]
+            assert O.objective(p.net, p.tc, st["x_best"][c]) == st["d_best"][c]
+        O.anneal(p.net, p.tc, osched, w.chain_seed, ch, g, 100, chain_ids=ids)
+        R.rn_anneal(ctx, sched, 100)
+        g += 100
+        after = R.rn_get_chain_state(ctx, p.id, w.n_chains)
+        _compare(after, ch, ids)
+        moved = (after["counters"][ids, 0] - st["counters"][ids, 0]).sum()
+        assert moved > 0          # neutral moves are still accepted this late
+    assert g == w.sweeps
+
+
+def test_anneal_paper_mode_last_levels(ctx):
+    # The paper's schedule (T = 1000 -> 0.001 by 0.99, reset to x_best at each
+    # level start, global argmin at each level end) near its end: the GPU runs
+    # 40 chains to the middle of level 1372, the oracle takes every chain's
+    # state there, and both run on across the boundaries into levels 1373 and
+    # 1374 to the end of level 1374, the last level above T = 0.001.
+    w = synth.make("hpg_9n_25e")
+    p = Problem(w, ctx)
+    n, iters = 40, 6
+    R.rn_init_chains(ctx, p.id, n, 79)
+    sched = R.schedule(1000.0, 0.99, iters_per_level=iters, reset_to_best=True,
+                       global_sync=True)
+    g = 1372 * iters + 2
+    R.rn_prepare_schedule(ctx, sched, g + 4 * iters)
+    R.rn_anneal(ctx, sched, g - 1000)
+    R.rn_anneal(ctx, sched, 1000)
+    st = R.rn_get_chain_state(ctx, p.id, n)
+    assert st["step"] == g
+    assert O.count_levels(1000.0, 1e-3, 0.99) == 1375
+    ch = _chains_of(st, list(range(n)))
+    k = 1375 * iters - g
+    O.anneal(p.net, p.tc, O.Schedule(1000.0, 0.99, iters, True, True), 79, ch, g, k)
+    R.rn_anneal(ctx, sched, k)
+    after = R.rn_get_chain_state(ctx, p.id, n)
+    assert after["step"] == 1375 * iters
+    _compare(after, ch, list(range(n)))
+    assert (after["d_best"] == after["d_best"][0]).all()    # the last level ended in the argmin
 
 
 def test_anneal_paper_mode(ctx):

@@ -69,6 +69,32 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     build.build()
     x = torch.zeros(16, dtype=torch.int8, device="cuda")
     d = torch.zeros(1, dtype=torch.int32, device="cuda")
+    # raw addresses, so that the library's own size check answers
     with pytest.raises(R.RNError) as e:
-        R.rn_level_sync_noalloc(x, d, (1 << 20) + 1, 16, 8)
+        R.rn_level_sync_noalloc(x.data_ptr(), d.data_ptr(), (1 << 20) + 1, 16, 8)
     assert e.value.code == R.RN_EINVAL and "1048576" in R.rn_last_error(None)
+
+
+def test_noalloc_refuses_host_and_short_buffers():
+    # a host pointer or a buffer shorter than n_chains rows is refused before
+    # any kernel runs; the buffers are left as they were
+    import torch
+    from paper_2506_19866_gb300 import build
+    build.build()
+    x = torch.arange(64, dtype=torch.int8, device="cuda")
+    d = torch.arange(4, dtype=torch.int32, device="cuda") + 5
+    host = np.zeros(64, np.int8)
+    with pytest.raises(R.RNError) as e:
+        R.rn_level_sync_noalloc(host.ctypes.data, d.data_ptr(), 4, 16, 8)
+    assert e.value.code == R.RN_EINVAL and "x_best" in R.rn_last_error(None)
+    with pytest.raises(R.RNError) as e:            # rows 2^40 bytes apart: past any allocation
+        R.rn_level_sync_noalloc(x.data_ptr(), d.data_ptr(), 2, 1 << 40, 8)
+    assert e.value.code == R.RN_EINVAL and "allocation" in R.rn_last_error(None)
+    with pytest.raises(R.RNError) as e:            # the binding's own checks on tensors
+        R.rn_level_sync_noalloc(x, d, 5, 16, 8)
+    assert e.value.code == R.RN_EINVAL
+    with pytest.raises(R.RNError) as e:
+        R.rn_level_sync_noalloc(x.cpu(), d, 4, 16, 8)
+    assert e.value.code == R.RN_EINVAL
+    torch.cuda.synchronize()
+    assert (x.cpu().numpy() == np.arange(64)).all() and (d.cpu().numpy() == np.arange(4) + 5).all()
