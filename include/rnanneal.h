@@ -275,22 +275,29 @@ int rn_launch_count(rn_ctx *ctx, int64_t *count);
  * 129-256 nodes; p = 2 shared-memory tables for all; warps per block 4 (w = 0)
  * or 2 (w = 1); the warps with a region large enough for any network are the
  * work share of those networks.  c = 6, 7: p = 0 with 4 / 2 warps per block,
- * every warp with a large region.  With the threshold tables cached by rn_prepare_schedule, the
- * launch is captured once in a CUDA graph and replayed.  This reports the
+ * every warp with a large region.  c = 8, 9: phased launches, one kernel per
+ * table path in sequence (the paths of p = 0 and p = 1), so that an SM never
+ * runs two paths' code at once; each phase's warp region fits its own path's
+ * largest network, and each phase takes the warps per block (4 or 2) its trial
+ * ran faster with (a phased candidate's trial time is the sum of its phases').
+ * With the threshold tables cached by rn_prepare_schedule, the launch (all
+ * phases) is captured once in a CUDA graph and replayed.  This reports the
  * configuration in use:
  *   info[0] networks in the batch (0: no batch yet)
- *   info[1] warps per block
+ *   info[1] warps per block (phased: of the phase with the most chains)
  *   info[2] networks on a large warp region (shared-memory or hybrid tables)
  *   info[3] 1 if calls replay a CUDA graph
  *   info[4] networks on the hybrid path
  *   info[5] the candidate in use (-1: not tuned yet)
- *   trial_ms[8] (may be NULL) milliseconds of the candidates' trials (0 when
+ *   info[6] kernels of the batched launch: 1, or the phases of a phased one
+ *   trial_ms[10] (may be NULL) milliseconds of the candidates' trials (0 when
  *   the candidate was pinned by rn_batch_tune). */
-int rn_batch_config(rn_ctx *ctx, int32_t info[6], double trial_ms[8]);
+int rn_batch_config(rn_ctx *ctx, int32_t info[7], double trial_ms[10]);
 
-/* Pin the batched launch to candidate `config` (0 .. 7, see rn_batch_config)
+/* Pin the batched launch to candidate `config` (0 .. 9, see rn_batch_config)
  * instead of timing the candidates, or return to autotuning with -1.  Takes
- * effect at the next batched rn_anneal call.  RN_EINVAL outside -1 .. 7. */
+ * effect at the next batched rn_anneal call (a pinned phased candidate still
+ * times its phases' warps per block).  RN_EINVAL outside -1 .. 9. */
 int rn_batch_tune(rn_ctx *ctx, int32_t config);
 
 /* For callers that cannot let a library allocate device memory -- an

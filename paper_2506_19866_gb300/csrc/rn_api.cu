@@ -442,21 +442,44 @@ int batch_items(rn_ctx *ctx, BatchState &B)
     std::iota(seq.begin(), seq.end(), 0);
     std::stable_sort(seq.begin(), seq.end(),
                      [&](size_t a, size_t b) { return B.host_path[a] > B.host_path[b]; });
+    B.phases.clear();
     for (int pass = 0; pass < 2; ++pass)
         for (size_t b : seq) {
             if (batch_shared_tables(B.host_path[b]) != (pass == 0)) continue;
             const Network &n = *ctx->nets[(size_t)B.order[b]];
+            // a phase of a phased launch: the run of global chains of one path
+            const int32_t path = B.host_path[b];
+            if (B.phases.empty() || B.phases.back().path != path) {
+                BatchPhase ph{};
+                ph.path = path;
+                ph.r0 = (int32_t)item_net.size();
+                ph.queue = (int32_t)B.phases.size();
+                B.phases.push_back(ph);
+            }
+            B.phases.back().n += n.n_chains;
             for (int32_t c = 0; c < n.n_chains; ++c) {
                 item_net.push_back((int32_t)b);
                 item_chain.push_back(c);
             }
             if (pass == 0) big += n.n_chains;
         }
+    if (B.phases.size() > (size_t)kMaxPhases)
+        return fail(ctx, RN_EINVAL, "%zu table paths in one batch", B.phases.size());
     B.total = (int32_t)item_net.size();
     B.total_big = big;
     RN_CUDA(ctx, B.item_net.upload(item_net));
     RN_CUDA(ctx, B.item_chain.upload(item_chain));
     return RN_OK;
+}
+
+// Warps per block of a phased launch's phase of table path `path` (paths
+// 0, 1, 2, 4, 6, 8 index the slots 0 .. 5); 4 until tuned.
+int phase_slot(int path) { return path == 0 ? 0 : path == 1 ? 1 : path == 2 ? 2 : path == 4 ? 3 : path == 6 ? 4 : 5; }
+
+int phase_wpb_of(const BatchState &B, int path)
+{
+    const size_t k = (size_t)phase_slot(path);
+    return k < B.phase_wpb.size() && B.phase_wpb[k] > 0 ? B.phase_wpb[k] : 4;
 }
 
 // Item lists, warp regions (large: any network; small: register-table
@@ -486,6 +509,22 @@ int batch_region(rn_ctx *ctx, BatchState &B)
         B.large = std::min(B.wpb - 1,
                            std::max(1, (int)std::ceil(B.wpb * work_big / std::max(work_all, 1.0))));
     RN_CUDA(ctx, B.path.upload(B.host_path));
+    if (B.phased) {
+        // each phase's warp region fits that path's largest network
+        for (BatchPhase &ph : B.phases) {
+            ph.region = 16;
+            for (size_t b = 0; b < B.order.size(); ++b)
+                if (B.host_path[b] == ph.path) {
+                    const Network &n = *ctx->nets[(size_t)B.order[b]];
+                    ph.region = std::max(ph.region, batch_region_bytes(ph.path, n.D, n.npl,
+                                                                       n.pstride, n.N));
+                }
+            ph.wpb = phase_wpb_of(B, ph.path);
+            const cudaError_t e = batch_phase_grid(ph, ctx->sm_count);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "batched phase configuration");
+        }
+        return RN_OK;
+    }
     const size_t smem = batch_smem_bytes(B.wpb, B.large, B.region_bytes, B.region_small);
     const cudaError_t e = batch_resident_warps(B.wpb, smem, ctx->sm_count, &B.grid);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batched kernel configuration");
@@ -575,10 +614,17 @@ DevBatch batch_desc(const BatchState &B, int64_t sweeps)
     return d;
 }
 
-// Autotuner: the table path of the networks (register tables where they fit,
-// or shared-memory tables for all) and the warps per block (2 or 4), each
-// timed on the real batch for a few steps from the current state, which is
-// saved before and restored after the trials.  The fastest is kept.
+// Autotuner.  Candidates c < 8 are single launches: c < 6 the table paths
+// (c % 3: register tables where they fit and shared-memory tables elsewhere /
+// the same with the hybrid path for 6 or 8 nodes per lane / shared-memory
+// tables for all) x warps per block (c / 3: 4 / 2), large-region warps by the
+// work share; c = 6, 7: register tables where they fit, 4 / 2 warps per block,
+// every warp with a large region (no warp idles once the register-table work
+// is done).  c = 8, 9 are phased launches, one kernel per table path (8: the
+// paths of candidate 0, 9: those of candidate 1), each phase with the warps per
+// block (4 or 2) that its own trial timed faster.  Each candidate is timed on
+// the real batch for a few steps from the current state, which is saved before
+// and restored after the trials; the fastest is kept.
 int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
 {
     BatchState &B = ctx->batch;
@@ -607,12 +653,6 @@ int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
         }
         return RN_OK;
     };
-    // candidate c < 6: table paths (c % 3: register tables where they fit and
-    // shared-memory tables elsewhere / the same with the hybrid path for 6 or 8
-    // nodes per lane / shared-memory tables for all) x warps per block (c / 3:
-    // 4 / 2), large-region warps by the work share; c = 6, 7: register tables
-    // where they fit, 4 / 2 warps per block, every warp with a large region
-    // (no warp idles once the register-table work is done)
     std::vector<int32_t> best_fit(B.order.size(), 0), hybrid(B.order.size(), 0);
     for (size_t b = 0; b < B.order.size(); ++b) {
         const Network &n = *ctx->nets[(size_t)B.order[b]];
@@ -622,14 +662,18 @@ int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
         hybrid[b] = best_fit[b] == 0 && smemreg_layout(n.npl) ? n.npl : best_fit[b];
     }
     const std::vector<int32_t> all_smem(B.host_path.size(), 0);
-    auto apply = [&](int cfg) {
-        B.all_large = cfg >= 6;
-        B.host_path = cfg >= 6 || cfg % 3 == 0 ? best_fit : cfg % 3 == 1 ? hybrid : all_smem;
-        B.wpb = cfg >= 6 ? (cfg == 6 ? 4 : 2) : cfg / 3 == 0 ? 4 : 2;
+    auto apply = [&](int cfg, int phase_wpb) {
+        B.phased = cfg >= 8;
+        B.all_large = cfg == 6 || cfg == 7;
+        B.host_path = cfg >= 8 ? (cfg == 8 ? best_fit : hybrid)
+                      : cfg >= 6 || cfg % 3 == 0 ? best_fit
+                      : cfg % 3 == 1 ? hybrid : all_smem;
+        B.wpb = cfg >= 8 ? 4 : cfg >= 6 ? (cfg == 6 ? 4 : 2) : cfg / 3 == 0 ? 4 : 2;
+        if (phase_wpb) B.phase_wpb.assign(kMaxPhases, phase_wpb);
         B.cfg = cfg;
     };
-    if (B.force >= 0) {
-        apply(B.force);
+    if (B.force >= 0 && B.force < 8) {
+        apply(B.force, 0);
         int rc = batch_region(ctx, B);
         if (rc) return rc;
         B.tuned = true;
@@ -638,37 +682,80 @@ int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
     const int64_t trial = std::min<int64_t>(sweeps, 16);
     double best = 1e300;
     int best_cfg = 0;
-    cudaEvent_t e0, e1;
-    RN_CUDA(ctx, cudaEventCreate(&e0));
-    RN_CUDA(ctx, cudaEventCreate(&e1));
-    int rc = copy_state(true);
-    for (int cfg = 0; cfg < 8 && !rc; ++cfg) {
-        apply(cfg);
-        if ((rc = batch_region(ctx, B))) break;
+    std::vector<int32_t> best_phase_wpb;
+    cudaEvent_t ev[2 + 2 * kMaxPhases];
+    for (auto &e : ev) RN_CUDA(ctx, cudaEventCreate(&e));
+    // one trial of the current configuration; phase times into phase_ms
+    auto run_trial = [&](double &ms_total, std::vector<double> &phase_ms) -> int {
+        int rc = batch_region(ctx, B);
+        if (rc) return rc;
         DevSched sc = sc0;
         sc.g0 = 0;
         sc.g1 = trial;
-        plan_batch_chunks(B, sc);
         const DevBatch d = batch_desc(B, trial);
-        cudaEventRecord(e0, ctx->stream);
-        const cudaError_t e = launch_batch(d, sc, B.wpb, B.grid, ctx->stream);
-        cudaEventRecord(e1, ctx->stream);
-        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "batched kernel (autotune)"); break; }
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = RN_ECUDA; break; }
+        cudaEventRecord(ev[0], ctx->stream);
+        cudaError_t e;
+        if (B.phased) {
+            e = launch_batch_phased(d, sc, B.phases.data(), (int)B.phases.size(), ctx->stream,
+                                    ev + 2);
+        } else {
+            plan_batch_chunks(B, sc);
+            e = launch_batch(d, sc, B.wpb, B.grid, ctx->stream);
+        }
+        cudaEventRecord(ev[1], ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batched kernel (autotune)");
+        if (cudaEventSynchronize(ev[1]) != cudaSuccess) return RN_ECUDA;
         float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        B.tune_ms[cfg] = ms;
-        if (ms < best) { best = ms; best_cfg = cfg; }
-        if ((rc = copy_state(false))) break;
-        if ((rc = upload_batch_steps(ctx, B))) break;
-        ctx->launches += 2;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        ms_total = ms;
+        phase_ms.assign(B.phases.size(), 0.0);
+        if (B.phased)
+            for (size_t k = 0; k < B.phases.size(); ++k) {
+                float pm = 0;
+                cudaEventElapsedTime(&pm, ev[2 + 2 * k], ev[3 + 2 * k]);
+                phase_ms[k] = pm;
+            }
+        if ((rc = copy_state(false))) return rc;
+        if ((rc = upload_batch_steps(ctx, B))) return rc;
+        ctx->launches += B.phased ? (int64_t)B.phases.size() + 1 : 2;
+        return RN_OK;
+    };
+    int rc = copy_state(true);
+    for (int cfg = 0; cfg < kBatchCandidates && !rc; ++cfg) {
+        if (B.force >= 0 && cfg != B.force) continue;
+        if (cfg < 8) {
+            apply(cfg, 0);
+            double ms = 0;
+            std::vector<double> pm;
+            if ((rc = run_trial(ms, pm))) break;
+            B.tune_ms[cfg] = ms;
+            if (ms < best) { best = ms; best_cfg = cfg; }
+            continue;
+        }
+        // phased: every phase at 4 and at 2 warps per block, each phase keeps
+        // its faster one; the candidate's time is the sum of its phases'
+        std::vector<double> t4, t2;
+        double ms = 0;
+        apply(cfg, 4);
+        if ((rc = run_trial(ms, t4))) break;
+        apply(cfg, 2);
+        if ((rc = run_trial(ms, t2))) break;
+        std::vector<int32_t> pw(kMaxPhases, 4);
+        double sum = 0;
+        for (size_t k = 0; k < B.phases.size(); ++k) {
+            const int slot = phase_slot(B.phases[k].path);
+            pw[(size_t)slot] = t2[k] < t4[k] ? 2 : 4;
+            sum += std::min(t2[k], t4[k]);
+        }
+        B.tune_ms[cfg] = sum;
+        if (sum < best) { best = sum; best_cfg = cfg; best_phase_wpb = pw; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (auto &e : ev) cudaEventDestroy(e);
     if (rc) return rc;
     RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (int frc = check_device_flag(ctx)) return frc;
-    apply(best_cfg);
+    apply(best_cfg, 0);
+    if (best_cfg >= 8) B.phase_wpb = best_phase_wpb;
     if ((rc = batch_region(ctx, B))) return rc;
     B.tuned = true;
     return RN_OK;
@@ -711,12 +798,18 @@ int anneal_batched(rn_ctx *ctx, const rn_schedule &s, int64_t sweeps)
     sc.g1 = sweeps;
     plan_batch_chunks(B, sc);
     const DevBatch d = batch_desc(B, sweeps);
+    auto launch = [&]() {
+        return B.phased ? launch_batch_phased(d, sc, B.phases.data(), (int)B.phases.size(),
+                                              ctx->stream, nullptr)
+                        : launch_batch(d, sc, B.wpb, B.grid, ctx->stream);
+    };
+    const int64_t per_call = B.phased ? (int64_t)B.phases.size() + 1 : 2;
     if (cached) {
         const bool same = B.exec && B.graph_sweeps == sweeps && B.graph_early == s.early_reject;
         if (!same) {
             B.drop_graph();
             RN_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-            const cudaError_t e = launch_batch(d, sc, B.wpb, B.grid, ctx->stream);
+            const cudaError_t e = launch();
             cudaGraph_t g = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "batched kernel (capture)");
@@ -728,10 +821,10 @@ int anneal_batched(rn_ctx *ctx, const rn_schedule &s, int64_t sweeps)
         }
         RN_CUDA(ctx, cudaGraphLaunch(B.exec, ctx->stream));
     } else {
-        const cudaError_t e = launch_batch(d, sc, B.wpb, B.grid, ctx->stream);
+        const cudaError_t e = launch();
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batched kernel");
     }
-    ctx->launches += 2;
+    ctx->launches += per_call;
     for (int id : B.order) ctx->nets[(size_t)id]->step += sweeps;
     return RN_OK;
 }
@@ -836,7 +929,7 @@ int rn_create(rn_ctx **out, int device, void *stream)
         ctx->own_stream = true;
     }
     if (ctx->status.alloc(1) != cudaSuccess || ctx->winner.alloc(1) != cudaSuccess ||
-        ctx->queue.alloc(2) != cudaSuccess || ctx->done.alloc(1) != cudaSuccess ||
+        ctx->queue.alloc(kQueueSlots) != cudaSuccess || ctx->done.alloc(1) != cudaSuccess ||
         ctx->dev_err.alloc(1) != cudaSuccess)
         return fail(nullptr, RN_ENOMEM, "cannot allocate context buffers");
     if (cudaMemset(ctx->dev_err.p, 0, sizeof(int32_t)) != cudaSuccess)
@@ -1348,13 +1441,20 @@ int rn_launch_count(rn_ctx *ctx, int64_t *count)
     return RN_OK;
 }
 
-int rn_batch_config(rn_ctx *ctx, int32_t info[6], double trial_ms[8])
+int rn_batch_config(rn_ctx *ctx, int32_t info[7], double trial_ms[10])
 {
     if (!ctx || !info) return RN_EINVAL;
     const BatchState &B = ctx->batch;
     const bool on = B.valid && B.gen == ctx->gen;
     info[0] = on ? (int32_t)B.order.size() : 0;
-    info[1] = on ? B.wpb : 0;
+    int32_t wpb = B.wpb;
+    if (on && B.phased) {     // the phase with the most chains
+        int32_t most = -1;
+        for (const BatchPhase &ph : B.phases)
+            if (ph.n > most) { most = ph.n; wpb = ph.wpb; }
+    }
+    info[1] = on ? wpb : 0;
+    info[6] = on ? (B.phased ? (int32_t)B.phases.size() : 1) : 0;
     int32_t shared = 0, hybrid = 0;
     if (on)
         for (int32_t p : B.host_path) {
@@ -1366,7 +1466,7 @@ int rn_batch_config(rn_ctx *ctx, int32_t info[6], double trial_ms[8])
     info[4] = hybrid;
     info[5] = on && B.tuned ? B.cfg : -1;
     if (trial_ms)
-        for (int k = 0; k < 8; ++k) trial_ms[k] = B.tune_ms[k];
+        for (int k = 0; k < kBatchCandidates; ++k) trial_ms[k] = B.tune_ms[k];
     return RN_OK;
 }
 
@@ -1374,7 +1474,8 @@ int rn_batch_tune(rn_ctx *ctx, int32_t config)
 {
     if (!ctx) return RN_EINVAL;
     ctx->err.clear();
-    if (config < -1 || config > 7) return fail(ctx, RN_EINVAL, "config %d outside -1 .. 7", config);
+    if (config < -1 || config >= kBatchCandidates)
+        return fail(ctx, RN_EINVAL, "config %d outside -1 .. %d", config, kBatchCandidates - 1);
     ctx->batch.force = config;
     ctx->batch.tuned = false;
     ctx->batch.drop_graph();

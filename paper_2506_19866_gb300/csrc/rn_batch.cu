@@ -100,6 +100,52 @@ __device__ __noinline__ void chunk_smemreg(const DevNet &net, const DevChains &c
                                   lane);
 }
 
+// Global chain r's chunk cj: its network's descriptors into the warp's shared
+// memory, then the chunk on the network's table path (PATH >= 0: a path fixed
+// at compile time, so that only that path's code is in the kernel; -1: read
+// per network).
+template <int PATH>
+__device__ __forceinline__ void batch_item(const DevBatch &b, const DevSched &sc, int r, int cj,
+                                           DevNet *net_s, DevChains *ch_s, uint8_t *sm,
+                                           uint32_t codes, uint8_t *region, int lane)
+{
+    const int nb = __ldg(b.item_net + r), chain = __ldg(b.item_chain + r);
+    warp_copy_words(net_s, b.nets + nb, (int)sizeof(DevNet), lane);
+    warp_copy_words(ch_s, b.chains + nb, (int)sizeof(DevChains), lane);
+    __syncwarp();
+    const DevNet &net = *net_s;
+    const DevChains &ch = *ch_s;
+    const int64_t g0 = __ldcg(b.g0 + nb);
+    const int64_t g_lo = g0 + (int64_t)cj * sc.chunk;
+    const int64_t g_hi = min(g0 + b.sweeps, g_lo + sc.chunk);
+    const int path = PATH >= 0 ? PATH : __ldg(b.path + nb);
+    int32_t *flag = sc.done + r;
+    const int dv = cj + 1;
+    switch (path) {
+    case 1:
+        chunk_reg<1, kBatchD0, 1>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv,
+                                  lane);
+        break;
+    case 2:
+        chunk_reg<2, kBatchD0, kBatchD1>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag,
+                                         dv, lane);
+        break;
+    case 4:
+        chunk_reg<4, kBatchD0, kBatchD1>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag,
+                                         dv, lane);
+        break;
+    case 6:
+        chunk_smemreg<6>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv, lane);
+        break;
+    case 8:
+        chunk_smemreg<8>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv, lane);
+        break;
+    default:
+        chunk_smem(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv, lane);
+        break;
+    }
+}
+
 __global__ void __launch_bounds__(128, 3) anneal_batch_kernel(DevBatch b, DevSched sc)
 {
     extern __shared__ __align__(256) uint8_t sm[];
@@ -129,41 +175,37 @@ __global__ void __launch_bounds__(128, 3) anneal_batch_kernel(DevBatch b, DevSch
         const int cj = (int)(item / (unsigned)n_cls);
         const int r = (cls == 0 ? 0 : b.total_big) + (int)(item - (unsigned)cj * (unsigned)n_cls);
         if (cj > 0 && !wait_for_chunk(sc.done + r, cj, sc.err, lane)) return;
-        const int nb = __ldg(b.item_net + r), chain = __ldg(b.item_chain + r);
-        warp_copy_words(net_s, b.nets + nb, (int)sizeof(DevNet), lane);
-        warp_copy_words(ch_s, b.chains + nb, (int)sizeof(DevChains), lane);
-        __syncwarp();
-        const DevNet &net = *net_s;
-        const DevChains &ch = *ch_s;
-        const int64_t g0 = __ldcg(b.g0 + nb);
-        const int64_t g_lo = g0 + (int64_t)cj * sc.chunk;
-        const int64_t g_hi = min(g0 + b.sweeps, g_lo + sc.chunk);
-        const int path = __ldg(b.path + nb);
-        int32_t *flag = sc.done + r;
-        const int dv = cj + 1;
-        switch (path) {
-        case 1:
-            chunk_reg<1, kBatchD0, 1>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv,
-                                      lane);
-            break;
-        case 2:
-            chunk_reg<2, kBatchD0, kBatchD1>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi,
-                                             flag, dv, lane);
-            break;
-        case 4:
-            chunk_reg<4, kBatchD0, kBatchD1>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi,
-                                             flag, dv, lane);
-            break;
-        case 6:
-            chunk_smemreg<6>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv, lane);
-            break;
-        case 8:
-            chunk_smemreg<8>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv, lane);
-            break;
-        default:
-            chunk_smem(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv, lane);
-            break;
-        }
+        batch_item<-1>(b, sc, r, cj, net_s, ch_s, sm, codes, region, lane);
+    }
+}
+
+// One phase of a phased batch: the chains [ph.r0, ph.r0 + ph.n) of the
+// networks on table path PATH, every warp with a region sized for that path's
+// largest network, and the same chunk-major queue as above (the predecessor
+// of an item was handed out ph.n items earlier).
+template <int PATH>
+__global__ void __launch_bounds__(128, 3) anneal_phase_kernel(DevBatch b, DevSched sc,
+                                                              BatchPhase ph)
+{
+    extern __shared__ __align__(256) uint8_t sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    uint8_t *desc = sm + (uint32_t)wpb * kCodeBytesPerWarp;
+    DevNet *net_s = reinterpret_cast<DevNet *>(desc) + warp;
+    DevChains *ch_s =
+        reinterpret_cast<DevChains *>(desc + (uint32_t)wpb * sizeof(DevNet)) + warp;
+    uint8_t *region = sm + batch_head_bytes(wpb) + (uint32_t)warp * ph.region;
+    const uint32_t codes = (uint32_t)warp * kCodeBytesPerWarp;
+    const int64_t n_items = (int64_t)sc.n_chunks * ph.n;
+    for (;;) {
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(sc.queue + ph.queue, 1u);
+        item = __shfl_sync(kFull, item, 0);
+        if ((int64_t)item >= n_items) break;
+        const int cj = (int)(item / (unsigned)ph.n);
+        const int r = ph.r0 + (int)(item - (unsigned)cj * (unsigned)ph.n);
+        if (cj > 0 && !wait_for_chunk(sc.done + r, cj, sc.err, lane)) return;
+        batch_item<PATH>(b, sc, r, cj, net_s, ch_s, sm, codes, region, lane);
     }
 }
 
@@ -213,12 +255,69 @@ cudaError_t launch_batch(const DevBatch &b, const DevSched &sc, int wpb, int gri
                          cudaStream_t st)
 {
     const size_t smem = batch_smem_bytes(wpb, b.large, b.region_bytes, b.region_small);
-    cudaError_t err = cudaMemsetAsync(sc.queue, 0, 2 * sizeof(unsigned int), st);
+    cudaError_t err = cudaMemsetAsync(sc.queue, 0, kQueueSlots * sizeof(unsigned int), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(sc.done, 0, sizeof(int32_t) * (size_t)b.total, st);
     if (err != cudaSuccess) return err;
     anneal_batch_kernel<<<grid, wpb * 32, smem, st>>>(b, sc);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
+    advance_kernel<<<(b.n_nets + 127) / 128, 128, 0, st>>>(b.g0, b.n_nets, b.sweeps);
+    return cudaGetLastError();
+}
+
+namespace {
+using PhaseKernel = void (*)(DevBatch, DevSched, BatchPhase);
+
+PhaseKernel phase_kernel(int path)
+{
+    switch (path) {
+    case 1: return anneal_phase_kernel<1>;
+    case 2: return anneal_phase_kernel<2>;
+    case 4: return anneal_phase_kernel<4>;
+    case 6: return anneal_phase_kernel<6>;
+    case 8: return anneal_phase_kernel<8>;
+    default: return anneal_phase_kernel<0>;
+    }
+}
+}  // namespace
+
+size_t batch_phase_smem(const BatchPhase &ph)
+{
+    return batch_head_bytes(ph.wpb) + (size_t)ph.wpb * ph.region;
+}
+
+cudaError_t batch_phase_grid(BatchPhase &ph, int sm_count)
+{
+    const PhaseKernel k = phase_kernel(ph.path);
+    const size_t smem = batch_phase_smem(ph);
+    cudaError_t err =
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, ph.wpb * 32, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    ph.grid = sm_count * per_sm;
+    return cudaSuccess;
+}
+
+cudaError_t launch_batch_phased(const DevBatch &b, const DevSched &sc, const BatchPhase *ph,
+                                int n_ph, cudaStream_t st, cudaEvent_t *marks)
+{
+    cudaError_t err = cudaMemsetAsync(sc.queue, 0, kQueueSlots * sizeof(unsigned int), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(sc.done, 0, sizeof(int32_t) * (size_t)b.total, st);
+    if (err != cudaSuccess) return err;
+    for (int k = 0; k < n_ph; ++k) {
+        DevSched s = sc;
+        // chunks of 16 steps once the phase's chains outnumber its resident warps
+        plan_chunks(s, ph[k].n, (int64_t)ph[k].grid * ph[k].wpb);
+        if (marks) cudaEventRecord(marks[2 * k], st);
+        phase_kernel(ph[k].path)<<<ph[k].grid, ph[k].wpb * 32, batch_phase_smem(ph[k]), st>>>(
+            b, s, ph[k]);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        if (marks) cudaEventRecord(marks[2 * k + 1], st);
+    }
     advance_kernel<<<(b.n_nets + 127) / 128, 128, 0, st>>>(b.g0, b.n_nets, b.sweeps);
     return cudaGetLastError();
 }

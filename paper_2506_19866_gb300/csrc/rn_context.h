@@ -141,6 +141,7 @@ struct SchedCache {
 
 // Device descriptors of a batched launch over every network with chains, the
 // autotuned configuration, and the CUDA graph that replays the launch.
+constexpr int kBatchCandidates = 10;
 struct BatchState {
     bool valid = false;
     uint64_t gen = 0;                 // context generation it was built for
@@ -159,7 +160,10 @@ struct BatchState {
     int wpb = 4, grid = 0;
     bool tuned = false;
     bool g0_synced = false;           // device g0 equals the host step counters
-    double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // trial times of the candidates
+    bool phased = false;              // one launch per table path (candidates 8, 9)
+    std::vector<BatchPhase> phases;   // of a phased launch, in launch order
+    std::vector<int32_t> phase_wpb;   // warps per block of each phase (by table path)
+    double tune_ms[kBatchCandidates] = {};   // trial times of the candidates
     int32_t force = -1;               // candidate pinned by rn_batch_tune (-1: autotune)
     int32_t cfg = 0;                  // candidate in use
     // graph of [queue reset, batched kernel, step advance]

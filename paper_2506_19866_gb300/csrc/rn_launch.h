@@ -90,4 +90,22 @@ cudaError_t batch_resident_warps(int wpb, size_t smem, int sm_count, int *grid);
 cudaError_t launch_batch(const DevBatch &b, const DevSched &sc, int wpb, int grid,
                          cudaStream_t st);
 
+// A phased batch runs one launch per table path, each over that path's global
+// chains [r0, r0 + n) with its own work queue (slot `queue`), warp region,
+// warps per block and resident grid.
+struct BatchPhase {
+    int32_t path, r0, n, queue;
+    uint32_t region;
+    int32_t wpb, grid;
+};
+constexpr int kMaxPhases = 6;           // table paths 8, 6, 0, 4, 2, 1
+constexpr int kQueueSlots = 8;          // work-queue counters of a context
+size_t batch_phase_smem(const BatchPhase &ph);
+// Resident grid of the phase's kernel (sets its dynamic shared-memory limit).
+cudaError_t batch_phase_grid(BatchPhase &ph, int sm_count);
+// Queue and done resets, every phase in order, the step advance.  With
+// `marks` (2 per phase, may be NULL) an event is recorded around each phase.
+cudaError_t launch_batch_phased(const DevBatch &b, const DevSched &sc, const BatchPhase *ph,
+                                int n_ph, cudaStream_t st, cudaEvent_t *marks);
+
 }  // namespace rn

@@ -270,13 +270,15 @@ def rn_launch_count(ctx):
 
 def rn_batch_config(ctx):
     """Networks, warps per block, large-region (shared-memory or hybrid) networks,
-    graph replay, hybrid networks, candidate in use, trial ms of the candidates."""
-    info = np.zeros(6, np.int32)
-    ms = np.zeros(8, np.float64)
+    graph replay, hybrid networks, candidate in use, kernels per batched launch
+    (phases), trial ms of the candidates."""
+    info = np.zeros(7, np.int32)
+    ms = np.zeros(10, np.float64)
     _check(ctx, load_library().rn_batch_config(ctx, _p(info), _p(ms)))
     return dict(networks=int(info[0]), warps_per_block=int(info[1]),
                 shared_path_networks=int(info[2]), graph=bool(info[3]),
-                hybrid_networks=int(info[4]), config=int(info[5]), trial_ms=ms.tolist())
+                hybrid_networks=int(info[4]), config=int(info[5]), phases=int(info[6]),
+                trial_ms=ms.tolist())
 
 
 def rn_set_update_scheme(ctx, net, scheme, selected=None):
@@ -287,7 +289,7 @@ def rn_set_update_scheme(ctx, net, scheme, selected=None):
 
 
 def rn_batch_tune(ctx, config):
-    """Pin the batched launch to candidate 0..7, or autotune again with -1."""
+    """Pin the batched launch to candidate 0..9, or autotune again with -1."""
     _check(ctx, load_library().rn_batch_tune(ctx, int(config)))
 
 

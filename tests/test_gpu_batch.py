@@ -30,11 +30,12 @@ def _state_all(ctx, probs, nets):
     return [R.rn_get_chain_state(ctx, p.id, w.n_chains) for p, w in zip(probs, nets)]
 
 
-@pytest.mark.parametrize("pin", [None, 0, 1, 2, 4, 6, 7])
+@pytest.mark.parametrize("pin", [None, 0, 1, 2, 4, 6, 7, 8, 9])
 def test_batched_equals_separate_runs(pin):
     # autotuned, and each table-path candidate pinned (1 and 4: the hybrid path
     # for the networks of 129-256 nodes, with 4 and 2 warps per block; 6 and 7:
-    # every warp with a large region)
+    # every warp with a large region; 8 and 9: one launch per table path, 9 with
+    # the hybrid path)
     from paper_2506_19866_gb300 import build
     build.build()
     nets = _batch()
@@ -52,13 +53,17 @@ def test_batched_equals_separate_runs(pin):
         cfg = R.rn_batch_config(ctx)
         assert cfg["networks"] == len(nets) and cfg["warps_per_block"] in (2, 4)
         if pin is None:
-            assert all(t > 0 for t in cfg["trial_ms"]) and 0 <= cfg["config"] <= 5
+            assert all(t > 0 for t in cfg["trial_ms"]) and 0 <= cfg["config"] <= 9
         else:
             assert cfg["config"] == pin
-            assert cfg["warps_per_block"] == (4 if pin in (0, 1, 2, 6) else 2)
+            if pin < 8:
+                assert cfg["warps_per_block"] == (4 if pin in (0, 1, 2, 6) else 2)
+                assert cfg["phases"] == 1
+            else:   # one kernel per table path present (at most 1, 2, 4, 6, 8, shared)
+                assert 3 <= cfg["phases"] <= 6
             n_hybrid = sum(128 < w.N <= 256 for w in nets)
             assert n_hybrid >= 2
-            assert cfg["hybrid_networks"] == (n_hybrid if pin in (1, 4) else 0)
+            assert cfg["hybrid_networks"] == (n_hybrid if pin in (1, 4, 9) else 0)
         R.rn_anneal(ctx, sched, sweeps)           # graph capture and replay
         R.rn_anneal(ctx, sched, sweeps)
         assert R.rn_batch_config(ctx)["graph"]
