@@ -60,6 +60,14 @@ def parse():
                          "against time and acceptance rate per stretch of levels")
     ap.add_argument("--protocol-iters", type=int, default=100,
                     help="proposals per level for the thread-count sweep (the paper: 5000)")
+    ap.add_argument("--protocol-runs", default=None,
+                    help="comma-separated network:threads:iters runs of --paper-protocol "
+                         "instead of the default plan")
+    ap.add_argument("--protocol-out", default=None,
+                    help="also write the --paper-protocol result (with every run's curves) "
+                         "to this JSON file")
+    ap.add_argument("--protocol-table", default=None, metavar="JSON",
+                    help="print the markdown table of a --protocol-out file and exit")
     ap.add_argument("--screen-gain", action="store_true",
                     help="instead of the throughput line: train a width-1024 screen on the "
                          "2000-node network (pairs logged from a plain run) and race plain "
@@ -372,10 +380,15 @@ def paper_protocol(args, R, device, stream):
     rate of each stretch (chain counters read outside the clock).  The sweep
     over thread counts uses --protocol-iters proposals per level; the paper's
     5000 are run at 32 threads (and 1024 on the 102-parameter network)."""
-    plan = [(name, threads, args.protocol_iters)
-            for name in ("hpg_9n_25e", "mtb_63n_178e")
-            for threads in (32, 256, 1024, 10240, 102400)]
-    plan += [("hpg_9n_25e", 32, 5000), ("hpg_9n_25e", 1024, 5000), ("mtb_63n_178e", 32, 5000)]
+    if args.protocol_runs:
+        plan = [(a, int(b), int(c)) for a, b, c in
+                (r.split(":") for r in args.protocol_runs.split(","))]
+    else:
+        plan = [(name, threads, args.protocol_iters)
+                for name in ("hpg_9n_25e", "mtb_63n_178e")
+                for threads in (32, 256, 1024, 10240, 102400)]
+        plan += [("hpg_9n_25e", 32, 5000), ("hpg_9n_25e", 1024, 5000),
+                 ("mtb_63n_178e", 32, 5000)]
     stretch = 55                                   # 25 stretches of the 1375 levels
     runs = []
     for name, threads, iters in plan:
@@ -644,6 +657,25 @@ def measure(args, R, dev, name, S, steps, warmup, rank, world, dist, screened=Fa
 SUB_RECORDS = (("batch256", 500, 3, 3), ("scaleup", 2, 10, 3))
 
 
+def protocol_table(path):
+    """Markdown table of a --paper-protocol result file: per run the network,
+    threads, proposals per level, total time, final best score, when it was
+    first reached, throughput, and the acceptance rate at the start, middle
+    and end of the schedule."""
+    with open(path) as f:
+        res = json.load(f)
+    rows = ["| network | threads | proposals per level | total s | final best y | first at s | "
+            "evals/s | acceptance: first / middle / last stretch |",
+            "|---|---|---|---|---|---|---|---|"]
+    for r in res["paper_protocol"]:
+        c = r["curve"]
+        acc = " / ".join(f"{c[k]['accept_rate']:.2f}" for k in (0, len(c) // 2, len(c) - 1))
+        rows.append(f"| {r['params']} params | {r['threads']} | {r['iters_per_level']} | "
+                    f"{r['seconds']:.1f} | {r['final_best']} | {r['seconds_to_final_best']:.2f} | "
+                    f"{r['evals_per_s']:.3g} | {acc} |")
+    return "\n".join(rows)
+
+
 def run_ours(args, rank, world, local_rank, R=None, dev=None):
     """The GPU arm.  R (the library binding) and dev (CudaDevice) are the real
     ones unless a test hands in stand-ins to check the multi-rank control flow
@@ -658,7 +690,11 @@ def run_ours(args, rank, world, local_rank, R=None, dev=None):
         dev = CudaDevice(local_rank)
     if args.paper_protocol:
         if rank == 0:
-            print(json.dumps(paper_protocol(args, R, local_rank, dev.stream)), flush=True)
+            res = paper_protocol(args, R, local_rank, dev.stream)
+            if args.protocol_out:
+                with open(args.protocol_out, "w") as f:
+                    json.dump(res, f, indent=1)
+            print(json.dumps(res), flush=True)
         return
     if args.screen_gain:
         if rank == 0:
@@ -1004,6 +1040,9 @@ def screen_gain(args, R, device, stream, name="n2000_c16_t33", budget_s=20.0):
 
 def main():
     args = parse()
+    if args.protocol_table:
+        print(protocol_table(args.protocol_table))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -56,3 +56,18 @@ def test_algorithmic_ops_per_evaluation(bench):
     from paper_2506_19866_gb300 import synth
     assert bench.algorithmic_ops_per_eval(synth.make("n120_c8_t21")) == 428491
     assert bench.algorithmic_ops_per_eval(synth.make("n2000_c16_t33")) == 25006931
+
+
+def test_protocol_table_from_a_result_file(bench, tmp_path):
+    # the F2 table is generated from the --paper-protocol result files
+    curve = [{"levels": 55 * (k + 1), "T": 1.0, "seconds": 0.5 * (k + 1), "best": 9 - k,
+              "accept_rate": 0.9 - 0.1 * k} for k in range(5)]
+    res = {"paper_protocol": [{"network": "mtb_63n_178e", "params": 723, "threads": 32,
+                               "iters_per_level": 5000, "levels": 1375, "seconds": 49.3,
+                               "final_best": 5, "seconds_to_final_best": 2.5,
+                               "evals_per_s": 4.46e6, "curve": curve}]}
+    p = tmp_path / "pp.json"
+    p.write_text(json.dumps(res))
+    rows = bench.protocol_table(str(p)).splitlines()
+    assert len(rows) == 3
+    assert rows[2] == "| 723 params | 32 | 5000 | 49.3 | 5 | 2.50 | 4.46e+06 | 0.90 / 0.70 / 0.50 |"
