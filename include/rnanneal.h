@@ -276,7 +276,8 @@ int rn_launch_count(rn_ctx *ctx, int64_t *count);
  * or 2 (w = 1); the warps with a region large enough for any network are the
  * work share of those networks.  c = 6, 7: p = 0 with 4 / 2 warps per block,
  * every warp with a large region.  c = 8, 9: phased launches, one kernel per
- * table path in sequence (the paths of p = 0 and p = 1), so that an SM never
+ * table path in sequence (the paths of p = 0, and of p = 1 with the hybrid
+ * path also for networks of 257-320 nodes), so that an SM never
  * runs two paths' code at once; each phase's warp region fits its own path's
  * largest network, and each phase takes the warps per block (4 or 2) its trial
  * ran faster with (a phased candidate's trial time is the sum of its phases').

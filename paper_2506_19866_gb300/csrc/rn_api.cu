@@ -151,8 +151,8 @@ void build_layout(Network &n)
     // up to 2048 nodes the block path keeps node state in registers, compiled
     // for an even number of nodes per thread
     if (L != 32 && n.npl > 0 && n.npl < 8) n.npl += n.npl & 1;
-    // 129 .. 256 nodes: 6 or 8 per lane, the hybrid path's compiled layouts
-    if (L == 32 && N > 128 && N <= 256) n.npl = N <= 192 ? 6 : 8;
+    // 129 .. 320 nodes: 6, 8 or 10 per lane, the hybrid path's compiled layouts
+    if (L == 32 && N > 128 && N <= 320) n.npl = N <= 192 ? 6 : N <= 256 ? 8 : 10;
     n.in_ptr.assign((size_t)N + 1, 0);
     n.out_ptr.assign((size_t)N + 1, 0);
     for (int32_t e = 0; e < E; ++e) {
@@ -473,8 +473,12 @@ int batch_items(rn_ctx *ctx, BatchState &B)
 }
 
 // Warps per block of a phased launch's phase of table path `path` (paths
-// 0, 1, 2, 4, 6, 8 index the slots 0 .. 5); 4 until tuned.
-int phase_slot(int path) { return path == 0 ? 0 : path == 1 ? 1 : path == 2 ? 2 : path == 4 ? 3 : path == 6 ? 4 : 5; }
+// 0, 1, 2, 4, 6, 8, 10 index the slots 0 .. 6); 4 until tuned.
+int phase_slot(int path)
+{
+    return path == 0 ? 0 : path == 1 ? 1 : path == 2 ? 2 : path == 4 ? 3 : path == 6 ? 4
+         : path == 8 ? 5 : 6;
+}
 
 int phase_wpb_of(const BatchState &B, int path)
 {
@@ -653,19 +657,24 @@ int tune_batch(rn_ctx *ctx, const DevSched &sc0, int64_t sweeps)
         }
         return RN_OK;
     };
+    // hybrid: 6 or 8 nodes per lane in the single launch, also 10 in a phased
+    // one (its phase kernel is compiled for 10 nodes' registers)
     std::vector<int32_t> best_fit(B.order.size(), 0), hybrid(B.order.size(), 0);
+    std::vector<int32_t> hybrid_phased(B.order.size(), 0);
     for (size_t b = 0; b < B.order.size(); ++b) {
         const Network &n = *ctx->nets[(size_t)B.order[b]];
         int drest = 0;
         for (int k = 1; k < n.npl; ++k) drest = std::max(drest, n.D[k]);
         best_fit[b] = batch_path_fits(n.npl, n.D[0], drest) ? n.npl : 0;
-        hybrid[b] = best_fit[b] == 0 && smemreg_layout(n.npl) ? n.npl : best_fit[b];
+        const bool h = best_fit[b] == 0 && smemreg_layout(n.npl);
+        hybrid[b] = h && n.npl <= 8 ? n.npl : best_fit[b];
+        hybrid_phased[b] = h ? n.npl : best_fit[b];
     }
     const std::vector<int32_t> all_smem(B.host_path.size(), 0);
     auto apply = [&](int cfg, int phase_wpb) {
         B.phased = cfg >= 8;
         B.all_large = cfg == 6 || cfg == 7;
-        B.host_path = cfg >= 8 ? (cfg == 8 ? best_fit : hybrid)
+        B.host_path = cfg >= 8 ? (cfg == 8 ? best_fit : hybrid_phased)
                       : cfg >= 6 || cfg % 3 == 0 ? best_fit
                       : cfg % 3 == 1 ? hybrid : all_smem;
         B.wpb = cfg >= 8 ? 4 : cfg >= 6 ? (cfg == 6 ? 4 : 2) : cfg / 3 == 0 ? 4 : 2;

@@ -25,9 +25,10 @@ namespace rn {
 
 // Table paths of a network in the batch: 1, 2, 4 = register tables, capacities
 // slot 0 up to 16 in-edges and the other slots up to 8; 0 = the shared-memory
-// path (any layout); 6, 8 = the hybrid path (table words in shared memory,
-// node state in registers) of 129-256-node networks.  Which of these a network
-// takes is chosen by the autotuner.
+// path (any layout); 6, 8, 10 = the hybrid path (table words in shared memory,
+// node state in registers) of 129-320-node networks (10 in phased launches
+// only, whose kernel is compiled for its register need).  Which of these a
+// network takes is chosen by the autotuner.
 constexpr int kBatchD0 = 16, kBatchD1 = 8;
 
 // Code region, then the per-warp copies of the item's DevNet and DevChains,
@@ -121,6 +122,10 @@ __device__ __forceinline__ void batch_item(const DevBatch &b, const DevSched &sc
     const int path = PATH >= 0 ? PATH : __ldg(b.path + nb);
     int32_t *flag = sc.done + r;
     const int dv = cj + 1;
+    if constexpr (PATH == 10) {
+        chunk_smemreg<10>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv, lane);
+        return;
+    }
     switch (path) {
     case 1:
         chunk_reg<1, kBatchD0, 1>(net, ch, sc, sm, codes, region, chain, g_lo, g_hi, flag, dv,
@@ -184,8 +189,8 @@ __global__ void __launch_bounds__(128, 3) anneal_batch_kernel(DevBatch b, DevSch
 // largest network, and the same chunk-major queue as above (the predecessor
 // of an item was handed out ph.n items earlier).
 template <int PATH>
-__global__ void __launch_bounds__(128, 3) anneal_phase_kernel(DevBatch b, DevSched sc,
-                                                              BatchPhase ph)
+__global__ void __launch_bounds__(128, PATH == 10 ? smemreg_min_blocks<10>() : 3)
+    anneal_phase_kernel(DevBatch b, DevSched sc, BatchPhase ph)
 {
     extern __shared__ __align__(256) uint8_t sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -225,7 +230,7 @@ bool batch_path_fits(int npl, int D0, int Drest)
 
 uint32_t batch_region_bytes(int path, const int *D, int npl, int pstride, int N)
 {
-    if (path == 6 || path == 8)
+    if (path == 6 || path == 8 || path == 10)
         return round16(smem_reg_warp_bytes(smem_path_lut_words(D, npl), pstride, N));
     return warp_region(path == 0, D, npl, pstride, N).bytes;
 }
@@ -276,6 +281,7 @@ PhaseKernel phase_kernel(int path)
     case 4: return anneal_phase_kernel<4>;
     case 6: return anneal_phase_kernel<6>;
     case 8: return anneal_phase_kernel<8>;
+    case 10: return anneal_phase_kernel<10>;
     default: return anneal_phase_kernel<0>;
     }
 }

@@ -35,8 +35,8 @@ cudaError_t launch_anneal(const DevNet &net, int d0, int d1, const DevChains &ch
                           const DevSched &sc, int sm_count, cudaStream_t st);
 cudaError_t launch_init(const DevNet &net, const DevChains &ch, int32_t *status, cudaStream_t st);
 
-// Hybrid path (rn_smemreg.cu): 6 or 8 nodes per lane, table words in shared
-// memory, node state in registers.
+// Hybrid path (rn_smemreg.cu): 6, 8 or 10 nodes per lane, table words in
+// shared memory, node state in registers.
 bool smemreg_layout(int npl);
 cudaError_t launch_anneal_smemreg(const DevNet &net, const DevChains &ch, const DevSched &sc,
                                   int sm_count, cudaStream_t st);
@@ -98,7 +98,7 @@ struct BatchPhase {
     uint32_t region;
     int32_t wpb, grid;
 };
-constexpr int kMaxPhases = 6;           // table paths 8, 6, 0, 4, 2, 1
+constexpr int kMaxPhases = 7;           // table paths 10, 8, 6, 0, 4, 2, 1
 constexpr int kQueueSlots = 8;          // work-queue counters of a context
 size_t batch_phase_smem(const BatchPhase &ph);
 // Resident grid of the phase's kernel (sets its dynamic shared-memory limit).

@@ -285,7 +285,15 @@ struct SmemPath {
 // warp's shared memory, gathered in groups of 4 rows, while the per-node
 // byte-SIMD update state lives in registers (the simulation of rn_device.cuh,
 // simulate_swar4_core), so that only the gather touches shared memory.
-constexpr int kSmemRegSlots[2] = {6, 8};
+constexpr int kSmemRegSlots[3] = {6, 8, 10};
+// Blocks of 4 warps per SM the hybrid kernels are compiled for: 3 (at most
+// 168 registers a thread) up to 8 nodes per lane; 10 nodes per lane keep their
+// node state in up to 255 registers at 2 blocks.
+template <int NPL>
+constexpr int smemreg_min_blocks()
+{
+    return NPL > 8 ? 2 : 3;
+}
 
 __host__ __device__ inline uint32_t smem_reg_warp_bytes(uint32_t lut_words, int pstride, int N)
 {

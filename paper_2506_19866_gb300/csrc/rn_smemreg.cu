@@ -1,5 +1,5 @@
-// rn_smemreg.cu -- kernels of the hybrid path (rn_smem.cuh SmemRegPath): 6 or
-// 8 nodes per lane, table words in the warp's shared memory, byte-SIMD node
+// rn_smemreg.cu -- kernels of the hybrid path (rn_smem.cuh SmemRegPath): 6, 8
+// or 10 nodes per lane, table words in the warp's shared memory, byte-SIMD node
 // state in registers.  Same persistent work queue and per-chain code as the
 // other warp-per-chain kernels (rn_kernels.cuh).
 #include "rn_kernels.cuh"
@@ -30,7 +30,7 @@ __device__ __forceinline__ SmemRegPathR<NPL> make_path(uint8_t *sm, int warp, in
 }
 
 template <int NPL>
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, smemreg_min_blocks<NPL>())
     anneal_smemreg_kernel(DevNet net, DevChains ch, DevSched sc, uint32_t region_bytes,
                           uint32_t lut_words)
 {
@@ -108,13 +108,17 @@ cudaError_t launch_evaluate_t(const DevNet &net, const int8_t *X, int64_t xstrid
 
 }  // namespace
 
-bool smemreg_layout(int npl) { return npl == kSmemRegSlots[0] || npl == kSmemRegSlots[1]; }
+bool smemreg_layout(int npl)
+{
+    return npl == kSmemRegSlots[0] || npl == kSmemRegSlots[1] || npl == kSmemRegSlots[2];
+}
 
 cudaError_t launch_anneal_smemreg(const DevNet &net, const DevChains &ch, const DevSched &sc,
                                   int sm_count, cudaStream_t st)
 {
     if (net.npl == 6) return launch_anneal_t<6>(net, ch, sc, sm_count, st);
     if (net.npl == 8) return launch_anneal_t<8>(net, ch, sc, sm_count, st);
+    if (net.npl == 10) return launch_anneal_t<10>(net, ch, sc, sm_count, st);
     return cudaErrorNotSupported;
 }
 
@@ -124,6 +128,8 @@ cudaError_t launch_evaluate_smemreg(const DevNet &net, const int8_t *X, int64_t 
 {
     if (net.npl == 6) return launch_evaluate_t<6>(net, X, xstride, n, score, score2, traj, grid, st);
     if (net.npl == 8) return launch_evaluate_t<8>(net, X, xstride, n, score, score2, traj, grid, st);
+    if (net.npl == 10)
+        return launch_evaluate_t<10>(net, X, xstride, n, score, score2, traj, grid, st);
     return cudaErrorNotSupported;
 }
 

@@ -18,9 +18,11 @@ def _batch():
     # one more network above 128 nodes (shared-memory tables) and a tiny one
     extra = synth.make_batch(n_nets=2, total_chains=90, seed=3, n_min=200, n_max=260)
     small = synth.make_batch(n_nets=1, total_chains=40, seed=4, n_min=10, n_max=12)
-    # and one of 129-192 nodes (6 nodes per lane on the hybrid path)
+    # one of 129-192 nodes (6 nodes per lane on the hybrid path) and one of
+    # 257-320 (10 nodes per lane on the hybrid path of a phased launch)
     mid = synth.make_batch(n_nets=1, total_chains=60, seed=5, n_min=140, n_max=180)
-    nets = nets + extra + small + mid
+    large = synth.make_batch(n_nets=1, total_chains=50, seed=6, n_min=270, n_max=310)
+    nets = nets + extra + small + mid + large
     sizes = [w.N for w in nets]
     assert min(sizes) <= 32 and max(sizes) > 128
     return nets
@@ -63,7 +65,9 @@ def test_batched_equals_separate_runs(pin):
                 assert 3 <= cfg["phases"] <= 6
             n_hybrid = sum(128 < w.N <= 256 for w in nets)
             assert n_hybrid >= 2
-            assert cfg["hybrid_networks"] == (n_hybrid if pin in (1, 4, 9) else 0)
+            n_hybrid_phased = sum(128 < w.N <= 320 for w in nets)     # 10 nodes per lane too
+            assert cfg["hybrid_networks"] == (n_hybrid if pin in (1, 4) else
+                                              n_hybrid_phased if pin == 9 else 0)
         R.rn_anneal(ctx, sched, sweeps)           # graph capture and replay
         R.rn_anneal(ctx, sched, sweeps)
         assert R.rn_batch_config(ctx)["graph"]
