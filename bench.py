@@ -627,6 +627,12 @@ def measure(args, R, dev, name, S, steps, warmup, rank, world, dist, screened=Fa
                 "roofline": roofline, "clocks": clk, "gpu_launches": launches}
         if len(ws) > 1:
             line["batch"] = R.rn_batch_config(ctx)
+            phases = line["batch"].get("phases", 1)
+            if phases > 1:
+                n_blk = sum(block_path(w) for w in ws)
+                roofline["kernel"] = (f"anneal_phase_kernel x {phases} (one launch per table path)"
+                                      + (f" + anneal_block_kernel ({n_blk} networks)" if n_blk
+                                         else "") + ", whole step")
         line["device_memory_used_gb"] = dev.memory_used_gb()
         if screened:
             h = screen_width

@@ -521,7 +521,7 @@ def test_scheduling_argument_errors(ctx):
     # out-of-range batch tuning candidates and group sizes are refused
     w = synth.make("hpg_9n_25e")
     p = Problem(w, ctx)
-    for bad in (-2, 8):
+    for bad in (-2, 10):
         with pytest.raises(R.RNError) as e:
             R.rn_batch_tune(ctx, bad)
         assert e.value.code == R.RN_EINVAL
