@@ -195,6 +195,11 @@ void build_layout(Network &n)
         n.q_node[(size_t)q] = (int16_t)i;
         n.D[slot] = std::max(n.D[slot], n.in_ptr[(size_t)i + 1] - n.in_ptr[(size_t)i]);
     }
+    // The hybrid and block-register paths gather two slots per loop (twice the
+    // independent loads in flight): slots 2j and 2j + 1 get the same number of
+    // table rows, the extra ones neutral padding.
+    if ((L == 32 && smemreg_layout(npl)) || (L != 32 && npl <= 8))
+        for (int k = 0; k + 1 < npl; k += 2) n.D[k] = n.D[k + 1] = std::max(n.D[k], n.D[k + 1]);
     n.dtab = 1;
     for (int k = 0; k < npl; ++k) n.dtab = std::max(n.dtab, n.D[k]);
     // in-degree capacity: 16 in registers (warp paths), 31 on the block path.

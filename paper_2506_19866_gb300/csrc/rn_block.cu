@@ -482,16 +482,16 @@ struct BlockRegPath {
     // Simulate(x) of Table 1 (Sections 2.1-2.3); y in every thread.
     __device__ int32_t simulate(const DevNet &net, int t, uint8_t *traj)
     {
-        int row0[NPL];
+        SlotGather<NPL, kBT, true> gather;
+        gather.lut = lut + t;
+        gather.sm = sm;
         int o = 0;
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
-            row0[k] = o;
-            o += groups4(net.D[k]);
+            gather.row0[k] = o;
+            gather.d4[k] = groups4(net.D[k]);
+            o += gather.d4[k];
         }
-        auto gather = [&](int k) -> uint32_t {
-            return gather_rows<kBT>(lut + row0[k] * kBT + t, groups4(net.D[k]), sm);
-        };
         const BlockSync<NPL> sync{bc, t & 31, t >> 5};
         return simulate_swar4_core<NPL, true, false, kBT>(u, m1, d2, net, sm, 0u, t, traj,
                                                           INT32_MAX, gather, sync);

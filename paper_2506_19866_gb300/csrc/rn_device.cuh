@@ -303,6 +303,83 @@ __device__ __forceinline__ uint32_t gather_rows(const uint32_t *lw, int D4, cons
     return acc;
 }
 
+// Two slots' images at once (slots of equal row counts, laid out one after the
+// other): the same loop as gather_rows over both, so that twice the table words
+// and state codes are in flight.
+template <int STRIDE>
+__device__ __forceinline__ void gather_rows_pair(const uint32_t *la, const uint32_t *lb, int D4,
+                                                 const uint8_t *sm, uint32_t &acc_a,
+                                                 uint32_t &acc_b)
+{
+    acc_a = kImage0 - 0x04040404u * (uint32_t)D4;
+    acc_b = acc_a;
+    if (D4 == 0) return;
+    uint32_t wa[4], wb[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        wa[i] = la[i * STRIDE];
+        wb[i] = lb[i * STRIDE];
+    }
+    for (int d = 0; d < D4; d += 4) {
+        uint32_t ca[4], cb[4], na[4] = {0u, 0u, 0u, 0u}, nb[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ca[i] = *reinterpret_cast<const uint16_t *>(sm + (wa[i] & 0xffffu));
+            cb[i] = *reinterpret_cast<const uint16_t *>(sm + (wb[i] & 0xffffu));
+        }
+        if (d + 4 < D4) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                na[i] = la[(d + 4 + i) * STRIDE];
+                nb[i] = lb[(d + 4 + i) * STRIDE];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            acc_a += prmt(wa[i], 0x04040404u, ca[i]);
+            acc_b += prmt(wb[i], 0x04040404u, cb[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            wa[i] = na[i];
+            wb[i] = nb[i];
+        }
+    }
+}
+
+// A gather functor that also serves two slots at once (pair(k, a, b) for slots
+// k and k + 1) advertises it with kPair; simulate_swar4_core then gathers in
+// pairs.
+template <class G, class = void>
+struct gathers_pairs {
+    static constexpr bool value = false;
+};
+template <class G>
+struct gathers_pairs<G, decltype((void)G::kPair)> {
+    static constexpr bool value = G::kPair;
+};
+
+// The image gather of the shared-memory table layouts (hybrid and block
+// paths): slot k's rows start at row0[k] of this thread's column and number
+// d4[k]; slots 2j and 2j + 1 have equal row counts (the layout pads them so),
+// so they are gathered in pairs.
+template <int NPL, int STRIDE, bool PIPE>
+struct SlotGather {
+    static constexpr bool kPair = true;
+    const uint32_t *lut;   // this thread's column of the table rows
+    const uint8_t *sm;
+    int row0[NPL], d4[NPL];
+    __device__ __forceinline__ uint32_t operator()(int k) const
+    {
+        return gather_rows<STRIDE, PIPE>(lut + row0[k] * STRIDE, d4[k], sm);
+    }
+    __device__ __forceinline__ void pair(int k, uint32_t &a, uint32_t &b) const
+    {
+        gather_rows_pair<STRIDE>(lut + row0[k] * STRIDE, lut + row0[k + 1] * STRIDE, d4[k], sm,
+                                 a, b);
+    }
+};
+
 template <int NPL>
 __device__ __forceinline__ void store_codes(uint8_t *p, const uint32_t (&code)[NPL])
 {
@@ -492,8 +569,14 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
             }
             if (tau > 0) {
                 uint32_t acc[NPL];
+                if constexpr (gathers_pairs<Gather>::value) {
+                    static_assert(NPL % 2 == 0, "pairs of slots");
 #pragma unroll
-                for (int k = 0; k < NPL; ++k) acc[k] = gather(k);
+                    for (int k = 0; k < NPL; k += 2) gather.pair(k, acc[k], acc[k + 1]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NPL; ++k) acc[k] = gather(k);
+                }
                 uint32_t sn[NPL], pr01[NPL], pr23[NPL], elm[NPL];
                 uint32_t m01 = 0, m23 = 0;
 #pragma unroll

@@ -388,16 +388,16 @@ struct SmemRegPath {
     __device__ int32_t simulate(const DevNet &net, int lane, uint8_t *traj,
                                 int32_t limit = INT32_MAX)
     {
-        int row0[NPL];
+        SlotGather<NPL, 32, (NPL > 6)> gather;
+        gather.lut = lut + lane;
+        gather.sm = sm;
         int o = 0;
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
-            row0[k] = o;
-            o += groups4(net.D[k]);
+            gather.row0[k] = o;
+            gather.d4[k] = groups4(net.D[k]);
+            o += gather.d4[k];
         }
-        auto gather = [&](int k) -> uint32_t {
-            return gather_rows<32, (NPL > 6)>(lut + row0[k] * 32 + lane, groups4(net.D[k]), sm);
-        };
         if (limit == INT32_MAX)
             return simulate_swar4_core<NPL, true, false>(u, m1, d2, net, sm, codes, lane, traj,
                                                          limit, gather);
