@@ -98,10 +98,10 @@ def algorithmic_ops_per_eval(w):
 ANNEAL_TRAFFIC = {"n120_c8_t21": 9.26e6, "n2000_c16_t33": 1.45e9}
 
 # Shared-memory wavefronts per proposal step of one chain from the same
-# captures: 110.3e6 over 4096 chains x 20 steps, and 7.88e9 over 16,384
+# captures: 110.3e6 over 4096 chains x 20 steps, and 6.74e9 over 16,384
 # chains x 2 steps (null moves included, as in the captured launches).
 ANNEAL_SMEM_WAVEFRONTS = {"n120_c8_t21": 110.3e6 / (4096 * 20),
-                          "n2000_c16_t33": 7.88e9 / (16384 * 2)}
+                          "n2000_c16_t33": 6.738e9 / (16384 * 2)}
 
 
 def hbm_peak_gbs():
