@@ -658,9 +658,13 @@ def measure(args, R, dev, name, S, steps, warmup, rank, world, dist, screened=Fa
     return line
 
 
-# The workloads recorded beside the headline line (N = 1): the batch of 256
-# uneven networks and the scale-up set, with their own step sizes and counts.
-SUB_RECORDS = (("batch256", 500, 3, 3), ("scaleup", 2, 10, 3))
+# The workloads recorded beside the headline line (N = 1), with their sweeps
+# per step, timed steps, warm-up steps and whether the oracle is timed beside
+# them: the 15-node network (a step is its whole 2000-sweep run), the
+# 723-parameter paper-shaped network, the batch of 256 uneven networks and the
+# scale-up set.
+SUB_RECORDS = (("n15_c3_t11", 2000, 3, 3, True), ("mtb_63n_178e", 500, 5, 3, True),
+               ("batch256", 500, 3, 3, False), ("scaleup", 2, 10, 3, False))
 
 
 def protocol_table(path):
@@ -720,9 +724,13 @@ def run_ours(args, rank, world, local_rank, R=None, dev=None):
                                                  dev.stream)
     if (rank == 0 and world == 1 and not args.no_sub_records and not args.screened and
             args.workload == "n120_c8_t21"):
-        line["sub_records"] = {
-            name: measure(args, R, dev, name, S, steps, warmup, rank, world, None, peaks=peaks)
-            for name, S, steps, warmup in SUB_RECORDS}
+        line["sub_records"] = {}
+        for name, S, steps, warmup, oracle in SUB_RECORDS:
+            rec = measure(args, R, dev, name, S, steps, warmup, rank, world, None, peaks=peaks)
+            if oracle and not args.no_cpu_baseline:
+                rec["cpu_baseline"] = oracle_rate(name, args.cpu_seconds / 3)
+                rec["cpu_baseline_1thread"] = oracle_rate(name, args.cpu_seconds / 4, cores=1)
+            line["sub_records"][name] = rec
     if rank == 0 and not args.no_cpu_baseline and world == 1 and single:
         line["cpu_baseline"] = oracle_rate(args.workload, args.cpu_seconds)
         line["cpu_baseline_1thread"] = oracle_rate(args.workload, args.cpu_seconds / 2, cores=1)
