@@ -40,6 +40,18 @@ struct GemmArgs {
     const __nv_bfloat16 *mask;  // [M][ldc] (kMaskBf16)
 };
 
+// The screen's layer-2 A operand produced inside the tcgen05 GEMM instead of
+// read from memory: row R (candidate R % K of chain R / K) is
+//   relu(A1[R / K] + (W1[rows[R].x] - W1[rows[R].y]))   rounded to BF16,
+// relu(A1[R / K]) when rows[R].x < 0 (no candidate), and 0 for R >= n_rows.
+struct HiddenArgs {
+    const int2 *rows;           // [M] (W1 row of the new value, W1 row of the old value)
+    const float *A1;            // [chains][K dimension of the GEMM] layer-1 pre-activations
+    const __nv_bfloat16 *W1b;   // [Dp][K dimension] BF16 layer-1 weights
+    int K;                      // candidates per chain
+    int n_rows;                 // chains * K
+};
+
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);

@@ -262,9 +262,12 @@ __global__ void embed_chains_kernel(DevChains ch, int32_t P, const int32_t *__re
     }
 }
 
-// Warp per chain: K candidates (lane k draws candidate k), then the K hidden
-// rows relu(A1 + W1[new] - W1[old]) in BF16.  Shared memory per warp: x_cur,
+// Warp per chain: K candidates (lane k draws candidate k), then either (ROWS)
+// each candidate's two W1 rows (new value, old value; -1 without a candidate)
+// for the GEMM that forms the hidden rows itself, or the K hidden rows
+// relu(A1 + W1[new] - W1[old]) in BF16.  Shared memory per warp: x_cur,
 // out_nz[N], pos_in[N].
+template <bool ROWS>
 __global__ void __launch_bounds__(kScreenWarps * 32) screen_propose_kernel(ScreenArgs a,
                                                                            int region)
 {
@@ -286,6 +289,12 @@ __global__ void __launch_bounds__(kScreenWarps * 32) screen_propose_kernel(Scree
         ok = get_candidate(a.net, xs, out_nz, pos_in, r.x, r.y, j, kind, idx, cur, v);
     }
     if (lane < a.K) a.cand[(size_t)c * a.K + lane] = ok ? (j << 8) | (v & 255) : -1;
+    if constexpr (ROWS) {
+        if (lane < a.K)
+            a.rows[(size_t)c * a.K + lane] =
+                ok ? make_int2(a.row_base[j] + v, a.row_base[j] + cur) : make_int2(-1, -1);
+        return;
+    }
 
     const int groups = a.H1 >> 8;
     float base[kMaxGroups][8];
@@ -719,8 +728,7 @@ int ensure_screen(rn_ctx *ctx, Mlp &m, const Network &n, int32_t K, int32_t top)
     const size_t M = (size_t)round_up((int32_t)(C * K), 128);
     RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     RN_CUDA(ctx, m.A1.alloc(C * m.H1));
-    RN_CUDA(ctx, m.hc.alloc(M * m.H1));
-    RN_CUDA(ctx, cudaMemset(m.hc.p, 0, M * m.H1 * sizeof(uint16_t)));
+    RN_CUDA(ctx, m.rows.alloc(M));
     RN_CUDA(ctx, m.pc.alloc(M * (m.H2 / 64)));
     RN_CUDA(ctx, m.cand.alloc(C * K));
     m.chains = n.n_chains;
@@ -1008,6 +1016,17 @@ int rn_mlp_train(rn_ctx *ctx, int32_t mlp, int32_t steps, int32_t batch, float l
     return RN_OK;
 }
 
+int rn_mlp_set_hidden_mode(rn_ctx *ctx, int32_t mlp, int32_t mode)
+{
+    if (!ctx) return RN_EINVAL;
+    ctx->err.clear();
+    Mlp *m = get_mlp(ctx, mlp);
+    if (!m) return fail(ctx, RN_EINVAL, "unknown screen %d", mlp);
+    if (mode != 0 && mode != 1) return fail(ctx, RN_EINVAL, "hidden-row mode %d is not 0 or 1", mode);
+    m->hidden_mode = mode;
+    return RN_OK;
+}
+
 int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K, int32_t top,
                        double eps, int64_t sweeps)
 {
@@ -1066,23 +1085,49 @@ int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K
     a.W1b = bp(m->W1b);
     a.b3 = m->theta.p + m->off_b3();
     a.A1 = m->A1.p;
-    a.hc = bp(m->hc);
+    a.rows = m->rows.p;
     a.pc = m->pc.p;
     a.cand = m->cand.p;
     const size_t smem = (size_t)pwarps * region;
-    RN_CUDA(ctx, cudaFuncSetAttribute(screen_propose_kernel,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int pblocks = (ch.n + pwarps - 1) / pwarps;
     const int32_t M = round_up(ch.n * K, 128);
     GemmArgs g{};
-    g.A = a.hc; g.lda = m->H1; g.B = bp(m->W2T); g.ldb = m->H1;
+    g.lda = m->H1; g.B = bp(m->W2T); g.ldb = m->H1;
     g.M = M; g.N = m->H2; g.K = m->H1; g.ldc = m->H2;
     g.bias = m->theta.p + m->off_b2(); g.w = m->theta.p + m->off_w3(); g.part = m->pc.p;
+    // layer 2 of the K candidates: hidden rows formed inside the GEMM (mode 0),
+    // or written by the propose kernel and read back (mode 1, and widths above
+    // 512, where the fused kernel would repeat the rows per 256 columns)
+    const bool fused = m->hidden_mode == 0 && gemm_hidden_supported(g);
+    HiddenArgs hid{};
+    if (fused) {
+        hid.rows = m->rows.p;
+        hid.A1 = m->A1.p;
+        hid.W1b = bp(m->W1b);
+        hid.K = K;
+        hid.n_rows = ch.n * K;
+    } else if (m->hc.n < (size_t)M * m->H1) {
+        RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        RN_CUDA(ctx, m->hc.alloc((size_t)M * m->H1));
+        RN_CUDA(ctx, cudaMemset(m->hc.p, 0, (size_t)M * m->H1 * sizeof(uint16_t)));
+    }
+    a.hc = bp(m->hc);
+    g.A = a.hc;
+    auto propose = fused ? screen_propose_kernel<true> : screen_propose_kernel<false>;
+    RN_CUDA(ctx, cudaFuncSetAttribute(propose, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
     for (int64_t k = 0; k < sweeps; ++k) {
         a.g = n->step + k;
-        screen_propose_kernel<<<pblocks, pwarps * 32, smem, ctx->stream>>>(a, region);
+        propose<<<pblocks, pwarps * 32, smem, ctx->stream>>>(a, region);
         if ((rc = check_launch(ctx, "screen propose kernel"))) return rc;
-        if ((rc = gemm(ctx, kBiasReluDot, g))) return rc;
+        if (fused) {
+            const cudaError_t e = launch_gemm_hidden(g, hid, ctx->dev_err.p, ctx->sm_count,
+                                                     ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "layer-2 GEMM with hidden rows");
+            ctx->launches += 1;
+        } else if ((rc = gemm(ctx, kBiasReluDot, g))) {
+            return rc;
+        }
         const cudaError_t e = n->lanes == 32 ? launch_finish(a, sc, ctx->stream)
                                              : launch_finish_block(a, sc, ctx->sm_count, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "screen finish kernel");

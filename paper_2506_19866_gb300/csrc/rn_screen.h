@@ -21,7 +21,8 @@ struct ScreenArgs {
     const __nv_bfloat16 *W1b;           // [Dp][H1]
     const float *b3;
     float *A1;                          // [chains][H1]
-    __nv_bfloat16 *hc;                  // [M][H1]
+    __nv_bfloat16 *hc;                  // [M][H1] (hidden rows through memory)
+    int2 *rows;                         // [M] W1 rows (new, old) per candidate (produced in the GEMM)
     const float *pc;                    // [M][nparts]
     int32_t *cand;                      // [chains][K]
 };

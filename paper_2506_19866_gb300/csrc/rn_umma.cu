@@ -56,6 +56,29 @@ cudaError_t launch_t(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs 
 
 }  // namespace
 
+cudaError_t launch_gemm_hidden(const GemmArgs &g, const HiddenArgs &h, int *err, int sm_count,
+                               cudaStream_t st)
+{
+    if (!gemm_hidden_supported(g) || !err || !h.rows || !h.A1 || !h.W1b || h.K < 1 ||
+        h.n_rows < 0 || h.n_rows > g.M)
+        return cudaErrorInvalidValue;
+    CUtensorMap b;
+    if (!make_map(&b, g.B, g.K, g.N, g.ldb, umma::BN)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(umma::gemm_hidden_kernel<kBiasReluDot>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)umma::HSMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int tiles = (g.M / umma::BM) * (g.N / umma::BN);
+    const int grid = tiles < sm_count ? tiles : sm_count;
+    umma::gemm_hidden_kernel<kBiasReluDot><<<grid, umma::HTHREADS, umma::HSMEM_BYTES, st>>>(b, g, h,
+                                                                                         err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gemm_tc(int epi, const GemmArgs &g, int *err, int sm_count, cudaStream_t st)
 {
     if (!gemm_tc_supported(g) || !err) return cudaErrorInvalidValue;

@@ -48,6 +48,7 @@ struct Ctl {
     uint32_t tmem;             // TMEM base address written by tcgen05.alloc
     int abort;
     int consumed;              // stages the MMA role consumed
+    int pflag[2];              // the hidden-row producers' shared wait result (per parity)
 };
 
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + sizeof(Ctl) + 64;
@@ -374,7 +375,288 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
+// ---- layer-2 GEMM of the screen with its A operand produced in the kernel ----
+//
+// The same warp roles as gemm_tc_kernel, with TMA loading only B (W2^T) and
+// eight more warps (6-13) producing each A stage from the candidates' W1 rows
+// and A1 (HiddenArgs): thread p of the producers owns row p / 2 of the tile and
+// its 32-column half p % 2 of the K block.  Its two W1 row segments (new and
+// old value, 64 bytes each) come through a ring of HDEPTH staging slots filled
+// by cp.async HDEPTH K blocks ahead, and its A1 segment is loaded into
+// registers one K block ahead, so that the gathers' L2 latency overlaps the
+// arithmetic and the MMAs.  Each producer thread writes its BF16 values into
+// the stage in the 128-byte-swizzled K-major layout that TMA would have
+// written, makes them visible to the tensor core's proxy
+// (fence.proxy.async.shared::cta) and arrives on the stage's full barrier (one
+// TMA arrival plus 256 producer arrivals).  One producer waits on the stage's
+// empty barrier (bounded) and passes the result to the others through a named
+// barrier, so that all producers leave together when a wait gives up.  This
+// replaces the HBM round trip of the hidden rows (written by the propose
+// kernel, read back by TMA): for 4096 chains x 32 candidates x 512 columns,
+// 134 MB each way per step.
+constexpr int HSTAGES = 3;                                  // GEMM stages (A produced, B by TMA)
+constexpr int HDEPTH = 2;                                   // staging slots (K blocks ahead)
+constexpr int HPROD = 256;                                  // producer threads
+constexpr int HTHREADS = 192 + HPROD;
+constexpr int HSTAGING_BYTES = BM * 2 * BK * 2;             // new and old W1 rows of a K block
+constexpr size_t HSMEM_BYTES =
+    1024 + (size_t)HSTAGES * STAGE_BYTES + (size_t)HDEPTH * HSTAGING_BYTES + sizeof(Ctl) + 64;
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void producers_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(HPROD) : "memory");
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(HTHREADS, 1)
+    gemm_hidden_kernel(const __grid_constant__ CUtensorMap tmB, GemmArgs g, HiddenArgs h, int *err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
+    uint8_t *staging = base + (size_t)HSTAGES * STAGE_BYTES;
+    Ctl *c = reinterpret_cast<Ctl *>(staging + (size_t)HDEPTH * HSTAGING_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tn = g.N / BN, tiles = (g.M / BM) * tn, nk = g.K / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < HSTAGES; ++s) {
+            mbar_init(&c->full[s], 1 + HPROD);
+            mbar_init(&c->empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&c->tfull[a], 1);
+            mbar_init(&c->tempty[a], 4);
+        }
+        mbar_init(&c->done, 1);
+        c->abort = 0;
+        c->consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&c->tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = c->tmem;
+    int issued = 0;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer of B
+        int stage = 0;
+        uint32_t phase = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+            const int n0 = (t % tn) * BN;
+            bool ok = true;
+            for (int kb = 0; kb < nk; ++kb) {
+                if (!mbar_wait(&c->empty[stage], phase ^ 1u, c, err)) { ok = false; break; }
+                uint8_t *sa = base + (size_t)stage * STAGE_BYTES;
+                mbar_expect_tx(&c->full[stage], B_BYTES);
+                tma_load_2d(sa + A_BYTES, &tmB, &c->full[stage], kb * BK, n0);
+                ++issued;
+                if (++stage == HSTAGES) { stage = 0; phase ^= 1u; }
+            }
+            if (!ok) break;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        int stage = 0, acc = 0, consumed = 0;
+        uint32_t phase = 0, aphase = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+            if (!mbar_wait(&c->tempty[acc], aphase ^ 1u, c, err)) break;
+            fence_after();
+            const uint32_t d = tmem + (uint32_t)acc * BN;
+            bool ok = true;
+            for (int kb = 0; kb < nk; ++kb) {
+                if (!mbar_wait(&c->full[stage], phase, c, err)) { ok = false; break; }
+                fence_after();
+                ++consumed;
+                const uint8_t *sa = base + (size_t)stage * STAGE_BYTES;
+                const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + A_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    mma_bf16(d, da + 2ull * kk, db + 2ull * kk, (kb | kk) != 0);
+                mma_commit(&c->empty[stage]);
+                if (++stage == HSTAGES) { stage = 0; phase ^= 1u; }
+            }
+            if (!ok) break;
+            mma_commit(&c->tfull[acc]);
+            acc ^= 1;
+            if (acc == 0) aphase ^= 1u;
+        }
+        c->consumed = consumed;
+        mma_commit(&c->done);
+        mbar_wait(&c->done, 0, c, err, false);
+    } else if (warp >= 2 && warp < 6) {
+        // epilogue (EPI = kBiasReluDot, the screen's layer 2): rows 32 (warp % 4)
+        // + lane of each tile
+        static_assert(EPI == kBiasReluDot, "the partial sums of the screen's layer 2");
+        const int q = warp & 3;
+        int acc = 0;
+        uint32_t aphase = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+            int ok = 0;
+            if (lane == 0) ok = mbar_wait(&c->tfull[acc], aphase, c, err);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            fence_after();
+            const int m0 = (t / tn) * BM, n0 = (t % tn) * BN;
+            const int row = m0 + q * 32 + lane;
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * BN;
+            float part[BN / 64];
+#pragma unroll 1
+            for (int hh = 0; hh < BN / 64; ++hh) {
+                float dot = 0.f;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    float v[32];
+                    tmem_ld32(ta + (uint32_t)(hh * 64 + s * 32), v);
+                    epilogue32<EPI>(g, row, n0 + hh * 64 + s * 32, v, dot);
+                }
+                part[hh] = dot;
+            }
+            float4 *o = reinterpret_cast<float4 *>(g.part + (size_t)row * (g.N / 64) + n0 / 64);
+#pragma unroll
+            for (int hh = 0; hh < BN / 256; ++hh)
+                o[hh] = make_float4(part[4 * hh], part[4 * hh + 1], part[4 * hh + 2], part[4 * hh + 3]);
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&c->tempty[acc]);
+            acc ^= 1;
+            if (acc == 0) aphase ^= 1u;
+        }
+    } else if (warp >= 6) {
+        // producers of A
+        const int p = threadIdx.x - 192;
+        const int r = p >> 1, half = p & 1;
+        const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        const int n_iter = my_tiles * nk;
+        const int ldw = g.K;   // W1 and A1 rows are K-dimension long
+        // K block i of this CTA: tile blockIdx.x + (i / nk) gridDim.x, block i % nk
+        auto row_of = [&](int i) { return ((blockIdx.x + (i / nk) * gridDim.x) / tn) * BM + r; };
+        auto issue = [&](int i) {
+            if (i < n_iter) {
+                const int R = row_of(i), kb = i % nk;
+                if (R < h.n_rows) {
+                    const int2 rw = __ldg(h.rows + R);
+                    if (rw.x >= 0) {
+                        uint8_t *slot = staging + (size_t)(i % HDEPTH) * HSTAGING_BYTES;
+                        const __nv_bfloat16 *wn = h.W1b + (size_t)rw.x * ldw + kb * BK + half * 32;
+                        const __nv_bfloat16 *wo = h.W1b + (size_t)rw.y * ldw + kb * BK + half * 32;
+#pragma unroll
+                        for (int ch = 0; ch < 4; ++ch) {
+                            cp_async16(slot + ((size_t)ch * HPROD + p) * 16, wn + ch * 8);
+                            cp_async16(slot + ((size_t)(4 + ch) * HPROD + p) * 16, wo + ch * 8);
+                        }
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+        auto load_a1 = [&](int i, float4 (&a)[8]) {
+            const int R = i < n_iter ? row_of(i) : h.n_rows;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) a[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (R < h.n_rows) {
+                const float4 *src = reinterpret_cast<const float4 *>(
+                    h.A1 + (size_t)(R / h.K) * ldw + (i % nk) * BK + half * 32);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) a[e] = __ldg(src + e);
+            }
+        };
+#pragma unroll
+        for (int i = 0; i < HDEPTH; ++i) issue(i);
+        float4 a1n[8];
+        load_a1(0, a1n);
+        int stage = 0;
+        uint32_t phase = 0;
+        for (int i = 0; i < n_iter; ++i) {
+            float4 a1[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) a1[e] = a1n[e];
+            load_a1(i + 1, a1n);
+            cp_async_wait<HDEPTH - 1>();
+            if (p == 0) c->pflag[i & 1] = mbar_wait(&c->empty[stage], phase ^ 1u, c, err) ? 1 : 0;
+            producers_sync();
+            if (!*(volatile int *)&c->pflag[i & 1]) break;
+            const int R = row_of(i);
+            const bool valid = R < h.n_rows;
+            const int2 rw = valid ? __ldg(h.rows + R) : make_int2(-1, -1);
+            const uint8_t *slot = staging + (size_t)(i % HDEPTH) * HSTAGING_BYTES;
+            uint8_t *sa = base + (size_t)stage * STAGE_BYTES + (size_t)r * 128;
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                float v[8] = {a1[2 * ch].x, a1[2 * ch].y, a1[2 * ch].z, a1[2 * ch].w,
+                              a1[2 * ch + 1].x, a1[2 * ch + 1].y, a1[2 * ch + 1].z,
+                              a1[2 * ch + 1].w};
+                if (valid && rw.x >= 0) {
+                    const uint4 wn = *reinterpret_cast<const uint4 *>(slot + ((size_t)ch * HPROD + p) * 16);
+                    const uint4 wo =
+                        *reinterpret_cast<const uint4 *>(slot + ((size_t)(4 + ch) * HPROD + p) * 16);
+                    const __nv_bfloat162 *pn = reinterpret_cast<const __nv_bfloat162 *>(&wn);
+                    const __nv_bfloat162 *po = reinterpret_cast<const __nv_bfloat162 *>(&wo);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 fn = __bfloat1622float2(pn[e]), fo = __bfloat1622float2(po[e]);
+                        v[2 * e] += fn.x - fo.x;
+                        v[2 * e + 1] += fn.y - fo.y;
+                    }
+                }
+                uint4 ov = make_uint4(0u, 0u, 0u, 0u);
+                if (valid) {
+                    __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(&ov);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        o2[e] = __floats2bfloat162_rn(fmaxf(v[2 * e], 0.f), fmaxf(v[2 * e + 1], 0.f));
+                }
+                // 16-byte chunk (half * 4 + ch) of the row, 128-byte swizzle
+                const int cc = (half * 4 + ch) ^ (r & 7);
+                *reinterpret_cast<uint4 *>(sa + cc * 16) = ov;
+            }
+            fence_proxy_async();
+            mbar_arrive(&c->full[stage]);
+            issue(i + HDEPTH);
+            if (++stage == HSTAGES) { stage = 0; phase ^= 1u; }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 0 && lane == 0 && *(volatile int *)&c->abort) {
+        for (int i = c->consumed; i < issued; ++i)
+            mbar_wait(&c->full[i % HSTAGES], (uint32_t)((i / HSTAGES) & 1), c, err, false);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
 }  // namespace umma
+
+// Shapes the fused layer-2 kernel covers: those of gemm_tc_supported with
+// N <= 512 (wider layers repeat the A production per 256 columns).
+inline bool gemm_hidden_supported(const GemmArgs &g)
+{
+    return g.M > 0 && g.M % umma::BM == 0 && g.N > 0 && g.N % umma::BN == 0 && g.N <= 512 &&
+           g.K > 0 && g.K % umma::BK == 0 && g.ldb % 8 == 0 && g.part && g.bias && g.w;
+}
+
+// The fused launch (rn_umma.cu); *err is set by a CTA whose wait gave up.
+cudaError_t launch_gemm_hidden(const GemmArgs &g, const HiddenArgs &h, int *err, int sm_count,
+                               cudaStream_t st);
 
 // Shapes the tcgen05 kernel covers: M % 128, N % 256, K % 64, 16-byte aligned
 // rows.

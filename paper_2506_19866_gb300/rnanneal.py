@@ -66,6 +66,7 @@ SIGNATURES = {
     "rn_mlp_train": (_c_int, [_vp, _c_i32, _c_i32, _c_i32, ctypes.c_float, _c_u64, _vp]),
     "rn_anneal_screened": (_c_int, [_vp, _c_i32, ctypes.POINTER(rn_schedule), _c_i32, _c_i32,
                                     ctypes.c_double, _c_i64]),
+    "rn_mlp_set_hidden_mode": (_c_int, [_vp, _c_i32, _c_i32]),
     "rn_synchronize": (_c_int, [_vp]),
 }
 
@@ -382,3 +383,9 @@ def rn_mlp_train(ctx, mlp, steps, batch=4096, lr=1e-3, seed=0):
 def rn_anneal_screened(ctx, mlp, sched: rn_schedule, sweeps, K=32, top=2, eps=0.0):
     _check(ctx, load_library().rn_anneal_screened(ctx, int(mlp), ctypes.byref(sched), int(K),
                                                   int(top), float(eps), int(sweeps)))
+
+
+def rn_mlp_set_hidden_mode(ctx, mlp, mode):
+    """0: the screened step forms the layer-2 input rows inside the GEMM
+    (default); 1: through device memory (propose kernel writes, TMA reads)."""
+    _check(ctx, load_library().rn_mlp_set_hidden_mode(ctx, int(mlp), int(mode)))

@@ -171,6 +171,36 @@ def test_screened_eps1_is_plain_annealing(ctx):
     np.testing.assert_array_equal(st["d_best"][ids], ch.d_best)
 
 
+@pytest.mark.parametrize("name,h,K", [("mtb_63n_178e", 512, 32), ("n120_c8_t21", 512, 7),
+                                      ("n15_c3_t11", 256, 32)])
+def test_hidden_rows_in_gemm_equal_through_memory(built, name, h, K):
+    """The screened step's two ways of forming the layer-2 input rows -- inside
+    the tcgen05 GEMM from A1 and gathered W1 rows (mode 0), or written to memory
+    by the propose kernel and read back by TMA (mode 1) -- give the same BF16
+    rows and the same MMAs, so the chains come out bit-identical.  301 chains:
+    the last row tile is partly padding; K = 7 puts chains across tile edges."""
+    w = synth.make(name)
+    n, steps = 301, 6
+    states = []
+    for mode in (0, 1):
+        c = R.rn_create(0)
+        try:
+            p = Problem(w, c)
+            mid, D, _ = _screen(c, p, h, h, 9)
+            R.rn_mlp_set_hidden_mode(c, mid, mode)
+            R.rn_init_chains(c, p.id, n, 5)
+            R.rn_anneal_screened(c, mid, R.schedule(2.0, 0.97), steps, K=K, top=2, eps=0.0)
+            states.append(R.rn_get_chain_state(c, p.id, n))
+            with pytest.raises(R.RNError) as e:
+                R.rn_mlp_set_hidden_mode(c, mid, 2)
+            assert e.value.code == R.RN_EINVAL
+        finally:
+            R.rn_destroy(c)
+    for k in ("x_cur", "d_cur", "x_best", "d_best", "counters"):
+        np.testing.assert_array_equal(states[0][k], states[1][k], err_msg=k)
+    assert states[0]["counters"][:, 0].sum() > 0
+
+
 def _candidates(net, x, seed, chain, g, K):
     """The K candidate moves of step g (oracle GetCandidate on the Philox words)."""
     out = []
