@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--batch-candidate", type=int, default=None,
                     help="pin the batched launch to one of the autotuner's candidates (0-7, "
                          "see rn_batch_config) instead of timing them")
+    ap.add_argument("--hidden-mode", type=int, default=None, choices=(0, 1),
+                    help="with --screened: how the layer-2 input rows are formed (1: through "
+                         "device memory, the default; 0: inside the GEMM)")
     ap.add_argument("--screened", action="store_true",
                     help="time screened steps (K = 32 candidates ranked by a seeded one-hot "
                          "MLP, top 2 simulated exactly) instead of plain sweeps; value counts "
@@ -561,6 +564,8 @@ def measure(args, R, dev, name, S, steps, warmup, rank, world, dist, screened=Fa
         screen_width = 1024 if any(block_path(w) for w in ws) else 512
         if screened:
             mid = screen_for(R, ctx_main, ids[0], ws[0], h=screen_width)
+            if getattr(args, "hidden_mode", None) is not None:
+                R.rn_mlp_set_hidden_mode(ctx_main, mid, args.hidden_mode)
             tops[0] = 2
             if both:
                 def step():

@@ -415,20 +415,23 @@ int rn_mlp_train(rn_ctx *ctx, int32_t mlp, int32_t steps, int32_t batch, float l
  * top: 1 .. 4 (<= K).  Covers every network the annealing kernels cover (a
  * warp or a block of threads per chain); RN_EUNSUPPORTED if one chain's x and
  * constraint counters exceed a block's shared memory.  The layer-2 input rows
- * of the K candidates, relu(A1 + W1[new] - W1[old]), are formed inside the
- * tcgen05 GEMM (see rn_mlp_set_hidden_mode). */
+ * of the K candidates, relu(A1 + W1[new] - W1[old]), go through device memory
+ * unless rn_mlp_set_hidden_mode selects forming them inside the GEMM. */
 int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K, int32_t top,
                        double eps, int64_t sweeps);
 
 /* How a screened step forms the layer-2 GEMM's input rows, the hidden rows
  * relu(A1 + W1[new] - W1[old]) of every chain's K candidates (an addition of
- * this library, no counterpart in the paper).  mode 0 (the default): the
- * propose kernel writes each candidate's two W1 row indices, and producer
- * warps of the tcgen05 GEMM form the rows in shared memory from A1 and the
- * gathered W1 rows.  mode 1: the propose kernel writes the BF16 rows to device
- * memory and the GEMM reads them back by TMA (M x H1 x 2 bytes each way per
- * step).  Both give bit-identical predictions and chains; layers wider than 512
- * always use mode 1.  RN_EINVAL for another mode or an unknown screen. */
+ * this library, no counterpart in the paper).  mode 1 (the default): the
+ * propose kernel writes the BF16 rows to device memory and the tcgen05 GEMM
+ * reads them back by TMA (M x H1 x 2 bytes each way per step).  mode 0: the
+ * propose kernel writes only each candidate's two W1 row indices, and producer
+ * warps of the GEMM form the rows in shared memory from A1 and the gathered W1
+ * rows; it saves the round trip through memory but measured slower on GB300
+ * (each SM's L2 intake for the row gathers and B tiles exceeds the MMAs' pace).
+ * Both give bit-identical predictions and chains; layers wider than 512 and
+ * fewer than 8 candidates always use mode 1.  RN_EINVAL for another mode or an
+ * unknown screen. */
 int rn_mlp_set_hidden_mode(rn_ctx *ctx, int32_t mlp, int32_t mode);
 
 /* Wait for all queued work on the context stream; reports device-side errors. */

@@ -222,7 +222,7 @@ struct Mlp {
     DevBuf<float> A1;                   // [chains][H1]
     DevBuf<uint16_t> hc;                // [Mc][H1] candidate hidden rows (bf16), hidden-row mode 1
     DevBuf<int2> rows;                  // [Mc] W1 rows (new, old) per candidate, hidden-row mode 0
-    int32_t hidden_mode = 0;            // 0: hidden rows formed in the GEMM; 1: through memory
+    int32_t hidden_mode = 1;            // 0: hidden rows formed in the GEMM; 1: through memory
     DevBuf<float> pc;                   // [Mc][H2 / 64] candidate layer-2 partials
     DevBuf<int32_t> cand;               // [chains][K] (j << 8) | (v & 255), -1 = null
     DevBuf<uint16_t> emb_oh;            // [kEmbedRows][Dp] one-hot rows of chains (large P)

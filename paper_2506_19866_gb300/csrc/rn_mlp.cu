@@ -289,10 +289,11 @@ __global__ void __launch_bounds__(kScreenWarps * 32) screen_propose_kernel(Scree
         ok = get_candidate(a.net, xs, out_nz, pos_in, r.x, r.y, j, kind, idx, cur, v);
     }
     if (lane < a.K) a.cand[(size_t)c * a.K + lane] = ok ? (j << 8) | (v & 255) : -1;
+    // lane k: the W1 rows of candidate k's new and old value (-1: no candidate)
+    const int rn_l = ok ? a.row_base[j] + v : -1;
+    const int ro_l = ok ? a.row_base[j] + cur : -1;
     if constexpr (ROWS) {
-        if (lane < a.K)
-            a.rows[(size_t)c * a.K + lane] =
-                ok ? make_int2(a.row_base[j] + v, a.row_base[j] + cur) : make_int2(-1, -1);
+        if (lane < a.K) a.rows[(size_t)c * a.K + lane] = make_int2(rn_l, ro_l);
         return;
     }
 
@@ -306,37 +307,50 @@ __global__ void __launch_bounds__(kScreenWarps * 32) screen_propose_kernel(Scree
         base[q][0] = u0.x; base[q][1] = u0.y; base[q][2] = u0.z; base[q][3] = u0.w;
         base[q][4] = u1.x; base[q][5] = u1.y; base[q][6] = u1.z; base[q][7] = u1.w;
     }
-    for (int k = 0; k < a.K; ++k) {
-        const int okk = __shfl_sync(0xffffffffu, (int)ok, k);
-        const int jk = __shfl_sync(0xffffffffu, j, k);
-        const int rn = a.row_base[jk] + __shfl_sync(0xffffffffu, v, k);
-        const int ro = a.row_base[jk] + __shfl_sync(0xffffffffu, cur, k);
-        bf16 *out = a.hc + ((size_t)c * a.K + k) * a.H1;
+    // four candidates per pass, their eight W1 row loads issued before any use
+    constexpr int U = 4;
+    for (int k0 = 0; k0 < a.K; k0 += U) {
 #pragma unroll
         for (int q = 0; q < kMaxGroups; ++q) {
             if (q >= groups) break;
             const int col = q * 256 + lane * 8;
-            float h[8];
+            uint4 wn[U], wo[U];
+            int rn[U];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) h[e] = base[q][e];
-            if (okk) {
-                const uint4 wn = *reinterpret_cast<const uint4 *>(a.W1b + (size_t)rn * a.H1 + col);
-                const uint4 wo = *reinterpret_cast<const uint4 *>(a.W1b + (size_t)ro * a.H1 + col);
-                const __nv_bfloat162 *pn = reinterpret_cast<const __nv_bfloat162 *>(&wn);
-                const __nv_bfloat162 *po = reinterpret_cast<const __nv_bfloat162 *>(&wo);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float2 fn = __bfloat1622float2(pn[e]), fo = __bfloat1622float2(po[e]);
-                    h[2 * e] += fn.x - fo.x;
-                    h[2 * e + 1] += fn.y - fo.y;
+            for (int u = 0; u < U; ++u) {
+                const int k = min(k0 + u, a.K - 1);
+                rn[u] = __shfl_sync(0xffffffffu, rn_l, k);
+                const int ro = __shfl_sync(0xffffffffu, ro_l, k);
+                wn[u] = wo[u] = make_uint4(0u, 0u, 0u, 0u);
+                if (rn[u] >= 0) {
+                    wn[u] = *reinterpret_cast<const uint4 *>(a.W1b + (size_t)rn[u] * a.H1 + col);
+                    wo[u] = *reinterpret_cast<const uint4 *>(a.W1b + (size_t)ro * a.H1 + col);
                 }
             }
-            uint4 ov;
-            __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(&ov);
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                o[e] = __floats2bfloat162_rn(fmaxf(h[2 * e], 0.f), fmaxf(h[2 * e + 1], 0.f));
-            *reinterpret_cast<uint4 *>(out + col) = ov;
+            for (int u = 0; u < U; ++u) {
+                if (k0 + u >= a.K) break;
+                float h[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) h[e] = base[q][e];
+                if (rn[u] >= 0) {
+                    const __nv_bfloat162 *pn = reinterpret_cast<const __nv_bfloat162 *>(&wn[u]);
+                    const __nv_bfloat162 *po = reinterpret_cast<const __nv_bfloat162 *>(&wo[u]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 fn = __bfloat1622float2(pn[e]), fo = __bfloat1622float2(po[e]);
+                        h[2 * e] += fn.x - fo.x;
+                        h[2 * e + 1] += fn.y - fo.y;
+                    }
+                }
+                uint4 ov;
+                __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(&ov);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    o[e] = __floats2bfloat162_rn(fmaxf(h[2 * e], 0.f), fmaxf(h[2 * e + 1], 0.f));
+                bf16 *out = a.hc + ((size_t)c * a.K + k0 + u) * a.H1;
+                *reinterpret_cast<uint4 *>(out + col) = ov;
+            }
         }
     }
 }
@@ -1095,10 +1109,10 @@ int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K
     g.lda = m->H1; g.B = bp(m->W2T); g.ldb = m->H1;
     g.M = M; g.N = m->H2; g.K = m->H1; g.ldc = m->H2;
     g.bias = m->theta.p + m->off_b2(); g.w = m->theta.p + m->off_w3(); g.part = m->pc.p;
-    // layer 2 of the K candidates: hidden rows formed inside the GEMM (mode 0),
-    // or written by the propose kernel and read back (mode 1, and widths above
-    // 512, where the fused kernel would repeat the rows per 256 columns)
-    const bool fused = m->hidden_mode == 0 && gemm_hidden_supported(g);
+    // layer 2 of the K candidates: hidden rows written by the propose kernel
+    // and read back by TMA (mode 1, the default), or formed inside the GEMM
+    // (mode 0; widths above 512 and fewer than 8 candidates use mode 1)
+    const bool fused = m->hidden_mode == 0 && gemm_hidden_supported(g, K);
     HiddenArgs hid{};
     if (fused) {
         hid.rows = m->rows.p;

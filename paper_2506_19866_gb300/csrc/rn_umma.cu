@@ -59,7 +59,7 @@ cudaError_t launch_t(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs 
 cudaError_t launch_gemm_hidden(const GemmArgs &g, const HiddenArgs &h, int *err, int sm_count,
                                cudaStream_t st)
 {
-    if (!gemm_hidden_supported(g) || !err || !h.rows || !h.A1 || !h.W1b || h.K < 1 ||
+    if (!gemm_hidden_supported(g, h.K) || !err || !h.rows || !h.A1 || !h.W1b || h.K < 1 ||
         h.n_rows < 0 || h.n_rows > g.M)
         return cudaErrorInvalidValue;
     CUtensorMap b;

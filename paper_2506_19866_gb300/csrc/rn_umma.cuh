@@ -88,16 +88,32 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity)
     return ok != 0;
 }
 
+// As mbar_test, but the thread may sleep up to about `ns` nanoseconds inside
+// the try_wait (woken when the phase completes), so that waiting roles take
+// few issue slots from the warps that work.
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t *b, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase of parity `parity` to complete.  Gives up (false) when
 // another role has aborted (watch_abort) or after kWaitCycles, then marks the
 // CTA aborted and records the failure.
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, Ctl *c, int *err,
-                                          bool watch_abort = true)
+                                          bool watch_abort = true, uint32_t sleep_ns = 0)
 {
     if (mbar_test(b, parity)) return true;
     const long long t0 = clock64();
     while (true) {
-        if (mbar_test(b, parity)) return true;
+        if (sleep_ns ? mbar_test_sleep(b, parity, sleep_ns) : mbar_test(b, parity)) return true;
         if (watch_abort && *(volatile int *)&c->abort) return false;
         if (clock64() - t0 > kWaitCycles) {
             *(volatile int *)&c->abort = 1;
@@ -386,21 +402,28 @@ __global__ void __launch_bounds__(THREADS, 1)
 // registers one K block ahead, so that the gathers' L2 latency overlaps the
 // arithmetic and the MMAs.  Each producer thread writes its BF16 values into
 // the stage in the 128-byte-swizzled K-major layout that TMA would have
-// written, makes them visible to the tensor core's proxy
-// (fence.proxy.async.shared::cta) and arrives on the stage's full barrier (one
-// TMA arrival plus 256 producer arrivals).  One producer waits on the stage's
-// empty barrier (bounded) and passes the result to the others through a named
-// barrier, so that all producers leave together when a wait gives up.  This
+// written and makes them visible to the tensor core's proxy
+// (fence.proxy.async.shared::cta); after a named barrier over the producers
+// one of them arrives on the stage's full barrier (one TMA arrival plus one
+// producer arrival: 256 arrivals on one barrier word would serialise).  The
+// same producer waits on the stage's empty barrier (bounded) and passes the
+// result to the others through the named barrier, so that all producers leave
+// together when a wait gives up.  This
 // replaces the HBM round trip of the hidden rows (written by the propose
 // kernel, read back by TMA): for 4096 chains x 32 candidates x 512 columns,
 // 134 MB each way per step.
-constexpr int HSTAGES = 3;                                  // GEMM stages (A produced, B by TMA)
-constexpr int HDEPTH = 2;                                   // staging slots (K blocks ahead)
+constexpr int HSTAGES = 2;                                  // GEMM stages (A produced, B by TMA)
+constexpr uint32_t kSleepNs = 2000;                         // try_wait sleep hint of waiting roles
+constexpr int HDEPTH = 3;                                   // staging slots (K blocks ahead)
 constexpr int HPROD = 256;                                  // producer threads
 constexpr int HTHREADS = 192 + HPROD;
+constexpr int HMIN_K = 8;                                   // candidates per chain, at least
 constexpr int HSTAGING_BYTES = BM * 2 * BK * 2;             // new and old W1 rows of a K block
+constexpr int HA1_BYTES = (BM / HMIN_K + 2) * BK * 4;       // A1 of the tile's chains
+constexpr int HSLOT_BYTES = HSTAGING_BYTES + HA1_BYTES;
 constexpr size_t HSMEM_BYTES =
-    1024 + (size_t)HSTAGES * STAGE_BYTES + (size_t)HDEPTH * HSTAGING_BYTES + sizeof(Ctl) + 64;
+    1024 + (size_t)HSTAGES * STAGE_BYTES + (size_t)HDEPTH * HSLOT_BYTES + sizeof(Ctl) + 64;
+static_assert(HSMEM_BYTES <= 232448, "one CTA's shared memory");
 
 __device__ __forceinline__ void fence_proxy_async()
 {
@@ -419,13 +442,13 @@ __global__ void __launch_bounds__(HTHREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
     uint8_t *staging = base + (size_t)HSTAGES * STAGE_BYTES;
-    Ctl *c = reinterpret_cast<Ctl *>(staging + (size_t)HDEPTH * HSTAGING_BYTES);
+    Ctl *c = reinterpret_cast<Ctl *>(staging + (size_t)HDEPTH * HSLOT_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tn = g.N / BN, tiles = (g.M / BM) * tn, nk = g.K / BK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < HSTAGES; ++s) {
-            mbar_init(&c->full[s], 1 + HPROD);
+            mbar_init(&c->full[s], 2);
             mbar_init(&c->empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -458,7 +481,7 @@ __global__ void __launch_bounds__(HTHREADS, 1)
             const int n0 = (t % tn) * BN;
             bool ok = true;
             for (int kb = 0; kb < nk; ++kb) {
-                if (!mbar_wait(&c->empty[stage], phase ^ 1u, c, err)) { ok = false; break; }
+                if (!mbar_wait(&c->empty[stage], phase ^ 1u, c, err, true, kSleepNs)) { ok = false; break; }
                 uint8_t *sa = base + (size_t)stage * STAGE_BYTES;
                 mbar_expect_tx(&c->full[stage], B_BYTES);
                 tma_load_2d(sa + A_BYTES, &tmB, &c->full[stage], kb * BK, n0);
@@ -472,12 +495,12 @@ __global__ void __launch_bounds__(HTHREADS, 1)
         int stage = 0, acc = 0, consumed = 0;
         uint32_t phase = 0, aphase = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-            if (!mbar_wait(&c->tempty[acc], aphase ^ 1u, c, err)) break;
+            if (!mbar_wait(&c->tempty[acc], aphase ^ 1u, c, err, true, kSleepNs)) break;
             fence_after();
             const uint32_t d = tmem + (uint32_t)acc * BN;
             bool ok = true;
             for (int kb = 0; kb < nk; ++kb) {
-                if (!mbar_wait(&c->full[stage], phase, c, err)) { ok = false; break; }
+                if (!mbar_wait(&c->full[stage], phase, c, err, true, kSleepNs)) { ok = false; break; }
                 fence_after();
                 ++consumed;
                 const uint8_t *sa = base + (size_t)stage * STAGE_BYTES;
@@ -505,7 +528,7 @@ __global__ void __launch_bounds__(HTHREADS, 1)
         uint32_t aphase = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
             int ok = 0;
-            if (lane == 0) ok = mbar_wait(&c->tfull[acc], aphase, c, err);
+            if (lane == 0) ok = mbar_wait(&c->tfull[acc], aphase, c, err, true, kSleepNs);
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             fence_after();
             const int m0 = (t / tn) * BM, n0 = (t % tn) * BN;
@@ -540,64 +563,84 @@ __global__ void __launch_bounds__(HTHREADS, 1)
         const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
         const int n_iter = my_tiles * nk;
         const int ldw = g.K;   // W1 and A1 rows are K-dimension long
-        // K block i of this CTA: tile blockIdx.x + (i / nk) gridDim.x, block i % nk
-        auto row_of = [&](int i) { return ((blockIdx.x + (i / nk) * gridDim.x) / tn) * BM + r; };
-        auto issue = [&](int i) {
-            if (i < n_iter) {
-                const int R = row_of(i), kb = i % nk;
-                if (R < h.n_rows) {
-                    const int2 rw = __ldg(h.rows + R);
-                    if (rw.x >= 0) {
-                        uint8_t *slot = staging + (size_t)(i % HDEPTH) * HSTAGING_BYTES;
-                        const __nv_bfloat16 *wn = h.W1b + (size_t)rw.x * ldw + kb * BK + half * 32;
-                        const __nv_bfloat16 *wo = h.W1b + (size_t)rw.y * ldw + kb * BK + half * 32;
+        // A K block of this CTA, advanced one block at a time (divisions only
+        // when it enters a new tile): the tile's first row, this thread's row
+        // R and its W1 rows, and the tile's first chain.
+        struct Pos {
+            int i, kb, tile, R, c0, cl;   // cl: this row's chain, counted from c0
+            int2 rw;
+        };
+        auto enter_tile = [&](Pos &q) {
+            const int m0 = (q.tile / tn) * BM;
+            q.R = m0 + r;
+            q.c0 = m0 / h.K;
+            q.cl = q.R / h.K - q.c0;
+            q.rw = q.R < h.n_rows ? __ldg(h.rows + q.R) : make_int2(-1, -1);
+        };
+        auto start = [&](int i) {
+            Pos q;
+            q.i = i;
+            q.kb = i % nk;
+            q.tile = blockIdx.x + (i / nk) * gridDim.x;
+            enter_tile(q);
+            return q;
+        };
+        auto advance = [&](Pos &q) {
+            ++q.i;
+            if (++q.kb == nk) {
+                q.kb = 0;
+                q.tile += gridDim.x;
+                if (q.i < n_iter) enter_tile(q);
+            }
+        };
+        // staging slot i % HDEPTH: this thread's W1 segments, then the tile's
+        // A1 segments (chains c0 .. of the tile's rows)
+        auto issue = [&](const Pos &q) {
+            if (q.i < n_iter) {
+                uint8_t *slot = staging + (size_t)(q.i % HDEPTH) * HSLOT_BYTES;
+                if (q.R < h.n_rows && q.rw.x >= 0) {
+                    const __nv_bfloat16 *wn = h.W1b + (size_t)q.rw.x * ldw + q.kb * BK + half * 32;
+                    const __nv_bfloat16 *wo = h.W1b + (size_t)q.rw.y * ldw + q.kb * BK + half * 32;
 #pragma unroll
-                        for (int ch = 0; ch < 4; ++ch) {
-                            cp_async16(slot + ((size_t)ch * HPROD + p) * 16, wn + ch * 8);
-                            cp_async16(slot + ((size_t)(4 + ch) * HPROD + p) * 16, wo + ch * 8);
-                        }
+                    for (int ch = 0; ch < 4; ++ch) {
+                        cp_async16(slot + ((size_t)ch * HPROD + p) * 16, wn + ch * 8);
+                        cp_async16(slot + ((size_t)(4 + ch) * HPROD + p) * 16, wo + ch * 8);
                     }
                 }
+                // A1: 16 chunks of 16 bytes per chain of the tile
+                const int m0 = q.R - r;
+                const int last = min(m0 + BM, h.n_rows) - 1;
+                const int n_chunks = last >= m0 ? (last / h.K - q.c0 + 1) * 16 : 0;
+                for (int k = p; k < n_chunks; k += HPROD)
+                    cp_async16(slot + HSTAGING_BYTES + (size_t)k * 16,
+                               h.A1 + (size_t)(q.c0 + (k >> 4)) * ldw + q.kb * BK + (k & 15) * 4);
             }
             cp_async_commit();
         };
-        auto load_a1 = [&](int i, float4 (&a)[8]) {
-            const int R = i < n_iter ? row_of(i) : h.n_rows;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) a[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (R < h.n_rows) {
-                const float4 *src = reinterpret_cast<const float4 *>(
-                    h.A1 + (size_t)(R / h.K) * ldw + (i % nk) * BK + half * 32);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) a[e] = __ldg(src + e);
-            }
-        };
-#pragma unroll
-        for (int i = 0; i < HDEPTH; ++i) issue(i);
-        float4 a1n[8];
-        load_a1(0, a1n);
+        Pos qc = start(0), qi = start(0);
+#pragma unroll 1
+        for (int k = 0; k < HDEPTH; ++k) {
+            issue(qi);
+            advance(qi);
+        }
         int stage = 0;
         uint32_t phase = 0;
         for (int i = 0; i < n_iter; ++i) {
-            float4 a1[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) a1[e] = a1n[e];
-            load_a1(i + 1, a1n);
             cp_async_wait<HDEPTH - 1>();
-            if (p == 0) c->pflag[i & 1] = mbar_wait(&c->empty[stage], phase ^ 1u, c, err) ? 1 : 0;
+            if (p == 0) c->pflag[i & 1] = mbar_wait(&c->empty[stage], phase ^ 1u, c, err, true, kSleepNs) ? 1 : 0;
             producers_sync();
             if (!*(volatile int *)&c->pflag[i & 1]) break;
-            const int R = row_of(i);
-            const bool valid = R < h.n_rows;
-            const int2 rw = valid ? __ldg(h.rows + R) : make_int2(-1, -1);
-            const uint8_t *slot = staging + (size_t)(i % HDEPTH) * HSTAGING_BYTES;
+            const bool valid = qc.R < h.n_rows;
+            const uint8_t *slot = staging + (size_t)(i % HDEPTH) * HSLOT_BYTES;
+            const float *a1 = reinterpret_cast<const float *>(slot + HSTAGING_BYTES) +
+                              (valid ? qc.cl * BK : 0) + half * 32;
             uint8_t *sa = base + (size_t)stage * STAGE_BYTES + (size_t)r * 128;
 #pragma unroll
             for (int ch = 0; ch < 4; ++ch) {
-                float v[8] = {a1[2 * ch].x, a1[2 * ch].y, a1[2 * ch].z, a1[2 * ch].w,
-                              a1[2 * ch + 1].x, a1[2 * ch + 1].y, a1[2 * ch + 1].z,
-                              a1[2 * ch + 1].w};
-                if (valid && rw.x >= 0) {
+                const float4 lo = *reinterpret_cast<const float4 *>(a1 + ch * 8);
+                const float4 hi = *reinterpret_cast<const float4 *>(a1 + ch * 8 + 4);
+                float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+                if (valid && qc.rw.x >= 0) {
                     const uint4 wn = *reinterpret_cast<const uint4 *>(slot + ((size_t)ch * HPROD + p) * 16);
                     const uint4 wo =
                         *reinterpret_cast<const uint4 *>(slot + ((size_t)(4 + ch) * HPROD + p) * 16);
@@ -622,8 +665,11 @@ __global__ void __launch_bounds__(HTHREADS, 1)
                 *reinterpret_cast<uint4 *>(sa + cc * 16) = ov;
             }
             fence_proxy_async();
-            mbar_arrive(&c->full[stage]);
-            issue(i + HDEPTH);
+            producers_sync();
+            if (p == 0) mbar_arrive(&c->full[stage]);
+            issue(qi);
+            advance(qi);
+            advance(qc);
             if (++stage == HSTAGES) { stage = 0; phase ^= 1u; }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -647,11 +693,13 @@ __global__ void __launch_bounds__(HTHREADS, 1)
 }  // namespace umma
 
 // Shapes the fused layer-2 kernel covers: those of gemm_tc_supported with
-// N <= 512 (wider layers repeat the A production per 256 columns).
-inline bool gemm_hidden_supported(const GemmArgs &g)
+// N <= 512 (wider layers repeat the A production per 256 columns) and at
+// least 8 candidates per chain (the A1 rows of a tile's chains are staged).
+inline bool gemm_hidden_supported(const GemmArgs &g, int candidates)
 {
     return g.M > 0 && g.M % umma::BM == 0 && g.N > 0 && g.N % umma::BN == 0 && g.N <= 512 &&
-           g.K > 0 && g.K % umma::BK == 0 && g.ldb % 8 == 0 && g.part && g.bias && g.w;
+           g.K > 0 && g.K % umma::BK == 0 && g.ldb % 8 == 0 && g.part && g.bias && g.w &&
+           candidates >= umma::HMIN_K;
 }
 
 // The fused launch (rn_umma.cu); *err is set by a CTA whose wait gave up.

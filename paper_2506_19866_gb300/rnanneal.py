@@ -386,6 +386,6 @@ def rn_anneal_screened(ctx, mlp, sched: rn_schedule, sweeps, K=32, top=2, eps=0.
 
 
 def rn_mlp_set_hidden_mode(ctx, mlp, mode):
-    """0: the screened step forms the layer-2 input rows inside the GEMM
-    (default); 1: through device memory (propose kernel writes, TMA reads)."""
+    """1: the screened step's layer-2 input rows go through device memory
+    (propose kernel writes, TMA reads; the default); 0: formed inside the GEMM."""
     _check(ctx, load_library().rn_mlp_set_hidden_mode(ctx, int(mlp), int(mode)))
