@@ -10,32 +10,55 @@
 namespace rn {
 
 // Seeded sample-and-repair x0 (the paper draws x0 with a constraint solver),
-// one thread per chain: uniform draws, then an activating in-edge for every
-// node without one, then a nonzero out-edge for every node without one.
+// one warp per chain: uniform draws, then an activating in-edge for every node
+// without one, then a nonzero out-edge for every node without one.  Lane l
+// draws parameters 4b .. 4b + 3 of blocks b = l, l + 32, ... from one Philox
+// call per block (counter (b, 0, chain, 1), word j % 4 for parameter j) and
+// stores them as one 32-bit word, so the row is written in whole lines.  In
+// the repairs the lanes take the nodes: a node's first repair reads and writes
+// only its own in-edges, its second only its own out-edges, so the nodes of a
+// repair are independent and the lanes give the result of the node-by-node
+// order (the second repair sees all of the first).
 __global__ void init_kernel(DevNet net, DevChains ch, int32_t *status)
 {
-    const int chain = blockIdx.x * blockDim.x + threadIdx.x;
-    if (chain >= ch.n) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t chain = (int64_t)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (chain >= ch.n) return;   // whole warps
     int8_t *x = ch.x_cur + (size_t)chain * ch.pstride;
     const int E = net.E, N = net.N, P = net.P;
-    uint4 r = make_uint4(0, 0, 0, 0);
-    for (int j = 0; j < P; ++j) {
-        if ((j & 3) == 0) r = philox(ch.seed, (uint32_t)(j >> 2), 0u, (uint32_t)chain, 1u);
-        if (net.frozen && net.frozen[j]) {
-            x[j] = net.frozen_val[j];
-            continue;
+    for (int b = lane; b < ch.pstride / 4; b += 32) {
+        uint32_t word4 = 0;
+        const int j0 = 4 * b;
+        if (j0 < P) {
+            const uint4 r = philox(ch.seed, (uint32_t)b, 0u, (uint32_t)chain, 1u);
+            const uint32_t words[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = j0 + q;
+                if (j >= P) break;
+                int8_t v;
+                if (net.frozen && net.frozen[j]) {
+                    v = net.frozen_val[j];
+                } else {
+                    int kind, idx;
+                    if (j < E) { kind = 0; idx = j; }
+                    else if (j < 2 * E) { kind = 1; idx = j - E; }
+                    else if (j < 3 * E) { kind = 2; idx = j - 2 * E; }
+                    else if (j < 3 * E + N) { kind = 3; idx = j - 3 * E; }
+                    else if (j < 3 * E + 2 * N) { kind = 4; idx = j - 3 * E - N; }
+                    else { kind = 5; idx = j - 3 * E - 2 * N; }
+                    int8_t vals[6];
+                    const int nd = domain(kind, kind == 3 && net.fast[idx], vals);
+                    v = vals[pick(words[q], (uint32_t)nd)];
+                }
+                word4 |= (uint32_t)(uint8_t)v << (8 * q);
+            }
         }
-        int kind, idx;
-        if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
-        else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
-        int8_t vals[6];
-        const int nd = domain(kind, kind == 3 && net.fast[idx], vals);
-        const uint32_t word = (j & 3) == 0 ? r.x : (j & 3) == 1 ? r.y : (j & 3) == 2 ? r.z : r.w;
-        x[j] = vals[pick(word, (uint32_t)nd)];
+        reinterpret_cast<uint32_t *>(x)[b] = word4;
     }
-    for (int j = P; j < ch.pstride; ++j) x[j] = 0;
+    __syncwarp();
     int ok = 1;
-    for (int i = 0; i < N && ok; ++i) {
+    for (int i = lane; i < N; i += 32) {
         int has = 0, n_cand = 0;
         for (int k = net.in_ptr[i]; k < net.in_ptr[i + 1]; ++k) {
             const int e = net.in_edges[k];
@@ -45,7 +68,7 @@ __global__ void init_kernel(DevNet net, DevChains ch, int32_t *status)
             n_cand += p_ok && w_ok;
         }
         if (has) continue;
-        if (n_cand == 0) { ok = 0; break; }
+        if (n_cand == 0) { ok = 0; continue; }
         const uint4 q = philox(ch.seed, (uint32_t)i, 0u, (uint32_t)chain, 3u);
         int want = (int)pick(q.x, (uint32_t)n_cand);
         for (int k = net.in_ptr[i]; k < net.in_ptr[i + 1]; ++k) {
@@ -59,31 +82,40 @@ __global__ void init_kernel(DevNet net, DevChains ch, int32_t *status)
             break;
         }
     }
-    for (int i = 0; i < N && ok; ++i) {
-        int has = 0, n_cand = 0;
-        for (int k = net.out_ptr[i]; k < net.out_ptr[i + 1]; ++k) {
-            const int e = net.out_edges[k];
-            has |= x[e] != 0;
-            n_cand += !(net.frozen && net.frozen[e]);
+    ok = __all_sync(0xffffffffu, ok);
+    __syncwarp();
+    if (ok) {
+        for (int i = lane; i < N; i += 32) {
+            int has = 0, n_cand = 0;
+            for (int k = net.out_ptr[i]; k < net.out_ptr[i + 1]; ++k) {
+                const int e = net.out_edges[k];
+                has |= x[e] != 0;
+                n_cand += !(net.frozen && net.frozen[e]);
+            }
+            if (has) continue;
+            if (n_cand == 0) { ok = 0; continue; }
+            const uint4 q = philox(ch.seed, (uint32_t)i, 1u, (uint32_t)chain, 3u);
+            int want = (int)pick(q.x, (uint32_t)n_cand);
+            for (int k = net.out_ptr[i]; k < net.out_ptr[i + 1]; ++k) {
+                const int e = net.out_edges[k];
+                if (net.frozen && net.frozen[e]) continue;
+                if (want-- != 0) continue;
+                x[e] = (int8_t)(1 + (q.y & 1u));
+                break;
+            }
         }
-        if (has) continue;
-        if (n_cand == 0) { ok = 0; break; }
-        const uint4 q = philox(ch.seed, (uint32_t)i, 1u, (uint32_t)chain, 3u);
-        int want = (int)pick(q.x, (uint32_t)n_cand);
-        for (int k = net.out_ptr[i]; k < net.out_ptr[i + 1]; ++k) {
-            const int e = net.out_edges[k];
-            if (net.frozen && net.frozen[e]) continue;
-            if (want-- != 0) continue;
-            x[e] = (int8_t)(1 + (q.y & 1u));
-            break;
-        }
+        ok = __all_sync(0xffffffffu, ok);
     }
-    int8_t *xb = ch.x_best + (size_t)chain * ch.pstride;
-    for (int j = 0; j < ch.pstride; ++j) xb[j] = x[j];
-    ch.cnt[3 * (size_t)chain + 0] = 0;
-    ch.cnt[3 * (size_t)chain + 1] = 0;
-    ch.cnt[3 * (size_t)chain + 2] = 0;
-    status[chain] = ok ? 0 : -2;
+    __syncwarp();
+    const uint4 *src = reinterpret_cast<const uint4 *>(x);
+    uint4 *dst = reinterpret_cast<uint4 *>(ch.x_best + (size_t)chain * ch.pstride);
+    for (int k = lane; k < ch.pstride / 16; k += 32) dst[k] = src[k];
+    if (lane == 0) {
+        ch.cnt[3 * (size_t)chain + 0] = 0;
+        ch.cnt[3 * (size_t)chain + 1] = 0;
+        ch.cnt[3 * (size_t)chain + 2] = 0;
+        status[chain] = ok ? 0 : -2;
+    }
 }
 
 // Table 1, end of a level: the lowest delta_best over the chains (lowest chain
@@ -273,7 +305,7 @@ cudaError_t launch_anneal(const DevNet &net, int d0, int d1, const DevChains &ch
 
 cudaError_t launch_init(const DevNet &net, const DevChains &ch, int32_t *status, cudaStream_t st)
 {
-    init_kernel<<<(ch.n + 127) / 128, 128, 0, st>>>(net, ch, status);
+    init_kernel<<<(unsigned)((ch.n + 3) / 4), 128, 0, st>>>(net, ch, status);
     return cudaGetLastError();
 }
 
