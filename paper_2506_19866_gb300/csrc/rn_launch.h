@@ -35,6 +35,12 @@ cudaError_t launch_anneal(const DevNet &net, int d0, int d1, const DevChains &ch
                           const DevSched &sc, int sm_count, cudaStream_t st);
 cudaError_t launch_init(const DevNet &net, const DevChains &ch, int32_t *status, cudaStream_t st);
 
+// Single-condition networks with four chains per warp in the byte lanes
+// (rn_chains4.cu): the layouts compiled for it, and its launch.
+bool chains4_layout(const DevNet &net, int d0, int d1);
+cudaError_t launch_anneal_chains4(const DevNet &net, int d0, int d1, const DevChains &ch,
+                                  const DevSched &sc, int sm_count, cudaStream_t st);
+
 // Hybrid path (rn_smemreg.cu): 6, 8 or 10 nodes per lane, table words in
 // shared memory, node state in registers.
 bool smemreg_layout(int npl);

@@ -661,3 +661,28 @@ def test_early_reject_is_exact(ctx, n_nodes, n_cond):
     cnt = runs[1]["counters"]
     rejected = n * sweeps - cnt[:, 0].sum() - cnt[:, 2].sum()
     assert rejected > n * sweeps // 50
+
+
+@pytest.mark.parametrize("n_nodes,n_chains,sync", [(9, 37, False), (20, 70, False),
+                                                   (45, 41, False), (63, 130, True),
+                                                   (60, 5, False)])
+def test_single_condition_four_chains_per_warp(ctx, n_nodes, n_chains, sync):
+    # one condition: four chains share a warp in the byte lanes (1 or 2 nodes
+    # per lane); every chain against the oracle, the last quad partly empty,
+    # under the priority and the synchronous scheme; then the same steps with
+    # exact early rejection, which keeps one chain per warp, must agree
+    w = synth.random_network(500 + n_nodes, n_nodes, lam=3.0, cap=min(7, n_nodes - 1), n_cond=1,
+                             n_times=14, obs_frac=0.5)
+    p = Problem(w, ctx, sync=sync)
+    R.rn_init_chains(ctx, p.id, n_chains, 21)
+    sched = R.schedule(3.0, 0.98)
+    R.rn_anneal(ctx, sched, 17)
+    R.rn_anneal(ctx, sched, 23)
+    st = R.rn_get_chain_state(ctx, p.id, n_chains)
+    ch = _oracle_run(p, 21, n_chains, O.Schedule(3.0, 0.98), 0, 40)
+    _compare(st, ch, list(range(n_chains)))
+    R.rn_init_chains(ctx, p.id, n_chains, 21)
+    R.rn_anneal(ctx, R.schedule(3.0, 0.98, early_reject=True), 40)
+    er = R.rn_get_chain_state(ctx, p.id, n_chains)
+    for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"):
+        np.testing.assert_array_equal(er[k], st[k], err_msg=k)
