@@ -301,13 +301,16 @@ __device__ __forceinline__ void undo4(Regs4<NPL, D0, D1> &R, const Undo4 &U, int
             });
             continue;
         }
+        // the constants of the four chains share registers: restore only
+        // chain cc's byte (half for u), since another chain's change to the
+        // same node may have been accepted in the same step
         const int slot = (int)((U.what[cc] >> 10) & 0x3fu);
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
             if (k != slot) continue;
-            if (kind == 3) (cc < 2 ? R.U01[k] : R.U23[k]) = ov;
-            else if (kind == 4) R.CM[k] = ov;
-            else R.D2[k] = ov;
+            if (kind == 3) put_half(cc < 2 ? R.U01[k] : R.U23[k], cc & 1, ov >> (16 * (cc & 1)));
+            else if (kind == 4) put_byte(R.CM[k], cc, ov >> (8 * cc));
+            else put_byte(R.D2[k], cc, ov >> (8 * cc));
         }
     }
 }
