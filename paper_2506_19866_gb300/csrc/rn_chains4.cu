@@ -370,27 +370,37 @@ __device__ __forceinline__ void run_chunk4(const DevNet &net, const DevChains &c
             for (int c = 0; c < 4; ++c) d_cur[c] = d_best[c];
         }
         ++in_level;
-        // candidates: cj (parameter), cv (new value | old value << 8); rz the
-        // acceptance words; own: bit c when this lane owns chain c's change
+        // candidates: lane group c (lanes 8c .. 8c + 7) draws chain c's words
+        // and runs its GetCandidate, then every lane takes the four results:
+        // cj (parameter), cv (new value | old value << 8), rz (acceptance word);
+        // own: bit c when this lane owns chain c's change
         int cj[4], cv[4];
         uint32_t rz[4];
         uint32_t has = 0, own = 0;
+        {
+            const int grp = lane >> 3;
+            int j = 0, kind, idx, cur = 0, v = 0, ok = 0;
+            uint32_t z = 0;
+            if (grp < n_here && net.n_free > 0) {
+                const uint4 r = philox(ch.seed, (uint32_t)g, (uint32_t)((uint64_t)g >> 32),
+                                       (uint32_t)(4 * quad + grp), 0u);
+                z = r.z;
+                ok = get_candidate(net, xs(grp), onz(grp), pin(grp), r.x, r.y, j, kind, idx, cur, v);
+            }
+            const int packed = ok ? ((v & 0xff) | ((cur & 0xff) << 8)) : -1;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                rz[c] = __shfl_sync(kFull, z, 8 * c);
+                cj[c] = __shfl_sync(kFull, j, 8 * c);
+                cv[c] = __shfl_sync(kFull, packed, 8 * c);
+            }
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            rz[c] = 0;
-            cj[c] = 0;
-            cv[c] = 0;
-            if (c >= n_here || net.n_free == 0) continue;
-            const uint4 r = philox(ch.seed, (uint32_t)g, (uint32_t)((uint64_t)g >> 32),
-                                   (uint32_t)(4 * quad + c), 0u);
-            rz[c] = r.z;
-            int j, kind, idx, cur, v;
-            if (!get_candidate(net, xs(c), onz(c), pin(c), r.x, r.y, j, kind, idx, cur, v))
-                continue;
+            if (cv[c] < 0) continue;
             has |= 1u << c;
-            cj[c] = j;
-            cv[c] = (v & 0xff) | ((cur & 0xff) << 8);
-            if (change4<NPL, D0, D1>(R, U, net, xs(c), c, lane, j, v)) own |= 1u << c;
+            if (change4<NPL, D0, D1>(R, U, net, xs(c), c, lane, cj[c], (int8_t)(cv[c] & 0xff)))
+                own |= 1u << c;
         }
         if (!has) {
             if (lane == 0)
