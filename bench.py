@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--gain-train-steps", type=int, default=1000,
                     help="Adam steps of the --screen-gain training")
     ap.add_argument("--batch-candidate", type=int, default=None,
-                    help="pin the batched launch to one of the autotuner's candidates (0-7, "
+                    help="pin the batched launch to one of the autotuner's candidates (0-9, "
                          "see rn_batch_config) instead of timing them")
     ap.add_argument("--hidden-mode", type=int, default=None, choices=(0, 1),
                     help="with --screened: how the layer-2 input rows are formed (1: through "

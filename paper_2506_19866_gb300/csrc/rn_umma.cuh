@@ -397,10 +397,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 // eight more warps (6-13) producing each A stage from the candidates' W1 rows
 // and A1 (HiddenArgs): thread p of the producers owns row p / 2 of the tile and
 // its 32-column half p % 2 of the K block.  Its two W1 row segments (new and
-// old value, 64 bytes each) come through a ring of HDEPTH staging slots filled
-// by cp.async HDEPTH K blocks ahead, and its A1 segment is loaded into
-// registers one K block ahead, so that the gathers' L2 latency overlaps the
-// arithmetic and the MMAs.  Each producer thread writes its BF16 values into
+// old value, 64 bytes each) and the A1 rows of the tile's chains come through
+// a ring of HDEPTH staging slots filled by cp.async HDEPTH K blocks ahead, so
+// that the gathers' L2 latency overlaps the arithmetic and the MMAs.  Each producer thread writes its BF16 values into
 // the stage in the 128-byte-swizzled K-major layout that TMA would have
 // written and makes them visible to the tensor core's proxy
 // (fence.proxy.async.shared::cta); after a named barrier over the producers
@@ -409,9 +408,12 @@ __global__ void __launch_bounds__(THREADS, 1)
 // same producer waits on the stage's empty barrier (bounded) and passes the
 // result to the others through the named barrier, so that all producers leave
 // together when a wait gives up.  This
-// replaces the HBM round trip of the hidden rows (written by the propose
-// kernel, read back by TMA): for 4096 chains x 32 candidates x 512 columns,
-// 134 MB each way per step.
+// avoids the HBM round trip of the hidden rows (written by the propose
+// kernel, read back by TMA: for 4096 chains x 32 candidates x 512 columns,
+// 134 MB each way per step), but it runs slower on GB300: per K block each SM
+// takes in 32 KB of scattered W1 segments beside the 32 KB B tile, and the A
+// stage is rebuilt for every 256-column output tile, so the library's default
+// is the round trip (rn_mlp_set_hidden_mode).
 constexpr int HSTAGES = 2;                                  // GEMM stages (A produced, B by TMA)
 constexpr uint32_t kSleepNs = 2000;                         // try_wait sleep hint of waiting roles
 constexpr int HDEPTH = 3;                                   // staging slots (K blocks ahead)
