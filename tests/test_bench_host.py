@@ -71,3 +71,21 @@ def test_protocol_table_from_a_result_file(bench, tmp_path):
     rows = bench.protocol_table(str(p)).splitlines()
     assert len(rows) == 3
     assert rows[2] == "| 723 params | 32 | 5000 | 49.3 | 5 | 2.50 | 4.46e+06 | 0.90 / 0.70 / 0.50 |"
+
+
+def test_alu_roofline_both_denominators(bench):
+    # achieved = algorithmic ops per launch / launch time, against the measured
+    # issue rate (the target's basis) and the nominal 128 INT32 lanes, both at
+    # the sampled SM clock
+    r = bench.alu_roofline(4.0e12, 0.5, 152, 2000.0, {"alu": 88.0, "lds": 1.0})
+    assert r["achieved"] == pytest.approx(8.0)
+    assert r["peak"] == pytest.approx(152 * 88.0 * 2.0e9 / 1e12)
+    assert r["frac"] == pytest.approx(8.0 / (152 * 88.0 * 2.0))
+    assert r["peak_nominal"] == pytest.approx(152 * 128 * 2.0e9 / 1e12)
+    assert r["frac_nominal"] == pytest.approx(8.0 / (152 * 128 * 2.0))
+    assert "measured" in r["target_basis"]
+    # no clock sample or no measured rate: no fractions, never a made-up peak
+    r = bench.alu_roofline(4.0e12, 0.5, 152, None, {"alu": 88.0})
+    assert r["peak"] is None and r["frac"] is None and r["frac_nominal"] is None
+    r = bench.alu_roofline(4.0e12, 0.5, 152, 2000.0, {})
+    assert r["peak"] is None and r["frac"] is None and r["frac_nominal"] is not None
