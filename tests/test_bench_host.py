@@ -80,9 +80,9 @@ def test_alu_roofline_both_denominators(bench):
     r = bench.alu_roofline(4.0e12, 0.5, 152, 2000.0, {"alu": 88.0, "lds": 1.0})
     assert r["achieved"] == pytest.approx(8.0)
     assert r["peak"] == pytest.approx(152 * 88.0 * 2.0e9 / 1e12)
-    assert r["frac"] == pytest.approx(8.0 / (152 * 88.0 * 2.0))
+    assert r["frac"] == pytest.approx(8.0 / (152 * 88.0 * 2.0e-3))
     assert r["peak_nominal"] == pytest.approx(152 * 128 * 2.0e9 / 1e12)
-    assert r["frac_nominal"] == pytest.approx(8.0 / (152 * 128 * 2.0))
+    assert r["frac_nominal"] == pytest.approx(8.0 / (152 * 128 * 2.0e-3))
     assert "measured" in r["target_basis"]
     # no clock sample or no measured rate: no fractions, never a made-up peak
     r = bench.alu_roofline(4.0e12, 0.5, 152, None, {"alu": 88.0})
