@@ -155,7 +155,8 @@ def kernel_label(ws):
         return "anneal_block_kernel" if block_path(ws[0]) else "anneal_kernel"
     n_blk = sum(block_path(w) for w in ws)
     return ("anneal_batch_kernel" +
-            (f" + anneal_block_kernel ({n_blk} networks)" if n_blk else "") + ", whole step")
+            (f" + anneal_block_kernel ({n_blk} networks, on side streams beside the batch)"
+             if n_blk else "") + ", whole step")
 
 L2_NOTE = ("working set (network tables + chain state) is L2-resident by design; L2 flushed "
            "with a 512 MiB write between timed steps, outside the step events")
@@ -636,8 +637,9 @@ def measure(args, R, dev, name, S, steps, warmup, rank, world, dist, screened=Fa
             if phases > 1:
                 n_blk = sum(block_path(w) for w in ws)
                 roofline["kernel"] = (f"anneal_phase_kernel x {phases} (one launch per table path)"
-                                      + (f" + anneal_block_kernel ({n_blk} networks)" if n_blk
-                                         else "") + ", whole step")
+                                      + (f" + anneal_block_kernel ({n_blk} networks, on side "
+                                         "streams beside the batch)" if n_blk else "")
+                                      + ", whole step")
         line["device_memory_used_gb"] = dev.memory_used_gb()
         if screened:
             h = screen_width

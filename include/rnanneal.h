@@ -176,7 +176,14 @@ int rn_prepare_schedule(rn_ctx *ctx, const rn_schedule *sched, int64_t total_ste
  * is simulated; otherwise the candidate is simulated over every condition and
  * scored, and accepted iff dE <= 0 or r2 < thr(T_l, dE).  x_best follows
  * strict improvements.  Asynchronous on the context stream except for the
- * small threshold-table upload.  Networks without chains are skipped;
+ * small threshold-table upload.  With several launches in one call (the
+ * batched launch and the networks it does not take, see below), cached tables
+ * (rn_prepare_schedule) and no global_sync, the networks with launches of their
+ * own run on up to four side streams of the context, most work first: they
+ * wait for the work already queued on the context stream, run beside one
+ * another and beside the batched launch once it is tuned, and the call makes
+ * the context stream wait for all of them (events; the host does not block),
+ * so later work on the context stream is ordered after the whole call.  Networks without chains are skipped;
  * RN_ESTATE if no network of the context has chains.  RN_EINVAL for sweeps < 0,
  * iters_per_level < 1, sync_group < 0, or T0 or alpha not positive and finite. */
 int rn_anneal(rn_ctx *ctx, const rn_schedule *sched, int64_t sweeps);

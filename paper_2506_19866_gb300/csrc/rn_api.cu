@@ -1278,6 +1278,102 @@ int rn_init_chains(rn_ctx *ctx, int32_t net, int32_t n_chains, uint64_t seed, co
     return RN_OK;
 }
 
+namespace {
+
+// Work of one network's chains for one sweep (the order of the side launches).
+int64_t network_work(const Network &n)
+{
+    return (int64_t)n.n_chains * n.C * std::max(1, n.T - 1) * (n.N + n.E);
+}
+
+bool cache_covers(const SchedCache &cc, const rn_schedule &s, int64_t l0, int64_t l1, int64_t cap)
+{
+    return cc.valid && cc.T0 == s.T0 && cc.alpha == s.alpha && cc.iters == s.iters_per_level &&
+           l0 >= cc.l0 && l1 <= cc.l1 && cc.cap >= cap;
+}
+
+// One network outside the batch advances by `sweeps` steps: one launch per
+// segment on `st`, with the work-item counter `queue` and the n_chains chunk
+// counters `done` of its own.  A segment ends at a level end when levels end
+// with a sync, and where uncached threshold tables would exceed their budget
+// (uncached tables are only built for launches on the context's stream).
+int anneal_separate(rn_ctx *ctx, Network &n, const rn_schedule &s, int64_t sweeps,
+                    unsigned int *queue, int32_t *done, cudaStream_t st)
+{
+    const int64_t iters = s.iters_per_level;
+    // at most this many threshold entries per launch segment
+    const size_t budget = (size_t)1 << 24;
+    const DevNet dn = n.dev();
+    const DevChains ch = n.chains();
+    int64_t g = n.step;
+    const int64_t g_end = n.step + sweeps;
+    while (g < g_end) {
+        int64_t seg_end = g_end;
+        if (s.global_sync) seg_end = std::min(seg_end, (g / iters + 1) * iters);
+        int64_t l0 = g / iters, l1 = (seg_end - 1) / iters;
+        DevSched sc{};
+        const SchedCache &cc = ctx->cache;
+        if (cache_covers(cc, s, l0, l1, n.max_score)) {
+            sc.level0 = cc.l0;
+            sc.thr_off = cc.off.p;
+            sc.thr_len = cc.len.p;
+            sc.thr = cc.thr.p;
+        } else {
+            if (st != ctx->stream) return fail(ctx, RN_ESTATE, "uncached tables on a side stream");
+            std::vector<uint32_t> thr;
+            std::vector<int32_t> off, len;
+            int rc = build_thresholds(ctx, s, l0, l1, n.max_score, thr, off, len);
+            if (rc) return rc;
+            while (thr.size() > budget && l1 > l0) {
+                l1 = l0 + (l1 - l0) / 2;
+                seg_end = std::min(seg_end, (l1 + 1) * iters);
+                if ((rc = build_thresholds(ctx, s, l0, l1, n.max_score, thr, off, len))) return rc;
+            }
+            if (thr.empty()) thr.push_back(0);
+            // the device tables may still be read by an earlier launch
+            RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            RN_CUDA(ctx, ctx->thr.reserve(thr.size()));
+            RN_CUDA(ctx, ctx->thr_off.reserve(off.size()));
+            RN_CUDA(ctx, ctx->thr_len.reserve(len.size()));
+            RN_CUDA(ctx, cudaMemcpy(ctx->thr.p, thr.data(), thr.size() * sizeof(uint32_t),
+                                    cudaMemcpyHostToDevice));
+            RN_CUDA(ctx, cudaMemcpy(ctx->thr_off.p, off.data(), off.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice));
+            RN_CUDA(ctx, cudaMemcpy(ctx->thr_len.p, len.data(), len.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice));
+            sc.level0 = l0;
+            sc.thr_off = ctx->thr_off.p;
+            sc.thr_len = ctx->thr_len.p;
+            sc.thr = ctx->thr.p;
+        }
+        sc.g0 = g;
+        sc.g1 = seg_end;
+        sc.iters = iters;
+        sc.reset_to_best = s.reset_to_best;
+        sc.early_reject = s.early_reject;
+        sc.queue = queue;
+        sc.done = done;
+        sc.err = ctx->dev_err.p;
+        cudaError_t e = n.lanes != 32 ? launch_anneal_block(dn, ch, sc, ctx->sm_count, st)
+                                      : launch_anneal(dn, n.d0, n.d1, ch, sc, ctx->sm_count, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "anneal kernel");
+        ctx->launches += 1;
+        if (s.global_sync && seg_end % iters == 0) {
+            // one winner per group of sync_group chains (one group: 0)
+            const int32_t G = s.sync_group > 0 ? s.sync_group : ch.n;
+            RN_CUDA(ctx, ctx->winner.reserve((size_t)((ch.n + G - 1) / G)));
+            e = launch_level_sync(ch, ctx->winner.p, s.sync_group, st);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "level sync kernels");
+            ctx->launches += 2;
+        }
+        g = seg_end;
+    }
+    n.step = g_end;
+    return RN_OK;
+}
+
+}  // namespace
+
 int rn_anneal(rn_ctx *ctx, const rn_schedule *s, int64_t sweeps)
 {
     if (!ctx) return RN_EINVAL;
@@ -1296,92 +1392,85 @@ int rn_anneal(rn_ctx *ctx, const rn_schedule *s, int64_t sweeps)
     // several networks: one persistent launch over all of their chains, and
     // separate launches for the networks it cannot take
     const bool batched = batchable(ctx, *s);
-    if (batched) {
-        if (int rc = anneal_batched(ctx, *s, sweeps)) return rc;
-    } else {
-        ctx->batch.g0_synced = false;
-    }
-    const int64_t iters = s->iters_per_level;
-    // at most this many threshold entries per launch segment
-    const size_t budget = (size_t)1 << 24;
-    for (auto &np : ctx->nets) {
-        Network &n = *np;
-        if (!n.chains_valid || (batched && in_batch(n))) continue;
-        const DevNet dn = n.dev();
-        const DevChains ch = n.chains();
-        int64_t g = n.step;
-        const int64_t g_end = n.step + sweeps;
-        while (g < g_end) {
-            // one segment: stop at the end of a level when levels end with a sync,
-            // and when the threshold tables would exceed the budget
-            int64_t seg_end = g_end;
-            if (s->global_sync) seg_end = std::min(seg_end, (g / iters + 1) * iters);
-            int64_t l0 = g / iters, l1 = (seg_end - 1) / iters;
-            DevSched sc{};
-            const SchedCache &cc = ctx->cache;
-            const bool cached = cc.valid && cc.T0 == s->T0 && cc.alpha == s->alpha &&
-                                cc.iters == iters && l0 >= cc.l0 && l1 <= cc.l1 &&
-                                cc.cap >= n.max_score;
-            if (cached) {
-                sc.level0 = cc.l0;
-                sc.thr_off = cc.off.p;
-                sc.thr_len = cc.len.p;
-                sc.thr = cc.thr.p;
-            } else {
-                std::vector<uint32_t> thr;
-                std::vector<int32_t> off, len;
-                int rc = build_thresholds(ctx, *s, l0, l1, n.max_score, thr, off, len);
-                if (rc) return rc;
-                while (thr.size() > budget && l1 > l0) {
-                    l1 = l0 + (l1 - l0) / 2;
-                    seg_end = std::min(seg_end, (l1 + 1) * iters);
-                    if ((rc = build_thresholds(ctx, *s, l0, l1, n.max_score, thr, off, len)))
-                        return rc;
-                }
-                if (thr.empty()) thr.push_back(0);
-                // the device tables may still be read by an earlier launch
-                RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-                RN_CUDA(ctx, ctx->thr.reserve(thr.size()));
-                RN_CUDA(ctx, ctx->thr_off.reserve(off.size()));
-                RN_CUDA(ctx, ctx->thr_len.reserve(len.size()));
-                RN_CUDA(ctx, cudaMemcpy(ctx->thr.p, thr.data(), thr.size() * sizeof(uint32_t),
-                                        cudaMemcpyHostToDevice));
-                RN_CUDA(ctx, cudaMemcpy(ctx->thr_off.p, off.data(), off.size() * sizeof(int32_t),
-                                        cudaMemcpyHostToDevice));
-                RN_CUDA(ctx, cudaMemcpy(ctx->thr_len.p, len.data(), len.size() * sizeof(int32_t),
-                                        cudaMemcpyHostToDevice));
-                sc.level0 = l0;
-                sc.thr_off = ctx->thr_off.p;
-                sc.thr_len = ctx->thr_len.p;
-                sc.thr = ctx->thr.p;
-            }
-            sc.g0 = g;
-            sc.g1 = seg_end;
-            sc.iters = iters;
-            sc.reset_to_best = s->reset_to_best;
-            sc.early_reject = s->early_reject;
-            RN_CUDA(ctx, ctx->done.reserve((size_t)ch.n));
-            sc.queue = ctx->queue.p;
-            sc.done = ctx->done.p;
-            sc.err = ctx->dev_err.p;
-            cudaError_t e = n.lanes != 32
-                                ? launch_anneal_block(dn, ch, sc, ctx->sm_count, ctx->stream)
-                                : launch_anneal(dn, n.d0, n.d1, ch, sc, ctx->sm_count, ctx->stream);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "anneal kernel");
-            ctx->launches += 1;
-            if (s->global_sync && seg_end % iters == 0) {
-                // one winner per group of sync_group chains (one group: 0)
-                const int32_t G = s->sync_group > 0 ? s->sync_group : ch.n;
-                RN_CUDA(ctx, ctx->winner.reserve((size_t)((ch.n + G - 1) / G)));
-                e = launch_level_sync(ch, ctx->winner.p, s->sync_group, ctx->stream);
-                if (e != cudaSuccess) return cuda_fail(ctx, e, "level sync kernels");
-                ctx->launches += 2;
-            }
-            g = seg_end;
+    if (!batched) ctx->batch.g0_synced = false;
+    std::vector<Network *> sep;
+    std::vector<int64_t> done_off;
+    int64_t side_chains = 0;
+    for (auto &np : ctx->nets)
+        if (np->chains_valid && !(batched && in_batch(*np))) {
+            sep.push_back(np.get());
+            done_off.push_back(side_chains);
+            side_chains += np->chains().n;
         }
-        n.step = g_end;
+    SideLaunch &S = ctx->side;
+    if (S.queue.n < sep.size() || S.done.n < (size_t)side_chains) {
+        // launches of earlier calls may still use the counters
+        RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        RN_CUDA(ctx, S.queue.reserve(sep.size()));
+        RN_CUDA(ctx, S.done.reserve((size_t)side_chains));
     }
-    return RN_OK;
+    // Side streams when at least two launches can overlap and every separate
+    // network reads prepared tables (one launch each, nothing synchronises).
+    const int64_t iters = s->iters_per_level;
+    bool concurrent = !s->global_sync && sep.size() + (batched ? 1u : 0u) >= 2;
+    for (Network *n : sep)
+        concurrent = concurrent && cache_covers(ctx->cache, *s, n->step / iters,
+                                                (n->step + sweeps - 1) / iters, n->max_score);
+    const BatchState &B = ctx->batch;
+    const bool batch_steady = B.valid && B.gen == ctx->gen && B.tuned && B.g0_synced;
+    // the autotuner times its trials with nothing beside them: an untuned
+    // batch goes first, and the side streams wait for it
+    const bool batch_first = batched && !(concurrent && batch_steady);
+    if (batch_first)
+        if (int rc = anneal_batched(ctx, *s, sweeps)) return rc;
+    if (!concurrent) {
+        for (size_t i = 0; i < sep.size(); ++i)
+            if (int rc = anneal_separate(ctx, *sep[i], *s, sweeps, S.queue.p + i,
+                                         S.done.p + done_off[i], ctx->stream))
+                return rc;
+        return RN_OK;
+    }
+    RN_CUDA(ctx, S.create());
+    RN_CUDA(ctx, cudaEventRecord(S.fork, ctx->stream));
+    // most work first, each onto the side stream with the least work so far:
+    // the persistent grids that start later fill the earlier ones' tails
+    std::vector<size_t> order(sep.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        return network_work(*sep[a]) > network_work(*sep[b]);
+    });
+    int64_t load[kSideStreams] = {};
+    bool used[kSideStreams] = {};
+    int rc = RN_OK;
+    for (size_t i : order) {
+        int k = 0;
+        for (int j = 1; j < kSideStreams; ++j)
+            if (load[j] < load[k]) k = j;
+        if (!used[k]) {
+            const cudaError_t e = cudaStreamWaitEvent(S.streams[k], S.fork, 0);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(ctx, e, "cudaStreamWaitEvent (side stream)");
+                break;
+            }
+            used[k] = true;
+        }
+        if ((rc = anneal_separate(ctx, *sep[i], *s, sweeps, S.queue.p + i, S.done.p + done_off[i],
+                                  S.streams[k])))
+            break;
+        load[k] += network_work(*sep[i]);
+    }
+    if (!rc && batched && !batch_first) rc = anneal_batched(ctx, *s, sweeps);
+    // every side stream joins the context's stream, after a failure too
+    for (int k = 0; k < kSideStreams; ++k) {
+        if (!used[k]) continue;
+        cudaError_t e = cudaEventRecord(S.join[k], S.streams[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, S.join[k], 0);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(S.streams[k]);
+            if (!rc) rc = cuda_fail(ctx, e, "joining the side streams");
+        }
+    }
+    return rc;
 }
 
 int rn_prepare_schedule(rn_ctx *ctx, const rn_schedule *s, int64_t total_steps)

@@ -235,6 +235,55 @@ struct Mlp {
     size_t off_b3() const { return off_w3() + H2; }
 };
 
+// Launches of the networks outside the batched launch.  Each network gets a
+// work-item counter and a region of per-chain chunk counters of its own, so its
+// launch may run beside the others: on side streams that fork from the
+// context's stream and join back into it within one rn_anneal call, so that
+// the launches of one network fill the tails of the others' persistent grids.
+constexpr int kSideStreams = 4;
+struct SideLaunch {
+    DevBuf<unsigned int> queue;   // one counter per separate network
+    DevBuf<int32_t> done;         // one region of n_chains counters per network
+    cudaStream_t streams[kSideStreams] = {};
+    cudaEvent_t join[kSideStreams] = {};
+    cudaEvent_t fork = nullptr;
+    bool ready = false;
+    SideLaunch() = default;
+    SideLaunch(const SideLaunch &) = delete;
+    SideLaunch &operator=(const SideLaunch &) = delete;
+    cudaError_t create()
+    {
+        if (ready) return cudaSuccess;
+        cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        for (int k = 0; e == cudaSuccess && k < kSideStreams; ++k) {
+            e = cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            destroy();
+            return e;
+        }
+        ready = true;
+        return cudaSuccess;
+    }
+    void destroy()
+    {
+        for (int k = 0; k < kSideStreams; ++k) {
+            if (streams[k]) {
+                cudaStreamSynchronize(streams[k]);
+                cudaStreamDestroy(streams[k]);
+            }
+            if (join[k]) cudaEventDestroy(join[k]);
+            streams[k] = nullptr;
+            join[k] = nullptr;
+        }
+        if (fork) cudaEventDestroy(fork);
+        fork = nullptr;
+        ready = false;
+    }
+    ~SideLaunch() { destroy(); }
+};
+
 }  // namespace rn
 
 struct rn_ctx {
@@ -253,8 +302,9 @@ struct rn_ctx {
     rn::DevBuf<int32_t> thr_off, thr_len;
     rn::DevBuf<int32_t> status;
     rn::DevBuf<int32_t> winner;
-    rn::DevBuf<unsigned int> queue;   // work-item counter of the anneal kernel
-    rn::DevBuf<int32_t> done;         // chunks finished per chain in the current launch
+    rn::DevBuf<unsigned int> queue;   // work-item counters of the batched launch
+    rn::DevBuf<int32_t> done;         // chunks finished per chain in the batched launch
+    rn::SideLaunch side;              // the networks launched on their own
     rn::DevBuf<int32_t> dev_err;      // set by a kernel whose wait gave up
     rn::DevBuf<int8_t> xbuf;
     rn::DevBuf<int32_t> sbuf;

@@ -259,12 +259,32 @@ __device__ __forceinline__ uint32_t target4(uint32_t a)
     return ((a >> 7) & kB1) + (((a - kB1) >> 7) & kB1);
 }
 
+// One group of four table rows (words w, state codes read through their
+// address halves) added into acc; the next group's words are loaded into wn
+// first when there is one (rows d + 4 .. d + 7 of D4).
+template <int STRIDE>
+__device__ __forceinline__ void gather_group(const uint32_t (&w)[4], uint32_t (&wn)[4],
+                                             const uint32_t *lw, int d, int D4,
+                                             const uint8_t *sm, uint32_t &acc)
+{
+    uint32_t c[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
+    if (d + 4 < D4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) wn[i] = lw[(d + 4 + i) * STRIDE];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
+}
+
 // Biased image bytes of one slot from its D4 = groups4(D) shared-memory table
 // rows at lw (row stride STRIDE words; word = code address | prmt selectors):
 // kH - 4 D4 per byte plus, per row, the source's state code picked into the
 // byte of each condition.  With PIPE the next group's four words are loaded
 // before the current group's codes are used, so that two groups are in flight
-// (measured faster with 8 nodes per lane, slower with 6).
+// (measured faster with 8 nodes per lane, slower with 6); the loop alternates
+// between two word buffers, so nothing is copied from one to the other.
 template <int STRIDE, bool PIPE = true>
 __device__ __forceinline__ uint32_t gather_rows(const uint32_t *lw, int D4, const uint8_t *sm)
 {
@@ -283,22 +303,15 @@ __device__ __forceinline__ uint32_t gather_rows(const uint32_t *lw, int D4, cons
         return acc;
     }
     if (D4 == 0) return acc;
-    uint32_t w[4];
+    // w1 is read only after the group before has loaded it
+    uint32_t w0[4], w1[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) w[i] = lw[i * STRIDE];
-    for (int d = 0; d < D4; d += 4) {
-        uint32_t c[4], wn[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            c[i] = *reinterpret_cast<const uint16_t *>(sm + (w[i] & 0xffffu));
-        if (d + 4 < D4) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) wn[i] = lw[(d + 4 + i) * STRIDE];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc += prmt(w[i], 0x04040404u, c[i]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) w[i] = wn[i];
+    for (int i = 0; i < 4; ++i) w0[i] = lw[i * STRIDE];
+    for (int d = 0;;) {
+        gather_group<STRIDE>(w0, w1, lw, d, D4, sm, acc);
+        if ((d += 4) >= D4) break;
+        gather_group<STRIDE>(w1, w0, lw, d, D4, sm, acc);
+        if ((d += 4) >= D4) break;
     }
     return acc;
 }
@@ -314,36 +327,20 @@ __device__ __forceinline__ void gather_rows_pair(const uint32_t *la, const uint3
     acc_a = kImage0 - 0x04040404u * (uint32_t)D4;
     acc_b = acc_a;
     if (D4 == 0) return;
-    uint32_t wa[4], wb[4];
+    // a1 and b1 are read only after the group before has loaded them
+    uint32_t a0[4], b0[4], a1[4], b1[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        wa[i] = la[i * STRIDE];
-        wb[i] = lb[i * STRIDE];
+        a0[i] = la[i * STRIDE];
+        b0[i] = lb[i * STRIDE];
     }
-    for (int d = 0; d < D4; d += 4) {
-        uint32_t ca[4], cb[4], na[4] = {0u, 0u, 0u, 0u}, nb[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            ca[i] = *reinterpret_cast<const uint16_t *>(sm + (wa[i] & 0xffffu));
-            cb[i] = *reinterpret_cast<const uint16_t *>(sm + (wb[i] & 0xffffu));
-        }
-        if (d + 4 < D4) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                na[i] = la[(d + 4 + i) * STRIDE];
-                nb[i] = lb[(d + 4 + i) * STRIDE];
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            acc_a += prmt(wa[i], 0x04040404u, ca[i]);
-            acc_b += prmt(wb[i], 0x04040404u, cb[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            wa[i] = na[i];
-            wb[i] = nb[i];
-        }
+    for (int d = 0;;) {
+        gather_group<STRIDE>(a0, a1, la, d, D4, sm, acc_a);
+        gather_group<STRIDE>(b0, b1, lb, d, D4, sm, acc_b);
+        if ((d += 4) >= D4) break;
+        gather_group<STRIDE>(a1, a0, la, d, D4, sm, acc_a);
+        gather_group<STRIDE>(b1, b0, lb, d, D4, sm, acc_b);
+        if ((d += 4) >= D4) break;
     }
 }
 

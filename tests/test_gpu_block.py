@@ -2,7 +2,8 @@
 CPU oracle through the C ABI: scores and trajectories of evaluated vectors,
 and whole annealing chains bit for bit, up to the 2000-node, 16-condition,
 33-time-point scale-up network; a batch that mixes a block-path network with
-warp-path networks equals separate runs."""
+warp-path networks equals separate runs, also with the separate launches on
+side streams."""
 import numpy as np
 import pytest
 
@@ -175,6 +176,60 @@ def test_batch_with_block_network_equals_separate_runs(built):
             R.rn_init_chains(c1, q.id, min(w.n_chains, 120), w.chain_seed)
             R.rn_anneal(c1, sched, 24)
             alone = R.rn_get_chain_state(c1, q.id, min(w.n_chains, 120))
+        finally:
+            R.rn_destroy(c1)
+        for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"):
+            np.testing.assert_array_equal(st[k], alone[k], err_msg=f"{w.name} {k}")
+
+
+@pytest.mark.parametrize("with_batch", [True, False])
+def test_side_stream_launches_equal_separate_runs(built, with_batch):
+    # With prepared threshold tables and no global sync, the networks outside
+    # the batched launch run on side streams, beside one another and, once the
+    # batch is tuned, beside the batched launch.  Three calls: the first tunes
+    # the batch (the batch goes first), the next two run in the steady order
+    # (side launches first).  The separate networks cover the block path by
+    # size and by in-degree, one condition with a warp per chain, and one
+    # condition with four chains per warp (24 or more chains per SM, a
+    # partial last quad).  Every chain of every network equals that network
+    # annealed alone in a context of its own.
+    nets, counts = [], []
+    if with_batch:
+        b = synth.make_batch(n_nets=3, total_chains=300, seed=31, n_min=20, n_max=200)
+        nets += b
+        counts += [w.n_chains for w in b]
+    for w, n in ((synth.random_network(64, 700, lam=4.0, cap=12, n_cond=3, n_times=6,
+                                       obs_frac=0.3), 150),
+                 (synth.random_network(65, 300, lam=20.0, cap=24, n_cond=2, n_times=5,
+                                       obs_frac=0.3), 100),
+                 (synth.random_network(66, 40, lam=3.0, cap=8, n_cond=1, n_times=8,
+                                       obs_frac=0.4), 200),
+                 (synth.random_network(67, 30, lam=3.0, cap=8, n_cond=1, n_times=8,
+                                       obs_frac=0.4), 24 * 152 + 5)):
+        nets.append(w)
+        counts.append(n)
+    assert int(np.bincount(nets[-3].dst, minlength=nets[-3].N).max()) > 16
+    sched = R.schedule(4.0, 0.97)
+    S, calls = 4, 3
+    ctx = R.rn_create(0)
+    try:
+        probs = [Problem(w, ctx) for w in nets]
+        for p, w, n in zip(probs, nets, counts):
+            R.rn_init_chains(ctx, p.id, n, w.chain_seed)
+        R.rn_prepare_schedule(ctx, sched, S * calls)
+        for _ in range(calls):
+            R.rn_anneal(ctx, sched, S)
+        assert R.rn_batch_config(ctx)["networks"] == (3 if with_batch else 0)
+        got = [R.rn_get_chain_state(ctx, p.id, n) for p, n in zip(probs, counts)]
+    finally:
+        R.rn_destroy(ctx)
+    for w, n, st in zip(nets, counts, got):
+        c1 = R.rn_create(0)
+        try:
+            q = Problem(w, c1)
+            R.rn_init_chains(c1, q.id, n, w.chain_seed)
+            R.rn_anneal(c1, sched, S * calls)
+            alone = R.rn_get_chain_state(c1, q.id, n)
         finally:
             R.rn_destroy(c1)
         for k in ("x_cur", "x_best", "d_cur", "d_best", "counters"):
