@@ -198,8 +198,33 @@ void build_layout(Network &n)
     // The hybrid and block-register paths gather two slots per loop (twice the
     // independent loads in flight): slots 2j and 2j + 1 get the same number of
     // table rows, the extra ones neutral padding.
-    if ((L == 32 && smemreg_layout(npl)) || (L != 32 && npl <= 8))
+    const bool paired = (L == 32 && smemreg_layout(npl)) || (L != 32 && npl <= 8);
+    if (paired)
         for (int k = 0; k + 1 < npl; k += 2) n.D[k] = n.D[k + 1] = std::max(n.D[k], n.D[k + 1]);
+    // The block path's loop over a slot's rows needs a bound that is uniform
+    // over a warp, not over the block: each warp's edges of a slot are placed
+    // in the first rows, as many as the largest in-degree among its own lanes
+    // (paired slots again equal), and the warp gathers only those.  Nodes are
+    // ranked by in-degree, so later warps of a slot stop earlier.
+    const int W = L / 32;
+    std::vector<int> dw;
+    n.warp_d4.clear();
+    if (L != 32) {
+        dw.assign((size_t)npl * W, 0);
+        for (int32_t r = 0; r < N; ++r) {
+            const int32_t i = order[(size_t)r];
+            int &d = dw[(size_t)(r / L) * W + (r % L) / 32];
+            d = std::max(d, n.in_ptr[(size_t)i + 1] - n.in_ptr[(size_t)i]);
+        }
+        if (paired)
+            for (int k = 0; k + 1 < npl; k += 2)
+                for (int wg = 0; wg < W; ++wg) {
+                    int &a = dw[(size_t)k * W + wg], &b = dw[(size_t)(k + 1) * W + wg];
+                    a = b = std::max(a, b);
+                }
+        n.warp_d4.resize(dw.size());
+        for (size_t k = 0; k < dw.size(); ++k) n.warp_d4[k] = (uint8_t)((dw[k] + 3) & ~3);
+    }
     n.dtab = 1;
     for (int k = 0; k < npl; ++k) n.dtab = std::max(n.dtab, n.D[k]);
     // in-degree capacity: 16 in registers (warp paths), 31 on the block path.
@@ -232,7 +257,8 @@ void build_layout(Network &n)
                 rem[(size_t)lane].push_back({n.node_q[(size_t)n.src[(size_t)e]] >> 1, e});
             }
         }
-        for (int d = 0; d < n.D[slot]; ++d) {
+        const int rows = L == 32 ? n.D[slot] : dw[(size_t)slot * W + wg];
+        for (int d = 0; d < rows; ++d) {
             int used[32];
             for (int b = 0; b < 32; ++b) used[b] = -1;
             std::vector<int> lanes(32);
@@ -251,7 +277,7 @@ void build_layout(Network &n)
                         break;
                     }
                 }
-                if (pick < 0 && !r.empty() && (int)r.size() >= n.D[slot] - d) pick = 0;
+                if (pick < 0 && !r.empty() && (int)r.size() >= rows - d) pick = 0;
                 if (pick < 0) {
                     padded.push_back(lane);
                     continue;
@@ -1032,6 +1058,7 @@ int rn_load_network(rn_ctx *ctx, int32_t n_nodes, int32_t n_edges, const int32_t
         RN_CUDA(ctx, n->d_edge_pos.upload(n->edge_pos));
         RN_CUDA(ctx, n->d_node_q.upload(n->node_q));
         RN_CUDA(ctx, n->d_q_node.upload(n->q_node));
+        if (!n->warp_d4.empty()) RN_CUDA(ctx, n->d_warp_d4.upload(n->warp_d4));
     }
     *net_id = (int32_t)ctx->nets.size();
     ctx->nets.push_back(std::move(n));

@@ -339,8 +339,7 @@ struct BlockSync {
     }
     template <int, bool>
     __device__ __forceinline__ uint32_t error(const Ahead &a, const uint32_t (&s4)[NPL],
-                                              const uint32_t (&)[NPL], const DevNet &, int, int,
-                                              int, int) const
+                                              const DevNet &, int, int, int, int) const
     {
         uint32_t e = 0;
 #pragma unroll
@@ -489,8 +488,9 @@ struct BlockRegPath {
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
             gather.row0[k] = o;
-            gather.d4[k] = groups4(net.D[k]);
-            o += gather.d4[k];
+            // this warp's rows of the slot (its edges come first)
+            gather.d4[k] = __ldg(net.warp_d4 + k * (kBT / 32) + (t >> 5));
+            o += groups4(net.D[k]);
         }
         const BlockSync<NPL> sync{bc, t & 31, t >> 5};
         return simulate_swar4_core<NPL, true, false, kBT>(u, m1, d2, net, sm, 0u, t, traj,

@@ -69,12 +69,13 @@ struct Network {
         out_edges;
     std::vector<int16_t> q_node;
     std::vector<uint8_t> edge_q2;
+    std::vector<uint8_t> warp_d4;       // block path: [npl][lanes / 32] rows gathered per warp
     bool supported = false;
     // device copies
     DevBuf<int32_t> d_edge_id, d_edge_pos, d_node_q, d_src, d_dst, d_free, d_in_ptr, d_in_edges,
         d_out_ptr, d_out_edges;
     DevBuf<int16_t> d_q_node;
-    DevBuf<uint8_t> d_edge_q2, d_fast, d_frozen;
+    DevBuf<uint8_t> d_edge_q2, d_fast, d_frozen, d_warp_d4;
     DevBuf<int8_t> d_frozen_val;
     // time course: conditions are simulated cg at a time, G groups
     bool has_tc = false;
@@ -110,6 +111,7 @@ struct Network {
         n.async_sel = async_ ? d_async_sel.p : nullptr;
         for (int k = 0; k < kMaxSlots; ++k) n.D[k] = D[k];
         n.edge_id = d_edge_id.p; n.edge_q2 = d_edge_q2.p; n.edge_pos = d_edge_pos.p;
+        n.warp_d4 = warp_d4.empty() ? nullptr : d_warp_d4.p;
         n.node_q = d_node_q.p; n.q_node = d_q_node.p; n.src = d_src.p; n.dst = d_dst.p;
         n.fast = d_fast.p; n.free_list = d_free.p;
         n.in_ptr = d_in_ptr.p; n.in_edges = d_in_edges.p;

@@ -45,6 +45,8 @@ struct DevNet {
     int32_t async;                      // 1: asynchronous scheme, movable_t below
     int32_t D[kMaxSlots];               // padded in-degree of each slot
     const int32_t *edge_id;             // [npl][dtab][32] edge index, or -1 - (code offset) for padding
+    const uint8_t *warp_d4;             // [npl][lanes / 32] rows of each slot a warp gathers
+                                        // (block path; null on the warp paths)
     const uint8_t *edge_q2;             // [E] 2 * internal index of the edge's source
     const int32_t *edge_pos;            // [E] (lane << 16) | (slot << 8) | d
     const int32_t *node_q;              // [N] internal index of node i
@@ -460,6 +462,40 @@ __device__ __forceinline__ uint32_t state_code(uint32_t s4)
     return prmt(v | (v >> 4), 0u, 0x4420u);
 }
 
+// The state codes of two nodes in one word (the first in the low half), as
+// the shared-memory code array holds them: one byte permutation for the pair.
+template <bool SMEM_FMT>
+__device__ __forceinline__ uint32_t state_code_pair(uint32_t s4a, uint32_t s4b)
+{
+    const uint32_t va = SMEM_FMT ? 4u * kB1 - s4a : s4a;
+    const uint32_t vb = SMEM_FMT ? 4u * kB1 - s4b : s4b;
+    return prmt(va | (va >> 4), vb | (vb >> 4), 0x6420u);
+}
+
+// Store the state codes of a thread's NPL nodes (2 bytes each, node k at p + 2 k).
+template <int NPL, bool SMEM_FMT>
+__device__ __forceinline__ void store_state_codes(uint8_t *p, const uint32_t (&s4)[NPL])
+{
+    if constexpr (NPL == 1) {
+        *reinterpret_cast<uint16_t *>(p) = (uint16_t)state_code<SMEM_FMT>(s4[0]);
+    } else {
+        static_assert(NPL % 2 == 0, "codes are stored in pairs");
+        uint32_t w[NPL / 2];
+#pragma unroll
+        for (int j = 0; j < NPL / 2; ++j) w[j] = state_code_pair<SMEM_FMT>(s4[2 * j], s4[2 * j + 1]);
+        if constexpr (NPL == 2) {
+            *reinterpret_cast<uint32_t *>(p) = w[0];
+        } else if constexpr (NPL == 4) {
+            *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+        } else if constexpr (NPL == 8) {
+            *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < NPL / 2; ++j) reinterpret_cast<uint32_t *>(p)[j] = w[j];
+        }
+    }
+}
+
 // Error of a node's four conditions at one time point (Section 2.3) from its
 // compact entry word (byte c = R_c | W_c << 2, W = 0 where unobserved), added
 // to acc in quarter units: 4 sum_c W_c |s_c - R_c|.  For s, R in 0..2, x = s ^ R
@@ -500,8 +536,8 @@ struct WarpSync {
     }
     template <int NPL, bool>
     __device__ __forceinline__ uint32_t error(const Ahead &, const uint32_t (&s4)[NPL],
-                                              const uint32_t (&)[NPL], const DevNet &net, int g,
-                                              int tau, int lane, int) const
+                                              const DevNet &net, int g, int tau, int lane,
+                                              int) const
     {
         uint32_t w[NPL];
         load_obs<NPL>(w, net.obs + (((size_t)g * net.T + tau) * 32 + lane) * NPL);
@@ -539,7 +575,7 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
     }
     uint32_t score = 0;
     for (int g = 0; g < net.G; ++g) {
-        uint32_t code[NPL], s4[NPL], cu[NPL], cd[NPL], ua01[NPL], ua23[NPL], mov[NPL];
+        uint32_t s4[NPL], cu[NPL], cd[NPL], ua01[NPL], ua23[NPL], mov[NPL];
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
             const size_t q = (size_t)g * LANES * NPL + lane * NPL + k;
@@ -549,9 +585,8 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
             cd[k] = 0;
             ua01[k] = U2[k];
             ua23[k] = U2[k];
-            code[k] = state_code<SMEM_FMT>(s4[k]);
         }
-        store_codes<NPL>(my_codes, code);
+        store_state_codes<NPL, SMEM_FMT>(my_codes, s4);
         const int ncg = min(net.C - 4 * g, 4);
         for (int tau = 0; tau < T; ++tau) {
             // the entry words of this time point, fetched ahead of the update
@@ -597,8 +632,11 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
                 sync.max4(m01, m23, P01, P23);   // the maxima over the chain's nodes
 #pragma unroll
                 for (int k = 0; k < NPL; ++k) {
-                    const uint32_t nz01 = ((pr01[k] ^ P01) + 0x7FFF7FFFu) & 0x80008000u;
-                    const uint32_t nz23 = ((pr23[k] ^ P23) + 0x7FFF7FFFu) & 0x80008000u;
+                    // bit 15 of a half: the node's priority is below the
+                    // maximum (P >= pr in each half and both are below 2^15,
+                    // so P - pr neither borrows across halves nor carries out)
+                    const uint32_t nz01 = (P01 - pr01[k] + 0x7FFF7FFFu) & 0x80008000u;
+                    const uint32_t nz23 = (P23 - pr23[k] + 0x7FFF7FFFu) & 0x80008000u;
                     const uint32_t upd = elm[k] & ~prmt(nz01, nz23, 0xFDB9u);
                     s4[k] = (s4[k] & ~upd) | (sn[k] & upd);
                     cu[k] &= ~upd;
@@ -606,13 +644,12 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
                     const uint32_t u01 = prmt(upd, 0u, 0x9988u), u23 = prmt(upd, 0u, 0xBBAAu);
                     ua01[k] = ((ua01[k] + U2[k]) & ~u01) | (U2[k] & u01);
                     ua23[k] = ((ua23[k] + U2[k]) & ~u23) | (U2[k] & u23);
-                    code[k] = state_code<SMEM_FMT>(s4[k]);
                 }
-                store_codes<NPL>(my_codes, code);
+                store_state_codes<NPL, SMEM_FMT>(my_codes, s4);
             }
             sync.sync();
             // error at this time point
-            score += sync.template error<NPL, SMEM_FMT>(ahead, s4, code, net, g, tau, lane, ncg);
+            score += sync.template error<NPL, SMEM_FMT>(ahead, s4, net, g, tau, lane, ncg);
             if (EARLY && (tau & 3) == 3) {
                 // exact early rejection: the partial score never decreases
                 const uint32_t tot = __reduce_add_sync(kFull, score) >> 2;
