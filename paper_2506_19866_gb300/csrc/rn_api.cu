@@ -126,6 +126,127 @@ void build_free_list(Network &n)
             n.free_list.push_back(j);
 }
 
+// Table rows of the block path's register variant, which keeps two copies of
+// the state codes (code_word2).  For each slot and warp, row d of the table is
+// read by the warp's 32 threads at once, each gathering the code of one
+// source; a bank serves one 4-byte word per wavefront.  Every entry may read
+// its source from either copy, which puts it in one of two banks.  Row by row,
+// lanes are matched to distinct banks (augmenting paths over every remaining
+// in-edge in both copies), lanes that must place an edge in this row (as many
+// edges left as rows) first; a lane that must place one and found no free bank
+// takes the option that adds the fewest words to a bank, and a lane with
+// nothing to place reads a word the row already reads.  The image sums the
+// same edges in any order, so the placement changes no result.
+void place_rows_two_copies(Network &n, const std::vector<int> &dw, int W)
+{
+    const int L = n.lanes, npl = n.npl;
+    const uint32_t copy2_word = block_code_bytes(npl) / 4u;   // word index of the second copy
+    struct Opt {
+        int bank, word, t;
+        bool c2;
+    };
+    for (int slot = 0; slot < npl; ++slot)
+    for (int wg = 0; wg < W; ++wg) {
+        std::vector<std::vector<std::pair<int, int32_t>>> rem(32);   // (first-copy word, edge)
+        for (int lane = 0; lane < 32; ++lane) {
+            const int i = n.q_node[(size_t)((32 * wg + lane) * npl + slot)];
+            if (i < 0) continue;
+            for (int32_t k = n.in_ptr[(size_t)i]; k < n.in_ptr[(size_t)i + 1]; ++k) {
+                const int32_t e = n.in_edges[(size_t)k];
+                rem[(size_t)lane].push_back({n.node_q[(size_t)n.src[(size_t)e]] >> 1, e});
+            }
+        }
+        const int rows = dw[(size_t)slot * W + wg];
+        for (int d = 0; d < rows; ++d) {
+            std::vector<std::vector<Opt>> opts(32);
+            bool must[32];
+            for (int lane = 0; lane < 32; ++lane) {
+                const auto &r = rem[(size_t)lane];
+                must[lane] = !r.empty() && (int)r.size() >= rows - d;
+                for (int t = 0; t < (int)r.size(); ++t) {
+                    const int w1 = r[(size_t)t].first;
+                    const int w2 = (int)(copy2_word + code_word2((uint32_t)w1));
+                    opts[(size_t)lane].push_back({w1 & 31, w1, t, false});
+                    opts[(size_t)lane].push_back({w2 & 31, w2, t, true});
+                }
+            }
+            int owner[32], choice[32];
+            for (int b = 0; b < 32; ++b) owner[b] = -1;
+            for (int l = 0; l < 32; ++l) choice[l] = -1;
+            bool seen[32];
+            // Kuhn's augmenting path from lane l over banks not yet visited
+            auto augment = [&](auto &&self, int l) -> bool {
+                const auto &o = opts[(size_t)l];
+                for (int k = 0; k < (int)o.size(); ++k) {
+                    const int b = o[(size_t)k].bank;
+                    if (seen[b]) continue;
+                    seen[b] = true;
+                    if (owner[b] < 0 || self(self, owner[b])) {
+                        owner[b] = l;
+                        choice[l] = k;
+                        return true;
+                    }
+                }
+                return false;
+            };
+            std::vector<int> lanes(32);
+            std::iota(lanes.begin(), lanes.end(), 0);
+            std::stable_sort(lanes.begin(), lanes.end(), [&](int a, int b) {
+                if (must[a] != must[b]) return must[a];
+                return rem[(size_t)a].size() > rem[(size_t)b].size();
+            });
+            for (int l : lanes) {
+                if (opts[(size_t)l].empty()) continue;
+                for (int b = 0; b < 32; ++b) seen[b] = false;
+                augment(augment, l);
+            }
+            std::vector<int> words[32];   // distinct words read per bank in this row
+            auto note = [&](const Opt &o) {
+                auto &v = words[o.bank];
+                if (std::find(v.begin(), v.end(), o.word) == v.end()) v.push_back(o.word);
+            };
+            for (int l = 0; l < 32; ++l)
+                if (choice[l] >= 0) note(opts[(size_t)l][(size_t)choice[l]]);
+            for (int l = 0; l < 32; ++l) {
+                if (choice[l] >= 0 || !must[l]) continue;
+                int best = 0, best_cost = 1 << 30;
+                for (int k = 0; k < (int)opts[(size_t)l].size(); ++k) {
+                    const Opt &o = opts[(size_t)l][(size_t)k];
+                    const auto &v = words[o.bank];
+                    const int cost = std::find(v.begin(), v.end(), o.word) != v.end()
+                                         ? 0
+                                         : (int)v.size() + 1;
+                    if (cost < best_cost) {
+                        best_cost = cost;
+                        best = k;
+                    }
+                }
+                choice[l] = best;
+                note(opts[(size_t)l][(size_t)best]);
+            }
+            int pad_word = 0;
+            for (int b = 0; b < 32; ++b)
+                if (!words[b].empty()) {
+                    pad_word = words[b][0];
+                    break;
+                }
+            for (int l = 0; l < 32; ++l) {
+                const size_t at = ((size_t)slot * n.dtab + d) * L + 32 * wg + l;
+                if (choice[l] < 0) {   // padding: -1 - (byte offset of a word the row reads)
+                    n.edge_id[at] = -1 - 4 * pad_word;
+                    continue;
+                }
+                const Opt &o = opts[(size_t)l][(size_t)choice[l]];
+                auto &r = rem[(size_t)l];
+                const int32_t e = r[(size_t)o.t].second;
+                r.erase(r.begin() + o.t);
+                n.edge_id[at] = e | (o.c2 ? kCodeCopy2 : 0);
+                n.edge_pos[(size_t)e] = ((32 * wg + l) << 16) | (slot << 8) | d;
+            }
+        }
+    }
+}
+
 // Node placement: nodes ranked by in-degree (descending, then index); rank r
 // goes to slot r / 32, lane r % 32, internal index q = lane * npl + slot.
 void build_layout(Network &n)
@@ -233,7 +354,7 @@ void build_layout(Network &n)
     // (s // t) w p with s, w <= 2), so 31 in-edges are the most a byte holds.
     if (n.dtab > (L == 32 ? 16 : 31)) return;
     // the block path's shared memory must fit one block (227 KiB on sm_103)
-    if (L != 32 && block_path_smem_bytes(n.D, npl, N) > 232448u) return;
+    if (L != 32 && block_path_smem_bytes(n.D, npl, N) > kBlockSmemMax) return;
     n.edge_id.assign((size_t)npl * n.dtab * L, -1);
     n.edge_q2.assign((size_t)E, 0);
     n.edge_pos.assign((size_t)E, 0);
@@ -245,7 +366,14 @@ void build_layout(Network &n)
     // one 4-byte word per wavefront, so the in-edges of each lane are spread over
     // the columns greedily such that no two lanes of a warp read different words
     // of one bank in a column; a padding entry reads a word already read in its
-    // column.  (The block path does this for each of its 8 warps.)
+    // column.  (The block path does this for each of its 8 warps; its register
+    // variant, which keeps two copies of the codes, matches lanes to banks
+    // instead: place_rows_two_copies.)
+    if (L != 32 && block_path_two_copies(n.D, npl, N)) {
+        place_rows_two_copies(n, dw, W);
+        n.supported = true;
+        return;
+    }
     for (int slot = 0; slot < npl; ++slot)
     for (int wg = 0; wg < L / 32; ++wg) {
         std::vector<std::vector<std::pair<int, int32_t>>> rem(32);   // (word, edge)

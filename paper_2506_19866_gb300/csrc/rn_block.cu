@@ -27,20 +27,16 @@ constexpr int kBW = kBT / 32;   // warps per chain
 
 __device__ __forceinline__ int xcg(const int8_t *x, int j) { return (int)__ldcg(x + j); }
 
-// Shared memory: codes [kBT * npl] u16 at offset 0, then the table rows, the
-// per-node fields (not on the register variant), the constraint counters, a
-// small scratch area and, where it fits, the chain's x (xbytes, 0 for none).
+// Shared memory: codes [kBT * npl] u16 at offset 0 (on the register variant,
+// which keeps node state in registers for 2, 4, 6 or 8 nodes per thread, a
+// second copy of them follows: code_word2), then the table rows, the per-node
+// fields (not on the register variant), the constraint counters, a small
+// scratch area and, where it fits, the chain's x (xbytes, 0 for none).
 struct BlockLayout {
-    uint32_t codes, lut, node, cnt, scratch, x, bytes;
+    uint32_t codes, codes2, lut, node, cnt, scratch, x, bytes;
 };
 
 __host__ __device__ inline uint32_t round256(uint32_t v) { return (v + 255u) & ~255u; }
-
-// Node state in registers for these nodes per thread (at most 2048 nodes).
-__host__ __device__ inline bool block_reg_npl(int npl)
-{
-    return npl == 2 || npl == 4 || npl == 6 || npl == 8;
-}
 
 __host__ __device__ inline BlockLayout block_layout(const int *D, int npl, int N,
                                                     uint32_t xbytes = 0)
@@ -48,11 +44,18 @@ __host__ __device__ inline BlockLayout block_layout(const int *D, int npl, int N
     BlockLayout L;
     uint32_t rows = 0;
     for (int k = 0; k < npl; ++k) rows += (uint32_t)groups4(D[k]);
+    const uint32_t cb = block_code_bytes(npl);
+    const uint32_t node = block_reg_npl(npl) ? 0u : (uint32_t)npl * kF_N * kBT * 4u;
+    const uint32_t cnt = round256(2u * (((uint32_t)N + 15u) & ~15u));
+    // everything but the codes and x
+    const uint32_t rest = rows * kBT * 4u + node + cnt + 256u;
+    const bool two = block_reg_npl(npl) && 2u * cb + rest <= kBlockSmemMax;
     L.codes = 0;
-    L.lut = round256(2u * kBT * (uint32_t)npl);
+    L.codes2 = two ? cb : 0u;
+    L.lut = two ? 2u * cb : cb;
     L.node = L.lut + rows * kBT * 4u;
-    L.cnt = L.node + (block_reg_npl(npl) ? 0u : (uint32_t)npl * kF_N * kBT * 4u);
-    L.scratch = L.cnt + round256(2u * (((uint32_t)N + 15u) & ~15u));
+    L.cnt = L.node + node;
+    L.scratch = L.cnt + cnt;
     L.x = L.scratch + 256u;
     L.bytes = L.x + xbytes;
     return L;
@@ -326,6 +329,7 @@ template <int NPL>
 struct BlockSync {
     Bcast *bc;
     int lane, warp;
+    uint32_t *codes2;   // the second copy of the codes (code_word2), or null
 
     struct Ahead {
         uint32_t w[NPL];
@@ -381,6 +385,33 @@ struct BlockSync {
         __syncthreads();
         return total;
     }
+    // Both copies of the thread's state codes: its NPL / 2 words at p (the
+    // first copy) and each word w = t NPL / 2 + j at code_word2(w) of the
+    // second (for 2, 4 and 8 nodes per thread a warp's stores of one j fall
+    // in 32 distinct banks).
+    template <int, bool SMEM_FMT>
+    __device__ __forceinline__ void store_codes(uint8_t *p, const uint32_t (&s4)[NPL], int t) const
+    {
+        static_assert(NPL % 2 == 0, "codes are stored in pairs");
+        uint32_t w[NPL / 2];
+#pragma unroll
+        for (int j = 0; j < NPL / 2; ++j) w[j] = state_code_pair<SMEM_FMT>(s4[2 * j], s4[2 * j + 1]);
+        if constexpr (NPL == 2) {
+            *reinterpret_cast<uint32_t *>(p) = w[0];
+        } else if constexpr (NPL == 4) {
+            *reinterpret_cast<uint2 *>(p) = make_uint2(w[0], w[1]);
+        } else if constexpr (NPL == 8) {
+            *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < NPL / 2; ++j) reinterpret_cast<uint32_t *>(p)[j] = w[j];
+        }
+        if (codes2) {
+#pragma unroll
+            for (int j = 0; j < NPL / 2; ++j)
+                codes2[code_word2((uint32_t)(t * (NPL / 2) + j))] = w[j];
+        }
+    }
 };
 
 // Register variant for 2, 4, 6 or 8 nodes per thread (513 .. 2048 nodes, and
@@ -397,6 +428,7 @@ struct BlockRegPath {
     Bcast *bc;
     int8_t *xs;   // the chain's x in shared memory (when the launch reserved it)
     static constexpr int npl = NPL;
+    uint32_t codes2;   // byte offset of the second copy of the codes (0: none)
     int32_t u[NPL], m1[NPL], d2[NPL];
     uint32_t undo_addr, undo_val;
     int undo_kind, undo_slot;
@@ -416,11 +448,18 @@ struct BlockRegPath {
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
             for (int d = 0; d < net.D[k]; ++d) {
-                const int e = net.edge_id[(k * net.dtab + d) * kBT + t];
-                lut[(o + d) * kBT + t] =
-                    e >= 0 ? edge_word_s(X(e), X(E + e), X(2 * E + e),
-                                         2u * (uint32_t)net.node_q[net.src[e]])
-                           : 0x04040000u | ((uint32_t)(-1 - e) & 0xffffu);
+                const int v = net.edge_id[(k * net.dtab + d) * kBT + t];
+                uint32_t w = 0x04040000u | ((uint32_t)(-1 - v) & 0xffffu);   // padding
+                if (v >= 0) {
+                    // the source's code in the copy the layout chose for this entry
+                    const int e = v & ~kCodeCopy2;
+                    const uint32_t q = (uint32_t)net.node_q[net.src[e]];
+                    const uint32_t a = (v & kCodeCopy2)
+                                           ? codes2 + 4u * code_word2(q >> 1) + 2u * (q & 1u)
+                                           : 2u * q;
+                    w = edge_word_s(X(e), X(E + e), X(2 * E + e), a);
+                }
+                lut[(o + d) * kBT + t] = w;
             }
             // neutral rows up to a whole group of 4: the code of node 2 t
             for (int d = net.D[k]; d < groups4(net.D[k]); ++d)
@@ -492,7 +531,8 @@ struct BlockRegPath {
             gather.d4[k] = __ldg(net.warp_d4 + k * (kBT / 32) + (t >> 5));
             o += groups4(net.D[k]);
         }
-        const BlockSync<NPL> sync{bc, t & 31, t >> 5};
+        const BlockSync<NPL> sync{bc, t & 31, t >> 5,
+                                  codes2 ? reinterpret_cast<uint32_t *>(sm + codes2) : nullptr};
         return simulate_swar4_core<NPL, true, false, kBT>(u, m1, d2, net, sm, 0u, t, traj,
                                                           INT32_MAX, gather, sync);
     }
@@ -504,6 +544,7 @@ __device__ __forceinline__ BlockRegPath<NPL> make_block_reg_path(const DevNet &n
     const BlockLayout L = block_layout(net.D, NPL, net.N);
     BlockRegPath<NPL> P;
     P.sm = sm;
+    P.codes2 = L.codes2;
     P.lut = reinterpret_cast<uint32_t *>(sm + L.lut);
     P.out_nz = sm + L.cnt;
     P.pos_in = P.out_nz + ((net.N + 15) & ~15);
@@ -856,6 +897,11 @@ cudaError_t block_smem(const DevNet &net, size_t *bytes)
 size_t block_path_smem_bytes(const int *D, int npl, int N)
 {
     return block_layout(D, npl, N).bytes;
+}
+
+bool block_path_two_copies(const int *D, int npl, int N)
+{
+    return block_layout(D, npl, N).codes2 != 0;
 }
 
 namespace {

@@ -100,6 +100,32 @@ struct DevSched {
 
 constexpr int kWaitLimit = 1 << 22;     // polls of a predecessor flag before giving up
 
+// The block path's register variant (2, 4, 6 or 8 nodes per thread) keeps two
+// copies of the chain's 16-bit state codes in shared memory.  Word w of the
+// first copy (codes of internal indices 2w and 2w + 1) is word code_word2(w) of
+// the second: each row of 32 words (one word per bank) rotated by its row
+// index, so that codes that share a bank in the first copy sit in different
+// banks of the second.  The host's layout picks, for every table entry, the
+// copy that keeps the 32 lanes of a warp on distinct banks in that row; an
+// entry of edge_id with kCodeCopy2 set reads the second copy.  (A network
+// whose tables leave no room for the second copy keeps one.)
+constexpr int32_t kCodeCopy2 = 1 << 30;
+__host__ __device__ __forceinline__ bool block_reg_npl(int npl)
+{
+    return npl == 2 || npl == 4 || npl == 6 || npl == 8;
+}
+__host__ __device__ __forceinline__ uint32_t code_word2(uint32_t w)
+{
+    return (w & ~31u) | ((w + (w >> 5)) & 31u);
+}
+// Shared memory one block may use (227 KiB on sm_103).
+constexpr uint32_t kBlockSmemMax = 232448u;
+// Bytes of one copy of the block path's codes (kBlockLanes x npl), rounded to 256.
+__host__ __device__ __forceinline__ uint32_t block_code_bytes(int npl)
+{
+    return (2u * (uint32_t)kBlockLanes * (uint32_t)npl + 255u) & ~255u;
+}
+
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round
 // multiplies counter words 0 and 2 by 0xD2511F53 / 0xCD9E8D57 and crosses the
 // high halves with words 1 and 3 and the key; the key is bumped by the Weyl
@@ -526,6 +552,12 @@ struct WarpSync {
     }
     __device__ __forceinline__ void sync() const { __syncwarp(); }
     __device__ __forceinline__ uint32_t sum(uint32_t v) const { return __reduce_add_sync(kFull, v); }
+    // the state codes of the thread's nodes, where the gather reads them
+    template <int NPL, bool SMEM_FMT>
+    __device__ __forceinline__ void store_codes(uint8_t *p, const uint32_t (&s4)[NPL], int) const
+    {
+        store_state_codes<NPL, SMEM_FMT>(p, s4);
+    }
     // Error of a time point (Section 2.3) from the compact entry words, read
     // where they are used (nothing is fetched ahead).
     struct Ahead {};
@@ -586,7 +618,7 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
             ua01[k] = U2[k];
             ua23[k] = U2[k];
         }
-        store_state_codes<NPL, SMEM_FMT>(my_codes, s4);
+        sync.template store_codes<NPL, SMEM_FMT>(my_codes, s4, lane);
         const int ncg = min(net.C - 4 * g, 4);
         for (int tau = 0; tau < T; ++tau) {
             // the entry words of this time point, fetched ahead of the update
@@ -645,7 +677,7 @@ __device__ __forceinline__ int32_t simulate_swar4_core(const int32_t (&u)[NPL],
                     ua01[k] = ((ua01[k] + U2[k]) & ~u01) | (U2[k] & u01);
                     ua23[k] = ((ua23[k] + U2[k]) & ~u23) | (U2[k] & u23);
                 }
-                store_state_codes<NPL, SMEM_FMT>(my_codes, s4);
+                sync.template store_codes<NPL, SMEM_FMT>(my_codes, s4, lane);
             }
             sync.sync();
             // error at this time point

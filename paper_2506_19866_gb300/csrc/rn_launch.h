@@ -53,6 +53,9 @@ cudaError_t launch_evaluate_smemreg(const DevNet &net, const int8_t *X, int64_t 
 // Block path (rn_block.cu): networks of 513 .. 4096 nodes, a block of
 // kBlockLanes threads per chain.  Shared memory of one block:
 size_t block_path_smem_bytes(const int *D, int npl, int N);
+// Whether the block's shared memory holds the second copy of the state codes
+// (code_word2): the register variant, where it fits.
+bool block_path_two_copies(const int *D, int npl, int N);
 cudaError_t launch_evaluate_block(const DevNet &net, const int8_t *X, int64_t xstride, int32_t n,
                                   int32_t *score, int32_t *score2, uint8_t *traj, int sm_count,
                                   cudaStream_t st);

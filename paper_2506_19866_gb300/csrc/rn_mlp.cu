@@ -271,7 +271,7 @@ template <bool ROWS>
 __global__ void __launch_bounds__(kScreenWarps * 32) screen_propose_kernel(ScreenArgs a,
                                                                            int region)
 {
-    extern __shared__ __align__(16) uint8_t sm[];
+    extern __shared__ __align__(256) uint8_t sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c = blockIdx.x * (blockDim.x >> 5) + warp;
     if (c >= a.ch.n) return;
