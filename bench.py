@@ -98,13 +98,14 @@ def algorithmic_ops_per_eval(w):
 # DRAM bytes per annealing launch (read + write) from an ncu capture of the
 # current kernel on the workload: the chain state read once (and, on the block
 # path, written back once) per launch, independent of sweeps per launch.
-ANNEAL_TRAFFIC = {"n120_c8_t21": 9.258e6, "n2000_c16_t33": 1.45e9}
+ANNEAL_TRAFFIC = {"n120_c8_t21": 9.258e6, "n2000_c16_t33": 1.4506e9}
 
 # Shared-memory wavefronts per proposal step of one chain from the same
-# captures: 110.3e6 over 4096 chains x 20 steps, and 6.74e9 over 16,384
-# chains x 2 steps (null moves included, as in the captured launches).
+# captures (loads and stores): 110.3e6 over 4096 chains x 20 steps, and
+# 5.491e9 over 16,384 chains x 2 steps (null moves included, as in the
+# captured launches).
 ANNEAL_SMEM_WAVEFRONTS = {"n120_c8_t21": 110.3e6 / (4096 * 20),
-                          "n2000_c16_t33": 6.738e9 / (16384 * 2)}
+                          "n2000_c16_t33": 5.491e9 / (16384 * 2)}
 
 
 def hbm_peak_gbs():
