@@ -39,7 +39,8 @@ def test_hbm_per_launch_traffic(bench, tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     r = bench.side_rooflines("n2000_c16_t33", 10, 3, 0.6, 152, 0.0, 1.0)
     assert "smem" not in r                      # no clock sample: no shared-memory figure
-    assert r["hbm"]["achieved"] == pytest.approx(1.45e9 * 3 / 0.6 / 1e9)
+    # three launches of the captured per-launch traffic in 0.6 s
+    assert r["hbm"]["achieved"] == pytest.approx(bench.ANNEAL_TRAFFIC["n2000_c16_t33"] * 3 / 0.6 / 1e9)
     assert r["hbm"]["peak"] == 6800.0 and "fallback" in r["hbm"]["peak_basis"]
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6767.4}))
     r = bench.side_rooflines("n2000_c16_t33", 10, 3, 0.6, 152, 0.0, 1.0)
