@@ -202,6 +202,8 @@ struct Mlp {
     size_t n_theta = 0;
     DevBuf<float> theta, grad, adam_m, adam_v;
     int64_t adam_t = 0;
+    DevBuf<float> adam_c;               // [2 x steps] Adam bias corrections of one training call
+    DevBuf<uint32_t> train_k;           // the step within a training call (advanced on the device)
     // BF16 copies (bit patterns): W1T [H1][Dp], W1b [Dp][H1], W2T [H2][H1], W2b [H1][H2]
     DevBuf<uint16_t> W1T, W1b, W2T, W2b;
     // training set (ring of logged pairs)

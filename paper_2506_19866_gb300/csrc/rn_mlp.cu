@@ -184,12 +184,16 @@ __global__ void colsum_finish_kernel(const float *__restrict__ part, int S, int 
     out[c] = s;
 }
 
-// Adam (Kingma & Ba, 2015) on the FP32 masters; c1 = 1 / (1 - beta1^t),
-// c2 = 1 / (1 - beta2^t).
+// Adam (Kingma & Ba, 2015) on the FP32 masters; the bias corrections of step k
+// of the call (k = *kstep) are cc[2k] = 1 / (1 - beta1^t), cc[2k + 1] =
+// 1 / (1 - beta2^t), computed on the host in double.
 __global__ void adam_kernel(float *__restrict__ theta, const float *__restrict__ g,
                             float *__restrict__ m, float *__restrict__ v, size_t n, float lr,
-                            float beta1, float beta2, float c1, float c2, float eps)
+                            float beta1, float beta2, const float *__restrict__ cc,
+                            const uint32_t *__restrict__ kstep, float eps)
 {
+    const uint32_t k = *kstep;
+    const float c1 = cc[2 * (size_t)k], c2 = cc[2 * (size_t)k + 1];
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -202,18 +206,23 @@ __global__ void adam_kernel(float *__restrict__ theta, const float *__restrict__
 }
 
 // Minibatch rows: slot idx[b] of the training set, drawn uniformly from the
-// `count` held pairs by Philox counter (step, 0, b, 8); tgt[b] its target.
-__global__ void sample_kernel(uint64_t seed, uint32_t step, int32_t B, uint32_t count,
-                              const float *__restrict__ set_y, int32_t *__restrict__ idx,
-                              float *__restrict__ tgt, float mu, float inv_sigma)
+// `count` held pairs by Philox counter (step, 0, b, 8), step = *kstep (the
+// step within the call); tgt[b] its target.
+__global__ void sample_kernel(uint64_t seed, const uint32_t *__restrict__ kstep, int32_t B,
+                              uint32_t count, const float *__restrict__ set_y,
+                              int32_t *__restrict__ idx, float *__restrict__ tgt, float mu,
+                              float inv_sigma)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    const uint4 r = philox(seed, step, 0u, (uint32_t)b, 8u);
+    const uint4 r = philox(seed, *kstep, 0u, (uint32_t)b, 8u);
     const uint32_t k = pick(r.x, count);
     idx[b] = (int32_t)k;
     tgt[b] = (set_y[k] - mu) * inv_sigma;
 }
+
+// The step counter of a training call, advanced once per step.
+__global__ void advance_step_kernel(uint32_t *kstep) { *kstep += 1u; }
 
 // Output layer w3 <- a w3, b3 <- a b3 + c (one block).
 __global__ void affine_head_kernel(float *__restrict__ w3, int H2, float *__restrict__ b3,
@@ -998,23 +1007,67 @@ int rn_mlp_train(rn_ctx *ctx, int32_t mlp, int32_t steps, int32_t batch, float l
                                                        (float)(-mu / sigma));
         if ((rc = check_launch(ctx, "output-layer scaling"))) return rc;
     }
+    // Each step's values that change from step to step (its index, for the
+    // minibatch draw, and Adam's bias corrections) are read on the device, so
+    // that every step is the same sequence of launches: step 0 runs directly
+    // (it also settles every first-use set-up), the sequence of step 1 is
+    // captured in a CUDA graph and replayed for the remaining steps, without a
+    // host launch per kernel.
     const double b1 = 0.9, b2 = 0.999;
-    for (int32_t s = 0; s < steps; ++s) {
+    if (steps > 0) {
+        std::vector<float> cc(2 * (size_t)steps);
+        for (int32_t s = 0; s < steps; ++s) {
+            const double t = (double)(m->adam_t + s + 1);
+            cc[2 * (size_t)s] = (float)(1.0 / (1.0 - std::pow(b1, t)));
+            cc[2 * (size_t)s + 1] = (float)(1.0 / (1.0 - std::pow(b2, t)));
+        }
+        RN_CUDA(ctx, m->adam_c.reserve(cc.size()));
+        RN_CUDA(ctx, m->train_k.reserve(1));
+        RN_CUDA(ctx, cudaMemcpyAsync(m->adam_c.p, cc.data(), sizeof(float) * cc.size(),
+                                     cudaMemcpyHostToDevice, ctx->stream));
+        RN_CUDA(ctx, cudaMemsetAsync(m->train_k.p, 0, sizeof(uint32_t), ctx->stream));
+        // the copy reads cc before the call goes on (pageable source)
+        RN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    auto one_step = [&]() -> int {
         sample_kernel<<<(batch + 255) / 256, 256, 0, ctx->stream>>>(
-            seed, (uint32_t)s, batch, (uint32_t)m->count, m->set_y.p, m->idx.p, m->tgt.p,
+            seed, m->train_k.p, batch, (uint32_t)m->count, m->set_y.p, m->idx.p, m->tgt.p,
             (float)mu, (float)(1.0 / sigma));
-        if ((rc = check_launch(ctx, "sample kernel"))) return rc;
-        if ((rc = run_batch(ctx, *m, m->set_x.p, m->pstride, m->idx.p, batch, batch, m->tgt.p)))
-            return rc;
-        m->adam_t += 1;
-        const double c1 = 1.0 / (1.0 - std::pow(b1, (double)m->adam_t));
-        const double c2 = 1.0 / (1.0 - std::pow(b2, (double)m->adam_t));
+        int r = check_launch(ctx, "sample kernel");
+        if (r) return r;
+        if ((r = run_batch(ctx, *m, m->set_x.p, m->pstride, m->idx.p, batch, batch, m->tgt.p)))
+            return r;
         adam_kernel<<<1024, 256, 0, ctx->stream>>>(m->theta.p, m->grad.p, m->adam_m.p,
                                                    m->adam_v.p, m->n_theta, lr, (float)b1,
-                                                   (float)b2, (float)c1, (float)c2, 1e-8f);
-        if ((rc = check_launch(ctx, "Adam kernel"))) return rc;
-        if ((rc = refresh_copies(ctx, *m))) return rc;
+                                                   (float)b2, m->adam_c.p, m->train_k.p, 1e-8f);
+        if ((r = check_launch(ctx, "Adam kernel"))) return r;
+        if ((r = refresh_copies(ctx, *m))) return r;
+        advance_step_kernel<<<1, 1, 0, ctx->stream>>>(m->train_k.p);
+        return check_launch(ctx, "step counter");
+    };
+    if (steps > 0 && (rc = one_step())) return rc;
+    if (steps > 1) {
+        const int64_t before = ctx->launches;
+        RN_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const int rs = one_step();
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
+        if (rs != RN_OK || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            (void)cudaGetLastError();
+            ctx->launches = before;
+            return rs != RN_OK ? rs : cuda_fail(ctx, ec, "training step (capture)");
+        }
+        const int64_t per_step = ctx->launches - before;
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        for (int32_t s = 1; e == cudaSuccess && s < steps; ++s) e = cudaGraphLaunch(exec, ctx->stream);
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "training step (graph)");
+        ctx->launches = before + per_step * (int64_t)(steps - 1);
     }
+    m->adam_t += steps;
     if (standardise) {
         affine_head_kernel<<<1, 256, 0, ctx->stream>>>(w3, m->H2, b3p, (float)sigma, (float)mu);
         if ((rc = check_launch(ctx, "output-layer scaling"))) return rc;

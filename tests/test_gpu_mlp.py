@@ -141,6 +141,34 @@ def test_training_learns_the_score(ctx):
     assert rmse <= 1.25 * np.std(y_true)
 
 
+def test_training_graph_replay_equals_single_steps(ctx):
+    """A training call runs its first Adam step directly and replays the next
+    ones from a CUDA graph, the step index and the bias corrections read on the
+    device.  With one pair in the training set every minibatch is that pair
+    whatever the draw, so k steps in one call must equal k calls of one step
+    (which never replay a graph) bit for bit; Adam's step count runs on across
+    calls in both."""
+    p = Problem(synth.make("n15_c3_t11"), ctx)
+    X = random_vectors(p.net, 1, 4)
+    screens = []
+    for _ in range(2):
+        mid, D, params = _screen(ctx, p, 256, 256, 17, capacity=4)
+        assert R.rn_mlp_add_samples(ctx, mid, X, np.array([0.3])) == 1
+        screens.append(mid)
+    before = float(R.rn_mlp_forward(ctx, screens[0], X)[0])
+    R.rn_mlp_train(ctx, screens[0], 6, batch=256, lr=1e-3, seed=2)
+    for _ in range(6):
+        R.rn_mlp_train(ctx, screens[1], 1, batch=256, lr=1e-3, seed=2)
+    wa = R.rn_mlp_get_weights(ctx, screens[0], D, 256, 256)
+    wb = R.rn_mlp_get_weights(ctx, screens[1], D, 256, 256)
+    for k in wa:
+        assert np.array_equal(wa[k], wb[k]), k
+    assert not np.array_equal(wa["W2"], params["W2"])   # the steps moved the weights
+    # towards the one target
+    after = float(R.rn_mlp_forward(ctx, screens[0], X)[0])
+    assert abs(after - 0.3) < abs(before - 0.3)
+
+
 def test_screened_eps1_is_plain_annealing(ctx):
     """With eps = 1 every step simulates only candidate 0, the plain proposal:
     chains are bit-identical to rn_anneal's (and so to the oracle's)."""
