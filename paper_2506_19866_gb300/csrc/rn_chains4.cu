@@ -513,9 +513,9 @@ template <int NPL, int D0, int D1>
 cudaError_t launch_t(const DevNet &net, const DevChains &ch, const DevSched &sc, int sm_count,
                      cudaStream_t st)
 {
-    const int wpb = 4;
+    int wpb = 4;
     const uint32_t rb = chain4_region(ch.pstride, net.N);
-    const size_t smem = (size_t)wpb * (kCodeBytesPerWarp + rb);
+    size_t smem = (size_t)wpb * (kCodeBytesPerWarp + rb);
     auto kern = anneal_c4_kernel<NPL, D0, D1>;
     cudaError_t err =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -524,8 +524,17 @@ cudaError_t launch_t(const DevNet &net, const DevChains &ch, const DevSched &sc,
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = sm_count * per_sm;
+    int grid = sm_count * per_sm;
     const int quads = (ch.n + 3) / 4;
+    if (quads > 0 && quads < grid * wpb) {
+        // Fewer quads than resident warps: a block of one warp per quad, which
+        // the hardware spreads evenly over the SMs.  (In the full grid the
+        // quads would go to whichever warps reach the queue first, and one
+        // SM could hold several times another's share.)
+        wpb = 1;
+        grid = quads;
+        smem = kCodeBytesPerWarp + rb;
+    }
     DevSched s = sc;
     plan_chunks(s, quads, (int64_t)grid * wpb);
     err = cudaMemsetAsync(s.queue, 0, sizeof(unsigned int), st);

@@ -516,9 +516,9 @@ template <int NPL, int CG, int D0, int D1>
 cudaError_t launch_anneal_t(const DevNet &net, const DevChains &ch, const DevSched &sc,
                             int sm_count, cudaStream_t st)
 {
-    const int wpb = 4;
+    int wpb = 4;
     const WarpRegion R = warp_region(false, net.D, net.npl, ch.pstride, net.N);
-    const size_t smem = (size_t)wpb * (kCodeBytesPerWarp + R.bytes);
+    size_t smem = (size_t)wpb * (kCodeBytesPerWarp + R.bytes);
     auto kern = anneal_kernel<NPL, CG, D0, D1>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
@@ -527,7 +527,14 @@ cudaError_t launch_anneal_t(const DevNet &net, const DevChains &ch, const DevSch
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = sm_count * per_sm;
+    int grid = sm_count * per_sm;
+    if (ch.n > 0 && ch.n < grid * wpb) {
+        // fewer chains than resident warps: a block of one warp per chain, which
+        // the hardware spreads evenly over the SMs
+        wpb = 1;
+        grid = ch.n;
+        smem = kCodeBytesPerWarp + R.bytes;
+    }
     DevSched s = sc;
     plan_chunks(s, ch.n, (int64_t)grid * wpb);
     err = cudaMemsetAsync(s.queue, 0, sizeof(unsigned int), st);
