@@ -20,6 +20,7 @@
 // bit-identical to the one-chain-per-warp run.  A work item is a chunk of
 // steps of a quad of chains; the last quad may be partly empty.
 #include "rn_kernels.cuh"
+#include "rn_screen.h"
 
 namespace rn {
 namespace {
@@ -544,7 +545,98 @@ cudaError_t launch_t(const DevNet &net, const DevChains &ch, const DevSched &sc,
     return cudaGetLastError();
 }
 
+// Finish of a screened step (after the propose kernel and the layer-2 GEMM),
+// two chains per warp: chain 2w + h's chosen moves s = 0, 1 (at most two) are
+// simulated together in byte lane 2h + s, whose tables are the chain's x_cur
+// with that one move applied (Table 1's Simulate of x with one parameter
+// changed); then for each chain the move of lowest exact score (first on ties)
+// goes to the Metropolis test and commit of screen_accept.  A step without a
+// candidate is a null move.  The scores are the exact ones of the one-chain
+// finish, which simulates the moves one after the other.
+template <int NPL, int D0, int D1>
+__global__ void __launch_bounds__(kScreenWarps * 32)
+    screen_finish_c4_kernel(ScreenArgs a, DevSched sc)
+{
+    extern __shared__ __align__(256) uint8_t sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c0 = 2 * (blockIdx.x * kScreenWarps + warp);
+    if (c0 >= a.ch.n) return;
+    const int nc = min(2, a.ch.n - c0);   // a lone last chain fills both halves
+    const DevNet &net = a.net;
+    uint4 r[2];
+    int chosen[2][kMaxTop];
+    int8_t *x[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = c0 + min(h, nc - 1);
+        r[h] = step_draw(a.ch, a.g, c, 0u);
+        select_candidates(a, c, lane, r[h], chosen[h]);
+        x[h] = a.ch.x_cur + (size_t)c * a.ch.pstride;
+    }
+    if (chosen[0][0] < 0 && chosen[1][0] < 0) {
+        if (lane == 0)
+            for (int h = 0; h < nc; ++h) a.ch.cnt[3 * (size_t)(c0 + h) + 2] += 1;
+        return;
+    }
+    Regs4<NPL, D0, D1> R;
+    Undo4 U;
+    int8_t *const xs[4] = {x[0], x[0], x[1], x[1]};
+    load_regs4<NPL, D0, D1>(R, net, xs, lane);
+#pragma unroll
+    for (int vc = 0; vc < 4; ++vc) {
+        const int move = chosen[vc >> 1][vc & 1];
+        if (move >= 0)
+            change4<NPL, D0, D1>(R, U, net, x[vc >> 1], vc, lane, move >> 8, (int8_t)(move & 255));
+    }
+    __syncwarp();
+    int32_t y[4];
+    simulate4<NPL, D0, D1>(R, net, sm, (uint32_t)warp * kCodeBytesPerWarp, lane, y);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (h >= nc) break;
+        const int c = c0 + h;
+        if (chosen[h][0] < 0) {
+            if (lane == 0) a.ch.cnt[3 * (size_t)c + 2] += 1;
+            continue;
+        }
+        int best = chosen[h][0];
+        int32_t d = y[2 * h];
+        if (chosen[h][1] >= 0 && y[2 * h + 1] < d) {
+            best = chosen[h][1];
+            d = y[2 * h + 1];
+        }
+        screen_accept(a, sc, c, lane, r[h], best, d);
+    }
+}
+
+template <int NPL, int D0, int D1>
+cudaError_t finish_t(const ScreenArgs &a, const DevSched &sc, cudaStream_t st)
+{
+    const int warps = (a.ch.n + 1) / 2;
+    const int blocks = (warps + kScreenWarps - 1) / kScreenWarps;
+    screen_finish_c4_kernel<NPL, D0, D1>
+        <<<blocks, kScreenWarps * 32, kScreenWarps * (size_t)kCodeBytesPerWarp, st>>>(a, sc);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_finish_chains4(const ScreenArgs &a, const DevSched &sc, int d0, int d1,
+                                  cudaStream_t st)
+{
+    const DevNet &net = a.net;
+    if (!chains4_layout(net, d0, d1) || a.top > 2) return cudaErrorNotSupported;
+    if (a.ch.n <= 0) return cudaSuccess;
+    if (net.npl == 1) {
+        if (d0 == 4) return finish_t<1, 4, 1>(a, sc, st);
+        if (d0 == 8) return finish_t<1, 8, 1>(a, sc, st);
+        if (d0 == 12) return finish_t<1, 12, 1>(a, sc, st);
+        return finish_t<1, 16, 1>(a, sc, st);
+    }
+    if (d0 == 4) return finish_t<2, 4, 4>(a, sc, st);
+    if (d1 == 4) return finish_t<2, 8, 4>(a, sc, st);
+    return finish_t<2, 8, 8>(a, sc, st);
+}
 
 bool chains4_layout(const DevNet &net, int d0, int d1)
 {

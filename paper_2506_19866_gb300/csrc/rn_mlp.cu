@@ -417,32 +417,7 @@ __device__ __forceinline__ void screen_finish(const ScreenArgs &a, const DevSche
         __syncwarp();
         if (best < 0 || ds < d) { best = move; d = ds; }
     }
-    const int32_t d_cur = a.ch.d_cur[c], d_best = a.ch.d_best[c];
-    const int32_t dE = d - d_cur;
-    bool accept = dE <= 0;
-    if (!accept) {
-        const int64_t l = a.g / sc.iters - sc.level0;
-        if (dE <= sc.thr_len[l]) accept = r.z < sc.thr[sc.thr_off[l] + dE - 1];
-    }
-    if (!accept) return;
-    const int j = best >> 8;
-    const int v = (int8_t)(best & 255);
-    const int rn = a.row_base[j] + v, ro = a.row_base[j] + x[j];
-    __syncwarp();
-    if (lane == 0) {
-        x[j] = (int8_t)v;
-        a.ch.d_cur[c] = d;
-        cnt[0] += 1;
-        cnt[1] += dE > 0;
-    }
-    __syncwarp();
-    if (d < d_best) {
-        warp_copy16(a.ch.x_best + (size_t)c * a.ch.pstride, x, a.ch.pstride, lane);
-        if (lane == 0) a.ch.d_best[c] = d;
-    }
-    for (int h = lane; h < a.H1; h += 32)
-        a.A1[(size_t)c * a.H1 + h] += __bfloat162float(a.W1b[(size_t)rn * a.H1 + h]) -
-                                      __bfloat162float(a.W1b[(size_t)ro * a.H1 + h]);
+    screen_accept(a, sc, c, lane, r, best, d);
 }
 
 // Register-table path (N <= 128), as evaluate_kernel: in-degree capacity 16.
@@ -1195,8 +1170,14 @@ int rn_anneal_screened(rn_ctx *ctx, int32_t mlp, const rn_schedule *s, int32_t K
         } else if ((rc = gemm(ctx, kBiasReluDot, g))) {
             return rc;
         }
-        const cudaError_t e = n->lanes == 32 ? launch_finish(a, sc, ctx->stream)
-                                             : launch_finish_block(a, sc, ctx->sm_count, ctx->stream);
+        cudaError_t e;
+        if (n->lanes != 32) {
+            e = launch_finish_block(a, sc, ctx->sm_count, ctx->stream);
+        } else {
+            // single-condition networks: the moves of two chains in one warp's byte lanes
+            e = launch_finish_chains4(a, sc, n->d0, n->d1, ctx->stream);
+            if (e == cudaErrorNotSupported) e = launch_finish(a, sc, ctx->stream);
+        }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "screen finish kernel");
         ctx->launches += 1;
     }

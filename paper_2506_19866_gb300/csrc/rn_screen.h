@@ -7,7 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
-#include "rn_device.cuh"
+#include "rn_kernels.cuh"
 
 namespace rn {
 
@@ -76,6 +76,51 @@ __device__ __forceinline__ void select_candidates(const ScreenArgs &a, int c, in
         if (mv == chosen[s]) alive = false;   // the winner and its duplicates
     }
 }
+
+// One warp: the Metropolis test of Table 1 for chain c's chosen move `best`
+// (exact score d) against the host threshold tables (word 2 of the step draw
+// r), and on acceptance the commit: x_cur, delta_cur, the counters, the best
+// vector (strict improvement) and the chain's layer-1 pre-activations A1.
+__device__ __forceinline__ void screen_accept(const ScreenArgs &a, const DevSched &sc, int c,
+                                              int lane, const uint4 &r, int best, int32_t d)
+{
+    int8_t *x = a.ch.x_cur + (size_t)c * a.ch.pstride;
+    int64_t *cnt = a.ch.cnt + 3 * (size_t)c;
+    const int32_t d_cur = a.ch.d_cur[c], d_best = a.ch.d_best[c];
+    const int32_t dE = d - d_cur;
+    bool accept = dE <= 0;
+    if (!accept) {
+        const int64_t l = a.g / sc.iters - sc.level0;
+        if (dE <= sc.thr_len[l]) accept = r.z < sc.thr[sc.thr_off[l] + dE - 1];
+    }
+    if (!accept) return;
+    const int j = best >> 8;
+    const int v = (int8_t)(best & 255);
+    const int rn = a.row_base[j] + v, ro = a.row_base[j] + x[j];
+    __syncwarp();
+    if (lane == 0) {
+        x[j] = (int8_t)v;
+        a.ch.d_cur[c] = d;
+        cnt[0] += 1;
+        cnt[1] += dE > 0;
+    }
+    __syncwarp();
+    if (d < d_best) {
+        warp_copy16(a.ch.x_best + (size_t)c * a.ch.pstride, x, a.ch.pstride, lane);
+        if (lane == 0) a.ch.d_best[c] = d;
+    }
+    for (int h = lane; h < a.H1; h += 32)
+        a.A1[(size_t)c * a.H1 + h] += __bfloat162float(a.W1b[(size_t)rn * a.H1 + h]) -
+                                      __bfloat162float(a.W1b[(size_t)ro * a.H1 + h]);
+}
+
+// Finish of a screened step for single-condition networks whose layout has a
+// four-chains-per-warp kernel (rn_chains4.cu) and top <= 2: two chains per
+// warp, their chosen moves simulated together in the byte lanes.  Returns
+// cudaErrorNotSupported (launching nothing) for any other network; d0, d1 are
+// the network's register-table capacities.
+cudaError_t launch_finish_chains4(const ScreenArgs &a, const DevSched &sc, int d0, int d1,
+                                  cudaStream_t st);
 
 // Finish of a screened step for block-path networks (a block of 256 threads
 // per chain): the chosen moves simulated exactly, Metropolis, commit.

@@ -241,16 +241,19 @@ def _candidates(net, x, seed, chain, g, K):
 
 
 @pytest.mark.parametrize("top", [1, 2])
-def test_screened_step_selection(ctx, top):
+@pytest.mark.parametrize("name,n", [("n15_c3_t11", 96), ("mtb_63n_178e", 97)])
+def test_screened_step_selection(ctx, top, name, n):
     """One greedy screened step (T ~ 0, eps = 0): a moved chain took a move that
     can be among the `top` best predicted (oracle prediction +- the derived
     bound) with exact dE <= 0; a chain that stayed had no candidate that is
-    surely among them with dE <= 0.  Exact scores are the oracle's."""
-    w = synth.make("n15_c3_t11")
+    surely among them with dE <= 0.  Exact scores are the oracle's.  The
+    single-condition network's finish simulates two chains' moves per warp in
+    the byte lanes; 97 chains leave the last warp one chain."""
+    w = synth.make(name)
     p = Problem(w, ctx)
     h1 = h2 = 256
     mid, D, params = _screen(ctx, p, h1, h2, 4)
-    n, K, seed, g = 96, 32, 23, 0
+    K, seed, g = 32, 23, 0
     R.rn_init_chains(ctx, p.id, n, seed)
     st0 = R.rn_get_chain_state(ctx, p.id, n)
     R.rn_anneal_screened(ctx, mid, R.schedule(1e-9, 1.0), 1, K=K, top=top, eps=0.0)
