@@ -268,9 +268,9 @@ void anneal_capacity(int npl, int D0, int Drest, int *d0, int *d1)
 static cudaError_t launch_anneal_smem(const DevNet &net, const DevChains &ch, const DevSched &sc,
                                       int sm_count, cudaStream_t st)
 {
-    const int wpb = 4;
+    int wpb = 4;
     const WarpRegion R = warp_region(true, net.D, net.npl, ch.pstride, net.N);
-    const size_t smem = (size_t)wpb * (kCodeBytesPerWarp + R.bytes);
+    size_t smem = (size_t)wpb * (kCodeBytesPerWarp + R.bytes);
     cudaError_t err = cudaFuncSetAttribute(anneal_smem_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -279,7 +279,14 @@ static cudaError_t launch_anneal_smem(const DevNet &net, const DevChains &ch, co
                                                         smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = sm_count * per_sm;
+    int grid = sm_count * per_sm;
+    if (ch.n > 0 && ch.n < grid * wpb) {
+        // fewer chains than resident warps: a block of one warp per chain, which
+        // the hardware spreads evenly over the SMs
+        wpb = 1;
+        grid = ch.n;
+        smem = kCodeBytesPerWarp + R.bytes;
+    }
     DevSched s = sc;
     plan_chunks(s, ch.n, (int64_t)grid * wpb);
     err = cudaMemsetAsync(s.queue, 0, sizeof(unsigned int), st);

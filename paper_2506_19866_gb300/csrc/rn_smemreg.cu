@@ -67,10 +67,10 @@ template <int NPL>
 cudaError_t launch_anneal_t(const DevNet &net, const DevChains &ch, const DevSched &sc,
                             int sm_count, cudaStream_t st)
 {
-    const int wpb = 4;
+    int wpb = 4;
     const uint32_t lw = smem_path_lut_words(net.D, net.npl);
     const uint32_t rb = round16(smem_reg_warp_bytes(lw, ch.pstride, net.N));
-    const size_t smem = (size_t)wpb * (kCodeBytesPerWarp + rb);
+    size_t smem = (size_t)wpb * (kCodeBytesPerWarp + rb);
     cudaError_t err = cudaFuncSetAttribute(anneal_smemreg_kernel<NPL>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -79,7 +79,14 @@ cudaError_t launch_anneal_t(const DevNet &net, const DevChains &ch, const DevSch
                                                         wpb * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = sm_count * per_sm;
+    int grid = sm_count * per_sm;
+    if (ch.n > 0 && ch.n < grid * wpb) {
+        // fewer chains than resident warps: a block of one warp per chain, which
+        // the hardware spreads evenly over the SMs
+        wpb = 1;
+        grid = ch.n;
+        smem = kCodeBytesPerWarp + rb;
+    }
     DevSched s = sc;
     plan_chunks(s, ch.n, (int64_t)grid * wpb);
     err = cudaMemsetAsync(s.queue, 0, sizeof(unsigned int), st);
