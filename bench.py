@@ -13,6 +13,7 @@ instead, on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -41,6 +42,9 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="n120_c8_t21")
     ap.add_argument("--sweeps-per-step", type=int, default=500)
+    ap.add_argument("--chains", type=int, default=None,
+                    help="run a single-network workload with this many chains instead of its "
+                         "own count (named in config.chains)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -545,6 +549,8 @@ def measure(args, R, dev, name, S, steps, warmup, rank, world, dist, screened=Fa
     every chain initialised (per-rank seeds), `warmup` untimed steps, then
     `steps` timed steps of S sweeps each (a screened step with --screened)."""
     ws = workload_set(name)
+    if getattr(args, "chains", None) and len(ws) == 1 and name == args.workload:
+        ws = [dataclasses.replace(ws[0], n_chains=args.chains)]
     ctx = R.rn_create(dev.index, dev.handle)
     # with --screened on a set of networks ("both patterns"), the first network
     # is annealed by the screened step in a context of its own and the others
