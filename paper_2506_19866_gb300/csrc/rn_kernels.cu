@@ -300,13 +300,14 @@ cudaError_t launch_anneal(const DevNet &net, int d0, int d1, const DevChains &ch
                           const DevSched &sc, int sm_count, cudaStream_t st)
 {
     if (ch.n <= 0 || sc.g1 <= sc.g0) return cudaSuccess;
-    // one condition: four chains per warp in the byte lanes, once there are
-    // enough chains to fill the GPU's warps with quads: a quad's step takes
-    // about 1.8 times a single chain's, so with fewer chains than about twice
-    // the resident warps (12 per SM) one chain per warp finishes a step sooner.
+    // one condition: four chains per warp in the byte lanes once the chains
+    // outnumber the one-chain kernel's resident warps (12 per SM).  Below that
+    // every chain has a warp of its own and one chain per warp finishes a step
+    // sooner (measured on the 102- and 723-parameter networks: one chain per
+    // warp ahead at 1024 chains, four per warp ahead at 2048 and 3072).
     // Exact early rejection stops a single chain's simulation, so it keeps one
     // chain per warp.
-    if (!sc.early_reject && ch.n >= 24 * sm_count && chains4_layout(net, d0, d1))
+    if (!sc.early_reject && ch.n >= 12 * sm_count && chains4_layout(net, d0, d1))
         return launch_anneal_chains4(net, d0, d1, ch, sc, sm_count, st);
     if (smemreg_layout(net.npl)) return launch_anneal_smemreg(net, ch, sc, sm_count, st);
     if (net.npl > kRegSlots) return launch_anneal_smem(net, ch, sc, sm_count, st);

@@ -666,7 +666,7 @@ def test_early_reject_is_exact(ctx, n_nodes, n_cond):
 @pytest.mark.parametrize("n_nodes,sync", [(9, False), (20, False), (45, False), (63, True),
                                           (60, False)])
 def test_single_condition_four_chains_per_warp(ctx, n_nodes, sync):
-    # one condition: with enough chains (at least 24 per SM) four chains share
+    # one condition: with enough chains (at least 12 per SM) four chains share
     # a warp in the byte lanes (1 or 2 nodes per lane); 3651 chains leave the
     # last quad with 3.  Sampled chains of every quad position against the
     # oracle, under the priority and the synchronous scheme; then the same
