@@ -404,7 +404,10 @@ int rn_mlp_log_chains(rn_ctx *ctx, int32_t mlp, int64_t *count);
  * to that scale before -- unless it has never been trained -- and back after,
  * so predictions stay in the targets' units).  *loss (may be NULL): mean
  * squared error of the last minibatch, on the standardised scale when the
- * targets were standardised. */
+ * targets were standardised.  The first step is launched directly; the
+ * launches of the next one are captured once per call in a CUDA graph on the
+ * context's stream and replayed for the remaining steps, so the call must not
+ * be made while that stream is being captured (RN_ECUDA). */
 int rn_mlp_train(rn_ctx *ctx, int32_t mlp, int32_t steps, int32_t batch, float lr, uint64_t seed,
                  float *loss);
 
