@@ -523,7 +523,7 @@ def alu_roofline(ops_per_launch, launch_s, sm_count, sm_mhz, peaks):
     """Achieved algorithmic integer ops/s against two denominators: the
     measured per-SM issue rate of an IADD3/LOP3 mix (peaks.cu) and the nominal
     128 INT32 lanes per SM per clock, both at the median SM clock sampled
-    during the timed steps.  The >= 0.5 target is judged on the measured rate
+    during the timed steps.  The >= 0.5 target applies to the measured rate
     (no integer instruction mix measured on this part issues faster)."""
     achieved = ops_per_launch / launch_s
     f_hz = (sm_mhz or 0.0) * 1e6
