@@ -166,6 +166,16 @@ __device__ __forceinline__ void simulate4(const Regs4<NPL, D0, D1> &R, const Dev
     store_codes<NPL>(my_codes, code);
     uint32_t e01 = 0, e23 = 0;   // per-chain error sums as 16-bit halves
     for (int tau = 0; tau < T; ++tau) {
+        // this time point's error words, loaded before the update step so that
+        // their latency overlaps it (with two nodes per lane; one node per lane
+        // loads them where they are used, which keeps its register allocation
+        // free of spills)
+        uint32_t ew[NPL];
+        if constexpr (NPL == 2) {
+#pragma unroll
+            for (int k = 0; k < NPL; ++k)
+                ew[k] = __ldg(net.obs + ((size_t)tau * 32 + lane) * NPL + k);
+        }
         if (tau > 0) {
             uint32_t acc[NPL];
             acc[0] = image4<D0>(R.lut0[0], R.lut0[1], R.lut0[2], R.lut0[3], net.D[0], base, sm);
@@ -220,8 +230,8 @@ __device__ __forceinline__ void simulate4(const Regs4<NPL, D0, D1> &R, const Dev
         uint32_t eb = 0;
 #pragma unroll
         for (int k = 0; k < NPL; ++k) {
-            const uint32_t ew = __ldg(net.obs + ((size_t)tau * 32 + lane) * NPL + k);
-            eb += __byte_perm(ew, ew, code[k]);
+            if constexpr (NPL != 2) ew[k] = __ldg(net.obs + ((size_t)tau * 32 + lane) * NPL + k);
+            eb += __byte_perm(ew[k], ew[k], code[k]);
         }
         e01 += __byte_perm(eb, 0u, 0x4140u);
         e23 += __byte_perm(eb, 0u, 0x4342u);
