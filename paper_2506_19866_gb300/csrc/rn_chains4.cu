@@ -243,16 +243,15 @@ __device__ __forceinline__ void simulate4(const Regs4<NPL, D0, D1> &R, const Dev
     y[3] = (int32_t)__reduce_add_sync(kFull, e23 >> 16);
 }
 
-// Chain c's table entry or node constant takes the candidate's value (owner
-// lane only), with an undo record.  Returns whether this lane is the owner.
+// Chain c's table entry or node constant (parameter kind `kind`, index idx in
+// its block of x) takes the candidate's value (owner lane only), with an undo
+// record.  Returns whether this lane is the owner.
 template <int NPL, int D0, int D1>
-__device__ __forceinline__ bool change4(Regs4<NPL, D0, D1> &R, Undo4 &U, const DevNet &net,
-                                        const int8_t *x, int c, int lane, int j, int v)
+__device__ __forceinline__ bool change4_ki(Regs4<NPL, D0, D1> &R, Undo4 &U, const DevNet &net,
+                                           const int8_t *x, int c, int lane, int kind, int idx,
+                                           int v)
 {
-    const int E = net.E, N = net.N;
-    int kind, idx;
-    if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
-    else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
+    const int E = net.E;
     if (kind < 3) {
         const int pos = net.edge_pos[idx];
         if (lane != (pos >> 16)) return false;
@@ -296,6 +295,18 @@ __device__ __forceinline__ bool change4(Regs4<NPL, D0, D1> &R, Undo4 &U, const D
         }
     }
     return true;
+}
+
+// The same for parameter j of x.
+template <int NPL, int D0, int D1>
+__device__ __forceinline__ bool change4(Regs4<NPL, D0, D1> &R, Undo4 &U, const DevNet &net,
+                                        const int8_t *x, int c, int lane, int j, int v)
+{
+    const int E = net.E, N = net.N;
+    int kind, idx;
+    if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
+    else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
+    return change4_ki<NPL, D0, D1>(R, U, net, x, c, lane, kind, idx, v);
 }
 
 template <int NPL, int D0, int D1>
@@ -383,9 +394,10 @@ __device__ __forceinline__ void run_chunk4(const DevNet &net, const DevChains &c
         ++in_level;
         // candidates: lane group c (lanes 8c .. 8c + 7) draws chain c's words
         // and runs its GetCandidate, then every lane takes the four results:
-        // cj (parameter), cv (new value | old value << 8), rz (acceptance word);
-        // own: bit c when this lane owns chain c's change
-        int cj[4], cv[4];
+        // cj (parameter), ck (its kind << 28 | index in its block of x), cv (new
+        // value | old value << 8), rz (acceptance word); own: bit c when this
+        // lane owns chain c's change
+        int cj[4], ck[4], cv[4];
         uint32_t rz[4];
         uint32_t has = 0, own = 0;
         {
@@ -399,10 +411,12 @@ __device__ __forceinline__ void run_chunk4(const DevNet &net, const DevChains &c
                 ok = get_candidate(net, xs(grp), onz(grp), pin(grp), r.x, r.y, j, kind, idx, cur, v);
             }
             const int packed = ok ? ((v & 0xff) | ((cur & 0xff) << 8)) : -1;
+            const int ki = ok ? (kind << 28) | idx : 0;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 rz[c] = __shfl_sync(kFull, z, 8 * c);
                 cj[c] = __shfl_sync(kFull, j, 8 * c);
+                ck[c] = __shfl_sync(kFull, ki, 8 * c);
                 cv[c] = __shfl_sync(kFull, packed, 8 * c);
             }
         }
@@ -410,7 +424,8 @@ __device__ __forceinline__ void run_chunk4(const DevNet &net, const DevChains &c
         for (int c = 0; c < 4; ++c) {
             if (cv[c] < 0) continue;
             has |= 1u << c;
-            if (change4<NPL, D0, D1>(R, U, net, xs(c), c, lane, cj[c], (int8_t)(cv[c] & 0xff)))
+            if (change4_ki<NPL, D0, D1>(R, U, net, xs(c), c, lane, ck[c] >> 28,
+                                        ck[c] & 0x0fffffff, (int8_t)(cv[c] & 0xff)))
                 own |= 1u << c;
         }
         if (!has) {
@@ -436,11 +451,8 @@ __device__ __forceinline__ void run_chunk4(const DevNet &net, const DevChains &c
             if (accept) {
                 const int j = cj[c], v = (int8_t)(cv[c] & 0xff), cur = (int8_t)(cv[c] >> 8);
                 if (lane == 0) {
-                    const int E = net.E, N = net.N;
-                    int kind, idx;
-                    if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
-                    else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
-                    apply_counters(net, xs(c), onz(c), pin(c), kind, idx, cur, v);
+                    apply_counters(net, xs(c), onz(c), pin(c), ck[c] >> 28, ck[c] & 0x0fffffff,
+                                   cur, v);
                     xs(c)[j] = (int8_t)v;
                     cnt[c] += 1;
                     cnt[4 + c] += dE > 0;
