@@ -825,8 +825,7 @@ __global__ void __launch_bounds__(kBT, 1) screen_finish_block_kernel(ScreenArgs 
             if (move < 0) continue;
             const int j = move >> 8, v = (int8_t)(move & 255);
             int kind, idx, owner;
-            if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
-            else { const int q = j - 3 * E; kind = 3 + q / N; idx = q - (kind - 3) * N; }
+            param_kind(j, E, N, kind, idx);
             if (kind < 3) {
                 const int pos = net.edge_pos[idx];
                 owner = pos >> 16;

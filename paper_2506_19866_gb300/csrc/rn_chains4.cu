@@ -304,8 +304,7 @@ __device__ __forceinline__ bool change4(Regs4<NPL, D0, D1> &R, Undo4 &U, const D
 {
     const int E = net.E, N = net.N;
     int kind, idx;
-    if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
-    else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
+    param_kind(j, E, N, kind, idx);
     return change4_ki<NPL, D0, D1>(R, U, net, x, c, lane, kind, idx, v);
 }
 

@@ -100,6 +100,23 @@ struct DevSched {
 
 constexpr int kWaitLimit = 1 << 22;     // polls of a predecessor flag before giving up
 
+// Block and index of parameter j in x = [w(E), p(E), t(E), u(N), m(N), d(N)]
+// (Section 2.5): kind 0..5 and the index within its block, by comparisons
+// (a division by the run-time E or N is a long dependent sequence on the
+// proposal's path).
+__host__ __device__ __forceinline__ void param_kind(int j, int E, int N, int &kind, int &idx)
+{
+    if (j < 3 * E) {
+        kind = (j >= E) + (j >= 2 * E);
+        idx = j - kind * E;
+    } else {
+        const int t = j - 3 * E;
+        const int k = (t >= N) + (t >= 2 * N);
+        kind = 3 + k;
+        idx = t - k * N;
+    }
+}
+
 // The block path's register variant (2, 4, 6 or 8 nodes per thread) keeps two
 // copies of the chain's 16-bit state codes in shared memory.  Word w of the
 // first copy (codes of internal indices 2w and 2w + 1) is word code_word2(w) of

@@ -204,8 +204,7 @@ __device__ __forceinline__ bool get_candidate_x(const DevNet &net, XR xr, const 
 {
     const int E = net.E, N = net.N;
     j = net.free_list[pick(r0, (uint32_t)net.n_free)];
-    if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
-    else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
+    param_kind(j, E, N, kind, idx);
     cur = xr(j);
     int8_t vals[6];
     const int nd = domain(kind, kind == 3 && net.fast[idx], vals);

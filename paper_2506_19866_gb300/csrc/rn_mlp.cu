@@ -398,8 +398,7 @@ __device__ __forceinline__ void screen_finish(const ScreenArgs &a, const DevSche
         if (move < 0) continue;
         const int j = move >> 8, v = (int8_t)(move & 255);
         int kind, idx, owner;
-        if (j < 3 * E) { kind = j / E; idx = j - kind * E; }
-        else { const int t = j - 3 * E; kind = 3 + t / N; idx = t - (kind - 3) * N; }
+        param_kind(j, E, N, kind, idx);
         if (kind < 3) {
             const int pos = net.edge_pos[idx];
             owner = pos >> 16;
