@@ -102,7 +102,7 @@ def algorithmic_ops_per_eval(w):
 # DRAM bytes per annealing launch (read + write) from an ncu capture of the
 # current kernel on the workload: the chain state read once (and, on the block
 # path, written back once) per launch, independent of sweeps per launch.
-ANNEAL_TRAFFIC = {"n120_c8_t21": 9.258e6, "n2000_c16_t33": 1.4506e9}
+ANNEAL_TRAFFIC = {"n120_c8_t21": 9.255e6, "n2000_c16_t33": 1.4488e9}
 
 # Shared-memory wavefronts per proposal step of one chain from the same
 # captures (loads and stores): 110.3e6 over 4096 chains x 20 steps, and
