@@ -407,7 +407,8 @@ __device__ __forceinline__ void run_chunk4(const DevNet &net, const DevChains &c
                 const uint4 r = philox(ch.seed, (uint32_t)g, (uint32_t)((uint64_t)g >> 32),
                                        (uint32_t)(4 * quad + grp), 0u);
                 z = r.z;
-                ok = get_candidate(net, xs(grp), onz(grp), pin(grp), r.x, r.y, j, kind, idx, cur, v);
+                ok = get_candidate<true>(net, xs(grp), onz(grp), pin(grp), r.x, r.y, j, kind, idx, cur,
+                                         v);
             }
             const int packed = ok ? ((v & 0xff) | ((cur & 0xff) << 8)) : -1;
             const int ki = ok ? (kind << 28) | idx : 0;

@@ -100,6 +100,39 @@ struct DevSched {
 
 constexpr int kWaitLimit = 1 << 22;     // polls of a predecessor flag before giving up
 
+// GetCandidate's new value (Table 1): the pick(r1)-th, in ascending order, of
+// the values of a kind-`kind` parameter's domain other than cur and, where
+// blocked0, other than 0 (the constraints of Section 2.5.3); false when none is
+// left (blocked_all, or nothing besides cur).  Every domain is a run of
+// consecutive integers (Section 2.1: w 0..2, p -1..1, t 1..2; Section 2.2: u
+// 1..6, or 10..12 for a fast node, m 0..2, d 1..2), so the value is the run's
+// pick-th with the excluded values stepped over, in ascending order, which
+// needs no per-kind branch (lanes of a warp that hold different kinds do not
+// diverge).  blocked0 arises only for w != 0, whose run starts at 0.
+__host__ __device__ __forceinline__ bool pick_alternative(int kind, bool fast, int cur,
+                                                          bool blocked0, bool blocked_all,
+                                                          uint32_t r1, int &v)
+{
+    // per kind, in nibble k: the run's lowest value + 1, and its length
+    int lo = (int)((0x212201u >> (4 * kind)) & 15u) - 1;
+    int n = (int)((0x236233u >> (4 * kind)) & 15u);
+    if (fast && kind == 3) {
+        lo = 10;
+        n = 3;
+    }
+    const int n_alt = blocked_all ? 0 : n - 1 - (blocked0 ? 1 : 0);
+    if (n_alt <= 0) return false;
+#ifdef __CUDA_ARCH__
+    const uint32_t m = __umulhi(r1, (uint32_t)n_alt);
+#else
+    const uint32_t m = (uint32_t)(((uint64_t)r1 * (uint32_t)n_alt) >> 32);
+#endif
+    v = lo + (int)m;
+    if (blocked0 && v >= 0) ++v;
+    if (v >= cur) ++v;
+    return true;
+}
+
 // Block and index of parameter j in x = [w(E), p(E), t(E), u(N), m(N), d(N)]
 // (Section 2.5): kind 0..5 and the index within its block, by comparisons
 // (a division by the run-time E or N is a long dependent sequence on the

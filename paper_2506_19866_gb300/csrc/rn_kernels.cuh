@@ -196,8 +196,12 @@ __device__ __forceinline__ void count_constraints(const DevNet &net, const int8_
 // free parameter j, then the pick(r1)-th of its domain values != x_j whose
 // single change keeps both constraints of Section 2.5.3 (counters out_nz,
 // pos_in of x).  Returns false for a null move (no such value).  `xr(j)`
-// reads x_j (shared memory, or global memory through L2).
-template <class XR>
+// reads x_j (shared memory, or global memory through L2).  With LANES_DIFFER
+// (lanes of one warp draw different candidates, so their parameter kinds
+// differ) the constraint inputs are read for every kind and combined without
+// branches; otherwise (one candidate per warp) only the kinds that need them
+// read them, and the value is found by walking the listed domain.
+template <bool LANES_DIFFER = false, class XR>
 __device__ __forceinline__ bool get_candidate_x(const DevNet &net, XR xr, const uint8_t *out_nz,
                                                 const uint8_t *pos_in, uint32_t r0, uint32_t r1,
                                                 int &j, int &kind, int &idx, int &cur, int &v)
@@ -206,38 +210,54 @@ __device__ __forceinline__ bool get_candidate_x(const DevNet &net, XR xr, const 
     j = net.free_list[pick(r0, (uint32_t)net.n_free)];
     param_kind(j, E, N, kind, idx);
     cur = xr(j);
-    int8_t vals[6];
-    const int nd = domain(kind, kind == 3 && net.fast[idx], vals);
-    bool blocked0 = false, blocked_all = false;
-    if (kind == 0 && cur != 0) {
-        const int a = net.src[idx], b = net.dst[idx];
-        blocked0 = out_nz[a] < 2 || (xr(E + idx) == 1 && pos_in[b] < 2);
-    } else if (kind == 1 && cur == 1 && xr(idx) != 0) {
-        blocked_all = pos_in[net.dst[idx]] < 2;
-    }
-    int8_t alts[6];
-    int n_alt = 0;
-    if (!blocked_all) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            if (k >= nd) break;
-            const int a = vals[k];
-            if (a == cur || (blocked0 && a == 0)) continue;
-            alts[n_alt++] = (int8_t)a;
+    if constexpr (LANES_DIFFER) {
+        // an edge parameter's own edge, edge 0 for a node parameter (in bounds,
+        // unused); every node has an in-edge, so E >= N
+        const int ie = kind < 3 ? idx : 0;
+        const int a = net.src[ie], b = net.dst[ie];
+        const bool out_low = out_nz[a] < 2, pos_low = pos_in[b] < 2;
+        const bool p_pos = xr(E + ie) == 1, w_nz = xr(ie) != 0;
+        const bool blocked0 = (kind == 0) & (cur != 0) & (out_low | (p_pos & pos_low));
+        const bool blocked_all = (kind == 1) & (cur == 1) & w_nz & pos_low;
+        const bool fast = (kind == 3) & (net.fast[kind == 3 ? idx : 0] != 0);
+        return pick_alternative(kind, fast, cur, blocked0, blocked_all, r1, v);
+    } else {
+        // the domain's listed values, walked (measured a little faster than the
+        // arithmetic choice where the whole warp holds one candidate)
+        int8_t vals[6];
+        const int nd = domain(kind, kind == 3 && net.fast[idx], vals);
+        bool blocked0 = false, blocked_all = false;
+        if (kind == 0 && cur != 0) {
+            const int a = net.src[idx], b = net.dst[idx];
+            blocked0 = out_nz[a] < 2 || (xr(E + idx) == 1 && pos_in[b] < 2);
+        } else if (kind == 1 && cur == 1 && xr(idx) != 0) {
+            blocked_all = pos_in[net.dst[idx]] < 2;
         }
+        int8_t alts[6];
+        int n_alt = 0;
+        if (!blocked_all) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                if (k >= nd) break;
+                const int a = vals[k];
+                if (a == cur || (blocked0 && a == 0)) continue;
+                alts[n_alt++] = (int8_t)a;
+            }
+        }
+        if (n_alt == 0) return false;
+        v = alts[pick(r1, (uint32_t)n_alt)];
+        return true;
     }
-    if (n_alt == 0) return false;
-    v = alts[pick(r1, (uint32_t)n_alt)];
-    return true;
 }
 
+template <bool LANES_DIFFER = false>
 __device__ __forceinline__ bool get_candidate(const DevNet &net, const int8_t *xs,
                                               const uint8_t *out_nz, const uint8_t *pos_in,
                                               uint32_t r0, uint32_t r1, int &j, int &kind,
                                               int &idx, int &cur, int &v)
 {
-    return get_candidate_x(net, [&](int k) { return (int)xs[k]; }, out_nz, pos_in, r0, r1, j,
-                           kind, idx, cur, v);
+    return get_candidate_x<LANES_DIFFER>(net, [&](int k) { return (int)xs[k]; }, out_nz, pos_in,
+                                         r0, r1, j, kind, idx, cur, v);
 }
 
 // Constraint counters after x_j: cur -> v (x still holds cur); xr as above.

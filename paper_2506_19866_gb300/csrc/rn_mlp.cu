@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kScreenWarps * 32) screen_propose_kernel(Scree
     bool ok = false;
     if (lane < a.K && a.net.n_free > 0) {
         const uint4 r = step_draw(a.ch, a.g, c, lane == 0 ? 0u : 16u + (uint32_t)lane);
-        ok = get_candidate(a.net, xs, out_nz, pos_in, r.x, r.y, j, kind, idx, cur, v);
+        ok = get_candidate<true>(a.net, xs, out_nz, pos_in, r.x, r.y, j, kind, idx, cur, v);
     }
     if (lane < a.K) a.cand[(size_t)c * a.K + lane] = ok ? (j << 8) | (v & 255) : -1;
     // lane k: the W1 rows of candidate k's new and old value (-1: no candidate)

@@ -1,9 +1,11 @@
-"""The block path's table layout, built by the library on the host (no GPU):
-every edge in exactly one entry of its node's lane and slot, edge_pos naming
-that entry, every code address inside the block's code region, and, on the
-register variant's two copies of the state codes, a code gather with fewer
-wavefronts than any placement over one copy could reach (tests/layout_check.cu
-reads the layout through the library's own builder)."""
+"""Host-side logic of the kernels, checked without a GPU.
+- The block path's table layout, built by the library on the host: every edge
+  in exactly one entry of its node's lane and slot, edge_pos naming that entry,
+  every code address inside the block's code region, and, on the register
+  variant's two copies of the state codes, a code gather with fewer wavefronts
+  than any placement over one copy could reach (tests/layout_check.cu reads the
+  layout through the library's own builder).
+- GetCandidate's choice of the new value (tests/candidate_check.cu)."""
 import os
 import subprocess
 
@@ -58,3 +60,14 @@ def test_block_layouts_place_every_edge_once(checker, tmp_path, seed, n_nodes, l
     assert s["supported"] == 1 and s["lanes"] == 256
     assert s["two_copies"] == (1 if s["npl"] <= 8 else 0)
     assert s["wavefronts"] >= s["rows"]
+
+
+def test_candidate_value_choice(tmp_path):
+    # GetCandidate's branch-free choice of the new value (pick_alternative)
+    # against a walk over the listed domains, every case that can arise
+    exe = tmp_path / "candidate_check"
+    subprocess.check_call([B._nvcc(), *B.ARCH, "-std=c++17", "-O2",
+                           os.path.join(HERE, "candidate_check.cu"), "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert int(r.stdout.split()[1]) > 1_000_000
