@@ -211,8 +211,8 @@ __device__ __forceinline__ bool get_candidate_x(const DevNet &net, XR xr, const 
     param_kind(j, E, N, kind, idx);
     cur = xr(j);
     if constexpr (LANES_DIFFER) {
-        // an edge parameter's own edge, edge 0 for a node parameter (in bounds,
-        // unused); every node has an in-edge, so E >= N
+        // an edge parameter's own edge, edge 0 for a node parameter (read and
+        // unused: a loaded network has at least one edge)
         const int ie = kind < 3 ? idx : 0;
         const int a = net.src[ie], b = net.dst[ie];
         const bool out_low = out_nz[a] < 2, pos_low = pos_in[b] < 2;
